@@ -1,0 +1,259 @@
+"""FP64 CPU oracle for the grand-potential phase-field step (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA product path never does; the
+two implementations share no code.  ``gp_oracle.cpp`` restates the paper's
+equations as plain per-cell loops (see its header for the passages followed
+and the readings taken where the paper is silent).
+
+Parity status per function (pins live in ``tests/test_oracle_pins.py``):
+  * pair_energy / its gradient, interpolation h, potentials, projection,
+    thermodynamics (c(mu), psi, chi, Coeff_B/C), the isotropic Laplacian
+    identity, planar sine / tanh profiles, Fourier-mode and Gaussian decay of
+    mu, mass conservation, sum(phi)=1, flat-interface equilibrium,
+    Gibbs-Thomson direction, anisotropic profile width, tangent vs finite
+    differences: pinned.
+  * The full multiphase (N >= 3) anisotropic dendrite / eutectic / multigrain
+    trajectories: parity unpinned beyond the identities above.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libgp_oracle.so")
+_SRC = os.path.join(_HERE, "gp_oracle.cpp")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile gp_oracle.cpp into oracle/_build/libgp_oracle.so (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("bc", ctypes.c_int * 3), ("N", ctypes.c_int), ("NM", ctypes.c_int),
+        ("potential", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("eps", ctypes.c_double),
+        ("tau", ctypes.c_double),
+        ("gamma", ctypes.c_void_p), ("delta", ctypes.c_void_p), ("rot", ctypes.c_void_p),
+        ("gamma3", ctypes.c_void_p), ("D", ctypes.c_void_p), ("A", ctypes.c_void_p),
+        ("ceq", ctypes.c_void_p), ("slopes", ctypes.c_void_p), ("f0", ctypes.c_void_p),
+        ("T_ref", ctypes.c_double), ("T0", ctypes.c_double), ("G", ctypes.c_double),
+        ("z0", ctypes.c_double), ("V", ctypes.c_double), ("t0", ctypes.c_double),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            dp = ctypes.POINTER(ctypes.c_double)
+            P = ctypes.POINTER(_Problem)
+            L.oracle_run.argtypes = [P, dp, dp, ctypes.c_int, dp, dp]
+            L.oracle_run_tangent.argtypes = [P, dp, dp, dp, dp, dp, ctypes.c_double, dp,
+                                             ctypes.c_int, dp, dp, dp, dp]
+            L.oracle_rate_parts.argtypes = [P, dp, dp, dp, dp, dp, dp]
+            L.oracle_diag.argtypes = [P, dp, dp, dp]
+            L.oracle_pair_energy.argtypes = [P, ctypes.c_int, ctypes.c_int, dp]
+            L.oracle_pair_energy.restype = ctypes.c_double
+            L.oracle_pair_energy_grad.argtypes = [P, ctypes.c_int, ctypes.c_int, dp, dp]
+            L.oracle_potential.argtypes = [P, dp, dp]
+            L.oracle_potential.restype = ctypes.c_double
+            L.oracle_interp.argtypes = [ctypes.c_int, dp, dp, dp]
+            L.oracle_project.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+            L.oracle_thermo.argtypes = [P, ctypes.c_int, dp, ctypes.c_double, dp, dp, dp]
+            L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_set_threads.argtypes = [ctypes.c_int]
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class OracleProblem:
+    """Marshals a problem description (duck-typed workloads.Problem) for the C oracle."""
+
+    def __init__(self, prob, t0: float = 0.0, **override):
+        g = lambda k: override.get(k, getattr(prob, k))
+        self.N = int(g("n_phases"))
+        self.NM = int(g("n_components")) - 1
+        self.dim = int(g("dim"))
+        self.nx, self.ny = int(g("nx")), int(g("ny"))
+        self.nz = int(g("nz")) if self.dim == 3 else 1
+        N, NM = self.N, self.NM
+        self._keep = []
+
+        def arr(x, shape):
+            a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(shape))
+            self._keep.append(a)
+            return a.ctypes.data
+
+        s = _Problem()
+        s.dim, s.nx, s.ny, s.nz = self.dim, self.nx, self.ny, self.nz
+        bc = list(g("bc")) + [3] * 3
+        s.bc = (ctypes.c_int * 3)(*bc[:3])
+        s.N, s.NM = N, NM
+        s.potential = 1 if g("potential") == "obstacle" else 2
+        s.dx, s.dt, s.eps, s.tau = float(g("dx")), float(g("dt")), float(g("eps")), float(g("tau"))
+        s.gamma = arr(g("gamma"), (N, N))
+        s.delta = arr(g("delta"), (N, N))
+        rot = g("rot")
+        s.rot = arr(rot, (N, N, 3, 3)) if rot is not None else None
+        g3 = g("gamma3")
+        s.gamma3 = arr(g3, (N, N, N)) if g3 is not None else None
+        s.D = arr(g("D"), (N, NM, NM))
+        s.A = arr(g("A"), (N, NM, NM))
+        s.ceq = arr(g("ceq"), (N, NM))
+        s.slopes = arr(g("slopes"), (N, NM))
+        f0 = g("f0")
+        s.f0 = arr(f0, (N,)) if f0 is not None else None
+        s.T_ref, s.T0, s.G = float(g("T_ref")), float(g("T0")), float(g("G"))
+        s.z0, s.V = float(g("z0")), float(g("V"))
+        s.t0 = float(t0)
+        self.s = s
+
+    @property
+    def cells(self):
+        return self.nx * self.ny * self.nz
+
+    def shape(self, nf):
+        return (nf, self.nz, self.ny, self.nx)
+
+    def ptr(self):
+        return ctypes.byref(self.s)
+
+
+def run(prob, phi0, mu0, nsteps: int, t0: float = 0.0, **override):
+    """nsteps explicit steps in FP64; returns (phi, mu) shaped [F][nz][ny][nx]."""
+    op = OracleProblem(prob, t0, **override)
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(op.shape(op.N))
+    mu0 = np.ascontiguousarray(mu0, dtype=np.float64).reshape(op.shape(op.NM))
+    phi = np.empty_like(phi0)
+    mu = np.empty_like(mu0)
+    rc = lib().oracle_run(op.ptr(), _dp(phi0), _dp(mu0), int(nsteps), _dp(phi), _dp(mu))
+    if rc:
+        raise ValueError("oracle_run rejected the problem")
+    return phi, mu
+
+
+def run_tangent(prob, phi0, mu0, nsteps: int, dphi0=None, dmu0=None, ddelta=None,
+                dmob: float = 0.0, dD=None, t0: float = 0.0, **override):
+    """Forward-mode tangent: returns (phi, mu, dphi, dmu)."""
+    op = OracleProblem(prob, t0, **override)
+    N, NM = op.N, op.NM
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(op.shape(N))
+    mu0 = np.ascontiguousarray(mu0, dtype=np.float64).reshape(op.shape(NM))
+    z = lambda sh: np.zeros(sh)
+    dphi0 = np.ascontiguousarray(z(phi0.shape) if dphi0 is None else dphi0, dtype=np.float64).reshape(phi0.shape)
+    dmu0 = np.ascontiguousarray(z(mu0.shape) if dmu0 is None else dmu0, dtype=np.float64).reshape(mu0.shape)
+    ddelta = np.ascontiguousarray(z((N, N)) if ddelta is None else ddelta, dtype=np.float64).reshape(N, N)
+    dD = np.ascontiguousarray(z((N, NM, NM)) if dD is None else dD, dtype=np.float64).reshape(N, NM, NM)
+    phi, mu = np.empty_like(phi0), np.empty_like(mu0)
+    dphi, dmu = np.empty_like(phi0), np.empty_like(mu0)
+    rc = lib().oracle_run_tangent(op.ptr(), _dp(phi0), _dp(mu0), _dp(dphi0), _dp(dmu0),
+                                  _dp(ddelta), float(dmob), _dp(dD), int(nsteps),
+                                  _dp(phi), _dp(mu), _dp(dphi), _dp(dmu))
+    if rc:
+        raise ValueError("oracle_run_tangent rejected the problem")
+    return phi, mu, dphi, dmu
+
+
+def rate_parts(prob, phi, mu, t0: float = 0.0, **override):
+    op = OracleProblem(prob, t0, **override)
+    phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(op.shape(op.N))
+    mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(op.shape(op.NM))
+    outs = [np.empty_like(phi) for _ in range(4)]
+    rc = lib().oracle_rate_parts(op.ptr(), _dp(phi), _dp(mu), *[_dp(o) for o in outs])
+    if rc:
+        raise ValueError("oracle_rate_parts rejected the problem")
+    return tuple(outs)
+
+
+def diag(prob, phi, mu, t0: float = 0.0, **override):
+    """[mass_1..mass_NM, max|sum phi - 1|, min phi, max phi] in FP64."""
+    op = OracleProblem(prob, t0, **override)
+    phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(op.shape(op.N))
+    mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(op.shape(op.NM))
+    out = np.zeros(op.NM + 3)
+    lib().oracle_diag(op.ptr(), _dp(phi), _dp(mu), _dp(out))
+    return out
+
+
+def pair_energy(prob, a, b, q, **override):
+    op = OracleProblem(prob, **override)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    return lib().oracle_pair_energy(op.ptr(), a, b, _dp(q))
+
+
+def pair_energy_grad(prob, a, b, q, **override):
+    op = OracleProblem(prob, **override)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    g = np.zeros_like(q)
+    lib().oracle_pair_energy_grad(op.ptr(), a, b, _dp(q), _dp(g))
+    return g
+
+
+def potential(prob, phi, **override):
+    op = OracleProblem(prob, **override)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    dw = np.zeros_like(phi)
+    w = lib().oracle_potential(op.ptr(), _dp(phi), _dp(dw))
+    return w, dw
+
+
+def interp(phi):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    N = phi.size
+    h = np.zeros(N)
+    dh = np.zeros((N, N))
+    lib().oracle_interp(N, _dp(phi), _dp(h), _dp(dh))
+    return h, dh
+
+
+def project(v, potential_kind: str):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros_like(v)
+    lib().oracle_project(v.size, 1 if potential_kind == "obstacle" else 2, _dp(v), _dp(out))
+    return out
+
+
+def thermo(prob, a, mu, T, **override):
+    """(c^a(mu,T), psi^a(mu,T), chi^a) for phase a."""
+    op = OracleProblem(prob, **override)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    c = np.zeros(op.NM)
+    psi = ctypes.c_double(0.0)
+    chi = np.zeros((op.NM, op.NM))
+    lib().oracle_thermo(op.ptr(), a, _dp(mu), float(T), _dp(c), ctypes.byref(psi), _dp(chi))
+    return c, psi.value, chi
+
+
+def num_threads() -> int:
+    return lib().oracle_num_threads()
+
+
+def set_threads(n: int):
+    lib().oracle_set_threads(int(n))
