@@ -1,0 +1,344 @@
+"""Benchmark of the grand-potential step on GB300.
+
+Workload (default): the 3-D 256^3 directional eutectic -- 3 phases (alpha,
+beta, liquid), ternary alloy, four-fold anisotropy 0.02, frozen pulled
+temperature gradient, seeded lamellae, no-flux z / periodic x,y, FP32 state
+with FP64 diagnostics every 100 steps.  One bench step = one explicit time step
+of the whole path (one fused step kernel; the diagnostics kernel every 100th).
+
+Prints ONE JSON line (rank 0).  `value` is whole-job MLUPS (cell updates per
+second / 1e6) with the state resident in HBM; `e2e` is the same metric through
+the public API with host buffers, host<->device copies inside the timed region;
+`roofline` relates the step kernel's algorithmic bytes to the measured HBM peak.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIAG_EVERY = 100
+E2E_SEGMENT = 100          # time steps per e2e iteration (one output interval)
+WORKLOAD = "3-D 256^3 directional eutectic: 3 phases, ternary (2 solutes), aniso 0.02, FP32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256, help="grid edge (256 = the benchmark workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def algorithmic_bytes_per_cell(prob, itemsize):
+    # read phi (N) and mu (K-1) once, write them once
+    return 2 * itemsize * (prob.n_phases + prob.n_components - 1)
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample_rate(prob, target_s):
+    """Time the FP64 oracle on a block of the same workload; returns (MLUPS, cores, sample)."""
+    import oracle
+    cores = oracle.num_threads()
+    nz_probe = 4
+    sub = crop(prob, prob.nx, prob.ny, nz_probe)
+    t0 = time.perf_counter()
+    oracle.run(sub, sub.phi0, sub.mu0, 1)
+    probe = time.perf_counter() - t0
+    per_cell = probe / sub.cells
+    nz = int(max(1, min(prob.nz, target_s / (per_cell * prob.nx * prob.ny))))
+    sub = crop(prob, prob.nx, prob.ny, nz)
+    t0 = time.perf_counter()
+    oracle.run(sub, sub.phi0, sub.mu0, 1)
+    el = time.perf_counter() - t0
+    sample = (f"1 FP64 oracle step of the bottom {nz} z-planes ({prob.nx}x{prob.ny}x{nz} = "
+              f"{sub.cells} cells, lamellae + interface) of the same initial state")
+    return sub.cells / el / 1e6, cores, sample, el
+
+
+def crop(prob, nx, ny, nz):
+    return prob.copy(nx=nx, ny=ny, nz=nz, phi0=prob.phi0[:, :nz, :ny, :nx].copy(),
+                     mu0=prob.mu0[:, :nz, :ny, :nx].copy())
+
+
+# ------------------------------------------------------------------- arms
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle as it stands, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    prob = workloads.cfg2(n=args.n)
+    cores = oracle.num_threads()
+    # size one bench step so that warmup + steps stay within ~3 minutes
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    probe = crop(prob, prob.nx, prob.ny, 2)
+    t0 = time.perf_counter()
+    oracle.run(probe, probe.phi0, probe.mu0, 1)
+    per_cell = (time.perf_counter() - t0) / probe.cells
+    plane = max(32, int(budget / per_cell) // 20)
+    nx = int(min(prob.nx, max(8, int(plane ** 0.5))))
+    ny = int(min(prob.ny, max(4, plane // nx)))
+    sub = crop(prob, nx, ny, 20)
+    for _ in range(args.warmup):
+        oracle.run(sub, sub.phi0, sub.mu0, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(sub, sub.phi0, sub.mu0, 1)
+    el = time.perf_counter() - t0
+    mlups = sub.cells * args.steps / el / 1e6
+    sample = (f"each step = 1 FP64 oracle step on a {nx}x{ny}x20 block (bottom planes) of the "
+              f"{prob.nx}^3 workload")
+    line = {"impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "oracle_block": [nx, ny, 20]},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import workloads
+    from paper_2404_01035_gb300 import Simulation
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    prob = workloads.cfg2(n=args.n)
+    cells = prob.cells
+    stream = torch.cuda.Stream(device=dev)
+    sim = Simulation(prob, dtype="f32", stream=stream)
+    sim.set_fields(prob.phi0, prob.mu0)
+    tuned_ms = None
+    if not args.no_tune:
+        tuned_ms = sim.tune(None, steps_per_trial=25)
+        sim.set_fields(prob.phi0, prob.mu0)
+    sim.set_diag_every(DIAG_EVERY)
+    sim.step(args.warmup)
+    sim.sync()
+
+    # ---- timed region: K steps, events on the library's stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    chunk_ev = []
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev[0].record(stream)
+    done = 0
+    launches = 0
+    # chunks aligned on the diagnostics interval: events around the pure
+    # step-kernel part of each chunk give the step kernel's own duration
+    while done < args.steps:
+        s0 = sim.time()[0]
+        n = min(DIAG_EVERY - s0 % DIAG_EVERY, args.steps - done)
+        pure = n - 1 if (s0 + n) % DIAG_EVERY == 0 else n
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(pure)
+        b.record(stream)
+        chunk_ev.append((a, b, pure))
+        if pure < n:
+            sim.step(1)
+            launches += 2   # diagnostics: partial + final reduction
+        launches += n
+        done += n
+    ev[1].record(stream)
+    stream.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    el = ev[0].elapsed_time(ev[1]) / 1e3
+    kern_ms = sum(a.elapsed_time(b) for a, b, _ in chunk_ev)
+    kern_n = sum(p for _, _, p in chunk_ev)
+    sim.sync()
+    if world > 1:
+        t = torch.tensor([el], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    value = world * cells * args.steps / el / 1e6
+
+    # ---- roofline of the step kernel
+    peaks, src = measured_peaks()
+    bpc = algorithmic_bytes_per_cell(prob, 4)
+    per_launch_s = kern_ms / max(1, kern_n) / 1e3
+    achieved = bpc * cells / per_launch_s / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic_cfg2_step.json")
+    if os.path.exists(tp):
+        with open(tp) as fh:
+            tj = json.load(fh)
+        if tj.get("kernel_digest") == kernel_digest():
+            traffic = tj.get("bytes_per_launch")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)",
+            "kernel": "k_gp_step<3,3,2,float>", "bytes_per_cell": bpc,
+            "kernel_ms_per_launch": per_launch_s * 1e3}
+
+    # ---- e2e through the public API with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        hphi = torch.empty((prob.n_phases,) + sim.shape, dtype=torch.float32, pin_memory=True)
+        hmu = torch.empty((prob.n_components - 1,) + sim.shape, dtype=torch.float32, pin_memory=True)
+        hphi.copy_(torch.from_numpy(prob.phi0.astype(np.float32)))
+        hmu.copy_(torch.from_numpy(prob.mu0.astype(np.float32)))
+        sim.set_diag_every(0)
+        iters = 3
+        for it in range(iters + 1):
+            if it == 1:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            sim.set_fields_from(hphi, hmu, on_device=False)
+            sim.step(E2E_SEGMENT)
+            sim.get_fields_into(hphi, hmu, on_device=False)   # synchronises
+        e2e_el = time.perf_counter() - t0
+        e2e_v = world * cells * E2E_SEGMENT * iters / e2e_el / 1e6
+        nbytes = hphi.numel() * 4 + hmu.numel() * 4
+        e2e = {"value": e2e_v, "unit": "MLUPS", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps_per_e2e_iteration": E2E_SEGMENT,
+               "note": "one e2e iteration = H2D of the full state from pinned memory, "
+                       f"{E2E_SEGMENT} steps, D2H of the full state"}
+    tiles = sim.tiles()
+    launch_info = {"tiles_compiled": tiles}
+    sim.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, sample, secs = oracle_sample_rate(prob, target_s=15.0)
+        cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": sample, "seconds": secs}
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "cells_per_gpu": cells, "grid": [args.n] * 3,
+                           "phases": prob.n_phases, "components": prob.n_components,
+                           "diag_every": DIAG_EVERY,
+                           "l2": "inputs larger than L2 (state 671 MB per buffer)",
+                           "tuned_ms_per_step": tuned_ms, **launch_info},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+
+
+def kernel_digest():
+    """Digest of the CUDA sources: ties a committed ncu traffic figure to a kernel version."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2404_01035_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * microsim_gb.h -- C ABI of the GB300 grand-potential phase-field step library.
+ *
+ * The library advances the multi-phase, multi-component grand-potential model
+ * of the MICROSIM paper (arXiv 2404.01035, Sec. 2.1 "Grand-potential
+ * formulation", Sec. 3 "Thermodynamic coupling") by explicit finite-difference
+ * time steps on a 2-D or 3-D grid.  One step computes, per cell:
+ *   - the anisotropic gradient-energy divergence div(da/dgrad phi_a) and the
+ *     centre term da/dphi_a (Eqs. Eqn_a, aniso_eqn, four-fold a_c),
+ *   - the obstacle or well potential derivative (Eqs. Obstacle, Well),
+ *   - the driving force dpsi/dphi_a = sum_b psi^b dh_b/dphi_a (Eq. hphi) with
+ *     parabolic free energies (Eqs. free_energy_density, Coeff_B, Coeff_C),
+ *   - the phi update of Eq. (phi_eqn) with the Lagrange multiplier realised
+ *     as the Euclidean projection onto the simplex (obstacle) or onto the
+ *     sum-one hyperplane (well),
+ *   - the chemical-potential update of Eq. (Mu_explicit_temperature) with
+ *     mobility M = sum_a h_a D^a chi^a and a frozen, pulled temperature field.
+ * Every step runs in hand-written sm_103a CUDA kernels; there is no CPU path.
+ *
+ * Conventions
+ *   - Field arrays exchanged with the caller are dense, row-major
+ *     [field][z][y][x] (x fastest), nz = 1 for 2-D grids, in the context's
+ *     dtype (float for MS_F32, double for MS_F64).  phi holds N fields,
+ *     mu holds K-1 fields (K = number of components).
+ *   - Phase N-1 is the liquid, the reference phase of the parabolic free
+ *     energies (B^l = C^l = 0).
+ *   - Every call returns ms_status; no exception crosses the ABI.  The text of
+ *     the last error of a context is returned by ms_last_error(ctx); errors
+ *     raised before a context exists are returned by ms_last_error(NULL)
+ *     (thread-local).
+ *   - Device-side faults (non-finite values, barrier timeouts) are recorded in a
+ *     sticky device status word that ms_sync / ms_diag / ms_grad read.
+ *   - All work is enqueued on the stream given at creation; calls return once
+ *     the work is enqueued unless stated otherwise.
+ *   - Buffers handed in are only read during the call (copied); the library
+ *     owns its device state and releases it in ms_destroy.
+ */
+#ifndef MICROSIM_GB_H
+#define MICROSIM_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ms_ctx ms_ctx;
+typedef struct ms_batch ms_batch;
+
+typedef enum {
+  MS_OK = 0,
+  MS_ERR_ARG = 1,          /* invalid argument or unsupported combination */
+  MS_ERR_CUDA = 2,         /* a CUDA runtime/driver call failed */
+  MS_ERR_OOM = 3,          /* device allocation failed */
+  MS_ERR_DT_UNSTABLE = 4,  /* dt above the explicit stability bound */
+  MS_ERR_NONFINITE = 5,    /* NaN/Inf found in the state (sticky) */
+  MS_ERR_TIMEOUT = 6,      /* a bounded device wait gave up (sticky) */
+  MS_ERR_BOUNDS = 7,       /* size beyond a fixed library limit */
+  MS_ERR_STATE = 8,        /* call not valid in the context's current state */
+  MS_ERR_UNSUPPORTED = 9   /* (dim, phases, components, dtype) not compiled in */
+} ms_status;
+
+typedef enum { MS_F32 = 0, MS_F64 = 1 } ms_dtype;
+
+/* Boundary codes of the paper's BOUNDARY key (Sec. "Input files"):
+ * 1 = Neumann (no-flux, mirror ghost cell), 3 = periodic. */
+enum { MS_BC_NOFLUX = 1, MS_BC_PERIODIC = 3 };
+
+/* Function_W: 1 = multi-obstacle (Eq. Obstacle), 2 = multi-well (Eq. Well). */
+enum { MS_POT_OBSTACLE = 1, MS_POT_WELL = 2 };
+
+/* Grid: DIMENSION, MESH_X/Y/Z, DELTA_X and BOUNDARY per axis. */
+typedef struct {
+  int dim;          /* 2 or 3 */
+  int nx, ny, nz;   /* cells per axis; nz is ignored (taken as 1) for dim = 2 */
+  double dx;        /* cell size (DELTA_X = DELTA_Y = DELTA_Z) */
+  int bc[3];        /* MS_BC_* for the x, y, z axes (both faces of an axis) */
+} ms_grid;
+
+/* Model inputs, named after the paper's infile keys.  All pointers are host
+ * arrays of doubles read during the call.  N = phases, M = K-1 solutes. */
+typedef struct {
+  ms_dtype dtype;          /* arithmetic type of the state and the step */
+  int potential;           /* MS_POT_OBSTACLE or MS_POT_WELL (Function_W) */
+  double eps;              /* epsilon: interface-width parameter */
+  double tau;              /* tau: relaxation constant; phase mobility is 1/tau */
+  double dt;               /* DELTA_t */
+  const double* gamma;     /* [N][N] GAMMA, symmetric */
+  const double* delta;     /* [N][N] dab, anisotropy strength; 0 = isotropic pair */
+  const double* rot;       /* [N][N][3][3] Rotation_matrix per pair; NULL = identity.
+                              2-D grids use the upper-left 2x2 block. */
+  const double* gamma3;    /* [N][N][N] Gamma_abc, symmetric; NULL = none */
+  const double* D;         /* [N][M][M] DIFFUSIVITY matrices */
+  const double* A;         /* [N][M][M] parabolic coefficients A_ij, i <= j used */
+  const double* ceq;       /* [N][M] equilibrium compositions at T_ref (ceq) */
+  const double* slopes;    /* [N][M] d c_eq / dT (slopes) */
+  const double* f0;        /* [N] constant added to f^a (isothermal drive); NULL = 0 */
+  double T_ref;            /* temperature at which ceq is given */
+  double T0, G, z0, V;     /* Tempgrady: T(s,t) = T0 + G (s - z0 - V t), s the
+                              cell-centre coordinate along the last axis */
+  double t0;               /* physical time of the initial state */
+} ms_params;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  NULL in
+ * ms_create means cudaMalloc / cudaFree.  alloc returns NULL on failure. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*release)(void* ptr, void* user);
+  void* user;
+} ms_allocator;
+
+/* Create a context: validates the inputs, derives the per-phase parabolic
+ * coefficients B^a(T), C^a(T), chi^a = (Hessian of f^a)^-1 (Eqs. Coeff_B,
+ * Coeff_C; the off-diagonal sum of Coeff_B taken with the sign its own equal-mu
+ * condition gives), checks dt against the explicit stability bound (FP64,
+ * MS_ERR_DT_UNSTABLE when above it), allocates the ping-pong device state and
+ * enqueues nothing.  stream is a cudaStream_t (NULL = legacy default stream).
+ * n_phases in [2, 8], n_components in [2, 4].  Returns MS_ERR_UNSUPPORTED when
+ * the (dim, N, K, dtype) step kernel is not compiled into this build. */
+ms_status ms_create(const ms_grid* grid, int n_phases, int n_components,
+                    const ms_params* params, void* stream, const ms_allocator* alloc,
+                    ms_ctx** out);
+
+/* Release all device and host resources (synchronises the stream first). */
+void ms_destroy(ms_ctx* ctx);
+
+/* Text of the last error on ctx (or of the calling thread when ctx is NULL). */
+const char* ms_last_error(const ms_ctx* ctx);
+
+/* Replace the model parameters (dt, eps, tau, delta, D, ...) without
+ * reallocating; grid, N, K and dtype must be unchanged. */
+ms_status ms_update_params(ms_ctx* ctx, const ms_params* params);
+
+/* Copy the state in.  phi: N fields, mu: K-1 fields, dense [f][z][y][x] in
+ * the context dtype; on_device = 1 if the pointers are device pointers, 0 for
+ * host memory (pinned or pageable).  Resets the step counter to 0 and the time
+ * to params->t0, and clears recorded adjoint checkpoints. */
+ms_status ms_set_fields(ms_ctx* ctx, const void* phi, const void* mu, int on_device);
+
+/* Copy the current state out (same layout as ms_set_fields); synchronous. */
+ms_status ms_get_fields(ms_ctx* ctx, void* phi, void* mu, int on_device);
+
+/* Borrowed device views of the current state: *phi_dev / *mu_dev point at
+ * cell (0,0,0) of field 0; element (f,z,y,x) is at
+ * base + f*strides[0] + z*strides[1] + y*strides[2] + x*strides[3] (elements).
+ * Valid until the next ms_step / ms_set_fields / ms_destroy. */
+ms_status ms_fields(ms_ctx* ctx, void** phi_dev, void** mu_dev, int64_t strides[4]);
+
+/* Enqueue n explicit steps (each a single fused kernel launch) and, every
+ * diag_every steps (ms_set_diag_every), the FP64 diagnostics kernel. */
+ms_status ms_step(ms_ctx* ctx, int64_t n);
+
+/* Run FP64 diagnostics of the current state and wait for them:
+ * out[0..K-2]   sum over cells of c_i = sum_a h_a c^a_i(mu, T)  (solute mass)
+ * out[K-1]      max |sum_a phi_a - 1|
+ * out[K]        min phi,   out[K+1] max phi
+ * out[K+2]      number of non-finite values in the state
+ * out[K+3]      max over cells of the explicit mu-diffusion number
+ *               dt * sum_faces max_i sum_j |(chi^-1 M_f)_ij| / dx^2
+ *               (the forward-Euler diffusion update is stable when <= 1)
+ * out[K+4]      step count,  out[K+5] physical time
+ * Also returns MS_ERR_NONFINITE when non-finite values are present. */
+ms_status ms_diag(ms_ctx* ctx, double* out);
+#define MS_DIAG_LEN(K) ((K) + 6)
+
+/* Run the diagnostics every k steps inside ms_step (0 = never, default). */
+ms_status ms_set_diag_every(ms_ctx* ctx, int64_t k);
+
+/* Wait for the stream; returns the sticky device status (MS_OK,
+ * MS_ERR_NONFINITE or MS_ERR_TIMEOUT). */
+ms_status ms_sync(ms_ctx* ctx);
+
+/* Step count and physical time of the current state. */
+ms_status ms_time(const ms_ctx* ctx, int64_t* step, double* t);
+
+/* Checkpoint / restore of the full state (binary, host buffer). */
+size_t ms_checkpoint_bytes(const ms_ctx* ctx);
+ms_status ms_checkpoint(ms_ctx* ctx, void* host_buf, size_t bytes);
+ms_status ms_restore(ms_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Launch shape: tile (index into ms_tile_shapes) and z-chunk (planes marched
+ * per CTA, 3-D only; 0 = automatic). */
+ms_status ms_set_launch(ms_ctx* ctx, int tile, int zchunk);
+/* Number of tile shapes compiled for this context and their (tx, ty). */
+int ms_tile_count(const ms_ctx* ctx);
+ms_status ms_tile_shape(const ms_ctx* ctx, int tile, int* tx, int* ty);
+
+/* Autotuner: times every compiled tile shape and a set of z-chunk sizes on
+ * the current state (the state is saved and restored), keeps the fastest and,
+ * when cache_path is not NULL, records it in that JSON file keyed by device,
+ * dim, N, K, dtype and grid, reusing a cached entry when present.
+ * best_ms_per_step may be NULL. */
+ms_status ms_tune(ms_ctx* ctx, const char* cache_path, int steps_per_trial,
+                  double* best_ms_per_step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MICROSIM_GB_H */

@@ -1,0 +1,7 @@
+"""GB300-native grand-potential phase-field step (MICROSIM, arXiv 2404.01035).
+
+The compute path is the CUDA library built from csrc/ (sm_103a) behind the C
+ABI in include/microsim_gb.h; this package is its thin Python binding.
+"""
+from ._binding import MSError, lib  # noqa: F401
+from .simulation import Simulation  # noqa: F401

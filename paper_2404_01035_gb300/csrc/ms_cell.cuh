@@ -1,0 +1,332 @@
+// One explicit grand-potential step for one cell, generic over
+//   - the scalar S (float, double, or a forward-mode Dual for the adjoint),
+//   - the accessor Acc that supplies the stencil (shared-memory tiles in the
+//     forward kernel, global memory with seeded duals in the adjoint).
+//
+// Steps, in order (MICROSIM paper, arXiv 2404.01035, Sec. 2.1):
+//   S1/S2  face values, face gradients and the anisotropic face flux
+//          J_a = da/dgrad phi_a = -sum_b phi_b g_ab(q_ab), q_ab = phi_a grad phi_b
+//          - phi_b grad phi_a, g = dA/dq (Eqs. Eqn_a, aniso_eqn);
+//   S3     divergence of J and the centre term da/dphi_a = sum_b g_ab . grad phi_b;
+//   S4     dw/dphi_a (Eq. Obstacle / Eq. Well), psi^b(mu, T) from the parabolic
+//          free energies (Sec. 3), dpsi/dphi_a = sum_b psi^b dh_b/dphi_a (Eq. hphi);
+//   S5     rate of Eq. (phi_eqn) divided by tau eps, explicit Euler, and the
+//          projection that realises the Lagrange multiplier;
+//   S6/S7  face mobilities and the mu update of Eq. (Mu_explicit_temperature)
+//          with chi(h(phi^{n+1})), c^a(mu^n), dh/dt and dT/dt as one-step
+//          differences, which keeps sum_cells c conserved to round-off.
+// Exactness of the bulk shortcut: a cell whose whole stencil holds a single
+// phase with value exactly 1 at the centre has q = 0 for every pair, dw/dphi
+// and dpsi/dphi that leave that vertex fixed under the projection, so
+// phi^{n+1} = phi^n there bit for bit; only the mu update is evaluated.
+#pragma once
+
+#include "ms_device.cuh"
+
+namespace msgb {
+
+template <class S, int P>
+struct DiffPrm {
+  S mob;         // phase-field mobility 1/tau
+  S delta[P];    // anisotropy strength per pair
+};
+
+template <int DIM>
+struct Off {
+  int x, y, z;
+};
+
+// Offset of unit step s along axis d.
+template <int DIM>
+__device__ __forceinline__ Off<DIM> unit(int d, int s) {
+  Off<DIM> o{0, 0, 0};
+  if (d == 0) o.x = s;
+  if (d == 1) o.y = s;
+  if (d == 2) o.z = s;
+  return o;
+}
+
+template <int DIM>
+__device__ __forceinline__ Off<DIM> add(Off<DIM> a, Off<DIM> b) {
+  return Off<DIM>{a.x + b.x, a.y + b.y, a.z + b.z};
+}
+
+// Normal component (axis D) of J_a on one face of the cell: side 0 = the
+// face shared with the -D neighbour, side 1 = with the +D neighbour.
+template <int DIM, int D, int NP, int NM, class Real, class S, class Acc>
+__device__ __forceinline__ void face_flux(const Acc& A, const StepArgs<Real, NP, NM>& g,
+                                          const DiffPrm<S, NP*(NP - 1) / 2>& dp, uint32_t mask,
+                                          int side, bool need_tan, S* Jn) {
+  const Off<DIM> L = unit<DIM>(D, side ? 0 : -1);
+  const Off<DIM> R = unit<DIM>(D, side ? 1 : 0);
+  S pf[NP];
+  S gr[NP][DIM];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    Jn[a] = S(Real(0));
+    if (!((mask >> a) & 1u)) continue;
+    S vl = A.phi(a, L.x, L.y, L.z);
+    S vr = A.phi(a, R.x, R.y, R.z);
+    pf[a] = Real(0.5) * (vl + vr);
+    gr[a][D] = (vr - vl) * g.inv_dx;
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      if (t == D) continue;
+      if (need_tan) {
+        const Off<DIM> up = unit<DIM>(t, 1), dn = unit<DIM>(t, -1);
+        const Off<DIM> Lu = add(L, up), Ru = add(R, up), Ld = add(L, dn), Rd = add(R, dn);
+        gr[a][t] = ((A.phi(a, Lu.x, Lu.y, Lu.z) + A.phi(a, Ru.x, Ru.y, Ru.z)) -
+                    (A.phi(a, Ld.x, Ld.y, Ld.z) + A.phi(a, Rd.x, Rd.y, Rd.z))) *
+                   g.quarter_inv_dx;
+      } else {
+        gr[a][t] = S(Real(0));
+      }
+    }
+  }
+  int p = 0;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int b = a + 1; b < NP; ++b, ++p) {
+      if (!(((mask >> a) & (mask >> b)) & 1u)) continue;
+      S q[DIM], gq[DIM];
+#pragma unroll
+      for (int t = 0; t < DIM; ++t) q[t] = pf[a] * gr[b][t] - pf[b] * gr[a][t];
+      pair_grad<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, g.rotated[p] != 0, g.rot[p], gq);
+      Jn[a] -= pf[b] * gq[D];
+      Jn[b] += pf[a] * gq[D];
+    }
+  }
+}
+
+// psi^b(mu, T) = C^b(T) - 1/2 (mu - B^b)^T chi^b (mu - B^b), s = T - T_ref.
+template <int NP, int NM, class Real, class S>
+__device__ __forceinline__ S grand_potential(const StepArgs<Real, NP, NM>& g, int b, const S* mu,
+                                             Real s) {
+  S y[NM];
+#pragma unroll
+  for (int j = 0; j < NM; ++j) y[j] = mu[j] - (g.B0[b][j] + g.B1[b][j] * s);
+  S quad = S(Real(0));
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+#pragma unroll
+    for (int j = 0; j < NM; ++j) quad += y[i] * (g.chi[b][i * NM + j] * y[j]);
+  }
+  const Real C = g.C0[b] + s * (g.C1[b] + s * g.C2[b]);
+  return C - Real(0.5) * quad;
+}
+
+// The full cell update.  kz = cell index along the last axis (for T).
+template <int DIM, int NP, int NM, class Real, class S, class Acc>
+__device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, NM>& g,
+                                        const DiffPrm<S, NP*(NP - 1) / 2>& dp, int kz, S* pn,
+                                        S* mn) {
+  S ph[NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) ph[a] = A.phi(a, 0, 0, 0);
+  const uint32_t mask = A.mask();
+  const int npresent = __popc(mask);
+  bool bulk = false;
+  if (npresent == 1) {
+    const int l = __ffs(mask) - 1;
+#pragma unroll
+    for (int a = 0; a < NP; ++a)
+      if (a == l) bulk = (val(ph[a]) == Real(1));
+  }
+  const Real s = g.tz0 + g.tzg * (Real(kz) + Real(0.5));   // T^n - T_ref
+  S mc[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) mc[i] = A.mu(i, 0, 0, 0);
+
+  if (bulk) {
+#pragma unroll
+    for (int a = 0; a < NP; ++a) pn[a] = ph[a];
+  } else {
+    S divJ[NP], Gc[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      divJ[a] = S(Real(0));
+      Gc[a] = S(Real(0));
+    }
+    if (npresent >= 2) {
+      bool need_tan = false;
+      {
+        int p = 0;
+#pragma unroll
+        for (int a = 0; a < NP; ++a)
+#pragma unroll
+          for (int b = a + 1; b < NP; ++b, ++p)
+            if ((((mask >> a) & (mask >> b)) & 1u) && g.aniso[p]) need_tan = true;
+      }
+      // S1-S3: divergence of the face fluxes
+      {
+        S Jm[NP], Jp[NP];
+        face_flux<DIM, 0>(A, g, dp, mask, 0, need_tan, Jm);
+        face_flux<DIM, 0>(A, g, dp, mask, 1, need_tan, Jp);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+      }
+      {
+        S Jm[NP], Jp[NP];
+        face_flux<DIM, 1>(A, g, dp, mask, 0, need_tan, Jm);
+        face_flux<DIM, 1>(A, g, dp, mask, 1, need_tan, Jp);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+      }
+      if constexpr (DIM == 3) {
+        S Jm[NP], Jp[NP];
+        face_flux<DIM, 2>(A, g, dp, mask, 0, need_tan, Jm);
+        face_flux<DIM, 2>(A, g, dp, mask, 1, need_tan, Jp);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+      }
+      // centre term, central differences
+      S gc[NP][DIM];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        if (!((mask >> a) & 1u)) {
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) gc[a][d] = S(Real(0));
+          continue;
+        }
+        gc[a][0] = (A.phi(a, 1, 0, 0) - A.phi(a, -1, 0, 0)) * g.half_inv_dx;
+        gc[a][1] = (A.phi(a, 0, 1, 0) - A.phi(a, 0, -1, 0)) * g.half_inv_dx;
+        if constexpr (DIM == 3) gc[a][2] = (A.phi(a, 0, 0, 1) - A.phi(a, 0, 0, -1)) * g.half_inv_dx;
+      }
+      int p = 0;
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+#pragma unroll
+        for (int b = a + 1; b < NP; ++b, ++p) {
+          if (!(((mask >> a) & (mask >> b)) & 1u)) continue;
+          S q[DIM], gq[DIM];
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) q[d] = ph[a] * gc[b][d] - ph[b] * gc[a][d];
+          pair_grad<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, g.rotated[p] != 0, g.rot[p],
+                         gq);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            Gc[a] += gq[d] * gc[b][d];
+            Gc[b] -= gq[d] * gc[a][d];
+          }
+        }
+      }
+    }
+    // S4: potential derivative
+    S W[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      W[a] = S(Real(0));
+#pragma unroll
+      for (int b = 0; b < NP; ++b) {
+        if (b == a) continue;
+        if (g.potential == 1)
+          W[a] += g.cw[a][b] * ph[b];
+        else
+          W[a] += g.cw[a][b] * (ph[a] * (ph[b] * ph[b]));
+      }
+      if (g.has_g3) {
+#pragma unroll
+        for (int b = 0; b < NP; ++b)
+#pragma unroll
+          for (int e = b + 1; e < NP; ++e)
+            if (b != a && e != a) W[a] += g.g3[a][b][e] * (ph[b] * ph[e]);
+      }
+    }
+    // S4: driving force sum_b psi^b dh_b/dphi_a
+    S psi[NP];
+#pragma unroll
+    for (int b = 0; b < NP; ++b) psi[b] = grand_potential<NP, NM, Real>(g, b, mc, s);
+    S e1 = ph[0];
+#pragma unroll
+    for (int a = 1; a < NP; ++a) e1 += ph[a];
+    S e2 = S(Real(0));
+    {
+      S run = ph[0];
+#pragma unroll
+      for (int a = 1; a < NP; ++a) {
+        e2 += ph[a] * run;
+        run += ph[a];
+      }
+    }
+    S v[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      S rest = e2 - ph[a] * (e1 - ph[a]);
+      S P = psi[a] * (Real(6) * ph[a] - Real(6) * (ph[a] * ph[a]) + Real(2) * rest);
+#pragma unroll
+      for (int b = 0; b < NP; ++b) {
+        if (b == a) continue;
+        P += psi[b] * (Real(2) * ph[b] * ((e1 - ph[a]) - ph[b]));
+      }
+      // S5: rate of Eq. (phi_eqn) / (tau eps), explicit Euler
+      S r = dp.mob * ((g.eps * (divJ[a] - Gc[a]) - W[a] * g.inv_eps - P) * g.inv_eps);
+      v[a] = ph[a] + g.dt * r;
+    }
+    project<NP>(g.potential, v, pn);
+  }
+
+  // ---- S6/S7: chemical-potential update
+  S h_new[NP];
+  interp_h<NP>(pn, h_new);
+  S Mc[NM * NM];
+  A.mobility(0, 0, 0, Mc);
+  S div[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) div[i] = S(Real(0));
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+    for (int sd = -1; sd <= 1; sd += 2) {
+      const Off<DIM> o = unit<DIM>(d, sd);
+      S Mn[NM * NM];
+      A.mobility(o.x, o.y, o.z, Mn);
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          S Mf = Real(0.5) * (Mc[i * NM + j] + Mn[i * NM + j]);
+          div[i] += Mf * ((A.mu(j, o.x, o.y, o.z) - mc[j]) * g.inv_dx2);
+        }
+      }
+    }
+  }
+  S rhs[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) rhs[i] = g.dt * div[i];
+  if (!bulk) {
+    S h_old[NP];
+    interp_h<NP>(ph, h_old);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      S dh = h_new[a] - h_old[a];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        S c_now = S(Real(0));
+#pragma unroll
+        for (int j = 0; j < NM; ++j)
+          c_now += g.chi[a][i * NM + j] * (mc[j] - (g.B0[a][j] + g.B1[a][j] * s));
+        rhs[i] -= c_now * dh;
+        rhs[i] -= h_new[a] * g.dcT[a][i];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < NP; ++a)
+#pragma unroll
+      for (int i = 0; i < NM; ++i) rhs[i] -= h_new[a] * g.dcT[a][i];
+  }
+  S chi[NM * NM];
+#pragma unroll
+  for (int k = 0; k < NM * NM; ++k) {
+    chi[k] = h_new[0] * g.chi[0][k];
+#pragma unroll
+    for (int a = 1; a < NP; ++a) chi[k] += h_new[a] * g.chi[a][k];
+  }
+  S dmu[NM];
+  solve_small<NM>(chi, rhs, dmu);
+#pragma unroll
+  for (int i = 0; i < NM; ++i) mn[i] = mc[i] + dmu[i];
+}
+
+}  // namespace msgb

@@ -1,0 +1,222 @@
+// FP64 diagnostics of one state: solute mass sum_cells c_i with
+// c = sum_a h_a c^a(mu, T) (the composition constraint under Eq.
+// Mu_explicit_temperature), max |sum phi - 1|, min/max phi, the count of
+// non-finite values, and the largest explicit mu-diffusion number
+// dt sum_faces ||chi(phi)^-1 M_f||_inf / dx^2 (the device-side dt check).
+// Two-stage reduction in a fixed order, so results are deterministic.
+#pragma once
+
+#include "ms_internal.h"
+#include "ms_step.cuh"
+
+namespace msgb {
+
+constexpr int kDiagThreads = 256;
+
+template <int NM>
+__device__ __forceinline__ void inv_small(const double* A, double* X) {
+  if constexpr (NM == 1) {
+    X[0] = 1.0 / A[0];
+  } else if constexpr (NM == 2) {
+    double det = A[0] * A[3] - A[1] * A[2];
+    X[0] = A[3] / det;
+    X[1] = -A[1] / det;
+    X[2] = -A[2] / det;
+    X[3] = A[0] / det;
+  } else {
+    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8];
+    double c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    X[0] = c00 / det;
+    X[3] = c01 / det;
+    X[6] = c02 / det;
+    X[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    X[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    X[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    X[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    X[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    X[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  }
+}
+
+template <int NP, int NM>
+struct DiagConsts {
+  double chi[NP][NM * NM];
+  double DX[NP][NM * NM];
+  double B0[NP][NM], B1[NP][NM];
+};
+
+template <int DIM, int NP, int NM, class Real>
+__global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ st, int nx, int ny,
+                                                       int nz, int pitch, int nyp, long long fstride,
+                                                       int xoff, int zoff, double tz0, double tzg,
+                                                       double dt, double inv_dx2,
+                                                       const __grid_constant__ DiagConsts<NP, NM> c,
+                                                       double* __restrict__ partials) {
+  constexpr int NV = NM + 5;
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) acc[i] = 0.0;
+  acc[NM] = 0.0;          // max |sum phi - 1|
+  acc[NM + 1] = 1e300;    // min phi
+  acc[NM + 2] = -1e300;   // max phi
+  acc[NM + 3] = 0.0;      // non-finite count
+  acc[NM + 4] = 0.0;      // max diffusion number
+  const long long cells = (long long)nx * ny * nz;
+  const long long plane = (long long)nyp * pitch;
+  auto idx = [&](int x, int y, int z) {
+    return (long long)(z + zoff) * plane + (long long)(y + 1) * pitch + x + xoff;
+  };
+  auto mob_at = [&](long long i0, double* M) {
+    double ph[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) ph[a] = (double)st[a * fstride + i0];
+    cell_mobility<NP, NM>(ph, c.DX, M);
+  };
+  for (long long cidx = blockIdx.x * (long long)blockDim.x + threadIdx.x; cidx < cells;
+       cidx += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(cidx % nx);
+    const int y = (int)((cidx / nx) % ny);
+    const int z = (int)(cidx / ((long long)nx * ny));
+    const long long i0 = idx(x, y, z);
+    double ph[NP], mu[NM], sum = 0.0;
+    bool finite = true;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      ph[a] = (double)st[a * fstride + i0];
+      finite = finite && isfinite(ph[a]);
+      sum += ph[a];
+      acc[NM + 1] = fmin(acc[NM + 1], ph[a]);
+      acc[NM + 2] = fmax(acc[NM + 2], ph[a]);
+    }
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      mu[i] = (double)st[(NP + i) * fstride + i0];
+      finite = finite && isfinite(mu[i]);
+    }
+    if (!finite) {
+      acc[NM + 3] += 1.0;
+      continue;
+    }
+    acc[NM] = fmax(acc[NM], fabs(sum - 1.0));
+    double h[NP];
+    interp_h<NP>(ph, h);
+    const double s = tz0 + tzg * ((DIM == 3 ? z : y) + 0.5);
+#pragma unroll
+    for (int a = 0; a < NP; ++a)
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        double ca = 0.0;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) ca += c.chi[a][i * NM + j] * (mu[j] - (c.B0[a][j] + c.B1[a][j] * s));
+        acc[i] += h[a] * ca;
+      }
+    // explicit diffusion number of the mu update at this cell
+    double chi[NM * NM], chinv[NM * NM], Mc[NM * NM];
+#pragma unroll
+    for (int k = 0; k < NM * NM; ++k) {
+      chi[k] = 0.0;
+#pragma unroll
+      for (int a = 0; a < NP; ++a) chi[k] += h[a] * c.chi[a][k];
+    }
+    inv_small<NM>(chi, chinv);
+    mob_at(i0, Mc);
+    double num = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+      for (int sd = -1; sd <= 1; sd += 2) {
+        const long long inb = idx(x + (d == 0 ? sd : 0), y + (d == 1 ? sd : 0), z + (d == 2 ? sd : 0));
+        double Mn[NM * NM];
+        mob_at(inb, Mn);
+        double rmax = 0.0;
+#pragma unroll
+        for (int i = 0; i < NM; ++i) {
+          double r = 0.0;
+#pragma unroll
+          for (int j = 0; j < NM; ++j) {
+            double e = 0.0;
+#pragma unroll
+            for (int k = 0; k < NM; ++k) e += chinv[i * NM + k] * 0.5 * (Mc[k * NM + j] + Mn[k * NM + j]);
+            r += fabs(e);
+          }
+          rmax = fmax(rmax, r);
+        }
+        num += rmax;
+      }
+    acc[NM + 4] = fmax(acc[NM + 4], dt * num * inv_dx2);
+  }
+  __shared__ double red[kDiagThreads];
+  for (int v = 0; v < NV; ++v) {
+    red[threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int w = kDiagThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        const double o = red[threadIdx.x + w];
+        double& r = red[threadIdx.x];
+        if (v < NM || v == NM + 3) r += o;
+        else if (v == NM + 1) r = fmin(r, o);
+        else r = fmax(r, o);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x * NV + v] = red[0];
+    __syncthreads();
+  }
+}
+
+template <int NM>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double* __restrict__ partials,
+                                                             int nblocks, double* __restrict__ out,
+                                                             int* status) {
+  constexpr int NV = NM + 5;
+  __shared__ double red[kDiagThreads];
+  for (int v = 0; v < NV; ++v) {
+    const bool is_sum = v < NM || v == NM + 3;
+    const bool is_min = v == NM + 1;
+    double r = is_sum ? 0.0 : (is_min ? 1e300 : -1e300);
+    for (int b = threadIdx.x; b < nblocks; b += kDiagThreads) {
+      const double o = partials[b * NV + v];
+      r = is_sum ? r + o : (is_min ? fmin(r, o) : fmax(r, o));
+    }
+    red[threadIdx.x] = r;
+    __syncthreads();
+    for (int w = kDiagThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        const double o = red[threadIdx.x + w];
+        double& q = red[threadIdx.x];
+        q = is_sum ? q + o : (is_min ? fmin(q, o) : fmax(q, o));
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[v] = red[0];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && out[NM + 3] > 0.0) atomicOr(status, kStatusNonFinite);
+}
+
+template <int DIM, int NP, int NM, class Real>
+cudaError_t launch_diag(const void* state, const HostModel& m, double t, double* partials,
+                        int nblocks, double* out, int* status, cudaStream_t st) {
+  DiagConsts<NP, NM> c;
+  for (int a = 0; a < NP; ++a) {
+    for (int k = 0; k < NM * NM; ++k) {
+      c.chi[a][k] = m.chi[a][k];
+      c.DX[a][k] = m.DX[a][k];
+    }
+    for (int i = 0; i < NM; ++i) {
+      c.B0[a][i] = m.B0[a][i];
+      c.B1[a][i] = m.B1[a][i];
+    }
+  }
+  const double tz0 = m.T0 - m.T_ref - m.G * (m.z0 + m.V * t);
+  k_diag<DIM, NP, NM, Real><<<nblocks, kDiagThreads, 0, st>>>(
+      reinterpret_cast<const Real*>(state), m.nx, m.ny, DIM == 3 ? m.nz : 1, m.pitch, m.nyp,
+      m.fstride, m.xoff, m.zoff, tz0, m.G * m.dx, m.dt, 1.0 / (m.dx * m.dx), c, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_diag_final<NM><<<1, kDiagThreads, 0, st>>>(partials, nblocks, out, status);
+  return cudaGetLastError();
+}
+
+}  // namespace msgb

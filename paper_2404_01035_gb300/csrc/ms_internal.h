@@ -1,0 +1,73 @@
+// Host-side internals shared by the runtime and the kernel instantiation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace msgb {
+
+constexpr int kNMax = 8;
+constexpr int kKMax = 3;
+
+// Status bits OR-ed into the device status word.
+constexpr int kStatusNonFinite = 1;
+constexpr int kStatusTimeout = 2;
+
+// Model constants derived in FP64 from the paper's inputs (Sec. 3).
+struct HostModel {
+  int dim = 2, N = 2, NM = 1, dtype = 0;
+  int nx = 1, ny = 1, nz = 1, bc[3] = {3, 3, 3};
+  // padded layout (elements)
+  int pitch = 0, nyp = 0, nzp = 0, xoff = 0, zoff = 0;
+  long long fstride = 0;
+  double dx = 1, dt = 0, eps = 1, tau = 1;
+  int potential = 1;
+  double gamma[kNMax][kNMax] = {};
+  double delta[kNMax][kNMax] = {};
+  double rot[kNMax][kNMax][9] = {};
+  bool rotated[kNMax][kNMax] = {};
+  double g3[kNMax][kNMax][kNMax] = {};
+  bool has_g3 = false;
+  double chi[kNMax][kKMax * kKMax] = {};   // (Hessian)^-1
+  double D[kNMax][kKMax * kKMax] = {};
+  double DX[kNMax][kKMax * kKMax] = {};    // D chi
+  double B0[kNMax][kKMax] = {}, B1[kNMax][kKMax] = {};
+  double C0[kNMax] = {}, C1[kNMax] = {}, C2[kNMax] = {};
+  double T0 = 0, G = 0, z0 = 0, V = 0, T_ref = 0, t0 = 0;
+};
+
+// Launch geometry of one step.
+struct LaunchGeom {
+  int tiles = 0;       // gridDim.x
+  int zchunks = 1;     // gridDim.y
+  int zchunk = 1;
+};
+
+// One compiled forward-step instantiation.
+struct StepKernel {
+  int dim, np, nm, dtype, tx, ty;
+  int smem_bytes;
+  size_t args_bytes;
+  // Fill the launch-argument blob from the model (all constants).
+  void (*fill)(void* blob, const HostModel& m, int zchunk, int* status);
+  // Launch one step: t = time of the input state, out = destination buffer.
+  cudaError_t (*launch)(const CUtensorMap* tm, void* blob, const HostModel& m, double t, void* out,
+                        const LaunchGeom& lg, cudaStream_t st);
+};
+
+// One compiled FP64 diagnostics instantiation.
+struct DiagKernel {
+  int dim, np, nm, dtype;
+  cudaError_t (*launch)(const void* state, const HostModel& m, double t, double* partials,
+                        int nblocks, double* out, int* status, cudaStream_t st);
+};
+
+std::vector<StepKernel>& step_registry();
+std::vector<DiagKernel>& diag_registry();
+void ensure_registered();
+
+}  // namespace msgb

@@ -1,0 +1,130 @@
+// Host launchers of the forward step and diagnostics kernels for one
+// (dim, phases, solutes, dtype) instantiation; included by the ms_inst_*.cu
+// units, each of which registers its instantiations.
+#pragma once
+
+#include <cmath>
+#include <cstring>
+
+#include "ms_diag.cuh"
+#include "ms_internal.h"
+#include "ms_step.cuh"
+
+namespace msgb {
+
+template <int DIM, int NP, int NM, class Real>
+void fill_args(void* blob, const HostModel& m, int zchunk, int* status) {
+  using A = StepArgs<Real, NP, NM>;
+  A& g = *reinterpret_cast<A*>(blob);
+  std::memset(&g, 0, sizeof(A));
+  g.nx = m.nx;
+  g.ny = m.ny;
+  g.nz = m.nz;
+  g.pitch = m.pitch;
+  g.nyp = m.nyp;
+  g.nzp = m.nzp;
+  g.fstride = m.fstride;
+  g.xoff = m.xoff;
+  g.zoff = m.zoff;
+  g.zchunk = zchunk;
+  for (int d = 0; d < 3; ++d) g.bc[d] = m.bc[d];
+  g.status = status;
+  g.dt = (Real)m.dt;
+  g.eps = (Real)m.eps;
+  g.inv_eps = (Real)(1.0 / m.eps);
+  g.mob = (Real)(1.0 / m.tau);
+  g.inv_dx = (Real)(1.0 / m.dx);
+  g.half_inv_dx = (Real)(0.5 / m.dx);
+  g.quarter_inv_dx = (Real)(0.25 / m.dx);
+  g.inv_dx2 = (Real)(1.0 / (m.dx * m.dx));
+  g.potential = m.potential;
+  g.has_g3 = m.has_g3 ? 1 : 0;
+  const double PI = 3.14159265358979323846;
+  int p = 0;
+  for (int a = 0; a < NP; ++a)
+    for (int b = a + 1; b < NP; ++b, ++p) {
+      g.gam2[p] = (Real)(2.0 * m.gamma[a][b]);
+      g.delta[p] = (Real)m.delta[a][b];
+      g.aniso[p] = m.delta[a][b] != 0.0;
+      g.rotated[p] = m.rotated[a][b];
+      for (int k = 0; k < 9; ++k) g.rot[p][k] = (Real)m.rot[a][b][k];
+    }
+  for (int a = 0; a < NP; ++a)
+    for (int b = 0; b < NP; ++b)
+      g.cw[a][b] = (Real)(m.potential == 1 ? 16.0 * m.gamma[a][b] / (PI * PI) : 18.0 * m.gamma[a][b]);
+  for (int a = 0; a < NP; ++a)
+    for (int b = 0; b < NP; ++b)
+      for (int e = 0; e < NP; ++e) g.g3[a][b][e] = (Real)m.g3[a][b][e];
+  for (int a = 0; a < NP; ++a) {
+    for (int k = 0; k < NM * NM; ++k) {
+      g.chi[a][k] = (Real)m.chi[a][k];
+      g.DX[a][k] = (Real)m.DX[a][k];
+    }
+    for (int i = 0; i < NM; ++i) {
+      g.B0[a][i] = (Real)m.B0[a][i];
+      g.B1[a][i] = (Real)m.B1[a][i];
+      double cb = 0;
+      for (int j = 0; j < NM; ++j) cb += m.chi[a][i * NM + j] * m.B1[a][j];
+      g.dcT[a][i] = (Real)(cb * m.G * m.V * m.dt);
+    }
+    g.C0[a] = (Real)m.C0[a];
+    g.C1[a] = (Real)m.C1[a];
+    g.C2[a] = (Real)m.C2[a];
+  }
+  g.tzg = (Real)(m.G * m.dx);
+}
+
+// T^n - T_ref at the first cell centre along the last axis, minus G dx / 2.
+inline double temp_offset(const HostModel& m, double t) {
+  return m.T0 - m.T_ref - m.G * (m.z0 + m.V * t);
+}
+
+template <int DIM, int NP, int NM, class Real, int TX, int TY>
+cudaError_t launch_step(const CUtensorMap* tm, void* blob, const HostModel& m, double t, void* out,
+                        const LaunchGeom& lg, cudaStream_t st) {
+  using A = StepArgs<Real, NP, NM>;
+  using Sh = StepShape<DIM, NP, NM, Real, TX, TY>;
+  A& g = *reinterpret_cast<A*>(blob);
+  g.out = reinterpret_cast<Real*>(out);
+  g.tz0 = (Real)temp_offset(m, t);
+  g.zchunk = lg.zchunk;
+  auto kern = k_gp_step<DIM, NP, NM, Real, TX, TY>;
+  static bool configured = false;   // attribute is per function, set once
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Sh::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  kern<<<dim3(lg.tiles, lg.zchunks), Sh::NT, Sh::SMEM_BYTES, st>>>(*tm, g);
+  return cudaGetLastError();
+}
+
+template <int DIM, int NP, int NM, class Real, int TX, int TY>
+StepKernel make_step_kernel() {
+  StepKernel k;
+  k.dim = DIM;
+  k.np = NP;
+  k.nm = NM;
+  k.dtype = sizeof(Real) == 8 ? 1 : 0;
+  k.tx = TX;
+  k.ty = TY;
+  k.smem_bytes = StepShape<DIM, NP, NM, Real, TX, TY>::SMEM_BYTES;
+  k.args_bytes = sizeof(StepArgs<Real, NP, NM>);
+  k.fill = &fill_args<DIM, NP, NM, Real>;
+  k.launch = &launch_step<DIM, NP, NM, Real, TX, TY>;
+  return k;
+}
+
+template <int DIM, int NP, int NM, class Real>
+DiagKernel make_diag_kernel() {
+  DiagKernel k;
+  k.dim = DIM;
+  k.np = NP;
+  k.nm = NM;
+  k.dtype = sizeof(Real) == 8 ? 1 : 0;
+  k.launch = &launch_diag<DIM, NP, NM, Real>;
+  return k;
+}
+
+}  // namespace msgb

@@ -1,0 +1,79 @@
+// The context object behind the opaque ms_ctx handle, and runtime helpers
+// shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/microsim_gb.h"
+#include "ms_internal.h"
+
+namespace msgb {
+
+struct AllocHook {
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*release)(void*, void*) = nullptr;
+  void* user = nullptr;
+};
+
+void* dev_alloc(const AllocHook& h, size_t bytes);
+void dev_free(const AllocHook& h, void* p);
+
+// Adjoint bookkeeping: snapshots of the state every `every` steps.
+struct AdjointStore {
+  int every = 0;               // 0 = recording off
+  int64_t first_step = 0;      // step of snapshot 0
+  std::vector<void*> snaps;    // device copies of the full padded state
+  void* seg = nullptr;         // recompute buffer: `every` states
+  size_t seg_bytes = 0;
+  void* adj[2] = {nullptr, nullptr};   // adjoint state ping-pong (padded)
+  double* gpart = nullptr;     // per-block FP64 gradient partials
+  int gblocks = 0;
+  double* gsum = nullptr;      // accumulated parameter gradients (device)
+};
+
+}  // namespace msgb
+
+struct ms_ctx {
+  msgb::HostModel m;
+  const msgb::StepKernel* kern = nullptr;
+  const msgb::DiagKernel* diagk = nullptr;
+  msgb::LaunchGeom lg;
+  std::vector<unsigned char> args;   // launch-argument blob of `kern`
+  CUtensorMap tm[2];
+  void* buf[2] = {nullptr, nullptr};
+  size_t state_bytes = 0;
+  int cur = 0;
+  int64_t step = 0;
+  double t = 0;
+  int64_t diag_every = 0;
+  cudaStream_t stream = nullptr;
+  msgb::AllocHook hook;
+  char* small = nullptr;        // status word + diag output + diag partials
+  int* status = nullptr;
+  double* diag_out = nullptr;
+  double* diag_partials = nullptr;
+  int diag_blocks = 0;
+  void* diag_host = nullptr;
+  std::string err;
+  msgb::AdjointStore adj;
+};
+
+namespace msgb {
+ms_status fail(ms_ctx* c, ms_status s, const std::string& msg);
+ms_status cuda_fail(ms_ctx* c, cudaError_t e, const char* what);
+ms_status launch_one_step(ms_ctx* c);
+ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk);
+std::vector<const StepKernel*> step_variants(int dim, int np, int nm, int dtype);
+cudaError_t fill_ghosts(const HostModel& m, void* buf, int nf, cudaStream_t st);
+cudaError_t copy_fields(const HostModel& m, void* padded, int f0, int nf, const void* dense, void* dense_out,
+                        int on_device, cudaStream_t st);
+}  // namespace msgb
+
+// Hooks implemented by the adjoint unit.
+ms_status ms_before_step(ms_ctx* c);   // records a snapshot when due
+void ms_reset_extra(ms_ctx* c);        // forget snapshots (state replaced)
+void ms_release_extra(ms_ctx* c);      // free adjoint buffers

@@ -1,0 +1,85 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+function include/microsim_gb.h declares, and rejects bad inputs with the
+documented status codes before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2404_01035_gb300 import _binding as B
+from paper_2404_01035_gb300.simulation import make_grid, make_params
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ms_[a-z0-9_]+)\s*\(", src))
+    return names - {"ms_status"}
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    L = B.lib()
+    decl = declared_functions()
+    assert len(decl) >= 19
+    missing = [n for n in sorted(decl) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(B.EXPORTS) <= decl
+
+
+def test_binding_lists_every_declared_function():
+    assert declared_functions() <= set(B.EXPORTS) | {"MS_DIAG_LEN"}
+
+
+def _create(prob, dtype="f32", **override):
+    L = B.lib()
+    keep = []
+    params = make_params(prob, dtype, keep, **override)
+    grid = make_grid(prob)
+    h = ctypes.c_void_p()
+    rc = L.ms_create(ctypes.byref(grid), prob.n_phases, prob.n_components, ctypes.byref(params),
+                     None, None, ctypes.byref(h))
+    return rc, h, L.ms_last_error(None).decode()
+
+
+def test_create_rejects_unstable_dt():
+    p = W.cfg1()
+    rc, h, msg = _create(p, dt=10.0)
+    assert rc == 4 and "stability" in msg and not h.value
+
+
+def test_create_rejects_bad_dimension_and_sizes():
+    p = W.cfg1()
+    bad = p.copy(dim=4)
+    assert _create(bad)[0] == 1
+    assert _create(p.copy(nx=0))[0] == 1
+    many = W.small_multiphase(n=4, dim=2, N=9, NM=1)
+    assert _create(many)[0] == 1
+
+
+def test_create_rejects_bad_boundary_and_potential():
+    p = W.cfg1()
+    assert _create(p.copy(bc=[2, 3, 3]))[0] == 1
+    assert _create(p, eps=-1.0)[0] == 1
+
+
+def test_create_reports_uncompiled_combination():
+    # 3-D with 5 phases is not compiled into this build
+    p = W.small_multiphase(n=8, dim=3, N=5, NM=1)
+    rc, h, msg = _create(p)
+    assert rc == 9 and "no compiled step kernel" in msg
+
+
+def test_null_handles_are_rejected():
+    L = B.lib()
+    assert L.ms_step(None, 1) == 1
+    assert L.ms_sync(None) == 1
+    assert L.ms_checkpoint_bytes(None) == 0
+    L.ms_destroy(None)

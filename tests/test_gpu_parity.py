@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 oracle.
+
+Bars: FP64 GPU build within 1e-10 of the oracle; FP32 GPU build within 1e-3
+(max |d phi|, |d mu|) after 1000 steps; bit-exact where the arithmetic is
+identical by construction (tile shapes, checkpoints, bulk cells).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+from gpu_util import pick_cells, windowed_one_step
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-3
+
+
+def gpu_run(prob, steps, dtype, phi0=None, mu0=None, **kw):
+    from paper_2404_01035_gb300 import Simulation
+    sim = Simulation(prob, dtype=dtype)
+    sim.set_fields(prob.phi0 if phi0 is None else phi0, prob.mu0 if mu0 is None else mu0)
+    for k, v in kw.items():
+        getattr(sim, k)(*v)
+    sim.step(steps)
+    sim.sync()
+    phi, mu = sim.get_fields()
+    sim.close()
+    return phi.astype(np.float64), mu.astype(np.float64)
+
+
+def max_err(a, b):
+    return max(np.abs(a[0] - b[0]).max(), np.abs(a[1] - b[1]).max())
+
+
+# ------------------------------------------------------------ whole-grid runs
+def test_cfg1_fp64_1000_steps():
+    p = W.cfg1()
+    g = gpu_run(p, p.steps, "f64")
+    o = oracle.run(p, p.phi0, p.mu0, p.steps)
+    assert max_err(g, o) <= FP64_TOL
+
+
+def test_cfg1_fp32_1000_steps():
+    p = W.cfg1()
+    g = gpu_run(p, p.steps, "f32")
+    o = oracle.run(p, p.phi0, p.mu0, p.steps)
+    assert max_err(g, o) <= FP32_TOL
+
+
+def test_anisotropic_2d_fp32_1000_steps():
+    p = W.binary_problem("aniso", 96, delta=0.04, Delta=0.25, R=8.0, potential="obstacle", ny=80)
+    g = gpu_run(p, 1000, "f32")
+    o = oracle.run(p, p.phi0, p.mu0, 1000)
+    assert max_err(g, o) <= FP32_TOL
+    assert np.abs(g[0] - p.phi0).max() > 0.1   # the seed did evolve
+
+
+@pytest.mark.parametrize("pot", ["obstacle", "well"])
+def test_3d_three_phase_ternary_fp64(pot):
+    p = W.small_multiphase(n=20, dim=3, N=3, NM=2, nx=37, ny=21, nz=19, potential=pot,
+                           rotate=True, gamma3=0.4)
+    g = gpu_run(p, 40, "f64")
+    o = oracle.run(p, p.phi0, p.mu0, 40)
+    assert max_err(g, o) <= FP64_TOL
+
+
+def test_3d_three_phase_ternary_fp32_1000_steps():
+    p = W.small_multiphase(n=16, dim=3, N=3, NM=2, nx=20, ny=18, nz=16, rotate=True)
+    g = gpu_run(p, 1000, "f32")
+    o = oracle.run(p, p.phi0, p.mu0, 1000)
+    assert max_err(g, o) <= FP32_TOL
+
+
+@pytest.mark.parametrize("dtype,steps,tol", [("f64", 30, FP64_TOL), ("f32", 300, FP32_TOL)])
+def test_3d_eight_phase_multigrain(dtype, steps, tol):
+    p = W.cfg5(n=40, grains=7, R=5.0, min_sep=14.0, seed=3)
+    g = gpu_run(p, steps, dtype)
+    o = oracle.run(p, p.phi0, p.mu0, steps)
+    assert max_err(g, o) <= tol
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_2d_three_phase_ternary(dtype):
+    p = W.small_multiphase(n=30, dim=2, N=3, NM=2, nx=70, ny=45, rotate=True, gamma3=0.3)
+    steps = 60 if dtype == "f64" else 400
+    g = gpu_run(p, steps, dtype)
+    o = oracle.run(p, p.phi0, p.mu0, steps)
+    assert max_err(g, o) <= (FP64_TOL if dtype == "f64" else FP32_TOL)
+
+
+def test_3d_binary_noflux_everywhere_fp64():
+    p = W.binary_problem("b3", 26, dim=3, delta=0.03, R=6.0, ny=23, nz=29,
+                         bc=[W.BC_NOFLUX] * 3)
+    g = gpu_run(p, 50, "f64")
+    o = oracle.run(p, p.phi0, p.mu0, 50)
+    assert max_err(g, o) <= FP64_TOL
+
+
+# ---------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("shape", [(3, 3, 3), (1, 5, 40), (33, 1, 9), (7, 9, 1)])
+def test_degenerate_3d_extents_fp64(shape):
+    nx, ny, nz = shape
+    p = W.small_multiphase(n=8, dim=3, N=3, NM=2, nx=nx, ny=ny, nz=nz)
+    g = gpu_run(p, 10, "f64")
+    o = oracle.run(p, p.phi0, p.mu0, 10)
+    assert max_err(g, o) <= FP64_TOL
+
+
+def test_one_row_strip_2d_fp64():
+    p = W.binary_problem("strip", 200, ny=1, R=0.0, potential="well")
+    x = np.arange(200) + 0.5
+    s = 0.5 * (1 + np.tanh((x - 60) / 6.0)) * 0.5 * (1 + np.tanh((140 - x) / 6.0))
+    p.phi0 = np.stack([s[None, None], 1 - s[None, None]])
+    p.mu0 = np.full((1, 1, 1, 200), 1.634)
+    g = gpu_run(p, 200, "f64")
+    o = oracle.run(p, p.phi0, p.mu0, 200)
+    assert max_err(g, o) <= FP64_TOL
+
+
+def test_zero_steps_is_identity():
+    p = W.cfg1()
+    g = gpu_run(p, 0, "f64")
+    assert np.array_equal(g[0], p.phi0) and np.array_equal(g[1], p.mu0)
+
+
+def test_single_phase_domain_stays_bitwise_fp32():
+    p = W.small_multiphase(n=24, dim=3, N=3, NM=2)
+    shape = (p.nz, p.ny, p.nx)
+    phi0 = np.stack([np.zeros(shape), np.zeros(shape), np.ones(shape)])
+    g = gpu_run(p, 50, "f32", phi0=phi0)
+    assert np.array_equal(g[0], phi0)
+
+
+# --------------------------------------------------- invariants, diagnostics
+@pytest.mark.parametrize("dtype,rtol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_mass_conservation_and_diag_match_oracle(dtype, rtol):
+    from paper_2404_01035_gb300 import Simulation
+    p = W.small_multiphase(n=20, dim=3, N=3, NM=2, nx=33, ny=20, nz=18, rotate=True)
+    sim = Simulation(p, dtype=dtype)
+    sim.set_fields(p.phi0, p.mu0)
+    d0 = sim.diag()
+    o0 = oracle.diag(p, sim.get_fields()[0], sim.get_fields()[1])
+    np.testing.assert_allclose(d0["mass"], o0[:2], rtol=1e-12 if dtype == "f64" else 1e-6)
+    sim.step(200)
+    d1 = sim.diag()
+    sim.close()
+    np.testing.assert_allclose(d1["mass"], d0["mass"], rtol=rtol)
+    assert d1["sum_err"] < (1e-13 if dtype == "f64" else 1e-5)
+    assert d1["phi_min"] >= 0.0 and d1["phi_max"] <= 1.0 + 1e-6
+    assert d1["nonfinite"] == 0
+    assert 0 < d1["mu_diffusion_number"] <= 1.0
+    assert d1["step"] == 200 and d1["t"] == pytest.approx(200 * p.dt)
+
+
+def test_tile_shapes_and_zchunks_are_bitwise_identical():
+    from paper_2404_01035_gb300 import Simulation
+    p = W.small_multiphase(n=20, dim=3, N=3, NM=2, nx=70, ny=37, nz=45, rotate=True)
+    ref = None
+    sim = Simulation(p, dtype="f32")
+    variants = [(t, z) for t in range(len(sim.tiles())) for z in (0, 5, 16)]
+    for t, z in variants:
+        sim.set_fields(p.phi0, p.mu0)
+        sim.set_launch(t, z)
+        sim.step(20)
+        phi, mu = sim.get_fields()
+        if ref is None:
+            ref = (phi, mu)
+        else:
+            assert np.array_equal(phi, ref[0]) and np.array_equal(mu, ref[1]), (t, z)
+    sim.close()
+
+
+def test_checkpoint_restore_is_bitwise_and_views_match():
+    from paper_2404_01035_gb300 import Simulation
+    import torch
+    p = W.small_multiphase(n=16, dim=3, N=3, NM=2, nx=30, ny=17, nz=15)
+    sim = Simulation(p, dtype="f32")
+    sim.set_fields(p.phi0, p.mu0)
+    sim.step(7)
+    blob = sim.checkpoint()
+    sim.step(9)
+    a = sim.get_fields()
+    vphi, vmu = sim.fields()
+    torch.cuda.synchronize()
+    assert np.array_equal(vphi.cpu().numpy(), a[0]) and np.array_equal(vmu.cpu().numpy(), a[1])
+    sim.restore(blob)
+    assert sim.time()[0] == 7
+    sim.step(9)
+    b = sim.get_fields()
+    sim.close()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_device_and_host_field_io_agree():
+    from paper_2404_01035_gb300 import Simulation
+    import torch
+    p = W.small_multiphase(n=16, dim=2, N=3, NM=2, nx=40, ny=33)
+    sim = Simulation(p, dtype="f64")
+    tphi = torch.tensor(p.phi0, device="cuda")
+    tmu = torch.tensor(p.mu0, device="cuda")
+    sim.set_fields(tphi, tmu)
+    sim.step(5)
+    h = sim.get_fields()
+    dphi = torch.empty_like(tphi)
+    dmu = torch.empty_like(tmu)
+    sim.get_fields_into(dphi, dmu, on_device=True)
+    sim.close()
+    assert np.array_equal(dphi.cpu().numpy(), h[0]) and np.array_equal(dmu.cpu().numpy(), h[1])
+
+
+def test_autotuner_picks_a_variant_and_caches(tmp_path):
+    from paper_2404_01035_gb300 import Simulation
+    p = W.cfg2(n=64, steps=10)
+    sim = Simulation(p, dtype="f32")
+    sim.set_fields(p.phi0, p.mu0)
+    cache = str(tmp_path / "tune.json")
+    ms = sim.tune(cache, steps_per_trial=5)
+    assert ms > 0
+    assert sim.time()[0] == 0            # state restored
+    ms2 = sim.tune(cache, steps_per_trial=5)
+    assert ms2 == pytest.approx(ms, rel=1e-5)
+    sim.close()
+
+
+# -------------------------------------------------- full-size, sampled parity
+def _full_size_sampled(prob, dtype, warm_steps, seed, tol):
+    from paper_2404_01035_gb300 import Simulation
+    rng = np.random.default_rng(seed)
+    sim = Simulation(prob, dtype=dtype)
+    sim.set_fields(prob.phi0, prob.mu0)
+    sim.step(warm_steps)
+    phi_n, mu_n = sim.get_fields()
+    t_n = sim.time()[1]
+    sim.step(1)
+    phi_1, mu_1 = sim.get_fields()
+    d = sim.diag()
+    sim.close()
+    cells = pick_cells(phi_n, rng)
+    ophi, omu = windowed_one_step(prob, phi_n, mu_n, cells, t0=t_n)
+    gphi = np.array([phi_1[:, z, y, x] for (z, y, x) in cells])
+    gmu = np.array([mu_1[:, z, y, x] for (z, y, x) in cells])
+    assert np.abs(gphi - ophi).max() <= tol
+    assert np.abs(gmu - omu).max() <= tol
+    assert d["nonfinite"] == 0
+    return d
+
+
+def test_cfg2_full_size_sampled_parity_fp32():
+    p = W.cfg2()
+    _full_size_sampled(p, "f32", warm_steps=300, seed=1, tol=2e-5)
+
+
+def test_cfg2_full_size_invariants_2000_steps():
+    from paper_2404_01035_gb300 import Simulation
+    p = W.cfg2()
+    sim = Simulation(p, dtype="f32")
+    sim.set_fields(p.phi0, p.mu0)
+    d0 = sim.diag()
+    sim.step(p.steps)
+    d1 = sim.diag()
+    sim.close()
+    np.testing.assert_allclose(d1["mass"], d0["mass"], rtol=2e-5)
+    assert d1["sum_err"] < 1e-5 and d1["phi_min"] >= 0 and d1["nonfinite"] == 0
+
+
+def test_cfg5_full_size_sampled_parity_fp32():
+    p = W.cfg5()
+    _full_size_sampled(p, "f32", warm_steps=20, seed=2, tol=2e-5)

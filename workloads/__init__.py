@@ -370,7 +370,7 @@ def small_multiphase(n: int = 24, dim: int = 3, N: int = 3, NM: int = 2, seed: i
     rng = PCG32(seed, seq=11)
     nx = n if nx is None else nx
     ny = n if ny is None else ny
-    nz = (n if dim == 3 else 1) if nz is None else nz
+    nz = 1 if dim == 2 else (n if nz is None else nz)
     gamma, dl, rot, D, A = _default_material(N, NM)
     for a in range(N):
         for b in range(a + 1, N):
