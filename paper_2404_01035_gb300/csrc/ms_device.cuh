@@ -38,6 +38,12 @@ struct StepArgs {
   int bc[3];
   Real* out;                // destination state (padded, NP + NM fields)
   int* status;              // sticky device status word
+  // Segment codes: one byte per 32-cell x-segment of every row of every
+  // plane, [nz][ny][segs]; l + 1 when all its cells are exactly pure phase l,
+  // else 0.  Read for the input state, written for the output state.
+  const uint8_t* codes_in;
+  uint8_t* codes_out;
+  int segs;
   // scalars
   Real dt, eps, inv_eps, mob, inv_dx, half_inv_dx, quarter_inv_dx, inv_dx2;
   int potential;            // 1 obstacle, 2 well
@@ -56,6 +62,9 @@ struct StepArgs {
   Real B0[NP][NM], B1[NP][NM];  // B^a(T) = B0 + B1 (T - T_ref)
   Real C0[NP], C1[NP], C2[NP];  // C^a(T) = C0 + C1 s + C2 s^2, s = T - T_ref
   Real dcT[NP][NM];         // c^a(mu, T^{n+1}) - c^a(mu, T^n) = chi B1 G V dt
+  // single-phase (bulk) mu update: mu += Kb (sum_nb mu_nb - 2d mu) - eb
+  Real Kb[NP][NM * NM];     // dt / dx^2 (chi^a)^-1 D^a chi^a
+  Real eb[NP][NM];          // (chi^a)^-1 dcT^a
   // temperature along the last axis: T = tz0 + tzg * (k + 1/2), tref subtracted
   Real tz0, tzg;
 };
@@ -181,6 +190,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {

@@ -1,9 +1,10 @@
-// FP64 diagnostics of one state: solute mass sum_cells c_i with
-// c = sum_a h_a c^a(mu, T) (the composition constraint under Eq.
+// Diagnostics of one state with FP64 reductions: solute mass sum_cells c_i
+// with c = sum_a h_a c^a(mu, T) (the composition constraint under Eq.
 // Mu_explicit_temperature), max |sum phi - 1|, min/max phi, the count of
 // non-finite values, and the largest explicit mu-diffusion number
 // dt sum_faces ||chi(phi)^-1 M_f||_inf / dx^2 (the device-side dt check).
-// Two-stage reduction in a fixed order, so results are deterministic.
+// Per-cell values are evaluated in the state's precision and accumulated in
+// FP64; the two-stage reduction runs in a fixed order (deterministic).
 #pragma once
 
 #include "ms_internal.h"
@@ -13,20 +14,20 @@ namespace msgb {
 
 constexpr int kDiagThreads = 256;
 
-template <int NM>
-__device__ __forceinline__ void inv_small(const double* A, double* X) {
+template <int NM, class R>
+__device__ __forceinline__ void inv_small(const R* A, R* X) {
   if constexpr (NM == 1) {
-    X[0] = 1.0 / A[0];
+    X[0] = R(1) / A[0];
   } else if constexpr (NM == 2) {
-    double det = A[0] * A[3] - A[1] * A[2];
+    R det = A[0] * A[3] - A[1] * A[2];
     X[0] = A[3] / det;
     X[1] = -A[1] / det;
     X[2] = -A[2] / det;
     X[3] = A[0] / det;
   } else {
-    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8];
-    double c02 = A[3] * A[7] - A[4] * A[6];
-    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    R c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8];
+    R c02 = A[3] * A[7] - A[4] * A[6];
+    R det = A[0] * c00 + A[1] * c01 + A[2] * c02;
     X[0] = c00 / det;
     X[3] = c01 / det;
     X[6] = c02 / det;
@@ -39,11 +40,11 @@ __device__ __forceinline__ void inv_small(const double* A, double* X) {
   }
 }
 
-template <int NP, int NM>
+template <class Real, int NP, int NM>
 struct DiagConsts {
-  double chi[NP][NM * NM];
-  double DX[NP][NM * NM];
-  double B0[NP][NM], B1[NP][NM];
+  Real chi[NP][NM * NM];
+  Real DX[NP][NM * NM];
+  Real B0[NP][NM], B1[NP][NM];
 };
 
 template <int DIM, int NP, int NM, class Real>
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ 
                                                        int nz, int pitch, int nyp, long long fstride,
                                                        int xoff, int zoff, double tz0, double tzg,
                                                        double dt, double inv_dx2,
-                                                       const __grid_constant__ DiagConsts<NP, NM> c,
+                                                       const __grid_constant__ DiagConsts<Real, NP, NM> c,
                                                        double* __restrict__ partials) {
   constexpr int NV = NM + 5;
   double acc[NV];
@@ -67,10 +68,10 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ 
   auto idx = [&](int x, int y, int z) {
     return (long long)(z + zoff) * plane + (long long)(y + 1) * pitch + x + xoff;
   };
-  auto mob_at = [&](long long i0, double* M) {
-    double ph[NP];
+  auto mob_at = [&](long long i0, Real* M) {
+    Real ph[NP];
 #pragma unroll
-    for (int a = 0; a < NP; ++a) ph[a] = (double)st[a * fstride + i0];
+    for (int a = 0; a < NP; ++a) ph[a] = st[a * fstride + i0];
     cell_mobility<NP, NM>(ph, c.DX, M);
   };
   for (long long cidx = blockIdx.x * (long long)blockDim.x + threadIdx.x; cidx < cells;
@@ -79,19 +80,20 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ 
     const int y = (int)((cidx / nx) % ny);
     const int z = (int)(cidx / ((long long)nx * ny));
     const long long i0 = idx(x, y, z);
-    double ph[NP], mu[NM], sum = 0.0;
+    Real ph[NP], mu[NM];
+    double sum = 0.0;
     bool finite = true;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
-      ph[a] = (double)st[a * fstride + i0];
+      ph[a] = st[a * fstride + i0];
       finite = finite && isfinite(ph[a]);
-      sum += ph[a];
-      acc[NM + 1] = fmin(acc[NM + 1], ph[a]);
-      acc[NM + 2] = fmax(acc[NM + 2], ph[a]);
+      sum += (double)ph[a];
+      acc[NM + 1] = fmin(acc[NM + 1], (double)ph[a]);
+      acc[NM + 2] = fmax(acc[NM + 2], (double)ph[a]);
     }
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
-      mu[i] = (double)st[(NP + i) * fstride + i0];
+      mu[i] = st[(NP + i) * fstride + i0];
       finite = finite && isfinite(mu[i]);
     }
     if (!finite) {
@@ -99,52 +101,55 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ 
       continue;
     }
     acc[NM] = fmax(acc[NM], fabs(sum - 1.0));
-    double h[NP];
+    Real h[NP];
     interp_h<NP>(ph, h);
-    const double s = tz0 + tzg * ((DIM == 3 ? z : y) + 0.5);
+    const Real s = (Real)(tz0 + tzg * ((DIM == 3 ? z : y) + 0.5));
 #pragma unroll
-    for (int a = 0; a < NP; ++a)
+    for (int i = 0; i < NM; ++i) {
+      Real ci = Real(0);
 #pragma unroll
-      for (int i = 0; i < NM; ++i) {
-        double ca = 0.0;
+      for (int a = 0; a < NP; ++a) {
+        Real ca = Real(0);
 #pragma unroll
         for (int j = 0; j < NM; ++j) ca += c.chi[a][i * NM + j] * (mu[j] - (c.B0[a][j] + c.B1[a][j] * s));
-        acc[i] += h[a] * ca;
+        ci += h[a] * ca;
       }
+      acc[i] += (double)ci;
+    }
     // explicit diffusion number of the mu update at this cell
-    double chi[NM * NM], chinv[NM * NM], Mc[NM * NM];
+    Real chi[NM * NM], chinv[NM * NM], Mc[NM * NM];
 #pragma unroll
     for (int k = 0; k < NM * NM; ++k) {
-      chi[k] = 0.0;
+      chi[k] = Real(0);
 #pragma unroll
       for (int a = 0; a < NP; ++a) chi[k] += h[a] * c.chi[a][k];
     }
     inv_small<NM>(chi, chinv);
     mob_at(i0, Mc);
-    double num = 0.0;
+    Real num = Real(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
       for (int sd = -1; sd <= 1; sd += 2) {
         const long long inb = idx(x + (d == 0 ? sd : 0), y + (d == 1 ? sd : 0), z + (d == 2 ? sd : 0));
-        double Mn[NM * NM];
+        Real Mn[NM * NM];
         mob_at(inb, Mn);
-        double rmax = 0.0;
+        Real rmax = Real(0);
 #pragma unroll
         for (int i = 0; i < NM; ++i) {
-          double r = 0.0;
+          Real r = Real(0);
 #pragma unroll
           for (int j = 0; j < NM; ++j) {
-            double e = 0.0;
+            Real e = Real(0);
 #pragma unroll
-            for (int k = 0; k < NM; ++k) e += chinv[i * NM + k] * 0.5 * (Mc[k * NM + j] + Mn[k * NM + j]);
+            for (int k = 0; k < NM; ++k) e += chinv[i * NM + k] * (Real(0.5) * (Mc[k * NM + j] + Mn[k * NM + j]));
             r += fabs(e);
           }
           rmax = fmax(rmax, r);
         }
         num += rmax;
       }
-    acc[NM + 4] = fmax(acc[NM + 4], dt * num * inv_dx2);
+    acc[NM + 4] = fmax(acc[NM + 4], dt * (double)num * inv_dx2);
   }
   __shared__ double red[kDiagThreads];
   for (int v = 0; v < NV; ++v) {
@@ -198,15 +203,15 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_final(const double* __res
 template <int DIM, int NP, int NM, class Real>
 cudaError_t launch_diag(const void* state, const HostModel& m, double t, double* partials,
                         int nblocks, double* out, int* status, cudaStream_t st) {
-  DiagConsts<NP, NM> c;
+  DiagConsts<Real, NP, NM> c;
   for (int a = 0; a < NP; ++a) {
     for (int k = 0; k < NM * NM; ++k) {
-      c.chi[a][k] = m.chi[a][k];
-      c.DX[a][k] = m.DX[a][k];
+      c.chi[a][k] = (Real)m.chi[a][k];
+      c.DX[a][k] = (Real)m.DX[a][k];
     }
     for (int i = 0; i < NM; ++i) {
-      c.B0[a][i] = m.B0[a][i];
-      c.B1[a][i] = m.B1[a][i];
+      c.B0[a][i] = (Real)m.B0[a][i];
+      c.B1[a][i] = (Real)m.B1[a][i];
     }
   }
   const double tz0 = m.T0 - m.T_ref - m.G * (m.z0 + m.V * t);

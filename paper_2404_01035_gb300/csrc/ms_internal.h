@@ -54,10 +54,17 @@ struct StepKernel {
   size_t args_bytes;
   // Fill the launch-argument blob from the model (all constants).
   void (*fill)(void* blob, const HostModel& m, int zchunk, int* status);
-  // Launch one step: t = time of the input state, out = destination buffer.
+  // Launch one step: t = time of the input state, out = destination buffer,
+  // codes_in / codes_out = segment codes of the input / output state.
   cudaError_t (*launch)(const CUtensorMap* tm, void* blob, const HostModel& m, double t, void* out,
-                        const LaunchGeom& lg, cudaStream_t st);
+                        const uint8_t* codes_in, uint8_t* codes_out, const LaunchGeom& lg,
+                        cudaStream_t st);
+  // Recompute the segment codes of a state loaded from outside.
+  cudaError_t (*codes)(const void* state, const HostModel& m, uint8_t* codes, cudaStream_t st);
 };
+
+// Number of 32-cell segments per row.
+inline int segments(const HostModel& m) { return (m.nx + 31) / 32; }
 
 // One compiled FP64 diagnostics instantiation.
 struct DiagKernel {

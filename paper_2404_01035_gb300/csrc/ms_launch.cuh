@@ -67,11 +67,46 @@ void fill_args(void* blob, const HostModel& m, int zchunk, int* status) {
       for (int j = 0; j < NM; ++j) cb += m.chi[a][i * NM + j] * m.B1[a][j];
       g.dcT[a][i] = (Real)(cb * m.G * m.V * m.dt);
     }
+    {
+      // (chi^a)^-1 = Hessian of f^a; Kb = dt/dx^2 H D chi, eb = H dcT
+      double Hm[9] = {0};
+      const double* c = m.chi[a];
+      if (NM == 1) {
+        Hm[0] = 1.0 / c[0];
+      } else if (NM == 2) {
+        double det = c[0] * c[3] - c[1] * c[2];
+        Hm[0] = c[3] / det; Hm[1] = -c[1] / det; Hm[2] = -c[2] / det; Hm[3] = c[0] / det;
+      } else {
+        double c00 = c[4] * c[8] - c[5] * c[7], c01 = c[5] * c[6] - c[3] * c[8];
+        double c02 = c[3] * c[7] - c[4] * c[6];
+        double det = c[0] * c00 + c[1] * c01 + c[2] * c02;
+        Hm[0] = c00 / det; Hm[3] = c01 / det; Hm[6] = c02 / det;
+        Hm[1] = (c[2] * c[7] - c[1] * c[8]) / det; Hm[4] = (c[0] * c[8] - c[2] * c[6]) / det;
+        Hm[7] = (c[1] * c[6] - c[0] * c[7]) / det; Hm[2] = (c[1] * c[5] - c[2] * c[4]) / det;
+        Hm[5] = (c[2] * c[3] - c[0] * c[5]) / det; Hm[8] = (c[0] * c[4] - c[1] * c[3]) / det;
+      }
+      const double scale = m.dt / (m.dx * m.dx);
+      for (int i = 0; i < NM; ++i) {
+        double e = 0;
+        for (int k = 0; k < NM; ++k) {
+          double cb = 0;
+          for (int j = 0; j < NM; ++j) cb += m.chi[a][k * NM + j] * m.B1[a][j];
+          e += Hm[i * NM + k] * cb * m.G * m.V * m.dt;
+        }
+        g.eb[a][i] = (Real)e;
+        for (int j = 0; j < NM; ++j) {
+          double kk = 0;
+          for (int k = 0; k < NM; ++k) kk += Hm[i * NM + k] * m.DX[a][k * NM + j];
+          g.Kb[a][i * NM + j] = (Real)(scale * kk);
+        }
+      }
+    }
     g.C0[a] = (Real)m.C0[a];
     g.C1[a] = (Real)m.C1[a];
     g.C2[a] = (Real)m.C2[a];
   }
   g.tzg = (Real)(m.G * m.dx);
+  g.segs = segments(m);
 }
 
 // T^n - T_ref at the first cell centre along the last axis, minus G dx / 2.
@@ -81,11 +116,14 @@ inline double temp_offset(const HostModel& m, double t) {
 
 template <int DIM, int NP, int NM, class Real, int TX, int TY>
 cudaError_t launch_step(const CUtensorMap* tm, void* blob, const HostModel& m, double t, void* out,
-                        const LaunchGeom& lg, cudaStream_t st) {
+                        const uint8_t* codes_in, uint8_t* codes_out, const LaunchGeom& lg,
+                        cudaStream_t st) {
   using A = StepArgs<Real, NP, NM>;
   using Sh = StepShape<DIM, NP, NM, Real, TX, TY>;
   A& g = *reinterpret_cast<A*>(blob);
   g.out = reinterpret_cast<Real*>(out);
+  g.codes_in = codes_in;
+  g.codes_out = codes_out;
   g.tz0 = (Real)temp_offset(m, t);
   g.zchunk = lg.zchunk;
   auto kern = k_gp_step<DIM, NP, NM, Real, TX, TY>;
@@ -96,7 +134,17 @@ cudaError_t launch_step(const CUtensorMap* tm, void* blob, const HostModel& m, d
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  kern<<<dim3(lg.tiles, lg.zchunks), Sh::NT, Sh::SMEM_BYTES, st>>>(*tm, g);
+  kern<<<dim3(lg.tiles, lg.zchunks), Sh::NTHREADS, Sh::SMEM_BYTES, st>>>(*tm, g);
+  return cudaGetLastError();
+}
+
+template <int DIM, int NP, class Real>
+cudaError_t launch_codes(const void* state, const HostModel& m, uint8_t* codes, cudaStream_t st) {
+  const long long warps = (long long)segments(m) * m.ny * m.nz;
+  const int blocks = (int)((warps * 32 + 255) / 256);
+  k_codes<DIM, NP, Real><<<blocks, 256, 0, st>>>(reinterpret_cast<const Real*>(state), m.nx, m.ny, m.nz,
+                                                 m.pitch, m.nyp, m.fstride, m.xoff, m.zoff, segments(m),
+                                                 codes);
   return cudaGetLastError();
 }
 
@@ -113,6 +161,7 @@ StepKernel make_step_kernel() {
   k.args_bytes = sizeof(StepArgs<Real, NP, NM>);
   k.fill = &fill_args<DIM, NP, NM, Real>;
   k.launch = &launch_step<DIM, NP, NM, Real, TX, TY>;
+  k.codes = &launch_codes<DIM, NP, Real>;
   return k;
 }
 

@@ -45,6 +45,7 @@ struct ms_ctx {
   std::vector<unsigned char> args;   // launch-argument blob of `kern`
   CUtensorMap tm[2];
   void* buf[2] = {nullptr, nullptr};
+  uint8_t* codes[2] = {nullptr, nullptr};   // segment codes of buf[0] / buf[1]
   size_t state_bytes = 0;
   int cur = 0;
   int64_t step = 0;
@@ -67,6 +68,7 @@ ms_status fail(ms_ctx* c, ms_status s, const std::string& msg);
 ms_status cuda_fail(ms_ctx* c, cudaError_t e, const char* what);
 ms_status launch_one_step(ms_ctx* c);
 ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk);
+ms_status refresh_codes(ms_ctx* c);   // segment codes of the current state
 std::vector<const StepKernel*> step_variants(int dim, int np, int nm, int dtype);
 cudaError_t fill_ghosts(const HostModel& m, void* buf, int nf, cudaStream_t st);
 cudaError_t copy_fields(const HostModel& m, void* padded, int f0, int nf, const void* dense, void* dense_out,

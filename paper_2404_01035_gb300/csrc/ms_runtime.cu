@@ -435,11 +435,18 @@ ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk) {
 
 ms_status launch_one_step(ms_ctx* c) {
   const int src = c->cur, dst = 1 - c->cur;
-  cudaError_t e = c->kern->launch(&c->tm[src], c->args.data(), c->m, c->t, c->buf[dst], c->lg, c->stream);
+  cudaError_t e = c->kern->launch(&c->tm[src], c->args.data(), c->m, c->t, c->buf[dst], c->codes[src],
+                                  c->codes[dst], c->lg, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
   c->cur = dst;
   c->step += 1;
   c->t = c->m.t0 + (double)c->step * c->m.dt;
+  return MS_OK;
+}
+
+ms_status refresh_codes(ms_ctx* c) {
+  cudaError_t e = c->kern->codes(c->buf[c->cur], c->m, c->codes[c->cur], c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "segment codes");
   return MS_OK;
 }
 
@@ -488,9 +495,11 @@ ms_status ms_create(const ms_grid* grid, int n_phases, int n_components, const m
   const size_t s_el = c->m.dtype == MS_F64 ? 8 : 4;
   const int nf = c->m.N + c->m.NM;
   c->state_bytes = (size_t)c->m.fstride * nf * s_el;
+  const size_t code_bytes = (size_t)segments(c->m) * c->m.ny * c->m.nz;
   for (int b = 0; b < 2; ++b) {
     c->buf[b] = dev_alloc(c->hook, c->state_bytes);
-    if (!c->buf[b]) {
+    c->codes[b] = static_cast<uint8_t*>(dev_alloc(c->hook, code_bytes));
+    if (!c->buf[b] || !c->codes[b]) {
       ms_destroy(c);
       return fail(nullptr, MS_ERR_OOM, "state allocation failed");
     }
@@ -512,7 +521,10 @@ ms_status ms_create(const ms_grid* grid, int n_phases, int n_components, const m
     return fail(nullptr, MS_ERR_OOM, "pinned allocation failed");
   }
   cudaError_t e = cudaMemsetAsync(c->small, 0, 4096, c->stream);
-  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(c->buf[b], 0, c->state_bytes, c->stream);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaMemsetAsync(c->buf[b], 0, c->state_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->codes[b], 0, code_bytes, c->stream);
+  }
   if (e != cudaSuccess) {
     ms_status r = cuda_fail(nullptr, e, "initial memset");
     ms_destroy(c);
@@ -533,7 +545,10 @@ void ms_destroy(ms_ctx* c) {
   if (!c) return;
   if (c->stream || true) cudaStreamSynchronize(c->stream);
   ms_release_extra(c);
-  for (int b = 0; b < 2; ++b) dev_free(c->hook, c->buf[b]);
+  for (int b = 0; b < 2; ++b) {
+    dev_free(c->hook, c->buf[b]);
+    dev_free(c->hook, c->codes[b]);
+  }
   dev_free(c->hook, c->small);
   if (c->diag_host) cudaFreeHost(c->diag_host);
   delete c;
@@ -565,6 +580,8 @@ ms_status ms_set_fields(ms_ctx* c, const void* phi, const void* mu, int on_devic
   MS_CUDA(c, copy_fields(c->m, c->buf[c->cur], 0, c->m.N, phi, nullptr, on_device, c->stream));
   MS_CUDA(c, copy_fields(c->m, c->buf[c->cur], c->m.N, c->m.NM, mu, nullptr, on_device, c->stream));
   MS_CUDA(c, fill_ghosts(c->m, c->buf[c->cur], c->m.N + c->m.NM, c->stream));
+  ms_status rs = refresh_codes(c);
+  if (rs != MS_OK) return rs;
   c->step = 0;
   c->t = c->m.t0;
   ms_reset_extra(c);
@@ -696,6 +713,8 @@ ms_status ms_restore(ms_ctx* c, const void* host_buf, size_t bytes) {
     return fail(c, MS_ERR_ARG, "checkpoint does not match this context");
   MS_CUDA(c, cudaMemcpyAsync(c->buf[c->cur], (const char*)host_buf + sizeof h, c->state_bytes,
                              cudaMemcpyHostToDevice, c->stream));
+  ms_status rs = refresh_codes(c);
+  if (rs != MS_OK) return rs;
   MS_CUDA(c, cudaStreamSynchronize(c->stream));
   c->step = h.step;
   c->t = h.t;

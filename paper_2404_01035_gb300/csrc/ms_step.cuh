@@ -9,13 +9,17 @@
 // CTA = TX x TY cells of one xy tile, marching over `zchunk` planes in z.
 // One elected thread loads each halo'ed plane of all NF fields with a single
 // 4-D TMA box {TX + 2H, TY + 2, 1, NF} into a ring of NST shared-memory stages
-// (completion on an mbarrier, bounded waits).  When a plane lands, the CTA
-// computes per cell of the plane (with halo) the phase-presence bits and the
-// cell mobility M = sum h D chi once; the stencil of a cell then ORs 19 (3-D)
-// or 9 (2-D) presence bytes, which lets the bulk shortcut and the pair skip
-// work without touching every phase value.  Outputs are written with plain
-// coalesced stores, boundary cells also writing their ghost images, so no
-// separate halo kernel runs between steps.
+// (completion on an mbarrier, bounded waits).  When a plane lands, each warp
+// classifies whole rows of it: per cell a presence code (which phases are
+// non-zero, and whether the cell is exactly a pure phase), per row a flag
+// saying "every cell of this halo'ed row is the same pure phase".  A warp whose
+// 3 x 3 neighbouring rows (3 rows x 3 planes in 3-D) all carry the same flag
+// is in bulk: phi is unchanged there bit for bit and mu follows a constant-
+// mobility diffusion update, so it skips the interface arithmetic entirely.
+// Other warps run the full cell update with the per-cell phase mask (absent
+// pairs are skipped exactly).  Outputs are written with coalesced stores;
+// boundary cells also write their ghost images, so no halo kernel runs
+// between steps.
 #pragma once
 
 #include "ms_cell.cuh"
@@ -33,19 +37,27 @@ struct StepShape {
   static constexpr int H = Halo<Real>::H;
   static constexpr int SX = TX + 2 * H;
   static constexpr int SY = TY + 2;
-  static constexpr int NT = TX * TY;
-  static constexpr int NST = DIM == 3 ? 6 : 1;          // ring stages
-  static constexpr int NAUX = DIM == 3 ? 3 : 1;         // preprocessed planes
-  static constexpr int AX = TX + 2, AY = TY + 2;       // aux plane extents
+  static constexpr int NT = TX * TY;                    // consumer threads (one per cell)
+  static constexpr int NCW = NT / 32;                   // consumer warps
+  static constexpr int NTHREADS = NT + 32;              // + one producer warp
+  static constexpr int WC = TX / 32;                    // warps per row
   static constexpr int STAGE_ELEMS = NF * SY * SX;
   static constexpr int STAGE_BYTES = STAGE_ELEMS * (int)sizeof(Real);
   static constexpr int STAGE_STRIDE = (STAGE_BYTES + 127) / 128 * 128;
-  static constexpr int MOB_BYTES = NAUX * NM * NM * AX * AY * (int)sizeof(Real);
-  static constexpr int BITS_BYTES = (NAUX * AX * AY + 15) / 16 * 16;
-  static constexpr int OFF_MOB = NST * STAGE_STRIDE;
-  static constexpr int OFF_BITS = OFF_MOB + (MOB_BYTES + 15) / 16 * 16;
-  static constexpr int OFF_BAR = OFF_BITS + BITS_BYTES;
-  static constexpr int SMEM_BYTES = OFF_BAR + NST * 8 + 128;  // + alignment slack
+  // Ring depth: as many planes in flight as a shared-memory budget allows
+  // (two CTAs per SM for up to 5 fields, one for more), 4..12 stages.
+  static constexpr int RING_BUDGET = NF <= 5 ? 100 * 1024 : 190 * 1024;
+  static constexpr int NST_RAW = RING_BUDGET / STAGE_STRIDE;
+  static constexpr int NST = DIM == 3 ? (NST_RAW < 4 ? 4 : (NST_RAW > 12 ? 12 : NST_RAW)) : 1;
+  static constexpr int NFL = SY * WC;                   // row flags per plane
+  static constexpr int FLAG_BYTES = (NST * NFL + 15) / 16 * 16;   // one flag set per stage
+  static constexpr int OFF_FLAG = NST * STAGE_STRIDE;
+  static constexpr int OFF_BAR = OFF_FLAG + FLAG_BYTES;            // full[NST], empty[NST]
+  static constexpr int OFF_ABORT = OFF_BAR + 2 * NST * 8;
+  static constexpr int SMEM_BYTES = OFF_ABORT + 16 + 128;         // + alignment slack
+  static constexpr int PF = 4;                                     // planes of codes prefetched
+  static_assert(TX % 32 == 0, "a warp must cover cells of a single row");
+  static_assert(NFL <= 32, "the producer warp holds one row flag per lane");
 };
 
 // Stencil accessor over the shared-memory ring (planes k-1, k, k+1).
@@ -53,9 +65,8 @@ template <int DIM, int NP, int NM, class Real, int TX, int TY>
 struct SmemAcc {
   using Sh = StepShape<DIM, NP, NM, Real, TX, TY>;
   const Real* st[3];
-  const Real* mob[3];
-  const uint8_t* bits[3];
-  int sidx, aidx;
+  const StepArgs<Real, NP, NM>* g;
+  int sidx;
 
   __device__ __forceinline__ Real phi(int a, int dx, int dy, int dz) const {
     return st[1 + dz][a * Sh::SY * Sh::SX + sidx + dy * Sh::SX + dx];
@@ -63,29 +74,105 @@ struct SmemAcc {
   __device__ __forceinline__ Real mu(int i, int dx, int dy, int dz) const {
     return st[1 + dz][(NP + i) * Sh::SY * Sh::SX + sidx + dy * Sh::SX + dx];
   }
+  // phases present anywhere in the 19-point (3-D) / 9-point (2-D) stencil
   __device__ __forceinline__ uint32_t mask() const {
-    const uint8_t* b = bits[1] + aidx;
-    uint32_t m = b[-Sh::AX - 1] | b[-Sh::AX] | b[-Sh::AX + 1] | b[-1] | b[0] | b[1] |
-                 b[Sh::AX - 1] | b[Sh::AX] | b[Sh::AX + 1];
-    if constexpr (DIM == 3) {
-      const uint8_t* u = bits[2] + aidx;
-      const uint8_t* d = bits[0] + aidx;
-      m |= u[0] | u[-1] | u[1] | u[-Sh::AX] | u[Sh::AX];
-      m |= d[0] | d[-1] | d[1] | d[-Sh::AX] | d[Sh::AX];
+    uint32_t m = 0;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      bool any = false;
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) any = any || phi(a, dx, dy, 0) != Real(0);
+      if constexpr (DIM == 3) {
+#pragma unroll
+        for (int dz = -1; dz <= 1; dz += 2)
+          any = any || phi(a, 0, 0, dz) != Real(0) || phi(a, -1, 0, dz) != Real(0) ||
+                phi(a, 1, 0, dz) != Real(0) || phi(a, 0, -1, dz) != Real(0) ||
+                phi(a, 0, 1, dz) != Real(0);
+      }
+      m |= (any ? 1u : 0u) << a;
     }
     return m;
   }
+  // cell mobility M = sum_a h_a D^a chi^a of a neighbour, from its phi
   __device__ __forceinline__ void mobility(int dx, int dy, int dz, Real* M) const {
-    const int i = aidx + dy * Sh::AX + dx;
+    Real ph[NP];
 #pragma unroll
-    for (int k = 0; k < NM * NM; ++k) M[k] = mob[1 + dz][k * Sh::AX * Sh::AY + i];
+    for (int a = 0; a < NP; ++a) ph[a] = phi(a, dx, dy, dz);
+    cell_mobility<NP, NM>(ph, g->DX, M);
   }
 };
 
-// Write one output value of cell (x, y, z) and its ghost images.
-template <int DIM, class Real, int NP, int NM>
-__device__ __forceinline__ void store_with_ghosts(const StepArgs<Real, NP, NM>& g, Real* base,
-                                                  int x, int y, int z, Real v) {
+// Index along an axis with the boundary mapping (ghost = periodic image or
+// the adjacent interior cell).
+__device__ __forceinline__ int bc_map(int i, int n, int bc) {
+  if (i >= 0 && i < n) return i;
+  if (bc == 3) return ((i % n) + n) % n;
+  return i < 0 ? 0 : n - 1;
+}
+
+// Row flag of (row y, plane z) for the warp covering segment s: the pure
+// phase + 1 when segments s-1, s, s+1 of that row are all that pure phase.
+template <class Real, int NP, int NM>
+__device__ __forceinline__ void load_codes(const StepArgs<Real, NP, NM>& g, int s, int y, int z,
+                                           uint32_t& c3) {
+  if (s >= g.segs) {   // no cell of this warp column exists
+    c3 = 0;
+    return;
+  }
+  const int yy = bc_map(y, g.ny, g.bc[1]);
+  const int zz = bc_map(z, g.nz, g.bc[2]);
+  const uint8_t* row = g.codes_in + ((long long)zz * g.ny + yy) * g.segs;
+  const uint32_t a = row[bc_map(s - 1, g.segs, g.bc[0])];
+  const uint32_t b = row[s];
+  const uint32_t c = row[bc_map(s + 1, g.segs, g.bc[0])];
+  c3 = a | (b << 8) | (c << 16);
+}
+
+__device__ __forceinline__ uint8_t combine_codes(uint32_t c3) {
+  const uint32_t a = c3 & 0xFF, b = (c3 >> 8) & 0xFF, c = (c3 >> 16) & 0xFF;
+  return (a == b && b == c) ? (uint8_t)b : (uint8_t)0;
+}
+
+// Bulk cell (whole stencil is the pure phase l): phi unchanged, and
+// mu^{n+1} = mu + Kb_l (sum_nb mu_nb - 2d mu) - eb_l, the constant-mobility
+// form of the mu update with M = D^l chi^l, chi = chi^l and dh = 0.
+template <int DIM, int NP, int NM, class Real, class Acc>
+__device__ __forceinline__ void bulk_cell(const Acc& A, const StepArgs<Real, NP, NM>& g, int l,
+                                          Real* pn, Real* mn) {
+#pragma unroll
+  for (int a = 0; a < NP; ++a) pn[a] = a == l ? Real(1) : Real(0);
+  Real L[NM], mc[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    mc[i] = A.mu(i, 0, 0, 0);
+    Real s = (A.mu(i, -1, 0, 0) + A.mu(i, 1, 0, 0)) + (A.mu(i, 0, -1, 0) + A.mu(i, 0, 1, 0));
+    if constexpr (DIM == 3) s += A.mu(i, 0, 0, -1) + A.mu(i, 0, 0, 1);
+    L[i] = s - Real(2 * DIM) * mc[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    Real d = mc[i] - g.eb[l][i];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) d += g.Kb[l][i * NM + j] * L[j];
+    mn[i] = d;
+  }
+}
+
+// Store the NF outputs of cell (x, y, z), plus ghost images on the boundary.
+template <int DIM, int NP, int NM, class Real>
+__device__ __forceinline__ void store_cell(const StepArgs<Real, NP, NM>& g, int x, int y, int z,
+                                           const Real* pn, const Real* mn) {
+  const long long plane = (long long)g.nyp * g.pitch;
+  Real* base = g.out + (long long)(z + g.zoff) * plane + (long long)(y + 1) * g.pitch + x + g.xoff;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) base[a * g.fstride] = pn[a];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) base[(NP + i) * g.fstride] = mn[i];
+  const bool edge = x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 ||
+                    (DIM == 3 && (z == 0 || z == g.nz - 1));
+  if (!edge) return;
   int xs[3], ys[3], zs[3];
   int nxs = 1, nys = 1, nzs = 1;
   xs[0] = x;
@@ -99,156 +186,225 @@ __device__ __forceinline__ void store_with_ghosts(const StepArgs<Real, NP, NM>& 
     if (z == 0) zs[nzs++] = g.bc[2] == 3 ? g.nz : -1;
     if (z == g.nz - 1) zs[nzs++] = g.bc[2] == 3 ? -1 : g.nz;
   }
-  const long long plane = (long long)g.nyp * g.pitch;
-  base[(long long)(z + g.zoff) * plane + (long long)(y + 1) * g.pitch + x + g.xoff] = v;
-  if (nxs == 1 && nys == 1 && nzs == 1) return;
   for (int iz = 0; iz < nzs; ++iz)
     for (int iy = 0; iy < nys; ++iy)
       for (int ix = 0; ix < nxs; ++ix) {
         if (ix == 0 && iy == 0 && iz == 0) continue;
-        base[(long long)(zs[iz] + g.zoff) * plane + (long long)(ys[iy] + 1) * g.pitch + xs[ix] +
-             g.xoff] = v;
+        Real* p = g.out + (long long)(zs[iz] + g.zoff) * plane + (long long)(ys[iy] + 1) * g.pitch +
+                  xs[ix] + g.xoff;
+#pragma unroll
+        for (int a = 0; a < NP; ++a) p[a * g.fstride] = pn[a];
+#pragma unroll
+        for (int i = 0; i < NM; ++i) p[(NP + i) * g.fstride] = mn[i];
       }
 }
 
+// Minimum CTAs per SM the register allocation must allow: two for the
+// few-phase kernels of up to 256 consumer threads, else one.
+template <int NP, int NT>
+struct MinBlocks {
+  static constexpr int value = (NP <= 4 && NT <= 256) ? 2 : 1;
+};
+
 template <int DIM, int NP, int NM, class Real, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_gp_step(const __grid_constant__ CUtensorMap tm,
-                                                    const __grid_constant__ StepArgs<Real, NP, NM> g) {
+__global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
+    k_gp_step(const __grid_constant__ CUtensorMap tm, const __grid_constant__ StepArgs<Real, NP, NM> g) {
   using Sh = StepShape<DIM, NP, NM, Real, TX, TY>;
   constexpr int NST = Sh::NST;
-  constexpr int NAUX = Sh::NAUX;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  Real* mobs = reinterpret_cast<Real*>(smem + Sh::OFF_MOB);
-  uint8_t* bits = smem + Sh::OFF_BITS;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR);
+  uint8_t* rowflag = smem + Sh::OFF_FLAG;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR);
+  uint64_t* empty = full + NST;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + Sh::OFF_ABORT);
   auto stage = [&](int s) { return reinterpret_cast<Real*>(smem + s * Sh::STAGE_STRIDE); };
 
   const int tid = threadIdx.x;
-  const int tx = tid % TX, ty = tid / TX;
+  const int lane = tid & 31;
   const int tiles_x = (g.nx + TX - 1) / TX;
   const int x0 = (blockIdx.x % tiles_x) * TX;
   const int y0 = (blockIdx.x / tiles_x) * TY;
   const int zb = DIM == 3 ? blockIdx.y * g.zchunk : 0;
   const int ze = DIM == 3 ? min(g.nz, zb + g.zchunk) : 1;
-  const int nplanes = DIM == 3 ? (ze - zb + 2) : 1;
-  const int bx = x0 + g.xoff - Sh::H;   // TMA box origin (16-byte aligned)
+  const int nplanes = DIM == 3 ? (ze - zb + 2) : 1;   // ring entries j <-> plane zb - 1 + j
+  const int nk = DIM == 3 ? (ze - zb) : 1;             // planes computed
 
   if (tid == 0) {
-    for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], Sh::NCW);
+    }
+    *abort_flag = 0;
     mbar_fence_init();
   }
-  __syncthreads();
+  __syncthreads();   // the only CTA-wide barrier: roles split below
 
-  int issued = 0;   // planes issued (meaningful in thread 0)
-  auto issue = [&](int j) {
-    const int s = j % NST;
-    mbar_expect_tx(&bars[s], Sh::STAGE_BYTES);
-    const int zc = DIM == 3 ? (zb - 1 + j + g.zoff) : 0;
-    tma_load_4d(stage(s), &tm, &bars[s], bx, y0, zc, 0);
-  };
-  if (tid == 0) {
-    prefetch_tensormap(&tm);
-    const int n0 = nplanes < NST ? nplanes : NST;
-    for (int j = 0; j < n0; ++j) issue(j);
-    issued = n0;
-  }
-
-  // presence bits and cell mobility of every (halo'ed) cell of plane j
-  auto preprocess = [&](int j) {
-    const Real* st = stage(j % NST);
-    const int slot = j % NAUX;
-    for (int i = tid; i < Sh::AX * Sh::AY; i += Sh::NT) {
-      const int ay = i / Sh::AX, ax = i % Sh::AX;
-      const int si = ay * Sh::SX + ax + Sh::H - 1;
-      Real ph[NP];
-      uint32_t b = 0;
+  if (tid >= Sh::NT) {
+    // ---------------- producer warp: TMA loads + row flags of every entry
+    const int bx = x0 + g.xoff - Sh::H;   // TMA box origin (16-byte aligned)
+    const int f_ay = lane / Sh::WC, f_wc = lane % Sh::WC;
+    const int f_seg = (x0 >> 5) + f_wc;
+    const bool fl = lane < Sh::NFL;
+    auto plane_of = [&](int j) { return DIM == 3 ? zb - 1 + j : 0; };
+    uint32_t pre[Sh::PF];
 #pragma unroll
-      for (int a = 0; a < NP; ++a) {
-        ph[a] = st[a * Sh::SY * Sh::SX + si];
-        b |= (ph[a] != Real(0) ? 1u : 0u) << a;
-      }
-      bits[slot * Sh::AX * Sh::AY + i] = (uint8_t)b;
-      Real M[NM * NM];
-      cell_mobility<NP, NM>(ph, g.DX, M);
-#pragma unroll
-      for (int k = 0; k < NM * NM; ++k)
-        mobs[(slot * NM * NM + k) * Sh::AX * Sh::AY + i] = M[k];
+    for (int i = 0; i < Sh::PF; ++i) {
+      pre[i] = 0;
+      if (fl && i < nplanes) load_codes(g, f_seg, y0 - 1 + f_ay, plane_of(i), pre[i]);
     }
-  };
-
-  // Abort path after a timed-out wait: wait (bounded) for the copies still in
-  // flight so that no TMA writes into freed shared memory, then leave.
-  auto abort_cta = [&]() {
-    if (tid == 0) {
+    if (lane == 0) prefetch_tensormap(&tm);
+    int issued = 0;
+    bool ok = true;
+    for (int j = 0; j < nplanes; ++j) {
+      const int s = j % NST;
+      if (j >= NST) ok = ok && mbar_wait_bounded(&empty[s], ((j / NST) - 1) & 1);
+      ok = ok && *abort_flag == 0;
+      if (__any_sync(0xffffffffu, !ok)) break;
+      uint32_t c3 = 0;
+#pragma unroll
+      for (int i = 0; i < Sh::PF; ++i)
+        if (i == j % Sh::PF) c3 = pre[i];
+      if (fl) {
+        rowflag[s * Sh::NFL + lane] = combine_codes(c3);
+        if (j + Sh::PF < nplanes) {
+          uint32_t nc;
+          load_codes(g, f_seg, y0 - 1 + f_ay, plane_of(j + Sh::PF), nc);
+#pragma unroll
+          for (int i = 0; i < Sh::PF; ++i)
+            if (i == j % Sh::PF) pre[i] = nc;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();
+        mbar_expect_tx(&full[s], Sh::STAGE_BYTES);   // arrive (release) + expected bytes
+        const int zc = DIM == 3 ? (zb - 1 + j + g.zoff) : 0;
+        tma_load_4d(stage(s), &tm, &full[s], bx, y0, zc, 0);
+      }
+      issued = j + 1;
+    }
+    if (!ok && lane == 0) {
+      // abort: record it, then wait (bounded) for the copies still in flight
+      // so that no TMA writes into shared memory after the CTA has exited
       atomicOr(g.status, kStatusTimeout);
+      *abort_flag = 1;
       for (int s = 0; s < NST; ++s) {
         if (issued <= s) continue;
-        const int j = s + ((issued - 1 - s) / NST) * NST;   // last plane issued into stage s
-        mbar_wait_bounded(&bars[s], (j / NST) & 1);
+        const int j = s + ((issued - 1 - s) / NST) * NST;
+        mbar_wait_bounded(&full[s], (j / NST) & 1);
       }
     }
-  };
-
-  bool ok = true;
-  const int first = DIM == 3 ? 2 : 1;   // planes needed before the first compute
-  for (int j = 0; j < first; ++j) {
-    ok = ok && mbar_wait_bounded(&bars[j % NST], (j / NST) & 1);
-    if (ok) preprocess(j);
+    return;
   }
-  const int nk = DIM == 3 ? (ze - zb) : 1;
+
+  // -------------------- consumer warps: one cell per thread, one plane at a time
+  const int tx = tid % TX, ty = tid / TX;
+  const int wc = tx >> 5;                     // warp column within the row
+  const int seg = (x0 >> 5) + wc;             // this warp's 32-cell segment
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < g.nx && y < g.ny;
+  SmemAcc<DIM, NP, NM, Real, TX, TY> acc;
+  acc.g = &g;
+  acc.sidx = (ty + 1) * Sh::SX + tx + Sh::H;
+  bool ok = true;
+  if constexpr (DIM == 3) ok = mbar_wait_bounded(&full[0], 0) && mbar_wait_bounded(&full[1], 0);
+  int s0 = 0, s1 = DIM == 3 ? 1 : 0, s2 = DIM == 3 ? 2 % NST : 0;
+  uint32_t par2 = DIM == 3 ? (2 / NST) & 1 : 0;
   for (int k = 0; k < nk; ++k) {
-    if constexpr (DIM == 3) {
-      const int j = k + 2;
-      ok = ok && mbar_wait_bounded(&bars[j % NST], (j / NST) & 1);
-      if (ok) preprocess(j);
-    }
-    if (__syncthreads_or(!ok)) {
-      abort_cta();
+    ok = ok && mbar_wait_bounded(&full[s2], par2) && *abort_flag == 0;
+    if (!ok) {
+      if (lane == 0) {
+        atomicOr(g.status, kStatusTimeout);
+        *abort_flag = 1;
+      }
       return;
     }
     const int z = zb + k;
-    const int x = x0 + tx, y = y0 + ty;
-    SmemAcc<DIM, NP, NM, Real, TX, TY> acc;
-    if constexpr (DIM == 3) {
+    // warp-uniform bulk test over the 3 x 3 (x 3 planes) rows around row ty
+    const int flag = rowflag[s1 * Sh::NFL + (ty + 1) * Sh::WC + wc];
+    bool bulk = flag != 0;
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        acc.st[r] = stage((k + r) % NST);
-        acc.mob[r] = mobs + ((k + r) % NAUX) * NM * NM * Sh::AX * Sh::AY;
-        acc.bits[r] = bits + ((k + r) % NAUX) * Sh::AX * Sh::AY;
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        acc.st[r] = stage(0);
-        acc.mob[r] = mobs;
-        acc.bits[r] = bits;
+    for (int dr = 0; dr < 3; ++dr) {
+      bulk = bulk && rowflag[s1 * Sh::NFL + (ty + dr) * Sh::WC + wc] == flag;
+      if constexpr (DIM == 3) {
+        bulk = bulk && rowflag[s0 * Sh::NFL + (ty + dr) * Sh::WC + wc] == flag;
+        bulk = bulk && rowflag[s2 * Sh::NFL + (ty + dr) * Sh::WC + wc] == flag;
       }
     }
-    acc.sidx = (ty + 1) * Sh::SX + tx + Sh::H;
-    acc.aidx = (ty + 1) * Sh::AX + tx + 1;
-    if (x < g.nx && y < g.ny) {
-      DiffPrm<Real, StepArgs<Real, NP, NM>::P> dp;
-      dp.mob = g.mob;
-#pragma unroll
-      for (int p = 0; p < StepArgs<Real, NP, NM>::P; ++p) dp.delta[p] = g.delta[p];
+    int code = 0;
+    if (active) {
+      acc.st[0] = stage(s0);
+      acc.st[1] = stage(s1);
+      acc.st[2] = stage(s2);
       Real pn[NP], mn[NM];
-      gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, DIM == 3 ? z : y, pn, mn);
+      if (bulk) {
+        bulk_cell<DIM, NP, NM, Real>(acc, g, flag - 1, pn, mn);
+        code = flag;
+      } else {
+        DiffPrm<Real, StepArgs<Real, NP, NM>::P> dp;
+        dp.mob = g.mob;
 #pragma unroll
-      for (int a = 0; a < NP; ++a) store_with_ghosts<DIM>(g, g.out + a * g.fstride, x, y, z, pn[a]);
+        for (int p = 0; p < StepArgs<Real, NP, NM>::P; ++p) dp.delta[p] = g.delta[p];
+        gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, DIM == 3 ? z : y, pn, mn);
+        uint32_t nzm = 0, one = 0;
 #pragma unroll
-      for (int i = 0; i < NM; ++i)
-        store_with_ghosts<DIM>(g, g.out + (NP + i) * g.fstride, x, y, z, mn[i]);
+        for (int a = 0; a < NP; ++a) {
+          nzm |= (pn[a] != Real(0) ? 1u : 0u) << a;
+          one |= (pn[a] == Real(1) ? 1u : 0u) << a;
+        }
+        code = (__popc(nzm) == 1 && nzm == one) ? __ffs(nzm) : 0;
+      }
+      store_cell<DIM>(g, x, y, z, pn, mn);
+    }
+    // segment code of the output row: lane 0 is active whenever any lane is
+    const int ref = __shfl_sync(0xffffffffu, code, 0);
+    const bool same = __all_sync(0xffffffffu, !active || code == ref);
+    if (lane == 0) {
+      if (active) g.codes_out[((long long)z * g.ny + y) * g.segs + seg] = same ? (uint8_t)ref : (uint8_t)0;
+      if constexpr (DIM == 3) mbar_arrive(&empty[s0]);   // this warp is done with entry k
     }
     if constexpr (DIM == 3) {
-      __syncthreads();   // everyone is done with plane k's stage
-      if (tid == 0 && k + NST < nplanes) {
-        issue(k + NST);
-        issued = k + NST + 1;
+      s0 = s1;
+      s1 = s2;
+      if (++s2 == NST) {
+        s2 = 0;
+        par2 ^= 1u;
       }
     }
   }
+}
+
+// Segment codes of a whole state (used when a state is loaded from outside):
+// one warp per 32-cell segment of one row.
+template <int DIM, int NP, class Real>
+__global__ void __launch_bounds__(256) k_codes(const Real* __restrict__ st, int nx, int ny, int nz,
+                                               int pitch, int nyp, long long fstride, int xoff,
+                                               int zoff, int segs, uint8_t* __restrict__ codes) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long nseg = (long long)segs * ny * nz;
+  if (w >= nseg) return;
+  const int s = (int)(w % segs);
+  const int y = (int)((w / segs) % ny);
+  const int z = (int)(w / ((long long)segs * ny));
+  const int x = s * 32 + lane;
+  const bool active = x < nx;
+  int code = 0;
+  if (active) {
+    const long long i0 = (long long)(z + zoff) * nyp * pitch + (long long)(y + 1) * pitch + x + xoff;
+    uint32_t nzm = 0, one = 0;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const Real v = st[a * fstride + i0];
+      nzm |= (v != Real(0) ? 1u : 0u) << a;
+      one |= (v == Real(1) ? 1u : 0u) << a;
+    }
+    code = (__popc(nzm) == 1 && nzm == one) ? __ffs(nzm) : 0;
+  }
+  const int ref = __shfl_sync(0xffffffffu, code, 0);
+  const bool same = __all_sync(0xffffffffu, !active || code == ref);
+  if (lane == 0) codes[w] = same ? (uint8_t)ref : (uint8_t)0;
 }
 
 }  // namespace msgb

