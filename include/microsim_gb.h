@@ -194,6 +194,37 @@ ms_status ms_tile_shape(const ms_ctx* ctx, int tile, int* tx, int* ty);
 ms_status ms_tune(ms_ctx* ctx, const char* cache_path, int steps_per_trial,
                   double* best_ms_per_step);
 
+/* Allocation-free diagnostics (the paper has no counterpart; this is a
+ * library service).  For callers that cannot allocate device memory while
+ * they run -- a host application that gives this library a fixed memory
+ * budget, code being recorded into a CUDA graph by stream capture (where a
+ * cudaMalloc would break the capture), or a latency-bound loop that must not
+ * stall on the allocator.  It computes the same quantities as ms_diag
+ * (out[0..K-2] solute masses, out[K-1] max |sum phi - 1|, out[K] min phi,
+ * out[K+1] max phi, out[K+2] non-finite count, out[K+3] mu-diffusion number)
+ * for a state the caller holds: phi_dev / mu_dev are dense device arrays
+ * [field][z][y][x] in params->dtype, t the physical time of that state, and
+ * out_dev a device buffer of at least K+4 doubles written on `stream`
+ * (asynchronously; synchronise the stream before reading it).
+ *   - No device memory is allocated or freed: the per-block reduction scratch
+ *     is a fixed array in the library's device image (512 KiB per GPU that
+ *     loads the library, held until the process exits).
+ *   - Size limit: grids of at most 268,435,456 cells (8192 blocks of 32,768
+ *     cells); larger grids return MS_ERR_BOUNDS with a message.
+ *   - The first call on each device resolves the scratch array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call before starting any stream capture on that device.
+ *   - All calls share the one scratch array, so calls whose kernels overlap on
+ *     the GPU (different streams without ordering) race and may return wrong
+ *     values; order them on one stream or with events.
+ *   - Errors: MS_ERR_ARG for bad inputs, MS_ERR_UNSUPPORTED for a
+ *     (dim, N, K) without compiled diagnostics, MS_ERR_BOUNDS as above,
+ *     MS_ERR_CUDA for a failed launch; text via ms_last_error(NULL). */
+ms_status ms_diag_noalloc(const ms_grid* grid, int n_phases, int n_components,
+                          const ms_params* params, double t, const void* phi_dev,
+                          const void* mu_dev, double* out_dev, void* stream);
+#define MS_DIAG_NOALLOC_LEN(K) ((K) + 4)
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ EXPORTS = [
     "ms_create", "ms_destroy", "ms_last_error", "ms_update_params", "ms_set_fields",
     "ms_get_fields", "ms_fields", "ms_step", "ms_diag", "ms_set_diag_every", "ms_sync",
     "ms_time", "ms_checkpoint_bytes", "ms_checkpoint", "ms_restore", "ms_set_launch",
-    "ms_tile_count", "ms_tile_shape", "ms_tune",
+    "ms_tile_count", "ms_tile_shape", "ms_tune", "ms_diag_noalloc",
 ]
 
 
@@ -103,6 +103,8 @@ def lib(build_if_missing: bool = True):
         L.ms_tile_shape.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]
         L.ms_tune.argtypes = [vp, ctypes.c_char_p, ctypes.c_int, dp]
+        L.ms_diag_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(Params), ctypes.c_double, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("ms_destroy", "ms_last_error", "ms_checkpoint_bytes"):
                 getattr(L, name).restype = ctypes.c_int
