@@ -194,6 +194,35 @@ ms_status ms_tile_shape(const ms_ctx* ctx, int tile, int* tx, int* ty);
 ms_status ms_tune(ms_ctx* ctx, const char* cache_path, int steps_per_trial,
                   double* best_ms_per_step);
 
+/* ---- Discrete adjoint (reverse mode through the explicit steps) ----------
+ * Gradients of a loss L on the state after n steps with respect to the
+ * initial fields and the parameters theta = (delta_ab for each pair a < b in
+ * row-major order, the phase mobility 1/tau, the entries D^a_ij).  The
+ * gradient is that of the discrete map the library steps (Eq. phi_eqn and
+ * Eq. Mu_explicit_temperature as discretised by ms_step), not of the PDE.
+ *
+ * ms_enable_checkpoints(ctx, every): from the current step on, ms_step stores
+ * a device snapshot of the state every `every` steps (0 turns recording off).
+ * Memory: one state per snapshot plus `every` states during ms_grad.
+ * Returns MS_ERR_UNSUPPORTED if no adjoint kernel is compiled for the
+ * context's (dim, N, K, dtype).  Resets on ms_set_fields / ms_restore. */
+ms_status ms_enable_checkpoints(ms_ctx* ctx, int every);
+
+/* Number of parameters in theta: N(N-1)/2 + 1 + N (K-1)^2. */
+int ms_grad_param_count(const ms_ctx* ctx);
+
+/* Reverse pass over the steps run since checkpoints were enabled.
+ * dphi_T / dmu_T: dense device arrays dL/dphi and dL/dmu of the current
+ * (final) state, layout as ms_set_fields, context dtype; dmu_T may be NULL
+ * (zero).  Outputs (each may be NULL): dparams, host array of
+ * ms_grad_param_count doubles (dL/dtheta, accumulated in FP64); dphi0 /
+ * dmu0, dense device arrays dL/dphi and dL/dmu of the state at the first
+ * recorded step.  Synchronous.  Segments between snapshots are recomputed with
+ * the forward kernel; per reverse step one adjoint kernel runs (deterministic
+ * gather, no atomics).  The current state is left unchanged. */
+ms_status ms_grad(ms_ctx* ctx, const void* dphi_T, const void* dmu_T, double* dparams,
+                  void* dphi0, void* dmu0);
+
 /* Allocation-free diagnostics (the paper has no counterpart; this is a
  * library service).  For callers that cannot allocate device memory while
  * they run -- a host application that gives this library a fixed memory

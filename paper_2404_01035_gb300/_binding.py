@@ -27,6 +27,7 @@ EXPORTS = [
     "ms_get_fields", "ms_fields", "ms_step", "ms_diag", "ms_set_diag_every", "ms_sync",
     "ms_time", "ms_checkpoint_bytes", "ms_checkpoint", "ms_restore", "ms_set_launch",
     "ms_tile_count", "ms_tile_shape", "ms_tune", "ms_diag_noalloc",
+    "ms_enable_checkpoints", "ms_grad_param_count", "ms_grad",
 ]
 
 
@@ -103,6 +104,9 @@ def lib(build_if_missing: bool = True):
         L.ms_tile_shape.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]
         L.ms_tune.argtypes = [vp, ctypes.c_char_p, ctypes.c_int, dp]
+        L.ms_enable_checkpoints.argtypes = [vp, ctypes.c_int]
+        L.ms_grad_param_count.argtypes = [vp]
+        L.ms_grad.argtypes = [vp, vp, vp, dp, vp, vp]
         L.ms_diag_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(Params), ctypes.c_double, vp, vp, vp, vp]
         for name in EXPORTS:

@@ -25,6 +25,18 @@
 
 namespace msgb {
 
+// Dual-number scalars take neither the bulk shortcut nor the pair skip: both
+// are exact for values but would drop derivatives (a perturbation of an absent
+// phase, or of a bulk cell, has a non-zero first-order effect).
+template <class S>
+struct IsDual {
+  static constexpr bool value = false;
+};
+template <class R, int W>
+struct IsDual<Dual<R, W>> {
+  static constexpr bool value = true;
+};
+
 template <class S, int P>
 struct DiffPrm {
   S mob;         // phase-field mobility 1/tau
@@ -127,7 +139,7 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
   const uint32_t mask = A.mask();
   const int npresent = __popc(mask);
   bool bulk = false;
-  if (npresent == 1) {
+  if (!IsDual<S>::value && npresent == 1) {
     const int l = __ffs(mask) - 1;
 #pragma unroll
     for (int a = 0; a < NP; ++a)

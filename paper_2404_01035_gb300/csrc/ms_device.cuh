@@ -132,6 +132,15 @@ __device__ __forceinline__ Dual<R, W> operator*(R s, const Dual<R, W>& a) {
 template <class R, int W>
 __device__ __forceinline__ Dual<R, W> operator*(const Dual<R, W>& a, R s) { return s * a; }
 template <class R, int W>
+__device__ __forceinline__ Dual<R, W> operator/(R s, const Dual<R, W>& b) {
+  Dual<R, W> r;
+  const R inv = R(1) / b.v;
+  r.v = s * inv;
+#pragma unroll
+  for (int i = 0; i < W; ++i) r.d[i] = -r.v * b.d[i] * inv;
+  return r;
+}
+template <class R, int W>
 __device__ __forceinline__ Dual<R, W> operator+(const Dual<R, W>& a, R s) {
   Dual<R, W> r = a;
   r.v += s;

@@ -192,6 +192,33 @@ class Simulation:
         params = make_params(self.prob, self.dtype, keep, **override)
         self._c(lib().ms_update_params(self.h, ctypes.byref(params)))
 
+    # --------------------------------------------------------------- adjoint
+    def enable_checkpoints(self, every: int):
+        self._c(lib().ms_enable_checkpoints(self.h, int(every)))
+
+    def param_count(self) -> int:
+        return lib().ms_grad_param_count(self.h)
+
+    def grad(self, dphi_T, dmu_T=None, want_fields: bool = True):
+        """Reverse pass; dphi_T / dmu_T are torch CUDA tensors shaped like the fields.
+
+        Returns (dparams [numpy, FP64], dphi0, dmu0 [torch tensors or None]).
+        dparams = [dL/d delta_ab for pairs a < b..., dL/d(1/tau), dL/dD^a_ij ...].
+        """
+        torch = self._torch
+        dphi_T = dphi_T.to(self.torch_dtype).contiguous()
+        dmu_T = None if dmu_T is None else dmu_T.to(self.torch_dtype).contiguous()
+        out = np.zeros(self.param_count())
+        dphi0 = torch.empty_like(dphi_T) if want_fields else None
+        dmu0 = (torch.empty((self.NM,) + self.shape, dtype=self.torch_dtype, device="cuda")
+                if want_fields else None)
+        self._c(lib().ms_grad(self.h, ctypes.c_void_p(dphi_T.data_ptr()),
+                              ctypes.c_void_p(dmu_T.data_ptr()) if dmu_T is not None else None,
+                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              ctypes.c_void_p(dphi0.data_ptr()) if dphi0 is not None else None,
+                              ctypes.c_void_p(dmu0.data_ptr()) if dmu0 is not None else None))
+        return out, dphi0, dmu0
+
     # ------------------------------------------------------------ checkpoints
     def checkpoint(self) -> bytes:
         n = lib().ms_checkpoint_bytes(self.h)
