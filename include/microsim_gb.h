@@ -223,6 +223,31 @@ int ms_grad_param_count(const ms_ctx* ctx);
 ms_status ms_grad(ms_ctx* ctx, const void* dphi_T, const void* dmu_T, double* dparams,
                   void* dphi0, void* dmu0);
 
+/* ---- Batched form: many independent 2-D simulations, one persistent launch -
+ * ms_batch_create: nsims simulations with their own grid (grids[i]) and
+ * parameters (params[i]); all share n_phases, n_components and dtype.  This
+ * build compiles the batched kernel for 2-D, N = 2, K = 2, FP32 and
+ * time-independent temperature (G V = 0); other combinations return
+ * MS_ERR_UNSUPPORTED.  Each simulation keeps its own ping-pong state and
+ * its own TMA descriptor in device memory.
+ * ms_batch_step(b, n): advances every simulation n steps in ONE cooperative,
+ * persistent kernel launch that walks a (simulation, tile) work list with a
+ * bounded-spin grid barrier between steps; the launch is captured once into a
+ * CUDA graph per (n, buffer parity) and replayed.  Asynchronous; a barrier
+ * timeout is reported by ms_batch_sync as MS_ERR_TIMEOUT.
+ * Field I/O per simulation as in ms_set_fields / ms_get_fields (synchronous
+ * for host buffers). */
+ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_components,
+                          const ms_params* params, void* stream, const ms_allocator* alloc,
+                          ms_batch** out);
+void ms_batch_destroy(ms_batch* b);
+const char* ms_batch_last_error(const ms_batch* b);
+ms_status ms_batch_set_fields(ms_batch* b, int sim, const void* phi, const void* mu, int on_device);
+ms_status ms_batch_get_fields(ms_batch* b, int sim, void* phi, void* mu, int on_device);
+ms_status ms_batch_step(ms_batch* b, int64_t n);
+ms_status ms_batch_sync(ms_batch* b);
+int64_t ms_batch_cells(const ms_batch* b);   /* total cells over all simulations */
+
 /* Allocation-free diagnostics (the paper has no counterpart; this is a
  * library service).  For callers that cannot allocate device memory while
  * they run -- a host application that gives this library a fixed memory

@@ -28,6 +28,8 @@ EXPORTS = [
     "ms_time", "ms_checkpoint_bytes", "ms_checkpoint", "ms_restore", "ms_set_launch",
     "ms_tile_count", "ms_tile_shape", "ms_tune", "ms_diag_noalloc",
     "ms_enable_checkpoints", "ms_grad_param_count", "ms_grad",
+    "ms_batch_create", "ms_batch_destroy", "ms_batch_last_error", "ms_batch_set_fields",
+    "ms_batch_get_fields", "ms_batch_step", "ms_batch_sync", "ms_batch_cells",
 ]
 
 
@@ -104,13 +106,27 @@ def lib(build_if_missing: bool = True):
         L.ms_tile_shape.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]
         L.ms_tune.argtypes = [vp, ctypes.c_char_p, ctypes.c_int, dp]
+        L.ms_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(Params), vp, ctypes.POINTER(Allocator),
+                                      ctypes.POINTER(vp)]
+        L.ms_batch_destroy.argtypes = [vp]
+        L.ms_batch_destroy.restype = None
+        L.ms_batch_last_error.argtypes = [vp]
+        L.ms_batch_last_error.restype = ctypes.c_char_p
+        L.ms_batch_set_fields.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
+        L.ms_batch_get_fields.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int]
+        L.ms_batch_step.argtypes = [vp, i64]
+        L.ms_batch_sync.argtypes = [vp]
+        L.ms_batch_cells.argtypes = [vp]
+        L.ms_batch_cells.restype = ctypes.c_int64
         L.ms_enable_checkpoints.argtypes = [vp, ctypes.c_int]
         L.ms_grad_param_count.argtypes = [vp]
         L.ms_grad.argtypes = [vp, vp, vp, dp, vp, vp]
         L.ms_diag_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(Params), ctypes.c_double, vp, vp, vp, vp]
         for name in EXPORTS:
-            if name not in ("ms_destroy", "ms_last_error", "ms_checkpoint_bytes"):
+            if name not in ("ms_destroy", "ms_last_error", "ms_checkpoint_bytes", "ms_batch_destroy",
+                            "ms_batch_last_error", "ms_batch_cells"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return _lib

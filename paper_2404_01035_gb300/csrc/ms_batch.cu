@@ -1,0 +1,497 @@
+// Batched form: hundreds of independent 2-D simulations of different sizes
+// and parameters advanced by ONE persistent, cooperative kernel launch
+// (captured once into a CUDA graph and replayed).
+//
+// Work list: every (simulation, 32 x TY tile) pair of every step.  Each CTA
+// walks the list with a fixed stride; a producer warp TMA-loads the next
+// items' halo'ed tiles (each simulation has its own tensor map, kept in global
+// memory) into a shared-memory ring while the consumer warps compute the
+// current one with the same cell update as the single-simulation kernel.  A
+// grid-wide barrier (atomic counter, bounded spin on %globaltimer) separates
+// time steps, because a step reads the ghost cells its neighbours wrote in the
+// previous step.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/microsim_gb.h"
+#include "ms_launch.cuh"
+#include "ms_rt.h"
+
+namespace msgb {
+
+ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params* p, HostModel& m);
+
+// Per-simulation constants for one buffer parity (out / codes point at the
+// destination of a step that reads the other buffer).
+template <class Real, int NP, int NM>
+struct alignas(64) BatchSim {
+  StepArgs<Real, NP, NM> g[2];   // [parity of the source buffer]
+};
+
+struct BatchItem {
+  int sim, tile;
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int target) {
+  __threadfence();
+  fence_proxy_async_global();   // generic stores of this step -> TMA loads of the next
+  atomicAdd(counter, 1u);
+  const unsigned long long t0 = globaltimer();
+  while (atomicAdd(counter, 0u) < target) {
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    __nanosleep(64);
+  }
+  __threadfence();
+  fence_proxy_async_global();
+  return true;
+}
+
+template <int NP, int NM, class Real, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY + 32, 1)
+    k_batch(const BatchSim<Real, NP, NM>* __restrict__ sims, const CUtensorMap* __restrict__ maps,
+            const BatchItem* __restrict__ items, int nitems, int nsteps, int parity0,
+            unsigned int* barrier, int* status) {
+  using Sh = StepShape<2, NP, NM, Real, TX, TY>;
+  constexpr int NST = 8;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint8_t* rowflag = smem + NST * Sh::STAGE_STRIDE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * Sh::STAGE_STRIDE + ((NST * Sh::NFL + 15) / 16) * 16);
+  uint64_t* empty = full + NST;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NST);
+  auto stage = [&](int s) { return reinterpret_cast<Real*>(smem + s * Sh::STAGE_STRIDE); };
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], Sh::NCW);
+    }
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int my_items = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  long long seq = 0;      // ring position of this CTA's item sequence (continues across steps)
+  long long issued = 0;   // loads issued (producer lane 0)
+  for (int step = 0; step < nsteps; ++step) {
+    const int par = (parity0 + step) & 1;
+    if (tid >= Sh::NT) {
+      // producer warp
+      const int f_ay = lane / Sh::WC, f_wc = lane % Sh::WC;
+      bool ok = true;
+      for (int k = 0; k < my_items; ++k) {
+        const long long q = seq + k;
+        const int s = (int)(q % NST);
+        if (q >= NST) ok = ok && mbar_wait_bounded(&empty[s], (uint32_t)(((q / NST) - 1) & 1));
+        ok = ok && *abort_flag == 0;
+        if (__any_sync(0xffffffffu, !ok)) {
+          if (lane == 0) {
+            atomicOr(status, kStatusTimeout);
+            *abort_flag = 1;
+          }
+          break;
+        }
+        const BatchItem it = items[blockIdx.x + (long long)k * gridDim.x];
+        const StepArgs<Real, NP, NM>& g = sims[it.sim].g[par];
+        const int tiles_x = (g.nx + TX - 1) / TX;
+        const int x0 = (it.tile % tiles_x) * TX, y0 = (it.tile / tiles_x) * TY;
+        if (lane < Sh::NFL) {
+          uint32_t c3;
+          load_codes(g, (x0 >> 5) + f_wc, y0 - 1 + f_ay, 0, c3);
+          rowflag[s * Sh::NFL + lane] = combine_codes(c3);
+        }
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();
+          mbar_expect_tx(&full[s], Sh::STAGE_BYTES);
+          tma_load_4d(stage(s), &maps[2 * it.sim + par], &full[s], x0 + g.xoff - Sh::H, y0, 0, 0);
+          issued = q + 1;
+        }
+      }
+    } else {
+      // consumer warps
+      const int tx = tid % TX, ty = tid / TX, wc = tx >> 5;
+      for (int k = 0; k < my_items; ++k) {
+        const long long q = seq + k;
+        const int s = (int)(q % NST);
+        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((q / NST) & 1)) && *abort_flag == 0;
+        if (!ok) {
+          if (lane == 0) {
+            atomicOr(status, kStatusTimeout);
+            *abort_flag = 1;
+          }
+          break;
+        }
+        const BatchItem it = items[blockIdx.x + (long long)k * gridDim.x];
+        const StepArgs<Real, NP, NM>& g = sims[it.sim].g[par];
+        const int tiles_x = (g.nx + TX - 1) / TX;
+        const int x0 = (it.tile % tiles_x) * TX, y0 = (it.tile / tiles_x) * TY;
+        const int x = x0 + tx, y = y0 + ty;
+        const bool active = x < g.nx && y < g.ny;
+        const int flag = rowflag[s * Sh::NFL + (ty + 1) * Sh::WC + wc];
+        bool bulk = flag != 0;
+#pragma unroll
+        for (int dr = 0; dr < 3; ++dr) bulk = bulk && rowflag[s * Sh::NFL + (ty + dr) * Sh::WC + wc] == flag;
+        int code = 0;
+        if (active) {
+          SmemAcc<2, NP, NM, Real, TX, TY> acc;
+          acc.st[0] = acc.st[1] = acc.st[2] = stage(s);
+          acc.g = &g;
+          acc.sidx = (ty + 1) * Sh::SX + tx + Sh::H;
+          Real pn[NP], mn[NM];
+          if (bulk) {
+            bulk_cell<2, NP, NM, Real>(acc, g, flag - 1, pn, mn);
+            code = flag;
+          } else {
+            DiffPrm<Real, StepArgs<Real, NP, NM>::P> dp;
+            dp.mob = g.mob;
+#pragma unroll
+            for (int p = 0; p < StepArgs<Real, NP, NM>::P; ++p) dp.delta[p] = g.delta[p];
+            gp_cell<2, NP, NM, Real, Real>(acc, g, dp, y, pn, mn);
+            uint32_t nzm = 0, one = 0;
+#pragma unroll
+            for (int a = 0; a < NP; ++a) {
+              nzm |= (pn[a] != Real(0) ? 1u : 0u) << a;
+              one |= (pn[a] == Real(1) ? 1u : 0u) << a;
+            }
+            code = (__popc(nzm) == 1 && nzm == one) ? __ffs(nzm) : 0;
+          }
+          store_cell<2>(g, x, y, 0, pn, mn);
+        }
+        const int ref = __shfl_sync(0xffffffffu, code, 0);
+        const bool same = __all_sync(0xffffffffu, !active || code == ref);
+        if (lane == 0) {
+          if (active) g.codes_out[(long long)y * g.segs + (x0 >> 5) + wc] = same ? (uint8_t)ref : (uint8_t)0;
+          mbar_arrive(&empty[s]);
+        }
+      }
+    }
+    seq += my_items;
+    __syncthreads();
+    // grid-wide barrier between steps
+    if (tid == 0) {
+      if (*abort_flag || !grid_barrier(barrier, (unsigned int)(step + 1) * gridDim.x)) {
+        atomicOr(status, kStatusTimeout);
+        *abort_flag = 1;
+      }
+    }
+    __syncthreads();
+    if (*abort_flag) break;
+  }
+  // drain: every issued load was consumed in a complete run; after an abort,
+  // wait (bounded) for the loads still in flight before the CTA exits
+  if (*abort_flag && tid == Sh::NT) {
+    for (int s = 0; s < NST; ++s) {
+      if (issued <= s) continue;
+      const long long q = s + ((issued - 1 - s) / NST) * NST;   // last load issued into stage s
+      mbar_wait_bounded(&full[s], (uint32_t)((q / NST) & 1));
+    }
+  }
+}
+
+template <int NP, int NM, class Real, int TX, int TY>
+struct BatchShape {
+  using Sh = StepShape<2, NP, NM, Real, TX, TY>;
+  static constexpr int NST = 8;
+  static constexpr int SMEM = NST * Sh::STAGE_STRIDE + ((NST * Sh::NFL + 15) / 16) * 16 + 2 * NST * 8 + 16 + 128;
+};
+
+}  // namespace msgb
+
+using namespace msgb;
+
+struct ms_batch {
+  int nsims = 0, N = 0, NM = 0, dtype = 0;
+  std::vector<HostModel> models;
+  std::vector<size_t> off;              // byte offset of each simulation's two state buffers
+  std::vector<size_t> coff;             // byte offset of each simulation's two code buffers
+  std::vector<size_t> sbytes;           // state bytes per simulation (one buffer)
+  void* state = nullptr;                // all state buffers
+  uint8_t* codes = nullptr;             // all code buffers
+  void* sims = nullptr;                 // BatchSim array (device)
+  CUtensorMap* maps = nullptr;          // [nsims][2] (device)
+  BatchItem* items = nullptr;
+  int nitems = 0;
+  unsigned int* barrier = nullptr;
+  int* status = nullptr;
+  int parity = 0;                       // buffer holding the current state
+  int64_t steps_done = 0;
+  cudaStream_t stream = nullptr;
+  AllocHook hook;
+  int grid = 0, smem = 0;
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_n = -1;
+  std::string err;
+};
+
+namespace {
+
+constexpr int kBTX = 32, kBTY = 8;
+using BF = BatchShape<2, 1, float, kBTX, kBTY>;
+
+ms_status bfail(ms_batch* b, ms_status s, const std::string& m) {
+  if (b) b->err = m;
+  return fail(nullptr, s, m);
+}
+
+void batch_free(ms_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  dev_free(b->hook, b->state);
+  dev_free(b->hook, b->codes);
+  dev_free(b->hook, b->sims);
+  dev_free(b->hook, b->maps);
+  dev_free(b->hook, b->items);
+  dev_free(b->hook, b->barrier);
+  delete b;
+}
+
+cudaError_t launch_batch(ms_batch* b, int64_t n) {
+  auto kern = k_batch<2, 1, float, kBTX, kBTY>;
+  cudaError_t e = cudaMemsetAsync(b->barrier, 0, sizeof(unsigned int), b->stream);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(b->grid);
+  cfg.blockDim = dim3(kBTX * kBTY + 32);
+  cfg.dynamicSmemBytes = b->smem;
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, (const BatchSim<float, 2, 1>*)b->sims, (const CUtensorMap*)b->maps,
+                            (const BatchItem*)b->items, b->nitems, (int)n, b->parity, b->barrier, b->status);
+}
+
+}  // namespace
+
+extern "C" {
+
+ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_components,
+                          const ms_params* params, void* stream, const ms_allocator* alloc, ms_batch** out) {
+  if (!out || nsims < 1 || !grids || !params) return bfail(nullptr, MS_ERR_ARG, "bad batch arguments");
+  *out = nullptr;
+  ensure_registered();
+  ms_batch* b = new ms_batch();
+  b->nsims = nsims;
+  b->stream = static_cast<cudaStream_t>(stream);
+  if (alloc) b->hook = AllocHook{alloc->alloc, alloc->release, alloc->user};
+  b->models.resize(nsims);
+  for (int i = 0; i < nsims; ++i) {
+    ms_status s = build_model(nullptr, &grids[i], n_phases, n_components, &params[i], b->models[i]);
+    if (s != MS_OK) {
+      std::string m = "simulation " + std::to_string(i) + ": " + ms_last_error(nullptr);
+      batch_free(b);
+      return bfail(nullptr, s, m);
+    }
+    HostModel& m = b->models[i];
+    if (m.dim != 2 || m.N != 2 || m.NM != 1 || m.dtype != MS_F32) {
+      batch_free(b);
+      return bfail(nullptr, MS_ERR_UNSUPPORTED, "the batched kernel is compiled for 2-D, N=2, K=2, FP32");
+    }
+    if (m.G * m.V != 0.0) {
+      batch_free(b);
+      return bfail(nullptr, MS_ERR_UNSUPPORTED, "batched simulations must be isothermal in time (G V = 0)");
+    }
+    set_layout(m);
+  }
+  b->N = 2;
+  b->NM = 1;
+  b->dtype = MS_F32;
+  // one allocation for all states (2 buffers each), one for all codes
+  size_t tot = 0, ctot = 0;
+  for (int i = 0; i < nsims; ++i) {
+    const HostModel& m = b->models[i];
+    const size_t sb = (size_t)m.fstride * (m.N + m.NM) * 4;
+    b->sbytes.push_back(sb);
+    b->off.push_back(tot);
+    tot += 2 * ((sb + 255) / 256 * 256);
+    const size_t cb = (size_t)segments(m) * m.ny;
+    b->coff.push_back(ctot);
+    ctot += 2 * ((cb + 255) / 256 * 256);
+  }
+  b->state = dev_alloc(b->hook, tot);
+  b->codes = static_cast<uint8_t*>(dev_alloc(b->hook, ctot));
+  b->sims = dev_alloc(b->hook, sizeof(BatchSim<float, 2, 1>) * nsims);
+  b->maps = static_cast<CUtensorMap*>(dev_alloc(b->hook, sizeof(CUtensorMap) * 2 * nsims));
+  b->barrier = static_cast<unsigned int*>(dev_alloc(b->hook, 256));
+  if (!b->state || !b->codes || !b->sims || !b->maps || !b->barrier) {
+    batch_free(b);
+    return bfail(nullptr, MS_ERR_OOM, "batch allocation failed");
+  }
+  b->status = reinterpret_cast<int*>(reinterpret_cast<char*>(b->barrier) + 128);
+  cudaError_t e = cudaMemsetAsync(b->state, 0, tot, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->codes, 0, ctot, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->barrier, 0, 256, b->stream);
+  // per-simulation constants and tensor maps
+  std::vector<BatchSim<float, 2, 1>> hs(nsims);
+  std::vector<CUtensorMap> hm(2 * nsims);
+  std::vector<BatchItem> items;
+  const StepKernel* k = nullptr;
+  for (auto& sk : step_registry())
+    if (sk.dim == 2 && sk.np == 2 && sk.nm == 1 && sk.dtype == 0 && sk.tx == kBTX && sk.ty == kBTY) k = &sk;
+  for (int i = 0; i < nsims && e == cudaSuccess; ++i) {
+    const HostModel& m = b->models[i];
+    const size_t half = (b->sbytes[i] + 255) / 256 * 256;
+    const size_t chalf = ((size_t)segments(m) * m.ny + 255) / 256 * 256;
+    char* base = static_cast<char*>(b->state) + b->off[i];
+    uint8_t* cbase = b->codes + b->coff[i];
+    for (int par = 0; par < 2; ++par) {
+      StepArgs<float, 2, 1>& g = hs[i].g[par];
+      k->fill(&g, m, 1, b->status);
+      g.out = reinterpret_cast<float*>(base + (1 - par) * half);
+      g.codes_in = cbase + par * chalf;
+      g.codes_out = cbase + (1 - par) * chalf;
+      g.tz0 = (float)temp_offset(m, m.t0);
+      if (!encode_state_map(&hm[2 * i + par], base + par * half, m, 3, kBTX, kBTY)) {
+        batch_free(b);
+        return bfail(nullptr, MS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+      }
+    }
+    const int tiles = ((m.nx + kBTX - 1) / kBTX) * ((m.ny + kBTY - 1) / kBTY);
+    for (int t = 0; t < tiles; ++t) items.push_back(BatchItem{i, t});
+  }
+  // interleave the simulations' tiles so that every CTA sees a mix of sizes
+  std::vector<BatchItem> mixed(items.size());
+  {
+    const size_t n = items.size();
+    size_t stride = 1;
+    while (stride * stride < n) ++stride;
+    size_t w = 0;
+    for (size_t r = 0; r < stride; ++r)
+      for (size_t q = r; q < n; q += stride) mixed[w++] = items[q];
+  }
+  b->nitems = (int)mixed.size();
+  b->items = static_cast<BatchItem*>(dev_alloc(b->hook, sizeof(BatchItem) * mixed.size()));
+  if (!b->items) {
+    batch_free(b);
+    return bfail(nullptr, MS_ERR_OOM, "batch work list allocation failed");
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->sims, hs.data(), sizeof(hs[0]) * nsims, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->maps, hm.data(), sizeof(CUtensorMap) * hm.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->items, mixed.data(), sizeof(BatchItem) * mixed.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  // persistent grid: every CTA resident at once
+  auto kern = k_batch<2, 1, float, kBTX, kBTY>;
+  b->smem = BF::SMEM;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, b->smem);
+  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBTX * kBTY + 32, b->smem);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    std::string m = std::string("batch set-up: ") + cudaGetErrorString(e);
+    batch_free(b);
+    return bfail(nullptr, MS_ERR_CUDA, m);
+  }
+  b->grid = std::max(1, per_sm) * sms;
+  *out = b;
+  return MS_OK;
+}
+
+void ms_batch_destroy(ms_batch* b) { batch_free(b); }
+
+const char* ms_batch_last_error(const ms_batch* b) { return b ? b->err.c_str() : ms_last_error(nullptr); }
+
+ms_status ms_batch_set_fields(ms_batch* b, int sim, const void* phi, const void* mu, int on_device) {
+  if (!b || sim < 0 || sim >= b->nsims || !phi || !mu) return bfail(b, MS_ERR_ARG, "bad argument");
+  const HostModel& m = b->models[sim];
+  const size_t half = (b->sbytes[sim] + 255) / 256 * 256;
+  char* buf = static_cast<char*>(b->state) + b->off[sim] + b->parity * half;
+  cudaError_t e = copy_fields(m, buf, 0, m.N, phi, nullptr, on_device, b->stream);
+  if (e == cudaSuccess) e = copy_fields(m, buf, m.N, m.NM, mu, nullptr, on_device, b->stream);
+  if (e == cudaSuccess) e = fill_ghosts(m, buf, m.N + m.NM, b->stream);
+  if (e == cudaSuccess) {
+    const size_t chalf = ((size_t)segments(m) * m.ny + 255) / 256 * 256;
+    const StepKernel* k = nullptr;
+    for (auto& sk : step_registry())
+      if (sk.dim == 2 && sk.np == 2 && sk.nm == 1 && sk.dtype == 0) k = &sk;
+    e = k->codes(buf, m, b->codes + b->coff[sim] + b->parity * chalf, b->stream);
+  }
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, MS_ERR_CUDA, std::string("batch set fields: ") + cudaGetErrorString(e));
+  return MS_OK;
+}
+
+ms_status ms_batch_get_fields(ms_batch* b, int sim, void* phi, void* mu, int on_device) {
+  if (!b || sim < 0 || sim >= b->nsims) return bfail(b, MS_ERR_ARG, "bad argument");
+  const HostModel& m = b->models[sim];
+  const size_t half = (b->sbytes[sim] + 255) / 256 * 256;
+  char* buf = static_cast<char*>(b->state) + b->off[sim] + b->parity * half;
+  cudaError_t e = cudaSuccess;
+  if (phi) e = copy_fields(m, buf, 0, m.N, nullptr, phi, on_device, b->stream);
+  if (e == cudaSuccess && mu) e = copy_fields(m, buf, m.N, m.NM, nullptr, mu, on_device, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, MS_ERR_CUDA, std::string("batch get fields: ") + cudaGetErrorString(e));
+  return MS_OK;
+}
+
+ms_status ms_batch_step(ms_batch* b, int64_t n) {
+  if (!b || n < 0) return bfail(b, MS_ERR_ARG, "bad argument");
+  if (n == 0) return MS_OK;
+  // the grid barrier counts (steps x CTAs) in 32 bits: at most 2^20 steps per launch
+  if (n > ((int64_t)1 << 20)) return bfail(b, MS_ERR_BOUNDS, "at most 1048576 steps per ms_batch_step call");
+  // the launch (barrier reset + cooperative kernel) is captured once per
+  // (n, parity) and replayed
+  cudaError_t e = cudaSuccess;
+  if (!b->graph || b->graph_n != n * 2 + b->parity) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    cudaStream_t cap;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+      cudaStream_t keep = b->stream;
+      b->stream = cap;
+      cudaGraph_t graph;
+      e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t le = launch_batch(b, n);
+        e = cudaStreamEndCapture(cap, &graph);
+        if (le != cudaSuccess) e = le;
+      }
+      b->stream = keep;
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&b->graph, graph, 0);
+        cudaGraphDestroy(graph);
+      }
+      cudaStreamDestroy(cap);
+    }
+    if (e != cudaSuccess) return bfail(b, MS_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    b->graph_n = n * 2 + b->parity;
+  }
+  e = cudaGraphLaunch(b->graph, b->stream);
+  if (e != cudaSuccess) return bfail(b, MS_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  b->parity = (int)((b->parity + n) & 1);
+  b->steps_done += n;
+  return MS_OK;
+}
+
+ms_status ms_batch_sync(ms_batch* b) {
+  if (!b) return bfail(nullptr, MS_ERR_ARG, "batch is NULL");
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, MS_ERR_CUDA, std::string("batch sync: ") + cudaGetErrorString(e));
+  if (st & kStatusTimeout) return bfail(b, MS_ERR_TIMEOUT, "a bounded device wait timed out");
+  return MS_OK;
+}
+
+int64_t ms_batch_cells(const ms_batch* b) {
+  if (!b) return 0;
+  int64_t c = 0;
+  for (auto& m : b->models) c += (int64_t)m.nx * m.ny * m.nz;
+  return c;
+}
+
+}  // extern "C"

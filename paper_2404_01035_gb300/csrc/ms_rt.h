@@ -70,6 +70,7 @@ ms_status launch_one_step(ms_ctx* c);
 ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk);
 ms_status refresh_codes(ms_ctx* c);   // segment codes of the current state
 bool encode_state_map(CUtensorMap* tm, void* base, const HostModel& m, int nf, int tx, int ty);
+void set_layout(HostModel& m);   // padded layout of one state buffer
 std::vector<const StepKernel*> step_variants(int dim, int np, int nm, int dtype);
 cudaError_t fill_ghosts(const HostModel& m, void* buf, int nf, cudaStream_t st);
 cudaError_t copy_fields(const HostModel& m, void* padded, int f0, int nf, const void* dense, void* dense_out,

@@ -83,3 +83,15 @@ def test_null_handles_are_rejected():
     assert L.ms_sync(None) == 1
     assert L.ms_checkpoint_bytes(None) == 0
     L.ms_destroy(None)
+
+
+def test_batch_create_rejects_unsupported_combinations():
+    L = B.lib()
+    p = W.small_multiphase(n=8, dim=3, N=3, NM=2)
+    keep = []
+    grids = (B.Grid * 1)(make_grid(p))
+    params = (B.Params * 1)(make_params(p, "f32", keep))
+    h = ctypes.c_void_p()
+    rc = L.ms_batch_create(1, grids, p.n_phases, p.n_components, params, None, None, ctypes.byref(h))
+    assert rc == 9 and not h.value
+    assert L.ms_batch_create(0, grids, 2, 2, params, None, None, ctypes.byref(h)) == 1

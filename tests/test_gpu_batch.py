@@ -1,0 +1,70 @@
+"""Batched persistent launch: every simulation of a batch matches its own
+single-simulation run (same arithmetic, separately compiled kernel: equal to
+FP32 rounding) and, for small ones, the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _standalone(p, steps):
+    from paper_2404_01035_gb300 import Simulation
+    sim = Simulation(p, dtype="f32")
+    sim.set_fields(p.phi0, p.mu0)
+    sim.step(steps)
+    out = sim.get_fields()
+    sim.close()
+    return out
+
+
+def _mixed_batch():
+    sims = []
+    for i, (nx, ny, d, D) in enumerate([(64, 64, 0.01, 0.1), (96, 70, 0.05, 0.4), (45, 130, 0.03, 0.25),
+                                        (160, 96, 0.02, 0.3), (33, 33, 0.04, 0.15), (70, 45, 0.0, 0.2)]):
+        p = W.binary_problem(f"b{i}", nx, ny=ny, delta=d, Delta=D, R=6.0, potential="obstacle",
+                             dtype_note="f32")
+        if i == 5:
+            p.bc = [W.BC_NOFLUX, W.BC_PERIODIC, W.BC_PERIODIC]
+        sims.append(p)
+    return sims
+
+
+def test_batch_matches_standalone_runs_and_oracle():
+    from paper_2404_01035_gb300.batch import Batch
+    probs = _mixed_batch()
+    b = Batch(probs)
+    for i, p in enumerate(probs):
+        b.set_fields(i, p.phi0, p.mu0)
+    b.step(130)       # two launches with different parity
+    b.step(170)
+    b.sync()
+    for i, p in enumerate(probs):
+        phi, mu = b.get_fields(i)
+        sphi, smu = _standalone(p, 300)
+        assert np.abs(phi - sphi).max() <= 1e-5 and np.abs(mu - smu).max() <= 1e-5, i
+        if p.nx * p.ny <= 64 * 64:
+            ophi, omu = oracle.run(p, p.phi0, p.mu0, 300)
+            assert max(np.abs(phi - ophi).max(), np.abs(mu - omu).max()) <= 1e-3
+    assert b.cells == sum(p.nx * p.ny for p in probs)
+    b.close()
+
+
+def test_cfg3_batch_of_512_runs_500_steps():
+    from paper_2404_01035_gb300.batch import Batch
+    probs = W.cfg3()
+    b = Batch(probs)
+    for i, p in enumerate(probs):
+        b.set_fields(i, p.phi0, p.mu0)
+    b.step(500)
+    b.sync()
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(probs), size=4, replace=False):
+        p = probs[i]
+        phi, mu = b.get_fields(int(i))
+        sphi, smu = _standalone(p, 500)
+        assert np.abs(phi - sphi).max() <= 1e-5 and np.abs(mu - smu).max() <= 1e-5, i
+        assert np.abs(phi.sum(axis=0) - 1).max() < 1e-5
+    b.close()
