@@ -66,6 +66,10 @@ typedef enum { MS_F32 = 0, MS_F64 = 1 } ms_dtype;
 /* Boundary codes of the paper's BOUNDARY key (Sec. "Input files"):
  * 1 = Neumann (no-flux, mirror ghost cell), 3 = periodic. */
 enum { MS_BC_NOFLUX = 1, MS_BC_PERIODIC = 3 };
+/* Library code (not a paper code) for the z faces of a 3-D sub-domain whose
+ * ghost planes are filled by ms_halo_exchange / ms_halo_mirror (slab
+ * decomposition of one domain into several contexts). */
+enum { MS_BC_HALO = 16 };
 
 /* Function_W: 1 = multi-obstacle (Eq. Obstacle), 2 = multi-well (Eq. Well). */
 enum { MS_POT_OBSTACLE = 1, MS_POT_WELL = 2 };
@@ -76,6 +80,9 @@ typedef struct {
   int nx, ny, nz;   /* cells per axis; nz is ignored (taken as 1) for dim = 2 */
   double dx;        /* cell size (DELTA_X = DELTA_Y = DELTA_Z) */
   int bc[3];        /* MS_BC_* for the x, y, z axes (both faces of an axis) */
+  int z_origin;     /* global index of this grid's first z-plane when it is one
+                       slab of a larger domain (0 otherwise); the temperature
+                       field is evaluated at the global plane index */
 } ms_grid;
 
 /* Model inputs, named after the paper's infile keys.  All pointers are host
@@ -247,6 +254,23 @@ ms_status ms_batch_get_fields(ms_batch* b, int sim, void* phi, void* mu, int on_
 ms_status ms_batch_step(ms_batch* b, int64_t n);
 ms_status ms_batch_sync(ms_batch* b);
 int64_t ms_batch_cells(const ms_batch* b);   /* total cells over all simulations */
+
+/* ---- Slab decomposition along z (3-D) ---------------------------------------
+ * A domain split into contexts that each own a contiguous range of z-planes
+ * (grid.bc[2] = MS_BC_HALO, grid.z_origin = the slab's first global plane, so
+ * the temperature field stays global) advances exactly like the whole domain
+ * when, after every step (and once after ms_set_fields), each internal cut is
+ * exchanged and each outer no-flux face is mirrored.  The exchange copies one
+ * padded z-plane of every field (and of the bulk codes) in each direction:
+ * the one exchange step of the explicit scheme (stencil radius 1).
+ * ms_halo_exchange(lower, upper): lower's top plane -> upper's bottom ghost,
+ *   upper's bottom plane -> lower's top ghost.  Same nx, ny, N, K, dtype and
+ *   the same stream are required (MS_ERR_ARG otherwise); enqueued on it.
+ *   For a periodic domain, also exchange (last, first).
+ * ms_halo_mirror(ctx, face): face 0 = bottom, 1 = top; no-flux ghost plane
+ *   (copy of the adjacent interior plane) for an outer face of a slab. */
+ms_status ms_halo_exchange(ms_ctx* lower, ms_ctx* upper);
+ms_status ms_halo_mirror(ms_ctx* ctx, int face);
 
 /* Allocation-free diagnostics (the paper has no counterpart; this is a
  * library service).  For callers that cannot allocate device memory while

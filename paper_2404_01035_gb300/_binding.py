@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_ARG", 2: "MS_ERR_CUDA", 3: "MS_ERR_OOM",
                 4: "MS_ERR_DT_UNSTABLE", 5: "MS_ERR_NONFINITE", 6: "MS_ERR_TIMEOUT",
                 7: "MS_ERR_BOUNDS", 8: "MS_ERR_STATE", 9: "MS_ERR_UNSUPPORTED"}
 MS_F32, MS_F64 = 0, 1
+MS_BC_HALO = 16
 
 # Every function the header declares (checked by the CPU test-suite).
 EXPORTS = [
@@ -30,6 +31,7 @@ EXPORTS = [
     "ms_enable_checkpoints", "ms_grad_param_count", "ms_grad",
     "ms_batch_create", "ms_batch_destroy", "ms_batch_last_error", "ms_batch_set_fields",
     "ms_batch_get_fields", "ms_batch_step", "ms_batch_sync", "ms_batch_cells",
+    "ms_halo_exchange", "ms_halo_mirror",
 ]
 
 
@@ -41,7 +43,8 @@ class MSError(RuntimeError):
 
 class Grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
-                ("nz", ctypes.c_int), ("dx", ctypes.c_double), ("bc", ctypes.c_int * 3)]
+                ("nz", ctypes.c_int), ("dx", ctypes.c_double), ("bc", ctypes.c_int * 3),
+                ("z_origin", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -119,6 +122,8 @@ def lib(build_if_missing: bool = True):
         L.ms_batch_sync.argtypes = [vp]
         L.ms_batch_cells.argtypes = [vp]
         L.ms_batch_cells.restype = ctypes.c_int64
+        L.ms_halo_exchange.argtypes = [vp, vp]
+        L.ms_halo_mirror.argtypes = [vp, ctypes.c_int]
         L.ms_enable_checkpoints.argtypes = [vp, ctypes.c_int]
         L.ms_grad_param_count.argtypes = [vp]
         L.ms_grad.argtypes = [vp, vp, vp, dp, vp, vp]

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(128) k_adjoint(const Real* __restrict__ st, co
             A.seed = seed;
             A.DX = &g.DX;
             DF pn[NP], mn[NM];
-            gp_cell<DIM, NP, NM, Real, DF>(A, g, dpf, DIM == 3 ? rz : ry, pn, mn);
+            gp_cell<DIM, NP, NM, Real, DF>(A, g, dpf, DIM == 3 ? rz + g.zorg : ry, pn, mn);
             const long long ri = dense(rx, ry, rz);
 #pragma unroll
             for (int a = 0; a < NP; ++a) {
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(128) k_adjoint(const Real* __restrict__ st, co
       A.seed = -1;
       A.DX = &DXd;
       DPm pn[NP], mn[NM];
-      gp_cell<DIM, NP, NM, Real, DPm>(A, g, dpp, DIM == 3 ? z : y, pn, mn);
+      gp_cell<DIM, NP, NM, Real, DPm>(A, g, dpp, DIM == 3 ? z + g.zorg : y, pn, mn);
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
         const Real l = lam_in[a * cells + j];

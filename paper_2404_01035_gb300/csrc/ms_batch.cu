@@ -314,7 +314,7 @@ ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_c
     b->sbytes.push_back(sb);
     b->off.push_back(tot);
     tot += 2 * ((sb + 255) / 256 * 256);
-    const size_t cb = (size_t)segments(m) * m.ny;
+    const size_t cb = code_bytes(m);
     b->coff.push_back(ctot);
     ctot += 2 * ((cb + 255) / 256 * 256);
   }
@@ -341,7 +341,7 @@ ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_c
   for (int i = 0; i < nsims && e == cudaSuccess; ++i) {
     const HostModel& m = b->models[i];
     const size_t half = (b->sbytes[i] + 255) / 256 * 256;
-    const size_t chalf = ((size_t)segments(m) * m.ny + 255) / 256 * 256;
+    const size_t chalf = (code_bytes(m) + 255) / 256 * 256;
     char* base = static_cast<char*>(b->state) + b->off[i];
     uint8_t* cbase = b->codes + b->coff[i];
     for (int par = 0; par < 2; ++par) {
@@ -411,7 +411,7 @@ ms_status ms_batch_set_fields(ms_batch* b, int sim, const void* phi, const void*
   if (e == cudaSuccess) e = copy_fields(m, buf, m.N, m.NM, mu, nullptr, on_device, b->stream);
   if (e == cudaSuccess) e = fill_ghosts(m, buf, m.N + m.NM, b->stream);
   if (e == cudaSuccess) {
-    const size_t chalf = ((size_t)segments(m) * m.ny + 255) / 256 * 256;
+    const size_t chalf = (code_bytes(m) + 255) / 256 * 256;
     const StepKernel* k = nullptr;
     for (auto& sk : step_registry())
       if (sk.dim == 2 && sk.np == 2 && sk.nm == 1 && sk.dtype == 0) k = &sk;

@@ -35,6 +35,7 @@ struct StepArgs {
   long long fstride;        // elements per field
   int xoff, zoff;           // index of interior x = 0 inside a row; of z = 0
   int zchunk;               // planes marched per CTA (3-D)
+  int zorg;                 // global index of z-plane 0 (temperature position)
   int bc[3];
   Real* out;                // destination state (padded, NP + NM fields)
   int* status;              // sticky device status word

@@ -50,7 +50,7 @@ struct DiagConsts {
 template <int DIM, int NP, int NM, class Real>
 __global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ st, int nx, int ny,
                                                        int nz, int pitch, int nyp, long long fstride,
-                                                       int xoff, int zoff, double tz0, double tzg,
+                                                       int xoff, int zoff, int zorg, double tz0, double tzg,
                                                        double dt, double inv_dx2,
                                                        const __grid_constant__ DiagConsts<Real, NP, NM> c,
                                                        double* __restrict__ partials) {
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ 
     acc[NM] = fmax(acc[NM], fabs(sum - 1.0));
     Real h[NP];
     interp_h<NP>(ph, h);
-    const Real s = (Real)(tz0 + tzg * ((DIM == 3 ? z : y) + 0.5));
+    const Real s = (Real)(tz0 + tzg * ((DIM == 3 ? z + zorg : y) + 0.5));
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
       Real ci = Real(0);
@@ -217,7 +217,7 @@ cudaError_t launch_diag(const void* state, const HostModel& m, double t, double*
   const double tz0 = m.T0 - m.T_ref - m.G * (m.z0 + m.V * t);
   k_diag<DIM, NP, NM, Real><<<nblocks, kDiagThreads, 0, st>>>(
       reinterpret_cast<const Real*>(state), m.nx, m.ny, DIM == 3 ? m.nz : 1, m.pitch, m.nyp,
-      m.fstride, m.xoff, m.zoff, tz0, m.G * m.dx, m.dt, 1.0 / (m.dx * m.dx), c, partials);
+      m.fstride, m.xoff, m.zoff, m.zorg, tz0, m.G * m.dx, m.dt, 1.0 / (m.dx * m.dx), c, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_diag_final<NM><<<1, kDiagThreads, 0, st>>>(partials, nblocks, out, status);

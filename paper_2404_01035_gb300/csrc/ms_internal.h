@@ -13,6 +13,10 @@ namespace msgb {
 constexpr int kNMax = 8;
 constexpr int kKMax = 3;
 
+// Boundary code of an internal cut whose ghost plane is filled by a halo
+// exchange (same value as MS_BC_HALO in the public header).
+constexpr int kBcHalo = 16;
+
 // Status bits OR-ed into the device status word.
 constexpr int kStatusNonFinite = 1;
 constexpr int kStatusTimeout = 2;
@@ -21,6 +25,7 @@ constexpr int kStatusTimeout = 2;
 struct HostModel {
   int dim = 2, N = 2, NM = 1, dtype = 0;
   int nx = 1, ny = 1, nz = 1, bc[3] = {3, 3, 3};
+  int zorg = 0;   // global index of the first z-plane (slab decomposition)
   // padded layout (elements)
   int pitch = 0, nyp = 0, nzp = 0, xoff = 0, zoff = 0;
   long long fstride = 0;
@@ -65,6 +70,8 @@ struct StepKernel {
 
 // Number of 32-cell segments per row.
 inline int segments(const HostModel& m) { return (m.nx + 31) / 32; }
+// Bytes of one segment-code array (3-D arrays carry a ghost plane per side).
+inline size_t code_bytes(const HostModel& m) { return (size_t)segments(m) * m.ny * m.nzp; }
 
 // One compiled FP64 diagnostics instantiation.
 struct DiagKernel {

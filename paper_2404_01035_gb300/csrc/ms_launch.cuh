@@ -27,6 +27,7 @@ void fill_args(void* blob, const HostModel& m, int zchunk, int* status) {
   g.xoff = m.xoff;
   g.zoff = m.zoff;
   g.zchunk = zchunk;
+  g.zorg = m.zorg;
   for (int d = 0; d < 3; ++d) g.bc[d] = m.bc[d];
   g.status = status;
   g.dt = (Real)m.dt;
@@ -140,7 +141,7 @@ cudaError_t launch_step(const CUtensorMap* tm, void* blob, const HostModel& m, d
 
 template <int DIM, int NP, class Real>
 cudaError_t launch_codes(const void* state, const HostModel& m, uint8_t* codes, cudaStream_t st) {
-  const long long warps = (long long)segments(m) * m.ny * m.nz;
+  const long long warps = (long long)segments(m) * m.ny * m.nz;   // interior planes
   const int blocks = (int)((warps * 32 + 255) / 256);
   k_codes<DIM, NP, Real><<<blocks, 256, 0, st>>>(reinterpret_cast<const Real*>(state), m.nx, m.ny, m.nz,
                                                  m.pitch, m.nyp, m.fstride, m.xoff, m.zoff, segments(m),

@@ -46,7 +46,7 @@ __device__ __forceinline__ int na_map(int i, int n, int bc) {
 template <int DIM, int NP, int NM, class Real>
 __global__ void __launch_bounds__(kNaThreads) k_diag_dense(
     const Real* __restrict__ phi, const Real* __restrict__ mu, int nx, int ny, int nz, int bcx, int bcy,
-    int bcz, double tz0, double tzg, double dt, double inv_dx2,
+    int bcz, int zorg, double tz0, double tzg, double dt, double inv_dx2,
     const __grid_constant__ DiagConsts<Real, NP, NM> c, double* __restrict__ partials) {
   constexpr int NV = NM + 5;
   double acc[NV];
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kNaThreads) k_diag_dense(
     acc[NM] = fmax(acc[NM], fabs(sum - 1.0));
     Real h[NP];
     interp_h<NP>(ph, h);
-    const Real s = (Real)(tz0 + tzg * ((DIM == 3 ? z : y) + 0.5));
+    const Real s = (Real)(tz0 + tzg * ((DIM == 3 ? z + zorg : y) + 0.5));
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
       Real ci = Real(0);
@@ -208,7 +208,7 @@ cudaError_t na_launch(const HostModel& m, double t, const void* phi, const void*
   const double tz0 = m.T0 - m.T_ref - m.G * (m.z0 + m.V * t);
   k_diag_dense<DIM, NP, NM, Real><<<nblocks, kNaThreads, 0, st>>>(
       static_cast<const Real*>(phi), static_cast<const Real*>(mu), m.nx, m.ny, DIM == 3 ? m.nz : 1, m.bc[0],
-      m.bc[1], m.bc[2], tz0, m.G * m.dx, m.dt, 1.0 / (m.dx * m.dx), c, partials);
+      m.bc[1], m.bc[2], m.zorg, tz0, m.G * m.dx, m.dt, 1.0 / (m.dx * m.dx), c, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_diag_dense_final<NM><<<1, kNaThreads, 0, st>>>(partials, nblocks, out);

@@ -117,9 +117,11 @@ ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params
   if (g->nx < 1 || g->ny < 1 || (g->dim == 3 && g->nz < 1))
     return fail(c, MS_ERR_ARG, "grid extents must be >= 1");
   if (!(g->dx > 0)) return fail(c, MS_ERR_ARG, "dx must be > 0");
-  for (int d = 0; d < 3; ++d)
+  for (int d = 0; d < 3; ++d) {
+    if (d == 2 && g->dim == 3 && g->bc[d] == MS_BC_HALO) continue;   // internal cut in z
     if (g->bc[d] != MS_BC_PERIODIC && g->bc[d] != MS_BC_NOFLUX)
-      return fail(c, MS_ERR_ARG, "boundary codes must be 1 (no-flux) or 3 (periodic)");
+      return fail(c, MS_ERR_ARG, "boundary codes must be 1 (no-flux) or 3 (periodic); 16 (halo) only for z in 3-D");
+  }
   if (p->dtype != MS_F32 && p->dtype != MS_F64) return fail(c, MS_ERR_ARG, "dtype must be MS_F32 or MS_F64");
   if (p->potential != MS_POT_OBSTACLE && p->potential != MS_POT_WELL)
     return fail(c, MS_ERR_ARG, "potential must be 1 (obstacle) or 2 (well)");
@@ -137,6 +139,8 @@ ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params
   m.ny = g->ny;
   m.nz = g->dim == 3 ? g->nz : 1;
   for (int d = 0; d < 3; ++d) m.bc[d] = g->bc[d];
+  m.zorg = g->dim == 3 ? g->z_origin : 0;
+  if (m.zorg < 0) return fail(c, MS_ERR_ARG, "z_origin must be >= 0");
   m.dx = g->dx;
   m.dt = p->dt;
   m.eps = p->eps;
@@ -339,6 +343,7 @@ __global__ void k_fill_ghosts(Real* buf, int nf, int nx, int ny, int nz, int pit
 
 cudaError_t fill_ghosts(const HostModel& m, void* buf, int nf, cudaStream_t st) {
   for (int axis = 0; axis < m.dim; ++axis) {
+    if (m.bc[axis] == kBcHalo) continue;   // filled by the halo exchange
     long long lines = axis == 0 ? (long long)nf * m.nz * m.ny
                       : axis == 1 ? (long long)nf * m.nz * (m.nx + 2)
                                   : (long long)nf * (m.ny + 2) * (m.nx + 2);
@@ -495,10 +500,10 @@ ms_status ms_create(const ms_grid* grid, int n_phases, int n_components, const m
   const size_t s_el = c->m.dtype == MS_F64 ? 8 : 4;
   const int nf = c->m.N + c->m.NM;
   c->state_bytes = (size_t)c->m.fstride * nf * s_el;
-  const size_t code_bytes = (size_t)segments(c->m) * c->m.ny * c->m.nz;
+  const size_t cbytes = code_bytes(c->m);
   for (int b = 0; b < 2; ++b) {
     c->buf[b] = dev_alloc(c->hook, c->state_bytes);
-    c->codes[b] = static_cast<uint8_t*>(dev_alloc(c->hook, code_bytes));
+    c->codes[b] = static_cast<uint8_t*>(dev_alloc(c->hook, cbytes));
     if (!c->buf[b] || !c->codes[b]) {
       ms_destroy(c);
       return fail(nullptr, MS_ERR_OOM, "state allocation failed");
@@ -523,7 +528,7 @@ ms_status ms_create(const ms_grid* grid, int n_phases, int n_components, const m
   cudaError_t e = cudaMemsetAsync(c->small, 0, 4096, c->stream);
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
     e = cudaMemsetAsync(c->buf[b], 0, c->state_bytes, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->codes[b], 0, code_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->codes[b], 0, cbytes, c->stream);
   }
   if (e != cudaSuccess) {
     ms_status r = cuda_fail(nullptr, e, "initial memset");
@@ -561,6 +566,7 @@ ms_status ms_update_params(ms_ctx* c, const ms_params* p) {
   g.nx = c->m.nx;
   g.ny = c->m.ny;
   g.nz = c->m.nz;
+  g.z_origin = c->m.zorg;
   g.dx = c->m.dx;
   for (int d = 0; d < 3; ++d) g.bc[d] = c->m.bc[d];
   if (!p || p->dtype != c->m.dtype) return fail(c, MS_ERR_ARG, "dtype cannot change");

@@ -122,7 +122,15 @@ __device__ __forceinline__ void load_codes(const StepArgs<Real, NP, NM>& g, int 
     return;
   }
   const int yy = bc_map(y, g.ny, g.bc[1]);
-  const int zz = bc_map(z, g.nz, g.bc[2]);
+  // plane index in the code array (3-D arrays carry one ghost plane per side,
+  // filled by the halo exchange when that face is an internal cut)
+  int zz;
+  if (z >= 0 && z < g.nz)
+    zz = z + g.zoff;
+  else if (g.bc[2] == kBcHalo)
+    zz = z < 0 ? 0 : g.nz + 1;
+  else
+    zz = bc_map(z, g.nz, g.bc[2]) + g.zoff;
   const uint8_t* row = g.codes_in + ((long long)zz * g.ny + yy) * g.segs;
   const uint32_t a = row[bc_map(s - 1, g.segs, g.bc[0])];
   const uint32_t b = row[s];
@@ -183,8 +191,9 @@ __device__ __forceinline__ void store_cell(const StepArgs<Real, NP, NM>& g, int 
   if (y == 0) ys[nys++] = g.bc[1] == 3 ? g.ny : -1;
   if (y == g.ny - 1) ys[nys++] = g.bc[1] == 3 ? -1 : g.ny;
   if constexpr (DIM == 3) {
-    if (z == 0) zs[nzs++] = g.bc[2] == 3 ? g.nz : -1;
-    if (z == g.nz - 1) zs[nzs++] = g.bc[2] == 3 ? -1 : g.nz;
+    // internal cuts (halo faces) get their ghost planes from the exchange
+    if (z == 0 && g.bc[2] != kBcHalo) zs[nzs++] = g.bc[2] == 3 ? g.nz : -1;
+    if (z == g.nz - 1 && g.bc[2] != kBcHalo) zs[nzs++] = g.bc[2] == 3 ? -1 : g.nz;
   }
   for (int iz = 0; iz < nzs; ++iz)
     for (int iy = 0; iy < nys; ++iy)
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
         dp.mob = g.mob;
 #pragma unroll
         for (int p = 0; p < StepArgs<Real, NP, NM>::P; ++p) dp.delta[p] = g.delta[p];
-        gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, DIM == 3 ? z : y, pn, mn);
+        gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, DIM == 3 ? z + g.zorg : y, pn, mn);
         uint32_t nzm = 0, one = 0;
 #pragma unroll
         for (int a = 0; a < NP; ++a) {
@@ -361,7 +370,8 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
     const int ref = __shfl_sync(0xffffffffu, code, 0);
     const bool same = __all_sync(0xffffffffu, !active || code == ref);
     if (lane == 0) {
-      if (active) g.codes_out[((long long)z * g.ny + y) * g.segs + seg] = same ? (uint8_t)ref : (uint8_t)0;
+      if (active)
+        g.codes_out[((long long)(z + g.zoff) * g.ny + y) * g.segs + seg] = same ? (uint8_t)ref : (uint8_t)0;
       if constexpr (DIM == 3) mbar_arrive(&empty[s0]);   // this warp is done with entry k
     }
     if constexpr (DIM == 3) {
@@ -381,6 +391,7 @@ template <int DIM, int NP, class Real>
 __global__ void __launch_bounds__(256) k_codes(const Real* __restrict__ st, int nx, int ny, int nz,
                                                int pitch, int nyp, long long fstride, int xoff,
                                                int zoff, int segs, uint8_t* __restrict__ codes) {
+  // codes[((z + zoff) * ny + y) * segs + s] for the interior planes
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const long long nseg = (long long)segs * ny * nz;
@@ -404,7 +415,7 @@ __global__ void __launch_bounds__(256) k_codes(const Real* __restrict__ st, int 
   }
   const int ref = __shfl_sync(0xffffffffu, code, 0);
   const bool same = __all_sync(0xffffffffu, !active || code == ref);
-  if (lane == 0) codes[w] = same ? (uint8_t)ref : (uint8_t)0;
+  if (lane == 0) codes[((long long)(z + zoff) * ny + y) * segs + s] = same ? (uint8_t)ref : (uint8_t)0;
 }
 
 }  // namespace msgb

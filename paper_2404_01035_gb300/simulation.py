@@ -53,6 +53,7 @@ def make_grid(prob) -> Grid:
     gr.dx = float(prob.dx)
     bc = list(prob.bc) + [3, 3, 3]
     gr.bc = (ctypes.c_int * 3)(*bc[:3])
+    gr.z_origin = int(getattr(prob, "meta", {}).get("z_origin", 0)) if prob.dim == 3 else 0
     return gr
 
 
