@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint lines")
     return ap.parse_args()
 
 
@@ -260,13 +261,13 @@ def run_ours(args, rank, world, local_rank):
             "kernel": "k_gp_step<3,3,2,float>", "bytes_per_cell": bpc,
             "kernel_ms_per_launch": per_launch_s * 1e3}
 
-    # ---- e2e through the public API with host (pinned) buffers
+    # ---- e2e through the public API with host (pinned) buffers, continuing
+    # from the evolved state of the timed run
     e2e = None
     if not args.no_e2e:
         hphi = torch.empty((prob.n_phases,) + sim.shape, dtype=torch.float32, pin_memory=True)
         hmu = torch.empty((prob.n_components - 1,) + sim.shape, dtype=torch.float32, pin_memory=True)
-        hphi.copy_(torch.from_numpy(prob.phi0.astype(np.float32)))
-        hmu.copy_(torch.from_numpy(prob.mu0.astype(np.float32)))
+        sim.get_fields_into(hphi, hmu, on_device=False)
         sim.set_diag_every(0)
         iters = 3
         for it in range(iters + 1):
@@ -287,6 +288,11 @@ def run_ours(args, rank, world, local_rank):
     launch_info = {"tiles_compiled": tiles}
     sim.close()
 
+    extra = {}
+    if not args.no_extras:
+        extra["batched"] = bench_batched(stream)
+        extra["adjoint"] = bench_adjoint(stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample, secs = oracle_sample_rate(prob, target_s=15.0)
@@ -303,8 +309,87 @@ def run_ours(args, rank, world, local_rank):
                            "l2": "inputs larger than L2 (state 671 MB per buffer)",
                            "tuned_ms_per_step": tuned_ms, **launch_info},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches}
+                "gpu_launches": launches, **extra}
         print(json.dumps(line), flush=True)
+
+
+def _events_ms(stream, fn):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def bench_batched(stream):
+    """512 independent 2-D dendrites, 500 steps in one persistent launch, against
+    the plain single-simulation step on the largest of them (512^2)."""
+    import workloads
+    from paper_2404_01035_gb300 import Simulation
+    from paper_2404_01035_gb300.batch import Batch
+    probs = workloads.cfg3()
+    b = Batch(probs, stream=stream)
+    for i, p in enumerate(probs):
+        b.set_fields(i, p.phi0, p.mu0)
+    b.step(20)            # warm-up launch (graph capture for n = 20)
+    b.sync()
+    steps = 500
+    b.step(steps)         # capture for n = 500, then time a replay
+    b.sync()
+    for i, p in enumerate(probs):
+        b.set_fields(i, p.phi0, p.mu0)
+    ms = _events_ms(stream, lambda: b.step(steps))
+    b.sync()
+    cells = b.cells
+    b.close()
+    big = max(probs, key=lambda q: q.cells)
+    sim = Simulation(big, dtype="f32", stream=stream)
+    sim.set_fields(big.phi0, big.mu0)
+    sim.step(20)
+    pms = _events_ms(stream, lambda: sim.step(steps))
+    sim.close()
+    batched = cells * steps / (ms / 1e3) / 1e6
+    plain = big.cells * steps / (pms / 1e3) / 1e6
+    return {"workload": "512 independent 2-D N=2 K=2 FP32 sims, edges 64..512, 500 steps, one "
+                        "graph-captured persistent launch", "cells": int(cells),
+            "mlups": batched, "ms_per_step": ms / steps,
+            "plain_step_mlups": plain, "plain_step": f"single {big.nx}^2 simulation, one launch per step",
+            "vs_plain_step": batched / plain,
+            "hbm_frac": batched * 1e6 * 24 / (measured_peaks()[0]["hbm_gbs"] * 1e9)}
+
+
+def bench_adjoint(stream):
+    """2-D 256^2 well-potential adjoint: 2000 steps forward with checkpoints every
+    100, then the reverse pass, FP32 and FP64, against the plain forward step."""
+    import torch
+    import workloads
+    from paper_2404_01035_gb300 import Simulation
+    out = {"workload": "2-D 256^2, N=2 K=2, well potential, 2000 steps, checkpoint every 100"}
+    for dtype in ("f32", "f64"):
+        p = workloads.cfg4(n=256, steps=2000, delta=0.02, mob=0.8)
+        sim = Simulation(p, dtype=dtype, stream=stream)
+        sim.set_fields(p.phi0, p.mu0)
+        sim.step(50)
+        sim.set_fields(p.phi0, p.mu0)
+        fwd = _events_ms(stream, lambda: sim.step(2000))
+        sim.set_fields(p.phi0, p.mu0)
+        sim.enable_checkpoints(100)
+        sim.step(2000)
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        seed = torch.ones((2, 1, 256, 256), dtype=tdt, device="cuda") * 1e-3
+        stream.synchronize()
+        t0 = time.perf_counter()
+        sim.grad(seed)
+        rev = (time.perf_counter() - t0) * 1e3
+        sim.close()
+        out[dtype] = {"forward_ms_per_step": fwd / 2000, "reverse_ms_per_step": rev / 2000,
+                      "reverse_vs_forward": rev / fwd,
+                      "forward_mlups": 65536 * 2000 / (fwd / 1e3) / 1e6,
+                      "reverse_mlups": 65536 * 2000 / (rev / 1e3) / 1e6}
+    return out
 
 
 def kernel_digest():
