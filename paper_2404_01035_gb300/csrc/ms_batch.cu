@@ -58,11 +58,13 @@ __global__ void __launch_bounds__(TX* TY + 32, 1)
             unsigned int* barrier, int* status) {
   using Sh = StepShape<2, NP, NM, Real, TX, TY>;
   constexpr int NST = 8;
+  constexpr int PF = 4;   // items whose descriptors and codes the producer holds ahead
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   uint8_t* rowflag = smem + NST * Sh::STAGE_STRIDE;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * Sh::STAGE_STRIDE + ((NST * Sh::NFL + 15) / 16) * 16);
+  int4* sitem = reinterpret_cast<int4*>(smem + NST * Sh::STAGE_STRIDE + ((NST * Sh::NWF + 15) / 16) * 16);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sitem + NST);
   uint64_t* empty = full + NST;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NST);
   auto stage = [&](int s) { return reinterpret_cast<Real*>(smem + s * Sh::STAGE_STRIDE); };
@@ -76,14 +78,33 @@ __global__ void __launch_bounds__(TX* TY + 32, 1)
     mbar_fence_init();
   }
   __syncthreads();
-  const int my_items = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  long long seq = 0;      // ring position of this CTA's item sequence (continues across steps)
+  // contiguous item range: consecutive tiles of one simulation share its constants
+  const int per = (nitems + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int ibeg = min(nitems, (int)blockIdx.x * per);
+  const int my_items = min(nitems, ibeg + per) - ibeg;
+  long long seq = 0;      // ring position (continues across steps)
   long long issued = 0;   // loads issued (producer lane 0)
   for (int step = 0; step < nsteps; ++step) {
     const int par = (parity0 + step) & 1;
     if (tid >= Sh::NT) {
-      // producer warp
+      // ---------------- producer warp
       const int f_ay = lane / Sh::WC, f_wc = lane % Sh::WC;
+      const bool fl = lane < Sh::NFL;
+      int psim[PF], px0[PF], py0[PF];
+      uint32_t pc3[PF];
+      auto fetch = [&](int k, int& sim, int& x0, int& y0, uint32_t& c3) {
+        const BatchItem it = items[ibeg + k];
+        const StepArgs<Real, NP, NM>& g = sims[it.sim].g[par];
+        const int tiles_x = (g.nx + TX - 1) / TX;
+        sim = it.sim;
+        x0 = (it.tile % tiles_x) * TX;
+        y0 = (it.tile / tiles_x) * TY;
+        c3 = 0;
+        if (fl) load_codes(g, (x0 >> 5) + f_wc, y0 - 1 + f_ay, 0, c3);
+      };
+#pragma unroll
+      for (int i = 0; i < PF; ++i)
+        if (i < my_items) fetch(i, psim[i], px0[i], py0[i], pc3[i]);
       bool ok = true;
       for (int k = 0; k < my_items; ++k) {
         const long long q = seq + k;
@@ -97,25 +118,45 @@ __global__ void __launch_bounds__(TX* TY + 32, 1)
           }
           break;
         }
-        const BatchItem it = items[blockIdx.x + (long long)k * gridDim.x];
-        const StepArgs<Real, NP, NM>& g = sims[it.sim].g[par];
-        const int tiles_x = (g.nx + TX - 1) / TX;
-        const int x0 = (it.tile % tiles_x) * TX, y0 = (it.tile / tiles_x) * TY;
-        if (lane < Sh::NFL) {
-          uint32_t c3;
-          load_codes(g, (x0 >> 5) + f_wc, y0 - 1 + f_ay, 0, c3);
-          rowflag[s * Sh::NFL + lane] = combine_codes(c3);
+        int sim = 0, x0 = 0, y0 = 0;
+        uint32_t c3 = 0;
+#pragma unroll
+        for (int i = 0; i < PF; ++i)
+          if (i == k % PF) {
+            sim = psim[i];
+            x0 = px0[i];
+            y0 = py0[i];
+            c3 = pc3[i];
+          }
+        if (k + PF < my_items) {
+          int a, b2, c;
+          uint32_t d;
+          fetch(k + PF, a, b2, c, d);
+#pragma unroll
+          for (int i = 0; i < PF; ++i)
+            if (i == k % PF) {
+              psim[i] = a;
+              px0[i] = b2;
+              py0[i] = c;
+              pc3[i] = d;
+            }
         }
+        // combined flag of each warp row (rows ay, ay+1, ay+2)
+        const int rf = fl ? (int)combine_codes(c3) : 0;
+        const int up = __shfl_down_sync(0xffffffffu, rf, Sh::WC);
+        const int up2 = __shfl_down_sync(0xffffffffu, rf, 2 * Sh::WC);
+        if (lane < Sh::NWF) rowflag[s * Sh::NWF + lane] = (uint8_t)((rf == up && up == up2) ? rf : 0);
+        if (lane == 0) sitem[s] = make_int4(sim, x0, y0, 0);
         __syncwarp();
         if (lane == 0) {
           __threadfence_block();
           mbar_expect_tx(&full[s], Sh::STAGE_BYTES);
-          tma_load_4d(stage(s), &maps[2 * it.sim + par], &full[s], x0 + g.xoff - Sh::H, y0, 0, 0);
+          tma_load_4d(stage(s), &maps[2 * sim + par], &full[s], x0 + sims[sim].g[par].xoff - Sh::H, y0, 0, 0);
           issued = q + 1;
         }
       }
     } else {
-      // consumer warps
+      // ---------------- consumer warps
       const int tx = tid % TX, ty = tid / TX, wc = tx >> 5;
       for (int k = 0; k < my_items; ++k) {
         const long long q = seq + k;
@@ -128,16 +169,13 @@ __global__ void __launch_bounds__(TX* TY + 32, 1)
           }
           break;
         }
-        const BatchItem it = items[blockIdx.x + (long long)k * gridDim.x];
-        const StepArgs<Real, NP, NM>& g = sims[it.sim].g[par];
-        const int tiles_x = (g.nx + TX - 1) / TX;
-        const int x0 = (it.tile % tiles_x) * TX, y0 = (it.tile / tiles_x) * TY;
+        const int4 it = sitem[s];
+        const StepArgs<Real, NP, NM>& g = sims[it.x].g[par];
+        const int x0 = it.y, y0 = it.z;
         const int x = x0 + tx, y = y0 + ty;
         const bool active = x < g.nx && y < g.ny;
-        const int flag = rowflag[s * Sh::NFL + (ty + 1) * Sh::WC + wc];
-        bool bulk = flag != 0;
-#pragma unroll
-        for (int dr = 0; dr < 3; ++dr) bulk = bulk && rowflag[s * Sh::NFL + (ty + dr) * Sh::WC + wc] == flag;
+        const int flag = rowflag[s * Sh::NWF + ty * Sh::WC + wc];
+        const bool bulk = flag != 0;
         int code = 0;
         if (active) {
           SmemAcc<2, NP, NM, Real, TX, TY> acc;
@@ -199,7 +237,8 @@ template <int NP, int NM, class Real, int TX, int TY>
 struct BatchShape {
   using Sh = StepShape<2, NP, NM, Real, TX, TY>;
   static constexpr int NST = 8;
-  static constexpr int SMEM = NST * Sh::STAGE_STRIDE + ((NST * Sh::NFL + 15) / 16) * 16 + 2 * NST * 8 + 16 + 128;
+  static constexpr int SMEM =
+      NST * Sh::STAGE_STRIDE + ((NST * Sh::NWF + 15) / 16) * 16 + NST * 16 + 2 * NST * 8 + 16 + 128;
 };
 
 }  // namespace msgb
@@ -359,16 +398,8 @@ ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_c
     const int tiles = ((m.nx + kBTX - 1) / kBTX) * ((m.ny + kBTY - 1) / kBTY);
     for (int t = 0; t < tiles; ++t) items.push_back(BatchItem{i, t});
   }
-  // interleave the simulations' tiles so that every CTA sees a mix of sizes
-  std::vector<BatchItem> mixed(items.size());
-  {
-    const size_t n = items.size();
-    size_t stride = 1;
-    while (stride * stride < n) ++stride;
-    size_t w = 0;
-    for (size_t r = 0; r < stride; ++r)
-      for (size_t q = r; q < n; q += stride) mixed[w++] = items[q];
-  }
+  // items in simulation order: each CTA takes a contiguous range of them
+  std::vector<BatchItem>& mixed = items;
   b->nitems = (int)mixed.size();
   b->items = static_cast<BatchItem*>(dev_alloc(b->hook, sizeof(BatchItem) * mixed.size()));
   if (!b->items) {

@@ -50,7 +50,8 @@ struct StepShape {
   static constexpr int NST_RAW = RING_BUDGET / STAGE_STRIDE;
   static constexpr int NST = DIM == 3 ? (NST_RAW < 4 ? 4 : (NST_RAW > 12 ? 12 : NST_RAW)) : 1;
   static constexpr int NFL = SY * WC;                   // row flags per plane
-  static constexpr int FLAG_BYTES = (NST * NFL + 15) / 16 * 16;   // one flag set per stage
+  static constexpr int NWF = TY * WC;                   // combined flags per plane (one per warp row)
+  static constexpr int FLAG_BYTES = (NST * NWF + 15) / 16 * 16;   // one flag set per stage
   static constexpr int OFF_FLAG = NST * STAGE_STRIDE;
   static constexpr int OFF_BAR = OFF_FLAG + FLAG_BYTES;            // full[NST], empty[NST]
   static constexpr int OFF_ABORT = OFF_BAR + 2 * NST * 8;
@@ -265,6 +266,8 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
     if (lane == 0) prefetch_tensormap(&tm);
     int issued = 0;
     bool ok = true;
+    // row flags (lane = halo'ed row ay, warp column wc) of entries j-2, j-1, j
+    int rf2 = 0, rf1 = 0, rf0 = 0;
     for (int j = 0; j < nplanes; ++j) {
       const int s = j % NST;
       if (j >= NST) ok = ok && mbar_wait_bounded(&empty[s], ((j / NST) - 1) & 1);
@@ -274,15 +277,25 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
 #pragma unroll
       for (int i = 0; i < Sh::PF; ++i)
         if (i == j % Sh::PF) c3 = pre[i];
-      if (fl) {
-        rowflag[s * Sh::NFL + lane] = combine_codes(c3);
-        if (j + Sh::PF < nplanes) {
-          uint32_t nc;
-          load_codes(g, f_seg, y0 - 1 + f_ay, plane_of(j + Sh::PF), nc);
+      rf2 = rf1;
+      rf1 = rf0;
+      rf0 = fl ? (int)combine_codes(c3) : 0;
+      if (fl && j + Sh::PF < nplanes) {
+        uint32_t nc;
+        load_codes(g, f_seg, y0 - 1 + f_ay, plane_of(j + Sh::PF), nc);
 #pragma unroll
-          for (int i = 0; i < Sh::PF; ++i)
-            if (i == j % Sh::PF) pre[i] = nc;
-        }
+        for (int i = 0; i < Sh::PF; ++i)
+          if (i == j % Sh::PF) pre[i] = nc;
+      }
+      // Combined flag of the centre entry (j-1 in 3-D, j in 2-D) for each warp
+      // row: non-zero only if the 3 rows x 3 planes around it are one phase.
+      {
+        const int pc = DIM == 3 ? ((rf2 == rf1 && rf1 == rf0) ? rf1 : 0) : rf0;
+        const int up = __shfl_down_sync(0xffffffffu, pc, Sh::WC);
+        const int up2 = __shfl_down_sync(0xffffffffu, pc, 2 * Sh::WC);
+        const int wf = (pc == up && up == up2) ? pc : 0;   // rows ay, ay+1, ay+2
+        const int centre = DIM == 3 ? j - 1 : j;
+        if (lane < Sh::NWF && centre >= 0) rowflag[(centre % NST) * Sh::NWF + lane] = (uint8_t)wf;
       }
       __syncwarp();
       if (lane == 0) {
@@ -330,17 +343,10 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
       return;
     }
     const int z = zb + k;
-    // warp-uniform bulk test over the 3 x 3 (x 3 planes) rows around row ty
-    const int flag = rowflag[s1 * Sh::NFL + (ty + 1) * Sh::WC + wc];
-    bool bulk = flag != 0;
-#pragma unroll
-    for (int dr = 0; dr < 3; ++dr) {
-      bulk = bulk && rowflag[s1 * Sh::NFL + (ty + dr) * Sh::WC + wc] == flag;
-      if constexpr (DIM == 3) {
-        bulk = bulk && rowflag[s0 * Sh::NFL + (ty + dr) * Sh::WC + wc] == flag;
-        bulk = bulk && rowflag[s2 * Sh::NFL + (ty + dr) * Sh::WC + wc] == flag;
-      }
-    }
+    // warp-uniform bulk test, combined by the producer over the 3 x 3 (x 3
+    // planes) rows around row ty
+    const int flag = rowflag[s1 * Sh::NWF + ty * Sh::WC + wc];
+    const bool bulk = flag != 0;
     int code = 0;
     if (active) {
       acc.st[0] = stage(s0);
