@@ -285,7 +285,10 @@ def run_ours(args, rank, world, local_rank):
                "note": "one e2e iteration = H2D of the full state from pinned memory, "
                        f"{E2E_SEGMENT} steps, D2H of the full state"}
     tiles = sim.tiles()
-    launch_info = {"tiles_compiled": tiles}
+    cur_tile, cur_zchunk = sim.launch()
+    tx, ty, split = tiles[cur_tile]
+    launch_info = {"tiles_compiled": tiles,
+                   "launch": {"tx": tx, "ty": ty, "split": split, "zchunk": cur_zchunk}}
     sim.close()
 
     extra = {}

@@ -187,11 +187,21 @@ ms_status ms_checkpoint(ms_ctx* ctx, void* host_buf, size_t bytes);
 ms_status ms_restore(ms_ctx* ctx, const void* host_buf, size_t bytes);
 
 /* Launch shape: tile (index into ms_tile_shapes) and z-chunk (planes marched
- * per CTA, 3-D only; 0 = automatic). */
+ * per CTA, 3-D only; 0 = automatic; values above 64 are clamped to 64). */
 ms_status ms_set_launch(ms_ctx* ctx, int tile, int zchunk);
 /* Number of tile shapes compiled for this context and their (tx, ty). */
 int ms_tile_count(const ms_ctx* ctx);
 ms_status ms_tile_shape(const ms_ctx* ctx, int tile, int* tx, int* ty);
+/* 1 when tile variant `tile` is a split step (3-D only): a streaming kernel
+ * updates the warp rows whose stencil holds one pure phase and lists the
+ * others, which a second kernel then updates with the full Sec. 2.1 cell
+ * update; results agree with the fused variant of the same tile to FP
+ * rounding.  The split variant allocates a work list of 4 bytes per 32-cell
+ * row segment (once, through the context's allocator) when first selected.
+ * 0 for a fused variant, -1 for a bad index. */
+int ms_tile_split(const ms_ctx* ctx, int tile);
+/* Current launch: tile index and z-chunk (either pointer may be NULL). */
+ms_status ms_get_launch(const ms_ctx* ctx, int* tile, int* zchunk);
 
 /* Autotuner: times every compiled tile shape and a set of z-chunk sizes on
  * the current state (the state is saved and restored), keeps the fastest and,

@@ -100,7 +100,10 @@ __global__ void __launch_bounds__(TX* TY + 32, 1)
         x0 = (it.tile % tiles_x) * TX;
         y0 = (it.tile / tiles_x) * TY;
         c3 = 0;
-        if (fl) load_codes(g, (x0 >> 5) + f_wc, y0 - 1 + f_ay, 0, c3);
+        const int sg = (x0 >> 5) + f_wc, yy = y0 - 1 + f_ay;
+        if (fl && sg < g.segs)
+          c3 = (uint32_t)load_code(g, sg - 1, yy, 0) | ((uint32_t)load_code(g, sg, yy, 0) << 8) |
+               ((uint32_t)load_code(g, sg + 1, yy, 0) << 16);
       };
 #pragma unroll
       for (int i = 0; i < PF; ++i)
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(TX* TY + 32, 1)
             }
         }
         // combined flag of each warp row (rows ay, ay+1, ay+2)
-        const int rf = fl ? (int)combine_codes(c3) : 0;
+        const int rf = fl ? combine_packed_codes(c3) : 0;
         const int up = __shfl_down_sync(0xffffffffu, rf, Sh::WC);
         const int up2 = __shfl_down_sync(0xffffffffu, rf, 2 * Sh::WC);
         if (lane < Sh::NWF) rowflag[s * Sh::NWF + lane] = (uint8_t)((rf == up && up == up2) ? rf : 0);

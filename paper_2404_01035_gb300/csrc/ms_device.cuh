@@ -45,6 +45,11 @@ struct StepArgs {
   const uint8_t* codes_in;
   uint8_t* codes_out;
   int segs;
+  // Interface work list of the split 3-D step: [0] = number of listed warp
+  // rows, [1] = completion ticket of the interface kernel, [2..] = row
+  // indices (z ny + y) segs + segment of the rows that are not bulk.
+  unsigned int* iface;
+  unsigned int iface_cap;
   // scalars
   Real dt, eps, inv_eps, mob, inv_dx, half_inv_dx, quarter_inv_dx, inv_dx2;
   int potential;            // 1 obstacle, 2 well
@@ -202,6 +207,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+// Adds expected transaction bytes to the current phase without arriving.
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -246,6 +257,12 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
 
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory accesses before later
+// async-proxy (TMA) accesses to the same memory.
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // ------------------------------------------------------------ model pieces

@@ -20,6 +20,10 @@ constexpr int kBcHalo = 16;
 // Status bits OR-ed into the device status word.
 constexpr int kStatusNonFinite = 1;
 constexpr int kStatusTimeout = 2;
+constexpr int kStatusLaunch = 4;   // launch geometry beyond a compiled limit (no work done)
+// Planes marched by one CTA of the 3-D step at most (bounds the shared-memory
+// copy of the segment codes a CTA reads).
+constexpr int kMaxZChunk = 64;
 
 // Model constants derived in FP64 from the paper's inputs (Sec. 3).
 struct HostModel {
@@ -50,18 +54,24 @@ struct LaunchGeom {
   int tiles = 0;       // gridDim.x
   int zchunks = 1;     // gridDim.y
   int zchunk = 1;
+  unsigned int* iface = nullptr;   // work list of split kernels (see StepArgs)
+  unsigned int iface_cap = 0;
+  int iface_blocks = 0;            // SMs: the interface grid is this x resident CTAs per SM
 };
 
 // One compiled forward-step instantiation.
 struct StepKernel {
   int dim, np, nm, dtype, tx, ty;
+  int split;   // 1: streaming kernel for bulk rows + interface kernel for the rest
   int smem_bytes;
   size_t args_bytes;
   // Fill the launch-argument blob from the model (all constants).
   void (*fill)(void* blob, const HostModel& m, int zchunk, int* status);
-  // Launch one step: t = time of the input state, out = destination buffer,
-  // codes_in / codes_out = segment codes of the input / output state.
-  cudaError_t (*launch)(const CUtensorMap* tm, void* blob, const HostModel& m, double t, void* out,
+  // Launch one step: tm = tensor map of the input state (tile box), tmi =
+  // its interface-box map (split variants; may be NULL otherwise), t = time
+  // of the input state, out = destination buffer, codes_in / codes_out =
+  // segment codes of the input / output state.
+  cudaError_t (*launch)(const CUtensorMap* tm, const CUtensorMap* tmi, void* blob, const HostModel& m, double t, void* out,
                         const uint8_t* codes_in, uint8_t* codes_out, const LaunchGeom& lg,
                         cudaStream_t st);
   // Recompute the segment codes of a state loaded from outside.

@@ -115,27 +115,46 @@ inline double temp_offset(const HostModel& m, double t) {
   return m.T0 - m.T_ref - m.G * (m.z0 + m.V * t);
 }
 
-template <int DIM, int NP, int NM, class Real, int TX, int TY>
-cudaError_t launch_step(const CUtensorMap* tm, void* blob, const HostModel& m, double t, void* out,
-                        const uint8_t* codes_in, uint8_t* codes_out, const LaunchGeom& lg,
-                        cudaStream_t st) {
+template <int DIM, int NP, int NM, class Real, int TX, int TY, bool SPLIT>
+cudaError_t launch_step(const CUtensorMap* tm, const CUtensorMap* tmi, void* blob, const HostModel& m,
+                        double t, void* out, const uint8_t* codes_in, uint8_t* codes_out,
+                        const LaunchGeom& lg, cudaStream_t st) {
   using A = StepArgs<Real, NP, NM>;
-  using Sh = StepShape<DIM, NP, NM, Real, TX, TY>;
+  using Sh = StepShape<DIM, NP, NM, Real, TX, TY, SPLIT>;
   A& g = *reinterpret_cast<A*>(blob);
   g.out = reinterpret_cast<Real*>(out);
   g.codes_in = codes_in;
   g.codes_out = codes_out;
   g.tz0 = (Real)temp_offset(m, t);
   g.zchunk = lg.zchunk;
-  auto kern = k_gp_step<DIM, NP, NM, Real, TX, TY>;
-  static bool configured = false;   // attribute is per function, set once
+  g.iface = lg.iface;
+  g.iface_cap = lg.iface_cap;
+  if (SPLIT && (!lg.iface || !tmi || lg.iface_blocks < 1)) return cudaErrorInvalidValue;
+  auto kern = k_gp_step<DIM, NP, NM, Real, TX, TY, SPLIT>;
+  static bool configured = false;   // attributes are per function, set once
+  static int iface_per_sm = 0;      // resident interface CTAs per SM
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Sh::SMEM_BYTES);
     if (e != cudaSuccess) return e;
+    if constexpr (SPLIT) {
+      using Si = IfaceShape<NP, NM, Real>;
+      auto ik = k_gp_iface<DIM, NP, NM, Real>;
+      e = cudaFuncSetAttribute(ik, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&iface_per_sm, ik, Si::THREADS, Si::SMEM_BYTES);
+      if (e != cudaSuccess) return e;
+      if (iface_per_sm < 1) iface_per_sm = 1;
+    }
     configured = true;
   }
   kern<<<dim3(lg.tiles, lg.zchunks), Sh::NTHREADS, Sh::SMEM_BYTES, st>>>(*tm, g);
+  if constexpr (SPLIT) {
+    using Si = IfaceShape<NP, NM, Real>;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_gp_iface<DIM, NP, NM, Real><<<lg.iface_blocks * iface_per_sm, Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
+  }
   return cudaGetLastError();
 }
 
@@ -149,7 +168,7 @@ cudaError_t launch_codes(const void* state, const HostModel& m, uint8_t* codes, 
   return cudaGetLastError();
 }
 
-template <int DIM, int NP, int NM, class Real, int TX, int TY>
+template <int DIM, int NP, int NM, class Real, int TX, int TY, bool SPLIT = false>
 StepKernel make_step_kernel() {
   StepKernel k;
   k.dim = DIM;
@@ -158,10 +177,11 @@ StepKernel make_step_kernel() {
   k.dtype = sizeof(Real) == 8 ? 1 : 0;
   k.tx = TX;
   k.ty = TY;
-  k.smem_bytes = StepShape<DIM, NP, NM, Real, TX, TY>::SMEM_BYTES;
+  k.split = SPLIT ? 1 : 0;
+  k.smem_bytes = StepShape<DIM, NP, NM, Real, TX, TY, SPLIT>::SMEM_BYTES;
   k.args_bytes = sizeof(StepArgs<Real, NP, NM>);
   k.fill = &fill_args<DIM, NP, NM, Real>;
-  k.launch = &launch_step<DIM, NP, NM, Real, TX, TY>;
+  k.launch = &launch_step<DIM, NP, NM, Real, TX, TY, SPLIT>;
   k.codes = &launch_codes<DIM, NP, Real>;
   return k;
 }

@@ -44,8 +44,10 @@ struct ms_ctx {
   msgb::LaunchGeom lg;
   std::vector<unsigned char> args;   // launch-argument blob of `kern`
   CUtensorMap tm[2];
+  CUtensorMap tmi[2];   // interface-box maps of buf[0] / buf[1] (split variants)
   void* buf[2] = {nullptr, nullptr};
   uint8_t* codes[2] = {nullptr, nullptr};   // segment codes of buf[0] / buf[1]
+  unsigned int* iface = nullptr;            // work list of the split step (lazily allocated)
   size_t state_bytes = 0;
   int cur = 0;
   int64_t step = 0;
@@ -69,7 +71,8 @@ ms_status cuda_fail(ms_ctx* c, cudaError_t e, const char* what);
 ms_status launch_one_step(ms_ctx* c);
 ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk);
 ms_status refresh_codes(ms_ctx* c);   // segment codes of the current state
-bool encode_state_map(CUtensorMap* tm, void* base, const HostModel& m, int nf, int tx, int ty);
+// Tiled map of a padded state: box of (tx + 2H) x (ty + 2) x bz planes x nf fields.
+bool encode_state_map(CUtensorMap* tm, void* base, const HostModel& m, int nf, int tx, int ty, int bz = 1);
 void set_layout(HostModel& m);   // padded layout of one state buffer
 std::vector<const StepKernel*> step_variants(int dim, int np, int nm, int dtype);
 cudaError_t fill_ghosts(const HostModel& m, void* buf, int nf, cudaStream_t st);

@@ -280,7 +280,7 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool encode_state_map(CUtensorMap* tm, void* base, const HostModel& m, int nf, int tx, int ty) {
+bool encode_state_map(CUtensorMap* tm, void* base, const HostModel& m, int nf, int tx, int ty, int bz) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const int s = m.dtype == MS_F64 ? 8 : 4;
@@ -288,7 +288,7 @@ bool encode_state_map(CUtensorMap* tm, void* base, const HostModel& m, int nf, i
   cuuint64_t dims[4] = {(cuuint64_t)m.pitch, (cuuint64_t)m.nyp, (cuuint64_t)m.nzp, (cuuint64_t)nf};
   cuuint64_t strides[3] = {(cuuint64_t)m.pitch * s, (cuuint64_t)m.pitch * m.nyp * s,
                            (cuuint64_t)m.fstride * s};
-  cuuint32_t box[4] = {(cuuint32_t)(tx + 2 * H), (cuuint32_t)(ty + 2), 1u, (cuuint32_t)nf};
+  cuuint32_t box[4] = {(cuuint32_t)(tx + 2 * H), (cuuint32_t)(ty + 2), (cuuint32_t)bz, (cuuint32_t)nf};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = fn(tm, m.dtype == MS_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                   4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -425,22 +425,38 @@ int default_zchunk(const HostModel& m, const StepKernel& k) {
 }
 
 ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk) {
+  if (k->split && !c->iface) {
+    // work list of the split step: count, ticket and one entry per warp row
+    const size_t cap = (size_t)segments(c->m) * c->m.ny * c->m.nz;
+    if (cap > 0xFFFFFFF0ull) return fail(c, MS_ERR_UNSUPPORTED, "grid too large for the split step");
+    c->iface = static_cast<unsigned int*>(dev_alloc(c->hook, (cap + 2) * sizeof(unsigned int)));
+    if (!c->iface) return fail(c, MS_ERR_OOM, "interface work-list allocation failed");
+    cudaError_t e = cudaMemsetAsync(c->iface, 0, 2 * sizeof(unsigned int), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "work-list reset");
+    c->lg.iface = c->iface;
+    c->lg.iface_cap = (unsigned int)cap;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->lg.iface_blocks = sms;
+  }
   c->kern = k;
-  c->lg.zchunk = c->m.dim == 3 ? (zchunk > 0 ? std::min(zchunk, c->m.nz) : default_zchunk(c->m, *k)) : 1;
+  c->lg.zchunk = c->m.dim == 3 ? std::min(zchunk > 0 ? std::min(zchunk, c->m.nz) : default_zchunk(c->m, *k), kMaxZChunk) : 1;
   c->lg.tiles = ((c->m.nx + k->tx - 1) / k->tx) * ((c->m.ny + k->ty - 1) / k->ty);
   c->lg.zchunks = c->m.dim == 3 ? (c->m.nz + c->lg.zchunk - 1) / c->lg.zchunk : 1;
   c->args.assign(k->args_bytes, 0);
   k->fill(c->args.data(), c->m, c->lg.zchunk, c->status);
   const int nf = c->m.N + c->m.NM;
   for (int b = 0; b < 2; ++b)
-    if (!encode_state_map(&c->tm[b], c->buf[b], c->m, nf, k->tx, k->ty))
+    if (!encode_state_map(&c->tm[b], c->buf[b], c->m, nf, k->tx, k->ty) ||
+        (k->split && !encode_state_map(&c->tmi[b], c->buf[b], c->m, nf, 32, 1, 3)))
       return fail(c, MS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return MS_OK;
 }
 
 ms_status launch_one_step(ms_ctx* c) {
   const int src = c->cur, dst = 1 - c->cur;
-  cudaError_t e = c->kern->launch(&c->tm[src], c->args.data(), c->m, c->t, c->buf[dst], c->codes[src],
+  cudaError_t e = c->kern->launch(&c->tm[src], &c->tmi[src], c->args.data(), c->m, c->t, c->buf[dst], c->codes[src],
                                   c->codes[dst], c->lg, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
   c->cur = dst;
@@ -555,6 +571,7 @@ void ms_destroy(ms_ctx* c) {
     dev_free(c->hook, c->codes[b]);
   }
   dev_free(c->hook, c->small);
+  dev_free(c->hook, c->iface);
   if (c->diag_host) cudaFreeHost(c->diag_host);
   delete c;
 }
@@ -645,6 +662,7 @@ static ms_status read_status(ms_ctx* c) {
   MS_CUDA(c, cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   MS_CUDA(c, cudaStreamSynchronize(c->stream));
   if (st & kStatusTimeout) return fail(c, MS_ERR_TIMEOUT, "a bounded device wait timed out");
+  if (st & kStatusLaunch) return fail(c, MS_ERR_BOUNDS, "launch geometry beyond a compiled limit");
   if (st & kStatusNonFinite) return fail(c, MS_ERR_NONFINITE, "non-finite values in the state");
   return MS_OK;
 }
@@ -725,6 +743,24 @@ ms_status ms_restore(ms_ctx* c, const void* host_buf, size_t bytes) {
   c->step = h.step;
   c->t = h.t;
   ms_reset_extra(c);
+  return MS_OK;
+}
+
+int ms_tile_split(const ms_ctx* c, int tile) {
+  if (!c) return -1;
+  auto v = step_variants(c->m.dim, c->m.N, c->m.NM, c->m.dtype);
+  if (tile < 0 || tile >= (int)v.size()) return -1;
+  return v[tile]->split;
+}
+
+ms_status ms_get_launch(const ms_ctx* c, int* tile, int* zchunk) {
+  if (!c) return fail(nullptr, MS_ERR_ARG, "ctx is NULL");
+  auto v = step_variants(c->m.dim, c->m.N, c->m.NM, c->m.dtype);
+  int idx = -1;
+  for (size_t i = 0; i < v.size(); ++i)
+    if (v[i] == c->kern) idx = (int)i;
+  if (tile) *tile = idx;
+  if (zchunk) *zchunk = c->lg.zchunk;
   return MS_OK;
 }
 

@@ -31,7 +31,7 @@ struct Halo {
   static constexpr int H = 16 / sizeof(Real);   // elements per 16 bytes
 };
 
-template <int DIM, int NP, int NM, class Real, int TX, int TY>
+template <int DIM, int NP, int NM, class Real, int TX, int TY, bool SPLIT = false>
 struct StepShape {
   static constexpr int NF = NP + NM;
   static constexpr int H = Halo<Real>::H;
@@ -45,21 +45,54 @@ struct StepShape {
   static constexpr int STAGE_BYTES = STAGE_ELEMS * (int)sizeof(Real);
   static constexpr int STAGE_STRIDE = (STAGE_BYTES + 127) / 128 * 128;
   // Ring depth: as many planes in flight as a shared-memory budget allows
-  // (two CTAs per SM for up to 5 fields, one for more), 4..12 stages.
-  static constexpr int RING_BUDGET = NF <= 5 ? 100 * 1024 : 190 * 1024;
+  // (two CTAs per SM for up to 5 fields, one for more; the streaming kernel
+  // of the split step, which holds few registers, one CTA more), 4..12 stages.
+  static constexpr int RING_BUDGET =
+      NF <= 5 ? (SPLIT ? 64 * 1024 : 100 * 1024) : (SPLIT ? 100 * 1024 : 190 * 1024);
   static constexpr int NST_RAW = RING_BUDGET / STAGE_STRIDE;
   static constexpr int NST = DIM == 3 ? (NST_RAW < 4 ? 4 : (NST_RAW > 12 ? 12 : NST_RAW)) : 1;
   static constexpr int NFL = SY * WC;                   // row flags per plane
   static constexpr int NWF = TY * WC;                   // combined flags per plane (one per warp row)
   static constexpr int FLAG_BYTES = (NST * NWF + 15) / 16 * 16;   // one flag set per stage
+  static constexpr int CSEG = WC + 2;                   // segments per halo row (one each side)
+  static constexpr int MAXPL = DIM == 3 ? kMaxZChunk + 2 : 1;     // ring entries of a CTA at most
+  static constexpr int CODE_ENTRIES = MAXPL * SY * CSEG;          // segment codes a CTA reads
+  static constexpr int CODE_BYTES = (CODE_ENTRIES + 15) / 16 * 16;
+  static constexpr int CODE_ITERS = (CODE_ENTRIES + NTHREADS - 1) / NTHREADS;
   static constexpr int OFF_FLAG = NST * STAGE_STRIDE;
-  static constexpr int OFF_BAR = OFF_FLAG + FLAG_BYTES;            // full[NST], empty[NST]
+  static constexpr int OFF_CODE = OFF_FLAG + FLAG_BYTES;
+  static constexpr int OFF_BAR = OFF_CODE + CODE_BYTES;            // full[NST], empty[NST]
   static constexpr int OFF_ABORT = OFF_BAR + 2 * NST * 8;
   static constexpr int SMEM_BYTES = OFF_ABORT + 16 + 128;         // + alignment slack
-  static constexpr int PF = 4;                                     // planes of codes prefetched
+  // CTAs per SM that the shared memory admits (228 KB per SM, 1 KB reserved per CTA)
+  static constexpr int SMEM_CTAS = (228 * 1024) / (SMEM_BYTES + 1024);
+  static constexpr int SPLIT_BLOCKS = SMEM_CTAS < 1 ? 1 : (SMEM_CTAS > 4 ? 4 : SMEM_CTAS);
   static_assert(TX % 32 == 0, "a warp must cover cells of a single row");
   static_assert(NFL <= 32, "the producer warp holds one row flag per lane");
 };
+
+// Phases present anywhere in the 19-point (3-D) / 9-point (2-D) stencil of
+// an accessor's centre cell (bit a set when phi_a != 0 somewhere).
+template <int DIM, int NP, class Acc>
+__device__ __forceinline__ uint32_t stencil_mask(const Acc& A) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    bool any = false;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) any = any || A.phi(a, dx, dy, 0) != 0;
+    if constexpr (DIM == 3) {
+#pragma unroll
+      for (int dz = -1; dz <= 1; dz += 2)
+        any = any || A.phi(a, 0, 0, dz) != 0 || A.phi(a, -1, 0, dz) != 0 || A.phi(a, 1, 0, dz) != 0 ||
+              A.phi(a, 0, -1, dz) != 0 || A.phi(a, 0, 1, dz) != 0;
+    }
+    m |= (any ? 1u : 0u) << a;
+  }
+  return m;
+}
 
 // Stencil accessor over the shared-memory ring (planes k-1, k, k+1).
 template <int DIM, int NP, int NM, class Real, int TX, int TY>
@@ -75,27 +108,7 @@ struct SmemAcc {
   __device__ __forceinline__ Real mu(int i, int dx, int dy, int dz) const {
     return st[1 + dz][(NP + i) * Sh::SY * Sh::SX + sidx + dy * Sh::SX + dx];
   }
-  // phases present anywhere in the 19-point (3-D) / 9-point (2-D) stencil
-  __device__ __forceinline__ uint32_t mask() const {
-    uint32_t m = 0;
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      bool any = false;
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) any = any || phi(a, dx, dy, 0) != Real(0);
-      if constexpr (DIM == 3) {
-#pragma unroll
-        for (int dz = -1; dz <= 1; dz += 2)
-          any = any || phi(a, 0, 0, dz) != Real(0) || phi(a, -1, 0, dz) != Real(0) ||
-                phi(a, 1, 0, dz) != Real(0) || phi(a, 0, -1, dz) != Real(0) ||
-                phi(a, 0, 1, dz) != Real(0);
-      }
-      m |= (any ? 1u : 0u) << a;
-    }
-    return m;
-  }
+  __device__ __forceinline__ uint32_t mask() const { return stencil_mask<DIM, NP>(*this); }
   // cell mobility M = sum_a h_a D^a chi^a of a neighbour, from its phi
   __device__ __forceinline__ void mobility(int dx, int dy, int dz, Real* M) const {
     Real ph[NP];
@@ -113,15 +126,12 @@ __device__ __forceinline__ int bc_map(int i, int n, int bc) {
   return i < 0 ? 0 : n - 1;
 }
 
-// Row flag of (row y, plane z) for the warp covering segment s: the pure
-// phase + 1 when segments s-1, s, s+1 of that row are all that pure phase.
+// Segment code of (segment s, row y, plane z) of the input state, with the
+// boundary mapping of each axis (out-of-range indices give the periodic image
+// or the adjacent interior segment, row or plane).
 template <class Real, int NP, int NM>
-__device__ __forceinline__ void load_codes(const StepArgs<Real, NP, NM>& g, int s, int y, int z,
-                                           uint32_t& c3) {
-  if (s >= g.segs) {   // no cell of this warp column exists
-    c3 = 0;
-    return;
-  }
+__device__ __forceinline__ uint8_t load_code(const StepArgs<Real, NP, NM>& g, int s, int y, int z) {
+  const int ss = bc_map(s, g.segs, g.bc[0]);
   const int yy = bc_map(y, g.ny, g.bc[1]);
   // plane index in the code array (3-D arrays carry one ghost plane per side,
   // filled by the halo exchange when that face is an internal cut)
@@ -132,16 +142,17 @@ __device__ __forceinline__ void load_codes(const StepArgs<Real, NP, NM>& g, int 
     zz = z < 0 ? 0 : g.nz + 1;
   else
     zz = bc_map(z, g.nz, g.bc[2]) + g.zoff;
-  const uint8_t* row = g.codes_in + ((long long)zz * g.ny + yy) * g.segs;
-  const uint32_t a = row[bc_map(s - 1, g.segs, g.bc[0])];
-  const uint32_t b = row[s];
-  const uint32_t c = row[bc_map(s + 1, g.segs, g.bc[0])];
-  c3 = a | (b << 8) | (c << 16);
+  return __ldg(g.codes_in + ((long long)zz * g.ny + yy) * g.segs + ss);
 }
 
-__device__ __forceinline__ uint8_t combine_codes(uint32_t c3) {
+// Row flag: the pure phase + 1 when three adjacent segments agree on it.
+__device__ __forceinline__ int combine_codes(const uint8_t* c) {
+  return (c[0] == c[1] && c[1] == c[2]) ? (int)c[1] : 0;
+}
+// The same for three codes packed in the low bytes of a word.
+__device__ __forceinline__ int combine_packed_codes(uint32_t c3) {
   const uint32_t a = c3 & 0xFF, b = (c3 >> 8) & 0xFF, c = (c3 >> 16) & 0xFF;
-  return (a == b && b == c) ? (uint8_t)b : (uint8_t)0;
+  return (a == b && b == c) ? (int)b : 0;
 }
 
 // Bulk cell (whole stencil is the pure phase l): phi unchanged, and
@@ -216,10 +227,12 @@ struct MinBlocks {
   static constexpr int value = (NP <= 4 && NT <= 256) ? 2 : 1;
 };
 
-template <int DIM, int NP, int NM, class Real, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
+template <int DIM, int NP, int NM, class Real, int TX, int TY, bool SPLIT>
+__global__ void __launch_bounds__(TX* TY + 32, SPLIT ? StepShape<DIM, NP, NM, Real, TX, TY, true>::SPLIT_BLOCKS
+                                                     : MinBlocks<NP, TX * TY>::value)
     k_gp_step(const __grid_constant__ CUtensorMap tm, const __grid_constant__ StepArgs<Real, NP, NM> g) {
-  using Sh = StepShape<DIM, NP, NM, Real, TX, TY>;
+  static_assert(!SPLIT || DIM == 3, "the split step streams planes along z");
+  using Sh = StepShape<DIM, NP, NM, Real, TX, TY, SPLIT>;
   constexpr int NST = Sh::NST;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
@@ -239,6 +252,10 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
   const int ze = DIM == 3 ? min(g.nz, zb + g.zchunk) : 1;
   const int nplanes = DIM == 3 ? (ze - zb + 2) : 1;   // ring entries j <-> plane zb - 1 + j
   const int nk = DIM == 3 ? (ze - zb) : 1;             // planes computed
+  if (nplanes > Sh::MAXPL) {   // the host clamps z-chunks; never touch smem beyond its size
+    if (tid == 0) atomicOr(g.status, kStatusLaunch);
+    return;
+  }
 
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -248,45 +265,69 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
     *abort_flag = 0;
     mbar_fence_init();
   }
-  __syncthreads();   // the only CTA-wide barrier: roles split below
+  __syncthreads();
+
+  // The producer starts the first ring entries (their flags are published
+  // later by a plain arrive), then every thread loads the segment codes of
+  // this CTA into shared memory: all loads in flight together, once.
+  const int bx = x0 + g.xoff - Sh::H;   // TMA box origin (16-byte aligned)
+  const int npre = nplanes < NST ? nplanes : NST;
+  if (tid == Sh::NT) {
+    prefetch_tensormap(&tm);
+    for (int j = 0; j < npre; ++j) {
+      mbar_expect_tx_only(&full[j], Sh::STAGE_BYTES);
+      const int zc = DIM == 3 ? (zb - 1 + j + g.zoff) : 0;
+      tma_load_4d(stage(j), &tm, &full[j], bx, y0, zc, 0);
+    }
+  }
+  {
+    const int seg0 = x0 >> 5;
+    const int ncode = nplanes * Sh::SY * Sh::CSEG;
+    uint8_t v[Sh::CODE_ITERS];
+#pragma unroll
+    for (int it = 0; it < Sh::CODE_ITERS; ++it) {
+      const int e = tid + it * Sh::NTHREADS;
+      v[it] = 0;
+      if (e < ncode) {
+        const int k = e % Sh::CSEG, r = e / Sh::CSEG;
+        const int ay = r % Sh::SY, j = r / Sh::SY;
+        v[it] = load_code(g, seg0 - 1 + k, y0 - 1 + ay, DIM == 3 ? zb - 1 + j : 0);
+      }
+    }
+    uint8_t* scode = smem + Sh::OFF_CODE;
+#pragma unroll
+    for (int it = 0; it < Sh::CODE_ITERS; ++it) {
+      const int e = tid + it * Sh::NTHREADS;
+      if (e < ncode) scode[e] = v[it];
+    }
+  }
+  __syncthreads();   // the last CTA-wide barrier: roles split below
 
   if (tid >= Sh::NT) {
     // ---------------- producer warp: TMA loads + row flags of every entry
-    const int bx = x0 + g.xoff - Sh::H;   // TMA box origin (16-byte aligned)
     const int f_ay = lane / Sh::WC, f_wc = lane % Sh::WC;
-    const int f_seg = (x0 >> 5) + f_wc;
-    const bool fl = lane < Sh::NFL;
-    auto plane_of = [&](int j) { return DIM == 3 ? zb - 1 + j : 0; };
-    uint32_t pre[Sh::PF];
-#pragma unroll
-    for (int i = 0; i < Sh::PF; ++i) {
-      pre[i] = 0;
-      if (fl && i < nplanes) load_codes(g, f_seg, y0 - 1 + f_ay, plane_of(i), pre[i]);
-    }
-    if (lane == 0) prefetch_tensormap(&tm);
-    int issued = 0;
+    const bool fl = lane < Sh::NFL && (x0 >> 5) + f_wc < g.segs;   // warp column exists
+    const uint8_t* scode = smem + Sh::OFF_CODE;
+    int issued = npre, arrived = 0;
     bool ok = true;
     // row flags (lane = halo'ed row ay, warp column wc) of entries j-2, j-1, j
     int rf2 = 0, rf1 = 0, rf0 = 0;
     for (int j = 0; j < nplanes; ++j) {
       const int s = j % NST;
-      if (j >= NST) ok = ok && mbar_wait_bounded(&empty[s], ((j / NST) - 1) & 1);
-      ok = ok && *abort_flag == 0;
-      if (__any_sync(0xffffffffu, !ok)) break;
-      uint32_t c3 = 0;
-#pragma unroll
-      for (int i = 0; i < Sh::PF; ++i)
-        if (i == j % Sh::PF) c3 = pre[i];
+      if (j >= NST) {
+        ok = ok && mbar_wait_bounded(&empty[s], ((j / NST) - 1) & 1);
+        ok = ok && *abort_flag == 0;
+        if (__any_sync(0xffffffffu, !ok)) break;
+        if (lane == 0) {
+          mbar_expect_tx_only(&full[s], Sh::STAGE_BYTES);
+          const int zc = DIM == 3 ? (zb - 1 + j + g.zoff) : 0;
+          tma_load_4d(stage(s), &tm, &full[s], bx, y0, zc, 0);
+        }
+        issued = j + 1;
+      }
       rf2 = rf1;
       rf1 = rf0;
-      rf0 = fl ? (int)combine_codes(c3) : 0;
-      if (fl && j + Sh::PF < nplanes) {
-        uint32_t nc;
-        load_codes(g, f_seg, y0 - 1 + f_ay, plane_of(j + Sh::PF), nc);
-#pragma unroll
-        for (int i = 0; i < Sh::PF; ++i)
-          if (i == j % Sh::PF) pre[i] = nc;
-      }
+      rf0 = fl ? combine_codes(scode + (j * Sh::SY + f_ay) * Sh::CSEG + f_wc) : 0;
       // Combined flag of the centre entry (j-1 in 3-D, j in 2-D) for each warp
       // row: non-zero only if the 3 rows x 3 planes around it are one phase.
       {
@@ -300,17 +341,17 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
       __syncwarp();
       if (lane == 0) {
         __threadfence_block();
-        mbar_expect_tx(&full[s], Sh::STAGE_BYTES);   // arrive (release) + expected bytes
-        const int zc = DIM == 3 ? (zb - 1 + j + g.zoff) : 0;
-        tma_load_4d(stage(s), &tm, &full[s], bx, y0, zc, 0);
+        mbar_arrive(&full[s]);   // publishes the flags (release); the data lands by complete_tx
       }
-      issued = j + 1;
+      arrived = j + 1;
     }
     if (!ok && lane == 0) {
-      // abort: record it, then wait (bounded) for the copies still in flight
-      // so that no TMA writes into shared memory after the CTA has exited
+      // abort: record it, complete the arrivals of entries already issued,
+      // then wait (bounded) for the copies still in flight so that no TMA
+      // writes into shared memory after the CTA has exited
       atomicOr(g.status, kStatusTimeout);
       *abort_flag = 1;
+      for (int j = arrived; j < issued; ++j) mbar_arrive(&full[j % NST]);
       for (int s = 0; s < NST; ++s) {
         if (issued <= s) continue;
         const int j = s + ((issued - 1 - s) / NST) * NST;
@@ -348,6 +389,25 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
     const int flag = rowflag[s1 * Sh::NWF + ty * Sh::WC + wc];
     const bool bulk = flag != 0;
     int code = 0;
+    if constexpr (SPLIT) {
+      // rows that are not bulk go to the interface kernel's work list
+      if (!bulk) {
+        if (lane == 0) {
+          if (y < g.ny && seg < g.segs) {
+            const unsigned int i = atomicAdd(&g.iface[0], 1u);
+            if (i < g.iface_cap) g.iface[2 + i] = (unsigned int)(((long long)z * g.ny + y) * g.segs + seg);
+          }
+          mbar_arrive(&empty[s0]);   // this warp is done with entry k
+        }
+        s0 = s1;
+        s1 = s2;
+        if (++s2 == NST) {
+          s2 = 0;
+          par2 ^= 1u;
+        }
+        continue;
+      }
+    }
     if (active) {
       acc.st[0] = stage(s0);
       acc.st[1] = stage(s1);
@@ -356,7 +416,7 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
       if (bulk) {
         bulk_cell<DIM, NP, NM, Real>(acc, g, flag - 1, pn, mn);
         code = flag;
-      } else {
+      } else if constexpr (!SPLIT) {
         DiffPrm<Real, StepArgs<Real, NP, NM>::P> dp;
         dp.mob = g.mob;
 #pragma unroll
@@ -387,6 +447,162 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
         s2 = 0;
         par2 ^= 1u;
       }
+    }
+  }
+}
+
+// Interface kernel of the split 3-D step (shape of its shared memory).  Each
+// warp owns two buffers of one TMA box: 32 + 2H cells x 3 rows x 3 planes x
+// all fields around one listed 32-cell row, so the next row is in flight
+// while the current one is updated.
+template <int NP, int NM, class Real>
+struct IfaceShape {
+  static constexpr int NF = NP + NM;
+  static constexpr int H = Halo<Real>::H;
+  static constexpr int BX = 32 + 2 * H;                 // box extent along x
+  static constexpr int BOX_ELEMS = NF * 9 * BX;
+  static constexpr int BOX_BYTES = BOX_ELEMS * (int)sizeof(Real);
+  static constexpr int BOX_STRIDE = (BOX_BYTES + 127) / 128 * 128;
+  static constexpr int WARPS = 4;                       // warps per CTA
+  static constexpr int THREADS = 32 * WARPS;
+  static constexpr int OFF_BAR = WARPS * 2 * BOX_STRIDE;
+  static constexpr int SMEM_BYTES = OFF_BAR + WARPS * 2 * 8 + 128;   // + alignment slack
+  static constexpr int MIN_BLOCKS = NP <= 4 ? 3 : 2;
+};
+
+// Stencil accessor over one interface box ([field][plane][row][x]).
+template <int DIM, int NP, int NM, class Real>
+struct BoxAcc {
+  using Sh = IfaceShape<NP, NM, Real>;
+  const Real* s;
+  const StepArgs<Real, NP, NM>* g;
+  int sidx;   // centre of this lane's cell: plane 1, row 1, x = H + lane
+
+  __device__ __forceinline__ Real ld(int f, int dx, int dy, int dz) const {
+    return s[f * (9 * Sh::BX) + sidx + dz * (3 * Sh::BX) + dy * Sh::BX + dx];
+  }
+  __device__ __forceinline__ Real phi(int a, int dx, int dy, int dz) const { return ld(a, dx, dy, dz); }
+  __device__ __forceinline__ Real mu(int i, int dx, int dy, int dz) const { return ld(NP + i, dx, dy, dz); }
+  __device__ __forceinline__ uint32_t mask() const { return stencil_mask<DIM, NP>(*this); }
+  __device__ __forceinline__ void mobility(int dx, int dy, int dz, Real* M) const {
+    Real ph[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) ph[a] = phi(a, dx, dy, dz);
+    cell_mobility<NP, NM>(ph, g->DX, M);
+  }
+};
+
+// Interface kernel of the split 3-D step: the full cell update of every warp
+// row the streaming kernel listed (32 cells of one row of one plane per
+// warp), from a TMA box of the input state; writes phi, mu, their ghost
+// images and the row's segment code.  The last CTA to finish clears the list
+// for the next step (ticket in iface[1]), so the pair of launches can be
+// replayed from a CUDA graph.
+template <int DIM, int NP, int NM, class Real>
+__global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<NP, NM, Real>::MIN_BLOCKS)
+    k_gp_iface(const __grid_constant__ CUtensorMap tmi, const __grid_constant__ StepArgs<Real, NP, NM> g) {
+  static_assert(DIM == 3, "the interface list is built by the 3-D streaming kernel");
+  using Sh = IfaceShape<NP, NM, Real>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  __shared__ unsigned int s_count;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR) + 2 * wid;
+  Real* buf0 = reinterpret_cast<Real*>(smem + (2 * wid) * Sh::BOX_STRIDE);
+  if (threadIdx.x == 0) s_count = min(*(volatile unsigned int*)&g.iface[0], g.iface_cap);
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+    prefetch_tensormap(&tmi);
+  }
+  __syncthreads();
+  const unsigned int count = s_count;
+  const unsigned int stride = gridDim.x * Sh::WARPS;
+  DiffPrm<Real, StepArgs<Real, NP, NM>::P> dp;
+  dp.mob = g.mob;
+#pragma unroll
+  for (int p = 0; p < StepArgs<Real, NP, NM>::P; ++p) dp.delta[p] = g.delta[p];
+
+  // row r = (z ny + y) segs + segment  ->  box origin (x, y - 1, z - 1 in padded coordinates)
+  auto issue = [&](unsigned int i, int b) {
+    const unsigned int r = g.iface[2 + i];
+    const int sg = (int)(r % (unsigned int)g.segs);
+    const unsigned int zy = r / (unsigned int)g.segs;
+    const int y = (int)(zy % (unsigned int)g.ny), z = (int)(zy / (unsigned int)g.ny);
+    fence_proxy_async_shared();
+    mbar_expect_tx(&bar[b], Sh::BOX_BYTES);
+    tma_load_4d(reinterpret_cast<unsigned char*>(buf0) + b * Sh::BOX_STRIDE, &tmi, &bar[b],
+                32 * sg + g.xoff - Sh::H, y, z + g.zoff - 1, 0);
+  };
+  bool pending[2] = {false, false};
+  uint32_t phase[2] = {0u, 0u};
+  bool aborted = false;
+  unsigned int i = blockIdx.x * Sh::WARPS + wid;
+  if (i < count && lane == 0) issue(i, 0);
+  pending[0] = i < count;
+  int b = 0;
+  while (i < count) {
+    const unsigned int nxt = i + stride;
+    if (nxt < count) {
+      if (lane == 0) issue(nxt, b ^ 1);
+      pending[b ^ 1] = true;
+    }
+    const bool ok = mbar_wait_bounded(&bar[b], phase[b]);
+    if (!__all_sync(0xffffffffu, ok)) {
+      aborted = true;
+      break;
+    }
+    pending[b] = false;
+    phase[b] ^= 1u;
+    const unsigned int r = g.iface[2 + i];
+    const int sg = (int)(r % (unsigned int)g.segs);
+    const unsigned int zy = r / (unsigned int)g.segs;
+    const int y = (int)(zy % (unsigned int)g.ny), z = (int)(zy / (unsigned int)g.ny);
+    const int x = 32 * sg + lane;
+    const bool active = x < g.nx;
+    int code = 0;
+    if (active) {
+      BoxAcc<DIM, NP, NM, Real> acc;
+      acc.s = reinterpret_cast<const Real*>(reinterpret_cast<unsigned char*>(buf0) + b * Sh::BOX_STRIDE);
+      acc.g = &g;
+      acc.sidx = 3 * Sh::BX + Sh::BX + Sh::H + lane;
+      Real pn[NP], mn[NM];
+      gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, z + g.zorg, pn, mn);
+      uint32_t nzm = 0, one = 0;
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        nzm |= (pn[a] != Real(0) ? 1u : 0u) << a;
+        one |= (pn[a] == Real(1) ? 1u : 0u) << a;
+      }
+      code = (__popc(nzm) == 1 && nzm == one) ? __ffs(nzm) : 0;
+      store_cell<DIM>(g, x, y, z, pn, mn);
+    }
+    const int ref = __shfl_sync(0xffffffffu, code, 0);
+    const bool same = __all_sync(0xffffffffu, !active || code == ref);
+    if (lane == 0)
+      g.codes_out[((long long)(z + g.zoff) * g.ny + y) * g.segs + sg] = same ? (uint8_t)ref : (uint8_t)0;
+    __syncwarp();   // every lane is done with buffer b before it is refilled
+    b ^= 1;
+    i = nxt;
+  }
+  if (aborted) {
+    // a copy did not complete in time: record it and wait (bounded) for the
+    // copies still in flight before the CTA exits
+    if (lane == 0) {
+      atomicOr(g.status, kStatusTimeout);
+      for (int k = 0; k < 2; ++k)
+        if (pending[k]) mbar_wait_bounded(&bar[k], phase[k]);
+    }
+  }
+  // every CTA read the count before taking its ticket
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&g.iface[1], 1u) == gridDim.x - 1) {
+      g.iface[0] = 0u;
+      g.iface[1] = 0u;
     }
   }
 }

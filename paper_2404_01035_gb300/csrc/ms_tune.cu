@@ -31,7 +31,8 @@ std::string cache_key(const ms_ctx* c) {
   return buf;
 }
 
-// Entries are lines of the form   "key": {"tx": 32, "ty": 8, "zchunk": 16, "ms": 0.1},
+// Entries are lines of the form
+//   "key": {"tx": 32, "ty": 8, "split": 1, "zchunk": 16, "ms": 0.1},
 std::map<std::string, std::string> read_cache(const char* path) {
   std::map<std::string, std::string> m;
   std::ifstream in(path);
@@ -73,11 +74,12 @@ extern "C" ms_status ms_tune(ms_ctx* c, const char* cache_path, int steps, doubl
   if (cache_path) {
     cache = read_cache(cache_path);
     auto it = cache.find(key);
-    int tx, ty, zc;
+    int tx, ty, zc, split = 0;
     if (it != cache.end() && parse_int(it->second, "tx", &tx) && parse_int(it->second, "ty", &ty) &&
         parse_int(it->second, "zchunk", &zc)) {
+      parse_int(it->second, "split", &split);
       for (auto* v : variants)
-        if (v->tx == tx && v->ty == ty) {
+        if (v->tx == tx && v->ty == ty && v->split == split) {
           if (best_ms) {
             size_t p = it->second.find("\"ms\"");
             double ms = 0;
@@ -152,8 +154,8 @@ extern "C" ms_status ms_tune(ms_ctx* c, const char* cache_path, int steps, doubl
   if (best_ms) *best_ms = best_t;
   if (cache_path) {
     char buf[160];
-    std::snprintf(buf, sizeof buf, "{\"tx\": %d, \"ty\": %d, \"zchunk\": %d, \"ms\": %.6f}", best->tx, best->ty,
-                  c->lg.zchunk, best_t);
+    std::snprintf(buf, sizeof buf, "{\"tx\": %d, \"ty\": %d, \"split\": %d, \"zchunk\": %d, \"ms\": %.9g}",
+                  best->tx, best->ty, best->split, c->lg.zchunk, best_t);
     cache[key] = buf;
     write_cache(cache_path, cache);
   }

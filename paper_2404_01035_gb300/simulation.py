@@ -233,13 +233,20 @@ class Simulation:
 
     # ----------------------------------------------------------- launch shape
     def tiles(self):
+        """Compiled launch variants: (tx, ty, split) per tile index."""
         n = lib().ms_tile_count(self.h)
         out = []
         for i in range(n):
             tx, ty = ctypes.c_int(), ctypes.c_int()
             lib().ms_tile_shape(self.h, i, ctypes.byref(tx), ctypes.byref(ty))
-            out.append((tx.value, ty.value))
+            out.append((tx.value, ty.value, int(lib().ms_tile_split(self.h, i))))
         return out
+
+    def launch(self):
+        """Current launch: (tile index, z-chunk)."""
+        t, z = ctypes.c_int(), ctypes.c_int()
+        self._c(lib().ms_get_launch(self.h, ctypes.byref(t), ctypes.byref(z)))
+        return t.value, z.value
 
     def set_launch(self, tile: int, zchunk: int = 0):
         self._c(lib().ms_set_launch(self.h, int(tile), int(zchunk)))
