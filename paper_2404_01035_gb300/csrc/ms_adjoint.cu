@@ -393,17 +393,18 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
       e = c->kern->codes(slots, m, c->codes[1 - cur_state], st);
       if (e != cudaSuccess) return cuda_fail(c, e, "segment codes");
     }
+    // the recompute writes into fresh slots: nothing to keep from them
+    LaunchGeom lg = c->lg;
+    lg.reuse_prev = 0;
     int cs = 1 - cur_state;
     for (int k = 1; k < len; ++k) {
       CUtensorMap tm, tmi;
       char* src = slots + (size_t)(k - 1) * c->state_bytes;
-      if (!encode_state_map(&tm, src, m, NF, c->kern->tx, c->kern->ty) ||
-          (c->kern->split && !encode_state_map(&tmi, src, m, NF, 32, 1, 3)))
-        return fail(c, MS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+      if (!encode_step_maps(*c->kern, &tm, &tmi, src, m)) return fail(c, MS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
       const double t = m.t0 + (double)(s0 + k - 1) * m.dt;
       e = c->kern->launch(&tm, &tmi, c->args.data(), m, t,
                           slots + (size_t)k * c->state_bytes, c->codes[cs],
-                          c->codes[1 - cs], c->lg, st);
+                          c->codes[1 - cs], lg, st);
       if (e != cudaSuccess) return cuda_fail(c, e, "segment recompute");
       cs = 1 - cs;
     }

@@ -50,6 +50,10 @@ struct StepArgs {
   // indices (z ny + y) segs + segment of the rows that are not bulk.
   unsigned int* iface;
   unsigned int iface_cap;
+  // 1 when the output buffer holds the state one step before the input
+  // (ping-pong stepping), so codes_out still describe it before they are
+  // overwritten: bulk rows whose pure phase is unchanged then skip phi.
+  int reuse_prev;
   // scalars
   Real dt, eps, inv_eps, mob, inv_dx, half_inv_dx, quarter_inv_dx, inv_dx2;
   int potential;            // 1 obstacle, 2 well
@@ -229,14 +233,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// As mbar_try_wait, but the thread may stay suspended (not issuing) for up
+// to `hint_ns` while the phase is incomplete; it resumes when the phase
+// completes.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for phase `parity` of the barrier, giving up after kWaitLimitNs.
+// Retries suspend the waiting warp so that it leaves the issue slots to the
+// warps that have work.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (;;) {
 #pragma unroll 1
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
+    for (int i = 0; i < 8; ++i)
+      if (mbar_try_wait_suspend(bar, parity, 20000u)) return true;
     if (globaltimer() - t0 > kWaitLimitNs) return false;
   }
 }
@@ -273,6 +294,15 @@ __host__ __device__ constexpr int pair_index(int a, int b) {
 }
 
 // g = dA/dq for A(q) = gamma a_c(R q)^2 |q|^2 with the four-fold
+// 1 / x: the hardware approximate reciprocal in FP32 (relative error of a
+// few ulp, far below the FP32 path's tolerance), an exact division otherwise.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+template <class R, int W>
+__device__ __forceinline__ Dual<R, W> recip(const Dual<R, W>& x) {
+  return R(1) / x;
+}
+
 // a_c(q) = 1 - delta (3 - 4 sum q_i^4 / |q|^4) (Eqs. Eqn_a, aniso_eqn);
 // g = 2 gamma q for an isotropic pair; g = 0 when |q|^2 < 1e-12 (anisotropic).
 template <int DIM, class S, class Real>
@@ -303,7 +333,7 @@ __device__ __forceinline__ void pair_grad(const S* q, Real gam2, const S& del, b
 #pragma unroll
     for (int i = 0; i < DIM; ++i) qr[i] = q[i];
   }
-  S invQ = Real(1) / Q;
+  S invQ = recip(Q);
   S q2[DIM];
   S s4 = S(Real(0));
 #pragma unroll
@@ -373,10 +403,10 @@ __device__ __forceinline__ void cell_mobility(const S* ph, const DXT& DX, S* M) 
 template <int NM, class S>
 __device__ __forceinline__ void solve_small(const S* A, const S* b, S* x) {
   if constexpr (NM == 1) {
-    x[0] = b[0] / A[0];
+    x[0] = b[0] * recip(A[0]);
   } else if constexpr (NM == 2) {
     S det = A[0] * A[3] - A[1] * A[2];
-    S inv = decltype(val(det))(1) / det;
+    S inv = recip(det);
     x[0] = (A[3] * b[0] - A[1] * b[1]) * inv;
     x[1] = (A[0] * b[1] - A[2] * b[0]) * inv;
   } else {
@@ -384,7 +414,7 @@ __device__ __forceinline__ void solve_small(const S* A, const S* b, S* x) {
     S c01 = A[5] * A[6] - A[3] * A[8];
     S c02 = A[3] * A[7] - A[4] * A[6];
     S det = A[0] * c00 + A[1] * c01 + A[2] * c02;
-    S inv = decltype(val(det))(1) / det;
+    S inv = recip(det);
     S c10 = A[2] * A[7] - A[1] * A[8];
     S c11 = A[0] * A[8] - A[2] * A[6];
     S c12 = A[1] * A[6] - A[0] * A[7];

@@ -6,7 +6,7 @@ namespace msgb {
 void register_3d_n8(std::vector<StepKernel>& s, std::vector<DiagKernel>& d) {
   s.push_back(make_step_kernel<3, 8, 1, float, 32, 8>());
   s.push_back(make_step_kernel<3, 8, 1, float, 32, 4>());
-  s.push_back(make_step_kernel<3, 8, 1, float, 32, 8, true>());
+  s.push_back(make_split_kernel<8, 1, 6>());
   s.push_back(make_step_kernel<3, 8, 1, double, 32, 8>());
   d.push_back(make_diag_kernel<3, 8, 1, float>());
   d.push_back(make_diag_kernel<3, 8, 1, double>());

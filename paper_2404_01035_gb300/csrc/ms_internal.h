@@ -57,6 +57,7 @@ struct LaunchGeom {
   unsigned int* iface = nullptr;   // work list of split kernels (see StepArgs)
   unsigned int iface_cap = 0;
   int iface_blocks = 0;            // SMs: the interface grid is this x resident CTAs per SM
+  int reuse_prev = 1;              // output buffer = state one step before the input (see StepArgs)
 };
 
 // One compiled forward-step instantiation.

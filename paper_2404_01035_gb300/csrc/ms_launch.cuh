@@ -8,6 +8,7 @@
 
 #include "ms_diag.cuh"
 #include "ms_internal.h"
+#include "ms_split.cuh"
 #include "ms_step.cuh"
 
 namespace msgb {
@@ -115,13 +116,9 @@ inline double temp_offset(const HostModel& m, double t) {
   return m.T0 - m.T_ref - m.G * (m.z0 + m.V * t);
 }
 
-template <int DIM, int NP, int NM, class Real, int TX, int TY, bool SPLIT>
-cudaError_t launch_step(const CUtensorMap* tm, const CUtensorMap* tmi, void* blob, const HostModel& m,
-                        double t, void* out, const uint8_t* codes_in, uint8_t* codes_out,
-                        const LaunchGeom& lg, cudaStream_t st) {
-  using A = StepArgs<Real, NP, NM>;
-  using Sh = StepShape<DIM, NP, NM, Real, TX, TY, SPLIT>;
-  A& g = *reinterpret_cast<A*>(blob);
+template <class Real, int NP, int NM>
+void set_launch_args(StepArgs<Real, NP, NM>& g, const HostModel& m, double t, void* out, const uint8_t* codes_in,
+                     uint8_t* codes_out, const LaunchGeom& lg) {
   g.out = reinterpret_cast<Real*>(out);
   g.codes_in = codes_in;
   g.codes_out = codes_out;
@@ -129,32 +126,56 @@ cudaError_t launch_step(const CUtensorMap* tm, const CUtensorMap* tmi, void* blo
   g.zchunk = lg.zchunk;
   g.iface = lg.iface;
   g.iface_cap = lg.iface_cap;
-  if (SPLIT && (!lg.iface || !tmi || lg.iface_blocks < 1)) return cudaErrorInvalidValue;
-  auto kern = k_gp_step<DIM, NP, NM, Real, TX, TY, SPLIT>;
-  static bool configured = false;   // attributes are per function, set once
-  static int iface_per_sm = 0;      // resident interface CTAs per SM
+  g.reuse_prev = lg.reuse_prev;
+}
+
+// Fused step: one kernel updates every cell.
+template <int DIM, int NP, int NM, class Real, int TX, int TY>
+cudaError_t launch_step(const CUtensorMap* tm, const CUtensorMap*, void* blob, const HostModel& m, double t,
+                        void* out, const uint8_t* codes_in, uint8_t* codes_out, const LaunchGeom& lg,
+                        cudaStream_t st) {
+  using Sh = StepShape<DIM, NP, NM, Real, TX, TY>;
+  auto& g = *reinterpret_cast<StepArgs<Real, NP, NM>*>(blob);
+  set_launch_args(g, m, t, out, codes_in, codes_out, lg);
+  auto kern = k_gp_step<DIM, NP, NM, Real, TX, TY>;
+  static bool configured = false;   // attribute is per function, set once
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Sh::SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    if constexpr (SPLIT) {
-      using Si = IfaceShape<NP, NM, Real>;
-      auto ik = k_gp_iface<DIM, NP, NM, Real>;
-      e = cudaFuncSetAttribute(ik, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
-      if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&iface_per_sm, ik, Si::THREADS, Si::SMEM_BYTES);
-      if (e != cudaSuccess) return e;
-      if (iface_per_sm < 1) iface_per_sm = 1;
-    }
     configured = true;
   }
   kern<<<dim3(lg.tiles, lg.zchunks), Sh::NTHREADS, Sh::SMEM_BYTES, st>>>(*tm, g);
-  if constexpr (SPLIT) {
-    using Si = IfaceShape<NP, NM, Real>;
-    cudaError_t e = cudaGetLastError();
+  return cudaGetLastError();
+}
+
+// Split 3-D FP32 step: the bulk streaming kernel (tm = mu-only tile map),
+// then the interface kernel over the rows it listed (tmi = interface boxes).
+template <int NP, int NM, int TY>
+cudaError_t launch_split(const CUtensorMap* tm, const CUtensorMap* tmi, void* blob, const HostModel& m,
+                         double t, void* out, const uint8_t* codes_in, uint8_t* codes_out, const LaunchGeom& lg,
+                         cudaStream_t st) {
+  using Ss = StreamShape<NP, NM, TY>;
+  using Si = IfaceShape<NP, NM, float>;
+  if (!lg.iface || !tmi || lg.iface_blocks < 1) return cudaErrorInvalidValue;
+  auto& g = *reinterpret_cast<StepArgs<float, NP, NM>*>(blob);
+  set_launch_args(g, m, t, out, codes_in, codes_out, lg);
+  auto ks = k_gp_stream<NP, NM, TY>;
+  auto ki = k_gp_iface<3, NP, NM, float>;
+  static bool configured = false;   // attributes are per function, set once
+  static int iface_per_sm = 0;      // resident interface CTAs per SM
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, Ss::SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&iface_per_sm, ki, Si::THREADS, Si::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    k_gp_iface<DIM, NP, NM, Real><<<lg.iface_blocks * iface_per_sm, Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
+    if (iface_per_sm < 1) iface_per_sm = 1;
+    configured = true;
   }
+  ks<<<dim3(lg.tiles, lg.zchunks), Ss::NTHREADS, Ss::SMEM_BYTES, st>>>(*tm, g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ki<<<lg.iface_blocks * iface_per_sm, Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
   return cudaGetLastError();
 }
 
@@ -168,7 +189,7 @@ cudaError_t launch_codes(const void* state, const HostModel& m, uint8_t* codes, 
   return cudaGetLastError();
 }
 
-template <int DIM, int NP, int NM, class Real, int TX, int TY, bool SPLIT = false>
+template <int DIM, int NP, int NM, class Real, int TX, int TY>
 StepKernel make_step_kernel() {
   StepKernel k;
   k.dim = DIM;
@@ -177,12 +198,31 @@ StepKernel make_step_kernel() {
   k.dtype = sizeof(Real) == 8 ? 1 : 0;
   k.tx = TX;
   k.ty = TY;
-  k.split = SPLIT ? 1 : 0;
-  k.smem_bytes = StepShape<DIM, NP, NM, Real, TX, TY, SPLIT>::SMEM_BYTES;
+  k.split = 0;
+  k.smem_bytes = StepShape<DIM, NP, NM, Real, TX, TY>::SMEM_BYTES;
   k.args_bytes = sizeof(StepArgs<Real, NP, NM>);
   k.fill = &fill_args<DIM, NP, NM, Real>;
-  k.launch = &launch_step<DIM, NP, NM, Real, TX, TY, SPLIT>;
+  k.launch = &launch_step<DIM, NP, NM, Real, TX, TY>;
   k.codes = &launch_codes<DIM, NP, Real>;
+  return k;
+}
+
+// Split 3-D FP32 variant; tiles are StreamShape::TX x TY cells.
+template <int NP, int NM, int TY>
+StepKernel make_split_kernel() {
+  StepKernel k;
+  k.dim = 3;
+  k.np = NP;
+  k.nm = NM;
+  k.dtype = 0;
+  k.tx = StreamShape<NP, NM, TY>::TX;
+  k.ty = TY;
+  k.split = 1;
+  k.smem_bytes = StreamShape<NP, NM, TY>::SMEM_BYTES;
+  k.args_bytes = sizeof(StepArgs<float, NP, NM>);
+  k.fill = &fill_args<3, NP, NM, float>;
+  k.launch = &launch_split<NP, NM, TY>;
+  k.codes = &launch_codes<3, NP, float>;
   return k;
 }
 

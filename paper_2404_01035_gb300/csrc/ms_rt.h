@@ -73,6 +73,10 @@ ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk);
 ms_status refresh_codes(ms_ctx* c);   // segment codes of the current state
 // Tiled map of a padded state: box of (tx + 2H) x (ty + 2) x bz planes x nf fields.
 bool encode_state_map(CUtensorMap* tm, void* base, const HostModel& m, int nf, int tx, int ty, int bz = 1);
+// Maps a step variant reads from a state buffer: tm = its tile map (mu only
+// for the streaming kernel of a split variant), tmi = the interface-box map
+// (split variants only).
+bool encode_step_maps(const StepKernel& k, CUtensorMap* tm, CUtensorMap* tmi, void* base, const HostModel& m);
 void set_layout(HostModel& m);   // padded layout of one state buffer
 std::vector<const StepKernel*> step_variants(int dim, int np, int nm, int dtype);
 cudaError_t fill_ghosts(const HostModel& m, void* buf, int nf, cudaStream_t st);

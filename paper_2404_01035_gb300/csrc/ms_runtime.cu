@@ -297,6 +297,14 @@ bool encode_state_map(CUtensorMap* tm, void* base, const HostModel& m, int nf, i
   return r == CUDA_SUCCESS;
 }
 
+bool encode_step_maps(const StepKernel& k, CUtensorMap* tm, CUtensorMap* tmi, void* base, const HostModel& m) {
+  const int nf = m.N + m.NM;
+  if (!k.split) return encode_state_map(tm, base, m, nf, k.tx, k.ty);
+  const size_t s = m.dtype == MS_F64 ? 8 : 4;
+  char* mu = static_cast<char*>(base) + (size_t)m.N * m.fstride * s;
+  return encode_state_map(tm, mu, m, m.NM, k.tx, k.ty) && encode_state_map(tmi, base, m, nf, 32, 1, 3);
+}
+
 // ----------------------------------------------------------------- ghost fill
 template <class Real>
 __global__ void k_fill_ghosts(Real* buf, int nf, int nx, int ny, int nz, int pitch, int nyp,
@@ -446,10 +454,8 @@ ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk) {
   c->lg.zchunks = c->m.dim == 3 ? (c->m.nz + c->lg.zchunk - 1) / c->lg.zchunk : 1;
   c->args.assign(k->args_bytes, 0);
   k->fill(c->args.data(), c->m, c->lg.zchunk, c->status);
-  const int nf = c->m.N + c->m.NM;
   for (int b = 0; b < 2; ++b)
-    if (!encode_state_map(&c->tm[b], c->buf[b], c->m, nf, k->tx, k->ty) ||
-        (k->split && !encode_state_map(&c->tmi[b], c->buf[b], c->m, nf, 32, 1, 3)))
+    if (!encode_step_maps(*k, &c->tm[b], &c->tmi[b], c->buf[b], c->m))
       return fail(c, MS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return MS_OK;
 }
@@ -467,6 +473,10 @@ ms_status launch_one_step(ms_ctx* c) {
 
 ms_status refresh_codes(ms_ctx* c) {
   cudaError_t e = c->kern->codes(c->buf[c->cur], c->m, c->codes[c->cur], c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "segment codes");
+  // the other buffer no longer holds the state before this one: its codes
+  // must not let the next step keep phi there
+  e = cudaMemsetAsync(c->codes[1 - c->cur], 0, code_bytes(c->m), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "segment codes");
   return MS_OK;
 }

@@ -31,7 +31,7 @@ struct Halo {
   static constexpr int H = 16 / sizeof(Real);   // elements per 16 bytes
 };
 
-template <int DIM, int NP, int NM, class Real, int TX, int TY, bool SPLIT = false>
+template <int DIM, int NP, int NM, class Real, int TX, int TY>
 struct StepShape {
   static constexpr int NF = NP + NM;
   static constexpr int H = Halo<Real>::H;
@@ -45,10 +45,8 @@ struct StepShape {
   static constexpr int STAGE_BYTES = STAGE_ELEMS * (int)sizeof(Real);
   static constexpr int STAGE_STRIDE = (STAGE_BYTES + 127) / 128 * 128;
   // Ring depth: as many planes in flight as a shared-memory budget allows
-  // (two CTAs per SM for up to 5 fields, one for more; the streaming kernel
-  // of the split step, which holds few registers, one CTA more), 4..12 stages.
-  static constexpr int RING_BUDGET =
-      NF <= 5 ? (SPLIT ? 64 * 1024 : 100 * 1024) : (SPLIT ? 100 * 1024 : 190 * 1024);
+  // (two CTAs per SM for up to 5 fields, one for more), 4..12 stages.
+  static constexpr int RING_BUDGET = NF <= 5 ? 100 * 1024 : 190 * 1024;
   static constexpr int NST_RAW = RING_BUDGET / STAGE_STRIDE;
   static constexpr int NST = DIM == 3 ? (NST_RAW < 4 ? 4 : (NST_RAW > 12 ? 12 : NST_RAW)) : 1;
   static constexpr int NFL = SY * WC;                   // row flags per plane
@@ -59,14 +57,17 @@ struct StepShape {
   static constexpr int CODE_ENTRIES = MAXPL * SY * CSEG;          // segment codes a CTA reads
   static constexpr int CODE_BYTES = (CODE_ENTRIES + 15) / 16 * 16;
   static constexpr int CODE_ITERS = (CODE_ENTRIES + NTHREADS - 1) / NTHREADS;
+  // codes of the previous state at this CTA's own rows (the output buffer
+  // still holds that state: bulk rows whose phase did not change skip phi)
+  static constexpr int PREV_ENTRIES = (DIM == 3 ? kMaxZChunk : 1) * TY * WC;
+  static constexpr int PREV_BYTES = (PREV_ENTRIES + 15) / 16 * 16;
+  static constexpr int PREV_ITERS = (PREV_ENTRIES + NTHREADS - 1) / NTHREADS;
   static constexpr int OFF_FLAG = NST * STAGE_STRIDE;
   static constexpr int OFF_CODE = OFF_FLAG + FLAG_BYTES;
-  static constexpr int OFF_BAR = OFF_CODE + CODE_BYTES;            // full[NST], empty[NST]
+  static constexpr int OFF_PREV = OFF_CODE + CODE_BYTES;
+  static constexpr int OFF_BAR = OFF_PREV + PREV_BYTES;            // full[NST], empty[NST]
   static constexpr int OFF_ABORT = OFF_BAR + 2 * NST * 8;
   static constexpr int SMEM_BYTES = OFF_ABORT + 16 + 128;         // + alignment slack
-  // CTAs per SM that the shared memory admits (228 KB per SM, 1 KB reserved per CTA)
-  static constexpr int SMEM_CTAS = (228 * 1024) / (SMEM_BYTES + 1024);
-  static constexpr int SPLIT_BLOCKS = SMEM_CTAS < 1 ? 1 : (SMEM_CTAS > 4 ? 4 : SMEM_CTAS);
   static_assert(TX % 32 == 0, "a warp must cover cells of a single row");
   static_assert(NFL <= 32, "the producer warp holds one row flag per lane");
 };
@@ -180,14 +181,17 @@ __device__ __forceinline__ void bulk_cell(const Acc& A, const StepArgs<Real, NP,
   }
 }
 
-// Store the NF outputs of cell (x, y, z), plus ghost images on the boundary.
+// Store the NF outputs of cell (x, y, z), plus ghost images on the boundary;
+// with write_phi false only mu (the output buffer already holds phi^{n+1}).
 template <int DIM, int NP, int NM, class Real>
 __device__ __forceinline__ void store_cell(const StepArgs<Real, NP, NM>& g, int x, int y, int z,
-                                           const Real* pn, const Real* mn) {
+                                           const Real* pn, const Real* mn, bool write_phi = true) {
   const long long plane = (long long)g.nyp * g.pitch;
   Real* base = g.out + (long long)(z + g.zoff) * plane + (long long)(y + 1) * g.pitch + x + g.xoff;
+  if (write_phi) {
 #pragma unroll
-  for (int a = 0; a < NP; ++a) base[a * g.fstride] = pn[a];
+    for (int a = 0; a < NP; ++a) base[a * g.fstride] = pn[a];
+  }
 #pragma unroll
   for (int i = 0; i < NM; ++i) base[(NP + i) * g.fstride] = mn[i];
   const bool edge = x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 ||
@@ -213,8 +217,10 @@ __device__ __forceinline__ void store_cell(const StepArgs<Real, NP, NM>& g, int 
         if (ix == 0 && iy == 0 && iz == 0) continue;
         Real* p = g.out + (long long)(zs[iz] + g.zoff) * plane + (long long)(ys[iy] + 1) * g.pitch +
                   xs[ix] + g.xoff;
+        if (write_phi) {
 #pragma unroll
-        for (int a = 0; a < NP; ++a) p[a * g.fstride] = pn[a];
+          for (int a = 0; a < NP; ++a) p[a * g.fstride] = pn[a];
+        }
 #pragma unroll
         for (int i = 0; i < NM; ++i) p[(NP + i) * g.fstride] = mn[i];
       }
@@ -227,12 +233,10 @@ struct MinBlocks {
   static constexpr int value = (NP <= 4 && NT <= 256) ? 2 : 1;
 };
 
-template <int DIM, int NP, int NM, class Real, int TX, int TY, bool SPLIT>
-__global__ void __launch_bounds__(TX* TY + 32, SPLIT ? StepShape<DIM, NP, NM, Real, TX, TY, true>::SPLIT_BLOCKS
-                                                     : MinBlocks<NP, TX * TY>::value)
+template <int DIM, int NP, int NM, class Real, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
     k_gp_step(const __grid_constant__ CUtensorMap tm, const __grid_constant__ StepArgs<Real, NP, NM> g) {
-  static_assert(!SPLIT || DIM == 3, "the split step streams planes along z");
-  using Sh = StepShape<DIM, NP, NM, Real, TX, TY, SPLIT>;
+  using Sh = StepShape<DIM, NP, NM, Real, TX, TY>;
   constexpr int NST = Sh::NST;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
@@ -294,11 +298,32 @@ __global__ void __launch_bounds__(TX* TY + 32, SPLIT ? StepShape<DIM, NP, NM, Re
         v[it] = load_code(g, seg0 - 1 + k, y0 - 1 + ay, DIM == 3 ? zb - 1 + j : 0);
       }
     }
+    // previous-state codes of this CTA's own rows (read before any is overwritten)
+    const int nprev = nk * TY * Sh::WC;
+    uint8_t w[Sh::PREV_ITERS];
+#pragma unroll
+    for (int it = 0; it < Sh::PREV_ITERS; ++it) {
+      const int e = tid + it * Sh::NTHREADS;
+      w[it] = 0;
+      if (e < nprev && g.reuse_prev) {
+        const int wc = e % Sh::WC, r = e / Sh::WC;
+        const int ty = r % TY, k = r / TY;
+        const int y = y0 + ty, sg = seg0 + wc;
+        if (y < g.ny && sg < g.segs)
+          w[it] = g.codes_out[((long long)((DIM == 3 ? zb + k : 0) + g.zoff) * g.ny + y) * g.segs + sg];
+      }
+    }
     uint8_t* scode = smem + Sh::OFF_CODE;
 #pragma unroll
     for (int it = 0; it < Sh::CODE_ITERS; ++it) {
       const int e = tid + it * Sh::NTHREADS;
       if (e < ncode) scode[e] = v[it];
+    }
+    uint8_t* sprev = smem + Sh::OFF_PREV;
+#pragma unroll
+    for (int it = 0; it < Sh::PREV_ITERS; ++it) {
+      const int e = tid + it * Sh::NTHREADS;
+      if (e < nprev) sprev[e] = w[it];
     }
   }
   __syncthreads();   // the last CTA-wide barrier: roles split below
@@ -369,6 +394,8 @@ __global__ void __launch_bounds__(TX* TY + 32, SPLIT ? StepShape<DIM, NP, NM, Re
   const bool active = x < g.nx && y < g.ny;
   SmemAcc<DIM, NP, NM, Real, TX, TY> acc;
   acc.g = &g;
+  const uint8_t* sprev = smem + Sh::OFF_PREV;
+
   acc.sidx = (ty + 1) * Sh::SX + tx + Sh::H;
   bool ok = true;
   if constexpr (DIM == 3) ok = mbar_wait_bounded(&full[0], 0) && mbar_wait_bounded(&full[1], 0);
@@ -376,7 +403,7 @@ __global__ void __launch_bounds__(TX* TY + 32, SPLIT ? StepShape<DIM, NP, NM, Re
   uint32_t par2 = DIM == 3 ? (2 / NST) & 1 : 0;
   for (int k = 0; k < nk; ++k) {
     ok = ok && mbar_wait_bounded(&full[s2], par2) && *abort_flag == 0;
-    if (!ok) {
+    if (!__all_sync(0xffffffffu, ok)) {   // the warp leaves together (votes below)
       if (lane == 0) {
         atomicOr(g.status, kStatusTimeout);
         *abort_flag = 1;
@@ -389,34 +416,17 @@ __global__ void __launch_bounds__(TX* TY + 32, SPLIT ? StepShape<DIM, NP, NM, Re
     const int flag = rowflag[s1 * Sh::NWF + ty * Sh::WC + wc];
     const bool bulk = flag != 0;
     int code = 0;
-    if constexpr (SPLIT) {
-      // rows that are not bulk go to the interface kernel's work list
-      if (!bulk) {
-        if (lane == 0) {
-          if (y < g.ny && seg < g.segs) {
-            const unsigned int i = atomicAdd(&g.iface[0], 1u);
-            if (i < g.iface_cap) g.iface[2 + i] = (unsigned int)(((long long)z * g.ny + y) * g.segs + seg);
-          }
-          mbar_arrive(&empty[s0]);   // this warp is done with entry k
-        }
-        s0 = s1;
-        s1 = s2;
-        if (++s2 == NST) {
-          s2 = 0;
-          par2 ^= 1u;
-        }
-        continue;
-      }
-    }
     if (active) {
       acc.st[0] = stage(s0);
       acc.st[1] = stage(s1);
       acc.st[2] = stage(s2);
       Real pn[NP], mn[NM];
+      bool write_phi = true;
       if (bulk) {
         bulk_cell<DIM, NP, NM, Real>(acc, g, flag - 1, pn, mn);
         code = flag;
-      } else if constexpr (!SPLIT) {
+        write_phi = sprev[(k * TY + ty) * Sh::WC + wc] != flag;
+      } else {
         DiffPrm<Real, StepArgs<Real, NP, NM>::P> dp;
         dp.mob = g.mob;
 #pragma unroll
@@ -430,7 +440,7 @@ __global__ void __launch_bounds__(TX* TY + 32, SPLIT ? StepShape<DIM, NP, NM, Re
         }
         code = (__popc(nzm) == 1 && nzm == one) ? __ffs(nzm) : 0;
       }
-      store_cell<DIM>(g, x, y, z, pn, mn);
+      store_cell<DIM>(g, x, y, z, pn, mn, write_phi);
     }
     // segment code of the output row: lane 0 is active whenever any lane is
     const int ref = __shfl_sync(0xffffffffu, code, 0);
@@ -447,162 +457,6 @@ __global__ void __launch_bounds__(TX* TY + 32, SPLIT ? StepShape<DIM, NP, NM, Re
         s2 = 0;
         par2 ^= 1u;
       }
-    }
-  }
-}
-
-// Interface kernel of the split 3-D step (shape of its shared memory).  Each
-// warp owns two buffers of one TMA box: 32 + 2H cells x 3 rows x 3 planes x
-// all fields around one listed 32-cell row, so the next row is in flight
-// while the current one is updated.
-template <int NP, int NM, class Real>
-struct IfaceShape {
-  static constexpr int NF = NP + NM;
-  static constexpr int H = Halo<Real>::H;
-  static constexpr int BX = 32 + 2 * H;                 // box extent along x
-  static constexpr int BOX_ELEMS = NF * 9 * BX;
-  static constexpr int BOX_BYTES = BOX_ELEMS * (int)sizeof(Real);
-  static constexpr int BOX_STRIDE = (BOX_BYTES + 127) / 128 * 128;
-  static constexpr int WARPS = 4;                       // warps per CTA
-  static constexpr int THREADS = 32 * WARPS;
-  static constexpr int OFF_BAR = WARPS * 2 * BOX_STRIDE;
-  static constexpr int SMEM_BYTES = OFF_BAR + WARPS * 2 * 8 + 128;   // + alignment slack
-  static constexpr int MIN_BLOCKS = NP <= 4 ? 3 : 2;
-};
-
-// Stencil accessor over one interface box ([field][plane][row][x]).
-template <int DIM, int NP, int NM, class Real>
-struct BoxAcc {
-  using Sh = IfaceShape<NP, NM, Real>;
-  const Real* s;
-  const StepArgs<Real, NP, NM>* g;
-  int sidx;   // centre of this lane's cell: plane 1, row 1, x = H + lane
-
-  __device__ __forceinline__ Real ld(int f, int dx, int dy, int dz) const {
-    return s[f * (9 * Sh::BX) + sidx + dz * (3 * Sh::BX) + dy * Sh::BX + dx];
-  }
-  __device__ __forceinline__ Real phi(int a, int dx, int dy, int dz) const { return ld(a, dx, dy, dz); }
-  __device__ __forceinline__ Real mu(int i, int dx, int dy, int dz) const { return ld(NP + i, dx, dy, dz); }
-  __device__ __forceinline__ uint32_t mask() const { return stencil_mask<DIM, NP>(*this); }
-  __device__ __forceinline__ void mobility(int dx, int dy, int dz, Real* M) const {
-    Real ph[NP];
-#pragma unroll
-    for (int a = 0; a < NP; ++a) ph[a] = phi(a, dx, dy, dz);
-    cell_mobility<NP, NM>(ph, g->DX, M);
-  }
-};
-
-// Interface kernel of the split 3-D step: the full cell update of every warp
-// row the streaming kernel listed (32 cells of one row of one plane per
-// warp), from a TMA box of the input state; writes phi, mu, their ghost
-// images and the row's segment code.  The last CTA to finish clears the list
-// for the next step (ticket in iface[1]), so the pair of launches can be
-// replayed from a CUDA graph.
-template <int DIM, int NP, int NM, class Real>
-__global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<NP, NM, Real>::MIN_BLOCKS)
-    k_gp_iface(const __grid_constant__ CUtensorMap tmi, const __grid_constant__ StepArgs<Real, NP, NM> g) {
-  static_assert(DIM == 3, "the interface list is built by the 3-D streaming kernel");
-  using Sh = IfaceShape<NP, NM, Real>;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  __shared__ unsigned int s_count;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR) + 2 * wid;
-  Real* buf0 = reinterpret_cast<Real*>(smem + (2 * wid) * Sh::BOX_STRIDE);
-  if (threadIdx.x == 0) s_count = min(*(volatile unsigned int*)&g.iface[0], g.iface_cap);
-  if (lane == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    mbar_fence_init();
-    prefetch_tensormap(&tmi);
-  }
-  __syncthreads();
-  const unsigned int count = s_count;
-  const unsigned int stride = gridDim.x * Sh::WARPS;
-  DiffPrm<Real, StepArgs<Real, NP, NM>::P> dp;
-  dp.mob = g.mob;
-#pragma unroll
-  for (int p = 0; p < StepArgs<Real, NP, NM>::P; ++p) dp.delta[p] = g.delta[p];
-
-  // row r = (z ny + y) segs + segment  ->  box origin (x, y - 1, z - 1 in padded coordinates)
-  auto issue = [&](unsigned int i, int b) {
-    const unsigned int r = g.iface[2 + i];
-    const int sg = (int)(r % (unsigned int)g.segs);
-    const unsigned int zy = r / (unsigned int)g.segs;
-    const int y = (int)(zy % (unsigned int)g.ny), z = (int)(zy / (unsigned int)g.ny);
-    fence_proxy_async_shared();
-    mbar_expect_tx(&bar[b], Sh::BOX_BYTES);
-    tma_load_4d(reinterpret_cast<unsigned char*>(buf0) + b * Sh::BOX_STRIDE, &tmi, &bar[b],
-                32 * sg + g.xoff - Sh::H, y, z + g.zoff - 1, 0);
-  };
-  bool pending[2] = {false, false};
-  uint32_t phase[2] = {0u, 0u};
-  bool aborted = false;
-  unsigned int i = blockIdx.x * Sh::WARPS + wid;
-  if (i < count && lane == 0) issue(i, 0);
-  pending[0] = i < count;
-  int b = 0;
-  while (i < count) {
-    const unsigned int nxt = i + stride;
-    if (nxt < count) {
-      if (lane == 0) issue(nxt, b ^ 1);
-      pending[b ^ 1] = true;
-    }
-    const bool ok = mbar_wait_bounded(&bar[b], phase[b]);
-    if (!__all_sync(0xffffffffu, ok)) {
-      aborted = true;
-      break;
-    }
-    pending[b] = false;
-    phase[b] ^= 1u;
-    const unsigned int r = g.iface[2 + i];
-    const int sg = (int)(r % (unsigned int)g.segs);
-    const unsigned int zy = r / (unsigned int)g.segs;
-    const int y = (int)(zy % (unsigned int)g.ny), z = (int)(zy / (unsigned int)g.ny);
-    const int x = 32 * sg + lane;
-    const bool active = x < g.nx;
-    int code = 0;
-    if (active) {
-      BoxAcc<DIM, NP, NM, Real> acc;
-      acc.s = reinterpret_cast<const Real*>(reinterpret_cast<unsigned char*>(buf0) + b * Sh::BOX_STRIDE);
-      acc.g = &g;
-      acc.sidx = 3 * Sh::BX + Sh::BX + Sh::H + lane;
-      Real pn[NP], mn[NM];
-      gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, z + g.zorg, pn, mn);
-      uint32_t nzm = 0, one = 0;
-#pragma unroll
-      for (int a = 0; a < NP; ++a) {
-        nzm |= (pn[a] != Real(0) ? 1u : 0u) << a;
-        one |= (pn[a] == Real(1) ? 1u : 0u) << a;
-      }
-      code = (__popc(nzm) == 1 && nzm == one) ? __ffs(nzm) : 0;
-      store_cell<DIM>(g, x, y, z, pn, mn);
-    }
-    const int ref = __shfl_sync(0xffffffffu, code, 0);
-    const bool same = __all_sync(0xffffffffu, !active || code == ref);
-    if (lane == 0)
-      g.codes_out[((long long)(z + g.zoff) * g.ny + y) * g.segs + sg] = same ? (uint8_t)ref : (uint8_t)0;
-    __syncwarp();   // every lane is done with buffer b before it is refilled
-    b ^= 1;
-    i = nxt;
-  }
-  if (aborted) {
-    // a copy did not complete in time: record it and wait (bounded) for the
-    // copies still in flight before the CTA exits
-    if (lane == 0) {
-      atomicOr(g.status, kStatusTimeout);
-      for (int k = 0; k < 2; ++k)
-        if (pending[k]) mbar_wait_bounded(&bar[k], phase[k]);
-    }
-  }
-  // every CTA read the count before taking its ticket
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&g.iface[1], 1u) == gridDim.x - 1) {
-      g.iface[0] = 0u;
-      g.iface[1] = 0u;
     }
   }
 }

@@ -200,6 +200,55 @@ def test_checkpoint_restore_is_bitwise_and_views_match():
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+def test_bulk_phi_reuse_survives_state_loads_and_adjoint_recompute():
+    # Bulk rows whose pure phase is unchanged keep phi from the ping-pong
+    # partner buffer.  Loading a state, restoring a checkpoint and the
+    # adjoint's recompute (which reuses the code buffers) must leave every
+    # later step bitwise equal to a fresh context started from the same state.
+    from paper_2404_01035_gb300 import Simulation
+    import torch
+    p = W.cfg2(n=48, steps=10)
+    p.nz = 40
+    p.phi0, p.mu0 = p.phi0[:, :40], p.mu0[:, :40]
+    sim = Simulation(p, dtype="f32")
+    for t, (tx, ty, split) in enumerate(sim.tiles()):
+        sim.set_launch(t, 16)
+        sim.set_fields(p.phi0, p.mu0)
+        sim.step(9)
+        blob = sim.checkpoint()
+        sim.set_fields(p.phi0[::-1].copy(), p.mu0)   # another state over the same buffers
+        sim.step(3)
+        sim.restore(blob)
+        sim.step(6)
+        a = sim.get_fields()
+        ref = Simulation(p, dtype="f32")
+        ref.set_launch(t, 16)
+        ref.restore(blob)
+        ref.step(6)
+        b = ref.get_fields()
+        ref.close()
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (tx, ty, split)
+    sim.close()
+    # adjoint recompute (3-D binary, FP64: the fused kernel's phi reuse)
+    q = W.binary_problem("reuse", 24, dim=3, R=6.0, nz=20)
+    sim = Simulation(q, dtype="f64")
+    sim.set_fields(q.phi0, q.mu0)
+    sim.enable_checkpoints(4)
+    sim.step(10)
+    blob = sim.checkpoint()
+    lam = torch.ones((2, 20, 24, 24), dtype=torch.float64, device="cuda")
+    sim.grad(lam, want_fields=False)
+    sim.step(5)
+    a = sim.get_fields()
+    sim.close()
+    ref = Simulation(q, dtype="f64")
+    ref.restore(blob)
+    ref.step(5)
+    b = ref.get_fields()
+    ref.close()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
 def test_device_and_host_field_io_agree():
     from paper_2404_01035_gb300 import Simulation
     import torch
