@@ -4,12 +4,16 @@ Workload (default): the 3-D 256^3 directional eutectic -- 3 phases (alpha,
 beta, liquid), ternary alloy, four-fold anisotropy 0.02, frozen pulled
 temperature gradient, seeded lamellae, no-flux z / periodic x,y, FP32 state
 with FP64 diagnostics every 100 steps.  One bench step = one explicit time step
-of the whole path (one fused step kernel; the diagnostics kernel every 100th).
+of the whole path (the launch variant the autotuner picks: one fused step
+kernel, or the split step's streaming + interface kernels; the diagnostics
+kernel every 100th).
 
 Prints ONE JSON line (rank 0).  `value` is whole-job MLUPS (cell updates per
 second / 1e6) with the state resident in HBM; `e2e` is the same metric through
 the public API with host buffers, host<->device copies inside the timed region;
-`roofline` relates the step kernel's algorithmic bytes to the measured HBM peak.
+`roofline` relates the step's algorithmic bytes (read and write every field
+once) to the measured HBM peak, with the DRAM traffic and per-kernel shares of
+the committed ncu summary for the same sources and launch variant.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -43,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint lines")
+    ap.add_argument("--launch", default=None,
+                    help="force a launch variant tx,ty,split,zchunk instead of tuning (e.g. 128,6,1,16)")
     return ap.parse_args()
 
 
@@ -192,9 +198,16 @@ def run_ours(args, rank, world, local_rank):
     sim = Simulation(prob, dtype="f32", stream=stream)
     sim.set_fields(prob.phi0, prob.mu0)
     tuned_ms = None
-    if not args.no_tune:
+    if args.launch:
+        tx, ty, sp, zc = (int(v) for v in args.launch.split(","))
+        sim.set_launch(sim.tiles().index((tx, ty, sp)), zc)
+    elif not args.no_tune:
         tuned_ms = sim.tune(None, steps_per_trial=25)
         sim.set_fields(prob.phi0, prob.mu0)
+    tiles = sim.tiles()
+    cur_tile, cur_zchunk = sim.launch()
+    tx, ty, split = tiles[cur_tile]
+    step_launches = 2 if split else 1   # kernels per time step
     sim.set_diag_every(DIAG_EVERY)
     sim.step(args.warmup)
     sim.sync()
@@ -226,7 +239,7 @@ def run_ours(args, rank, world, local_rank):
         if pure < n:
             sim.step(1)
             launches += 2   # diagnostics: partial + final reduction
-        launches += n
+        launches += n * step_launches
         done += n
     ev[1].record(stream)
     stream.synchronize()
@@ -243,23 +256,20 @@ def run_ours(args, rank, world, local_rank):
         el = float(t.item())
     value = world * cells * args.steps / el / 1e6
 
-    # ---- roofline of the step kernel
+    # ---- roofline of the step (all of its kernels)
     peaks, src = measured_peaks()
     bpc = algorithmic_bytes_per_cell(prob, 4)
-    per_launch_s = kern_ms / max(1, kern_n) / 1e3
-    achieved = bpc * cells / per_launch_s / 1e9
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic_cfg2_step.json")
-    if os.path.exists(tp):
-        with open(tp) as fh:
-            tj = json.load(fh)
-        if tj.get("kernel_digest") == kernel_digest():
-            traffic = tj.get("bytes_per_launch")
+    per_step_s = kern_ms / max(1, kern_n) / 1e3
+    achieved = bpc * cells / per_step_s / 1e9
+    launch = {"tx": tx, "ty": ty, "split": split, "zchunk": cur_zchunk}
+    prof = committed_profile(launch, args.n)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "frac": achieved / peaks["hbm_gbs"],
+            "traffic": prof["dram_bytes_per_step"] if prof else None,
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)",
-            "kernel": "k_gp_step<3,3,2,float>", "bytes_per_cell": bpc,
-            "kernel_ms_per_launch": per_launch_s * 1e3}
+            "scope": "one time step: " + ("k_gp_stream + k_gp_iface" if split else "k_gp_step"),
+            "bytes_per_cell": bpc, "step_ms": per_step_s * 1e3,
+            "kernel_shares": prof["kernel_shares"] if prof else None}
 
     # ---- e2e through the public API with host (pinned) buffers, continuing
     # from the evolved state of the timed run
@@ -284,11 +294,7 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": nbytes, "steps_per_e2e_iteration": E2E_SEGMENT,
                "note": "one e2e iteration = H2D of the full state from pinned memory, "
                        f"{E2E_SEGMENT} steps, D2H of the full state"}
-    tiles = sim.tiles()
-    cur_tile, cur_zchunk = sim.launch()
-    tx, ty, split = tiles[cur_tile]
-    launch_info = {"tiles_compiled": tiles,
-                   "launch": {"tx": tx, "ty": ty, "split": split, "zchunk": cur_zchunk}}
+    launch_info = {"tiles_compiled": tiles, "launch": launch}
     sim.close()
 
     extra = {}
@@ -393,6 +399,21 @@ def bench_adjoint(stream):
                       "forward_mlups": 65536 * 2000 / (fwd / 1e3) / 1e6,
                       "reverse_mlups": 65536 * 2000 / (rev / 1e3) / 1e6}
     return out
+
+
+def committed_profile(launch, n):
+    """The ncu figures committed for this source version, launch variant and grid
+    (profiles/traffic_cfg2_step.json), or None."""
+    path = os.path.join(ROOT, "profiles", "traffic_cfg2_step.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        entries = json.load(fh)
+    digest = kernel_digest()
+    for e in entries:
+        if e.get("kernel_digest") == digest and e.get("launch") == launch and e.get("grid") == n:
+            return e
+    return None
 
 
 def kernel_digest():
