@@ -37,6 +37,74 @@ struct IsDual<Dual<R, W>> {
   static constexpr bool value = true;
 };
 
+// g = dA/dq of the unrotated anisotropic pair, evaluated in real arithmetic
+// through the factorisation g_i = 2 gamma a_c q_i (a_c + 16 delta (q_i^2 /
+// |q|^2 - r)), r = sum_j q_j^4 / |q|^4, a_c = (1 - 3 delta) + 4 delta r (the
+// derivative of Eq. (aniso_eqn)'s A written out once), g = 0 when |q|^2 <
+// 1e-12 (often the whole warp: a pair absent around it has q = 0 exactly).
+// Rotated pairs and dual numbers use pair_grad.
+template <int DIM, class Real>
+__device__ __forceinline__ void aniso_grad_factored(const Real* q, Real gam2, Real del, Real* g,
+                                                    int only = -1) {
+  Real q2[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) q2[i] = q[i] * q[i];
+  Real Q = q2[0], s4 = q2[0] * q2[0];
+#pragma unroll
+  for (int i = 1; i < DIM; ++i) {
+    Q += q2[i];
+    s4 += q2[i] * q2[i];
+  }
+  if (Q < Real(1e-12)) {
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) g[i] = Real(0);
+    return;
+  }
+  const Real invQ = recip(Q);
+  const Real r = s4 * invQ * invQ;
+  const Real ac = (Real(1) - Real(3) * del) + Real(4) * del * r;
+  const Real ga = gam2 * ac;
+  const Real k16 = Real(16) * del;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+    if (only < 0 || i == only) g[i] = ga * q[i] * (ac + k16 * (q2[i] * invQ - r));
+}
+
+// pair_grad for the forward step: the factored form for unrotated
+// anisotropic pairs in real arithmetic, pair_grad otherwise.
+template <int DIM, class S, class Real>
+__device__ __forceinline__ void pair_grad_fwd(const S* q, Real gam2, const S& del, bool aniso, bool rotated,
+                                              const Real* R, S* g) {
+  if constexpr (!IsDual<S>::value) {
+    if (aniso && !rotated) {
+      aniso_grad_factored<DIM, Real>(q, gam2, del, g);
+      return;
+    }
+  }
+  pair_grad<DIM>(q, gam2, del, aniso, rotated, R, g);
+}
+
+// Normal component (axis D) of g_ab at a face from the face values pa, pb
+// and face gradients ga, gb of the pair (q = pa gb - pb ga): isotropic pairs
+// need q_D only, unrotated anisotropic ones the factored form's D component.
+template <int DIM, int D, class S, class Real>
+__device__ __forceinline__ S face_pair_flux(const S& pa, const S& pb, const S* ga, const S* gb, Real gam2,
+                                            const S& del, bool aniso, bool rotated, const Real* R) {
+  const S qD = pa * gb[D] - pb * ga[D];
+  if (!aniso) return gam2 * qD;
+  S q[DIM], gq[DIM];
+#pragma unroll
+  for (int t = 0; t < DIM; ++t) q[t] = t == D ? qD : pa * gb[t] - pb * ga[t];
+  if constexpr (!IsDual<S>::value) {
+    if (!rotated) {
+      aniso_grad_factored<DIM, Real>(q, gam2, del, gq, D);
+      return gq[D];
+    }
+  }
+  pair_grad<DIM>(q, gam2, del, true, rotated, R, gq);
+  return gq[D];
+}
+
 template <class S, int P>
 struct DiffPrm {
   S mob;         // phase-field mobility 1/tau
@@ -101,12 +169,10 @@ __device__ __forceinline__ void face_flux(const Acc& A, const StepArgs<Real, NP,
 #pragma unroll
     for (int b = a + 1; b < NP; ++b, ++p) {
       if (!(((mask >> a) & (mask >> b)) & 1u)) continue;
-      S q[DIM], gq[DIM];
-#pragma unroll
-      for (int t = 0; t < DIM; ++t) q[t] = pf[a] * gr[b][t] - pf[b] * gr[a][t];
-      pair_grad<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, g.rotated[p] != 0, g.rot[p], gq);
-      Jn[a] -= pf[b] * gq[D];
-      Jn[b] += pf[a] * gq[D];
+      const S gD = face_pair_flux<DIM, D>(pf[a], pf[b], gr[a], gr[b], g.gam2[p], dp.delta[p], g.aniso[p] != 0,
+                                          g.rotated[p] != 0, g.rot[p]);
+      Jn[a] -= pf[b] * gD;
+      Jn[b] += pf[a] * gD;
     }
   }
 }
@@ -214,8 +280,7 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
           S q[DIM], gq[DIM];
 #pragma unroll
           for (int d = 0; d < DIM; ++d) q[d] = ph[a] * gc[b][d] - ph[b] * gc[a][d];
-          pair_grad<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, g.rotated[p] != 0, g.rot[p],
-                         gq);
+          pair_grad_fwd<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, g.rotated[p] != 0, g.rot[p], gq);
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
             Gc[a] += gq[d] * gc[b][d];
