@@ -2,14 +2,18 @@
 // and parameters advanced by ONE persistent, cooperative kernel launch
 // (captured once into a CUDA graph and replayed).
 //
-// Work list: every (simulation, 32 x TY tile) pair of every step.  Each CTA
-// walks the list with a fixed stride; a producer warp TMA-loads the next
-// items' halo'ed tiles (each simulation has its own tensor map, kept in global
-// memory) into a shared-memory ring while the consumer warps compute the
-// current one with the same cell update as the single-simulation kernel.  A
-// grid-wide barrier (atomic counter, bounded spin on %globaltimer) separates
-// time steps, because a step reads the ghost cells its neighbours wrote in the
-// previous step.
+// Work list: every (simulation, 32 x TY tile) pair, as precomputed
+// descriptors.  Each CTA takes a contiguous range of it every step; a producer
+// warp reads the descriptors 32 at a time (one coalesced load, the next chunk
+// in flight) and TMA-loads the items' halo'ed tiles (each simulation has its
+// own tensor map, kept in global memory) into a shared-memory ring, while the
+// consumer warps compute the current one with the same cell update as the
+// single-simulation kernel.  A consumer warp takes the bulk update when the
+// three halo rows around its row, its 32 columns and the column on each side,
+// hold one pure phase in the staged data itself (the exact condition of the
+// bulk shortcut; no segment codes are kept).  A grid-wide barrier (atomic
+// counter, bounded spin on %globaltimer) separates time steps, because a step
+// reads the ghost cells its neighbours wrote in the previous step.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -26,15 +30,16 @@ namespace msgb {
 
 ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params* p, HostModel& m);
 
-// Per-simulation constants for one buffer parity (out / codes point at the
+// Per-simulation constants for one buffer parity (out points at the
 // destination of a step that reads the other buffer).
 template <class Real, int NP, int NM>
 struct alignas(64) BatchSim {
   StepArgs<Real, NP, NM> g[2];   // [parity of the source buffer]
 };
 
-struct BatchItem {
-  int sim, tile;
+// One work item: simulation, tile origin, TMA x coordinate of its box.
+struct alignas(16) BatchItem {
+  int sim, x0, y0, bx;
 };
 
 __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int target) {
@@ -52,18 +57,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int
 }
 
 template <int NP, int NM, class Real, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY + 32, 1)
+__global__ void __launch_bounds__(TX* TY + 32, 3)
     k_batch(const BatchSim<Real, NP, NM>* __restrict__ sims, const CUtensorMap* __restrict__ maps,
             const BatchItem* __restrict__ items, int nitems, int nsteps, int parity0,
             unsigned int* barrier, int* status) {
   using Sh = StepShape<2, NP, NM, Real, TX, TY>;
+  static_assert(TX == 32, "one warp per tile row");
   constexpr int NST = 8;
-  constexpr int PF = 4;   // items whose descriptors and codes the producer holds ahead
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  uint8_t* rowflag = smem + NST * Sh::STAGE_STRIDE;
-  int4* sitem = reinterpret_cast<int4*>(smem + NST * Sh::STAGE_STRIDE + ((NST * Sh::NWF + 15) / 16) * 16);
+  int4* sitem = reinterpret_cast<int4*>(smem + NST * Sh::STAGE_STRIDE);
   uint64_t* full = reinterpret_cast<uint64_t*>(sitem + NST);
   uint64_t* empty = full + NST;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NST);
@@ -87,29 +91,22 @@ __global__ void __launch_bounds__(TX* TY + 32, 1)
   for (int step = 0; step < nsteps; ++step) {
     const int par = (parity0 + step) & 1;
     if (tid >= Sh::NT) {
-      // ---------------- producer warp
-      const int f_ay = lane / Sh::WC, f_wc = lane % Sh::WC;
-      const bool fl = lane < Sh::NFL;
-      int psim[PF], px0[PF], py0[PF];
-      uint32_t pc3[PF];
-      auto fetch = [&](int k, int& sim, int& x0, int& y0, uint32_t& c3) {
-        const BatchItem it = items[ibeg + k];
-        const StepArgs<Real, NP, NM>& g = sims[it.sim].g[par];
-        const int tiles_x = (g.nx + TX - 1) / TX;
-        sim = it.sim;
-        x0 = (it.tile % tiles_x) * TX;
-        y0 = (it.tile / tiles_x) * TY;
-        c3 = 0;
-        const int sg = (x0 >> 5) + f_wc, yy = y0 - 1 + f_ay;
-        if (fl && sg < g.segs)
-          c3 = (uint32_t)load_code(g, sg - 1, yy, 0) | ((uint32_t)load_code(g, sg, yy, 0) << 8) |
-               ((uint32_t)load_code(g, sg + 1, yy, 0) << 16);
+      // ---------------- producer warp: descriptors 32 at a time, one TMA per item
+      auto fetch = [&](int k0) {
+        int4 d = make_int4(0, 0, 0, 0);
+        if (k0 + lane < my_items) {
+          const BatchItem it = items[ibeg + k0 + lane];
+          d = make_int4(it.sim, it.x0, it.y0, it.bx);
+        }
+        return d;
       };
-#pragma unroll
-      for (int i = 0; i < PF; ++i)
-        if (i < my_items) fetch(i, psim[i], px0[i], py0[i], pc3[i]);
+      int4 cur = fetch(0), nxt = fetch(32);
       bool ok = true;
       for (int k = 0; k < my_items; ++k) {
+        if ((k & 31) == 0 && k > 0) {
+          cur = nxt;
+          nxt = fetch(k + 32);
+        }
         const long long q = seq + k;
         const int s = (int)(q % NST);
         if (q >= NST) ok = ok && mbar_wait_bounded(&empty[s], (uint32_t)(((q / NST) - 1) & 1));
@@ -121,51 +118,27 @@ __global__ void __launch_bounds__(TX* TY + 32, 1)
           }
           break;
         }
-        int sim = 0, x0 = 0, y0 = 0;
-        uint32_t c3 = 0;
-#pragma unroll
-        for (int i = 0; i < PF; ++i)
-          if (i == k % PF) {
-            sim = psim[i];
-            x0 = px0[i];
-            y0 = py0[i];
-            c3 = pc3[i];
-          }
-        if (k + PF < my_items) {
-          int a, b2, c;
-          uint32_t d;
-          fetch(k + PF, a, b2, c, d);
-#pragma unroll
-          for (int i = 0; i < PF; ++i)
-            if (i == k % PF) {
-              psim[i] = a;
-              px0[i] = b2;
-              py0[i] = c;
-              pc3[i] = d;
-            }
-        }
-        // combined flag of each warp row (rows ay, ay+1, ay+2)
-        const int rf = fl ? combine_packed_codes(c3) : 0;
-        const int up = __shfl_down_sync(0xffffffffu, rf, Sh::WC);
-        const int up2 = __shfl_down_sync(0xffffffffu, rf, 2 * Sh::WC);
-        if (lane < Sh::NWF) rowflag[s * Sh::NWF + lane] = (uint8_t)((rf == up && up == up2) ? rf : 0);
-        if (lane == 0) sitem[s] = make_int4(sim, x0, y0, 0);
-        __syncwarp();
+        const int j = k & 31;
+        const int sim = __shfl_sync(0xffffffffu, cur.x, j);
+        const int x0 = __shfl_sync(0xffffffffu, cur.y, j);
+        const int y0 = __shfl_sync(0xffffffffu, cur.z, j);
+        const int bx = __shfl_sync(0xffffffffu, cur.w, j);
         if (lane == 0) {
+          sitem[s] = make_int4(sim, x0, y0, 0);
           __threadfence_block();
-          mbar_expect_tx(&full[s], Sh::STAGE_BYTES);
-          tma_load_4d(stage(s), &maps[2 * sim + par], &full[s], x0 + sims[sim].g[par].xoff - Sh::H, y0, 0, 0);
+          mbar_expect_tx(&full[s], Sh::STAGE_BYTES);   // arrive (release) + expected bytes
+          tma_load_4d(stage(s), &maps[2 * sim + par], &full[s], bx, y0, 0, 0);
           issued = q + 1;
         }
       }
     } else {
-      // ---------------- consumer warps
-      const int tx = tid % TX, ty = tid / TX, wc = tx >> 5;
+      // ---------------- consumer warps: one tile row each
+      const int tx = tid % TX, ty = tid / TX;
       for (int k = 0; k < my_items; ++k) {
         const long long q = seq + k;
         const int s = (int)(q % NST);
         const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((q / NST) & 1)) && *abort_flag == 0;
-        if (!ok) {
+        if (!__all_sync(0xffffffffu, ok)) {   // the warp leaves together (votes below)
           if (lane == 0) {
             atomicOr(status, kStatusTimeout);
             *abort_flag = 1;
@@ -177,40 +150,51 @@ __global__ void __launch_bounds__(TX* TY + 32, 1)
         const int x0 = it.y, y0 = it.z;
         const int x = x0 + tx, y = y0 + ty;
         const bool active = x < g.nx && y < g.ny;
-        const int flag = rowflag[s * Sh::NWF + ty * Sh::WC + wc];
-        const bool bulk = flag != 0;
-        int code = 0;
+        // bulk test on the staged phi: rows ty..ty+2 (halo'ed) of this lane's
+        // column, and of the columns beside the row for lanes 0 and 31
+        const Real* st = stage(s);
+        auto column_code = [&](int col) {
+          int c = -1;
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            uint32_t nz = 0, one = 0;
+#pragma unroll
+            for (int a = 0; a < NP; ++a) {
+              const Real v = st[a * Sh::SY * Sh::SX + (ty + r) * Sh::SX + col];
+              nz |= (v != Real(0) ? 1u : 0u) << a;
+              one |= (v == Real(1) ? 1u : 0u) << a;
+            }
+            const int pc = (__popc(nz) == 1 && nz == one) ? __ffs(nz) : 0;
+            c = (c == -1 || c == pc) ? pc : 0;
+          }
+          return c;
+        };
+        int mine = column_code(Sh::H + tx);
+        if (tx == 0 || tx == TX - 1) {
+          const int side = column_code(tx == 0 ? Sh::H - 1 : Sh::H + TX);
+          mine = mine == side ? mine : 0;
+        }
+        const int ref = __shfl_sync(0xffffffffu, mine, 0);
+        const int flag = __all_sync(0xffffffffu, mine == ref) ? ref : 0;
         if (active) {
           SmemAcc<2, NP, NM, Real, TX, TY> acc;
-          acc.st[0] = acc.st[1] = acc.st[2] = stage(s);
+          acc.st[0] = acc.st[1] = acc.st[2] = st;
           acc.g = &g;
           acc.sidx = (ty + 1) * Sh::SX + tx + Sh::H;
           Real pn[NP], mn[NM];
-          if (bulk) {
+          if (flag != 0) {
             bulk_cell<2, NP, NM, Real>(acc, g, flag - 1, pn, mn);
-            code = flag;
           } else {
             DiffPrm<Real, StepArgs<Real, NP, NM>::P> dp;
             dp.mob = g.mob;
 #pragma unroll
             for (int p = 0; p < StepArgs<Real, NP, NM>::P; ++p) dp.delta[p] = g.delta[p];
             gp_cell<2, NP, NM, Real, Real>(acc, g, dp, y, pn, mn);
-            uint32_t nzm = 0, one = 0;
-#pragma unroll
-            for (int a = 0; a < NP; ++a) {
-              nzm |= (pn[a] != Real(0) ? 1u : 0u) << a;
-              one |= (pn[a] == Real(1) ? 1u : 0u) << a;
-            }
-            code = (__popc(nzm) == 1 && nzm == one) ? __ffs(nzm) : 0;
           }
           store_cell<2>(g, x, y, 0, pn, mn);
         }
-        const int ref = __shfl_sync(0xffffffffu, code, 0);
-        const bool same = __all_sync(0xffffffffu, !active || code == ref);
-        if (lane == 0) {
-          if (active) g.codes_out[(long long)y * g.segs + (x0 >> 5) + wc] = same ? (uint8_t)ref : (uint8_t)0;
-          mbar_arrive(&empty[s]);
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
       }
     }
     seq += my_items;
@@ -240,8 +224,7 @@ template <int NP, int NM, class Real, int TX, int TY>
 struct BatchShape {
   using Sh = StepShape<2, NP, NM, Real, TX, TY>;
   static constexpr int NST = 8;
-  static constexpr int SMEM =
-      NST * Sh::STAGE_STRIDE + ((NST * Sh::NWF + 15) / 16) * 16 + NST * 16 + 2 * NST * 8 + 16 + 128;
+  static constexpr int SMEM = NST * Sh::STAGE_STRIDE + NST * 16 + 2 * NST * 8 + 16 + 128;
 };
 
 }  // namespace msgb
@@ -252,10 +235,8 @@ struct ms_batch {
   int nsims = 0, N = 0, NM = 0, dtype = 0;
   std::vector<HostModel> models;
   std::vector<size_t> off;              // byte offset of each simulation's two state buffers
-  std::vector<size_t> coff;             // byte offset of each simulation's two code buffers
   std::vector<size_t> sbytes;           // state bytes per simulation (one buffer)
   void* state = nullptr;                // all state buffers
-  uint8_t* codes = nullptr;             // all code buffers
   void* sims = nullptr;                 // BatchSim array (device)
   CUtensorMap* maps = nullptr;          // [nsims][2] (device)
   BatchItem* items = nullptr;
@@ -287,7 +268,6 @@ void batch_free(ms_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   dev_free(b->hook, b->state);
-  dev_free(b->hook, b->codes);
   dev_free(b->hook, b->sims);
   dev_free(b->hook, b->maps);
   dev_free(b->hook, b->items);
@@ -348,30 +328,25 @@ ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_c
   b->N = 2;
   b->NM = 1;
   b->dtype = MS_F32;
-  // one allocation for all states (2 buffers each), one for all codes
-  size_t tot = 0, ctot = 0;
+  // one allocation for all states (2 buffers each)
+  size_t tot = 0;
   for (int i = 0; i < nsims; ++i) {
     const HostModel& m = b->models[i];
     const size_t sb = (size_t)m.fstride * (m.N + m.NM) * 4;
     b->sbytes.push_back(sb);
     b->off.push_back(tot);
     tot += 2 * ((sb + 255) / 256 * 256);
-    const size_t cb = code_bytes(m);
-    b->coff.push_back(ctot);
-    ctot += 2 * ((cb + 255) / 256 * 256);
   }
   b->state = dev_alloc(b->hook, tot);
-  b->codes = static_cast<uint8_t*>(dev_alloc(b->hook, ctot));
   b->sims = dev_alloc(b->hook, sizeof(BatchSim<float, 2, 1>) * nsims);
   b->maps = static_cast<CUtensorMap*>(dev_alloc(b->hook, sizeof(CUtensorMap) * 2 * nsims));
   b->barrier = static_cast<unsigned int*>(dev_alloc(b->hook, 256));
-  if (!b->state || !b->codes || !b->sims || !b->maps || !b->barrier) {
+  if (!b->state || !b->sims || !b->maps || !b->barrier) {
     batch_free(b);
     return bfail(nullptr, MS_ERR_OOM, "batch allocation failed");
   }
   b->status = reinterpret_cast<int*>(reinterpret_cast<char*>(b->barrier) + 128);
   cudaError_t e = cudaMemsetAsync(b->state, 0, tot, b->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->codes, 0, ctot, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->barrier, 0, 256, b->stream);
   // per-simulation constants and tensor maps
   std::vector<BatchSim<float, 2, 1>> hs(nsims);
@@ -383,23 +358,19 @@ ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_c
   for (int i = 0; i < nsims && e == cudaSuccess; ++i) {
     const HostModel& m = b->models[i];
     const size_t half = (b->sbytes[i] + 255) / 256 * 256;
-    const size_t chalf = (code_bytes(m) + 255) / 256 * 256;
     char* base = static_cast<char*>(b->state) + b->off[i];
-    uint8_t* cbase = b->codes + b->coff[i];
     for (int par = 0; par < 2; ++par) {
       StepArgs<float, 2, 1>& g = hs[i].g[par];
       k->fill(&g, m, 1, b->status);
       g.out = reinterpret_cast<float*>(base + (1 - par) * half);
-      g.codes_in = cbase + par * chalf;
-      g.codes_out = cbase + (1 - par) * chalf;
       g.tz0 = (float)temp_offset(m, m.t0);
       if (!encode_state_map(&hm[2 * i + par], base + par * half, m, 3, kBTX, kBTY)) {
         batch_free(b);
         return bfail(nullptr, MS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
       }
     }
-    const int tiles = ((m.nx + kBTX - 1) / kBTX) * ((m.ny + kBTY - 1) / kBTY);
-    for (int t = 0; t < tiles; ++t) items.push_back(BatchItem{i, t});
+    for (int y0 = 0; y0 < m.ny; y0 += kBTY)
+      for (int x0 = 0; x0 < m.nx; x0 += kBTX) items.push_back(BatchItem{i, x0, y0, x0 + m.xoff - 16 / 4});
   }
   // items in simulation order: each CTA takes a contiguous range of them
   std::vector<BatchItem>& mixed = items;
@@ -418,6 +389,8 @@ ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_c
   auto kern = k_batch<2, 1, float, kBTX, kBTY>;
   b->smem = BF::SMEM;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, b->smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   int per_sm = 0, dev = 0, sms = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBTX * kBTY + 32, b->smem);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -444,13 +417,6 @@ ms_status ms_batch_set_fields(ms_batch* b, int sim, const void* phi, const void*
   cudaError_t e = copy_fields(m, buf, 0, m.N, phi, nullptr, on_device, b->stream);
   if (e == cudaSuccess) e = copy_fields(m, buf, m.N, m.NM, mu, nullptr, on_device, b->stream);
   if (e == cudaSuccess) e = fill_ghosts(m, buf, m.N + m.NM, b->stream);
-  if (e == cudaSuccess) {
-    const size_t chalf = (code_bytes(m) + 255) / 256 * 256;
-    const StepKernel* k = nullptr;
-    for (auto& sk : step_registry())
-      if (sk.dim == 2 && sk.np == 2 && sk.nm == 1 && sk.dtype == 0) k = &sk;
-    e = k->codes(buf, m, b->codes + b->coff[sim] + b->parity * chalf, b->stream);
-  }
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(b, MS_ERR_CUDA, std::string("batch set fields: ") + cudaGetErrorString(e));
   return MS_OK;
