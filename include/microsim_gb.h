@@ -196,7 +196,7 @@ ms_status ms_tile_shape(const ms_ctx* ctx, int tile, int* tx, int* ty);
  * updates the warp rows whose stencil holds one pure phase and lists the
  * others, which a second kernel then updates with the full Sec. 2.1 cell
  * update; results agree with the fused variant of the same tile to FP
- * rounding.  The split variant allocates a work list of 4 bytes per 32-cell
+ * rounding.  The split variant allocates work lists of 8 bytes per 32-cell
  * row segment (once, through the context's allocator) when first selected.
  * 0 for a fused variant, -1 for a bad index. */
 int ms_tile_split(const ms_ctx* ctx, int tile);

@@ -406,4 +406,305 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
   for (int i = 0; i < NM; ++i) mn[i] = mc[i] + dmu[i];
 }
 
+// ------------------------------------------------------------------------
+// The same update for many phases, when the phase mask (uniform over the
+// warp; a superset of every cell's stencil) names at most KP phases: the
+// gradient work -- face fluxes, centre term, face mobilities -- runs on the
+// compact list of present phases; the potential, driving force, rates and the
+// projection run over all NP phases (an absent phase has phi = 0 on the whole
+// stencil, so every gradient term it would enter is exactly zero, but its
+// rate need not be).  Sums keep the order of gp_cell over the non-zero terms.
+// Real arithmetic only (the adjoint's dual numbers use gp_cell).
+
+// Normal face fluxes of the present phases on one face (compact index k).
+template <int DIM, int D, int NP, int NM, int KP, class Real, class Acc>
+__device__ __forceinline__ void face_flux_sparse(const Acc& A, const StepArgs<Real, NP, NM>& g, const int* map,
+                                                 int kn, int side, bool need_tan, Real* Jk) {
+  const Off<DIM> L = unit<DIM>(D, side ? 0 : -1);
+  const Off<DIM> R = unit<DIM>(D, side ? 1 : 0);
+  Real pf[KP], gr[KP][DIM];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    Jk[k] = Real(0);
+    if (k >= kn) continue;
+    const int a = map[k];
+    const Real vl = A.phi(a, L.x, L.y, L.z), vr = A.phi(a, R.x, R.y, R.z);
+    pf[k] = Real(0.5) * (vl + vr);
+    gr[k][D] = (vr - vl) * g.inv_dx;
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      if (t == D) continue;
+      if (need_tan) {
+        const Off<DIM> up = unit<DIM>(t, 1), dn = unit<DIM>(t, -1);
+        const Off<DIM> Lu = add(L, up), Ru = add(R, up), Ld = add(L, dn), Rd = add(R, dn);
+        gr[k][t] = ((A.phi(a, Lu.x, Lu.y, Lu.z) + A.phi(a, Ru.x, Ru.y, Ru.z)) -
+                    (A.phi(a, Ld.x, Ld.y, Ld.z) + A.phi(a, Rd.x, Rd.y, Rd.z))) *
+                   g.quarter_inv_dx;
+      } else {
+        gr[k][t] = Real(0);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+#pragma unroll
+    for (int l = k + 1; l < KP; ++l) {
+      if (l >= kn) continue;
+      const int p = pair_index<NP>(map[k], map[l]);
+      const Real gD = face_pair_flux<DIM, D>(pf[k], pf[l], gr[k], gr[l], g.gam2[p], g.delta[p], g.aniso[p] != 0,
+                                             g.rotated[p] != 0, g.rot[p]);
+      Jk[k] -= pf[l] * gD;
+      Jk[l] += pf[k] * gD;
+    }
+  }
+}
+
+// Cell mobility of a stencil cell from the present phases only (the absent
+// ones have h = 0 there): e1, e2 and the sum over phases as in cell_mobility.
+template <int DIM, int NP, int NM, int KP, class Real, class Acc>
+__device__ __forceinline__ void mobility_sparse(const Acc& A, const StepArgs<Real, NP, NM>& g, const int* map,
+                                                int kn, int dx, int dy, int dz, Real* M) {
+  Real f[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) f[k] = k < kn ? A.phi(map[k], dx, dy, dz) : Real(0);
+  Real e1 = f[0];
+#pragma unroll
+  for (int k = 1; k < KP; ++k) e1 += f[k];
+  Real e2 = Real(0);
+  {
+    Real run = f[0];
+#pragma unroll
+    for (int k = 1; k < KP; ++k) {
+      e2 += f[k] * run;
+      run += f[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    if (k >= kn) break;
+    const Real rest = e2 - f[k] * (e1 - f[k]);
+    const Real p2 = f[k] * f[k];
+    const Real h = Real(3) * p2 - Real(2) * p2 * f[k] + Real(2) * f[k] * rest;
+    const int a = map[k];
+#pragma unroll
+    for (int q = 0; q < NM * NM; ++q) M[q] = k == 0 ? h * g.DX[a][q] : M[q] + h * g.DX[a][q];
+  }
+}
+
+template <int DIM, int NP, int NM, int KP, class Real, class Acc>
+__device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real, NP, NM>& g, int kz, Real* pn,
+                                               Real* mn) {
+  static_assert(!IsDual<Real>::value, "real arithmetic only");
+  const uint32_t mask = A.mask();
+  const int kn = __popc(mask);
+  int map[KP];   // present phases, increasing
+  {
+    uint32_t m = mask;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      map[k] = m ? __ffs(m) - 1 : 0;
+      m &= m - 1u;
+    }
+  }
+  Real ph[NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) ph[a] = ((mask >> a) & 1u) ? A.phi(a, 0, 0, 0) : Real(0);
+  const bool bulk = kn == 1 && A.phi(map[0], 0, 0, 0) == Real(1);
+  const Real s = g.tz0 + g.tzg * (Real(kz) + Real(0.5));   // T^n - T_ref
+  Real mc[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) mc[i] = A.mu(i, 0, 0, 0);
+
+  if (bulk) {
+#pragma unroll
+    for (int a = 0; a < NP; ++a) pn[a] = ph[a];
+  } else {
+    Real dg[KP];   // divJ - Gc of the present phases
+#pragma unroll
+    for (int k = 0; k < KP; ++k) dg[k] = Real(0);
+    if (kn >= 2) {
+      bool need_tan = false;
+#pragma unroll
+      for (int k = 0; k < KP; ++k)
+#pragma unroll
+        for (int l = k + 1; l < KP; ++l)
+          if (l < kn && g.aniso[pair_index<NP>(map[k], map[l])]) need_tan = true;
+      Real divJ[KP];
+#pragma unroll
+      for (int k = 0; k < KP; ++k) divJ[k] = Real(0);
+      {
+        Real Jm[KP], Jp[KP];
+        face_flux_sparse<DIM, 0, NP, NM, KP>(A, g, map, kn, 0, need_tan, Jm);
+        face_flux_sparse<DIM, 0, NP, NM, KP>(A, g, map, kn, 1, need_tan, Jp);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) divJ[k] += (Jp[k] - Jm[k]) * g.inv_dx;
+      }
+      {
+        Real Jm[KP], Jp[KP];
+        face_flux_sparse<DIM, 1, NP, NM, KP>(A, g, map, kn, 0, need_tan, Jm);
+        face_flux_sparse<DIM, 1, NP, NM, KP>(A, g, map, kn, 1, need_tan, Jp);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) divJ[k] += (Jp[k] - Jm[k]) * g.inv_dx;
+      }
+      if constexpr (DIM == 3) {
+        Real Jm[KP], Jp[KP];
+        face_flux_sparse<DIM, 2, NP, NM, KP>(A, g, map, kn, 0, need_tan, Jm);
+        face_flux_sparse<DIM, 2, NP, NM, KP>(A, g, map, kn, 1, need_tan, Jp);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) divJ[k] += (Jp[k] - Jm[k]) * g.inv_dx;
+      }
+      // centre term, central differences
+      Real gc[KP][DIM], Gc[KP], phk[KP];
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        Gc[k] = Real(0);
+        phk[k] = k < kn ? A.phi(map[k], 0, 0, 0) : Real(0);
+        if (k >= kn) continue;
+        const int a = map[k];
+        gc[k][0] = (A.phi(a, 1, 0, 0) - A.phi(a, -1, 0, 0)) * g.half_inv_dx;
+        gc[k][1] = (A.phi(a, 0, 1, 0) - A.phi(a, 0, -1, 0)) * g.half_inv_dx;
+        if constexpr (DIM == 3) gc[k][2] = (A.phi(a, 0, 0, 1) - A.phi(a, 0, 0, -1)) * g.half_inv_dx;
+      }
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+#pragma unroll
+        for (int l = k + 1; l < KP; ++l) {
+          if (l >= kn) continue;
+          const int p = pair_index<NP>(map[k], map[l]);
+          Real q[DIM], gq[DIM];
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) q[d] = phk[k] * gc[l][d] - phk[l] * gc[k][d];
+          pair_grad_fwd<DIM>(q, g.gam2[p], g.delta[p], g.aniso[p] != 0, g.rotated[p] != 0, g.rot[p], gq);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            Gc[k] += gq[d] * gc[l][d];
+            Gc[l] -= gq[d] * gc[k][d];
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KP; ++k) dg[k] = divJ[k] - Gc[k];
+    }
+    // S4: potential derivative over all phases, sums over the present ones
+    Real W[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      W[a] = Real(0);
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        if (k >= kn || map[k] == a) continue;
+        const int b = map[k];
+        if (g.potential == 1)
+          W[a] += g.cw[a][b] * ph[b];
+        else
+          W[a] += g.cw[a][b] * (ph[a] * (ph[b] * ph[b]));
+      }
+      if (g.has_g3) {
+#pragma unroll
+        for (int k = 0; k < KP; ++k)
+#pragma unroll
+          for (int l = k + 1; l < KP; ++l)
+            if (l < kn && map[k] != a && map[l] != a) W[a] += g.g3[a][map[k]][map[l]] * (ph[map[k]] * ph[map[l]]);
+      }
+    }
+    // S4: driving force
+    Real psi[NP];
+#pragma unroll
+    for (int b = 0; b < NP; ++b) psi[b] = grand_potential<NP, NM, Real>(g, b, mc, s);
+    Real e1 = ph[0];
+#pragma unroll
+    for (int a = 1; a < NP; ++a) e1 += ph[a];
+    Real e2 = Real(0);
+    {
+      Real run = ph[0];
+#pragma unroll
+      for (int a = 1; a < NP; ++a) {
+        e2 += ph[a] * run;
+        run += ph[a];
+      }
+    }
+    Real v[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      Real rest = e2 - ph[a] * (e1 - ph[a]);
+      Real P = psi[a] * (Real(6) * ph[a] - Real(6) * (ph[a] * ph[a]) + Real(2) * rest);
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        if (k >= kn || map[k] == a) continue;
+        const int b = map[k];
+        P += psi[b] * (Real(2) * ph[b] * ((e1 - ph[a]) - ph[b]));
+      }
+      Real d = Real(0);
+#pragma unroll
+      for (int k = 0; k < KP; ++k)
+        if (k < kn && map[k] == a) d = dg[k];
+      // S5: rate of Eq. (phi_eqn) / (tau eps), explicit Euler
+      Real r = g.mob * ((g.eps * d - W[a] * g.inv_eps - P) * g.inv_eps);
+      v[a] = ph[a] + g.dt * r;
+    }
+    project<NP>(g.potential, v, pn);
+  }
+
+  // ---- S6/S7: chemical-potential update (mobilities from the present phases)
+  Real h_new[NP];
+  interp_h<NP>(pn, h_new);
+  Real Mc[NM * NM];
+  mobility_sparse<DIM, NP, NM, KP>(A, g, map, kn, 0, 0, 0, Mc);
+  Real div[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) div[i] = Real(0);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+    for (int sd = -1; sd <= 1; sd += 2) {
+      const Off<DIM> o = unit<DIM>(d, sd);
+      Real Mn[NM * NM];
+      mobility_sparse<DIM, NP, NM, KP>(A, g, map, kn, o.x, o.y, o.z, Mn);
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          Real Mf = Real(0.5) * (Mc[i * NM + j] + Mn[i * NM + j]);
+          div[i] += Mf * ((A.mu(j, o.x, o.y, o.z) - mc[j]) * g.inv_dx2);
+        }
+      }
+    }
+  }
+  Real rhs[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) rhs[i] = g.dt * div[i];
+  if (!bulk) {
+    Real h_old[NP];
+    interp_h<NP>(ph, h_old);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      Real dh = h_new[a] - h_old[a];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        Real c_now = Real(0);
+#pragma unroll
+        for (int j = 0; j < NM; ++j) c_now += g.chi[a][i * NM + j] * (mc[j] - (g.B0[a][j] + g.B1[a][j] * s));
+        rhs[i] -= c_now * dh;
+        rhs[i] -= h_new[a] * g.dcT[a][i];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < NP; ++a)
+#pragma unroll
+      for (int i = 0; i < NM; ++i) rhs[i] -= h_new[a] * g.dcT[a][i];
+  }
+  Real chi[NM * NM];
+#pragma unroll
+  for (int k = 0; k < NM * NM; ++k) {
+    chi[k] = h_new[0] * g.chi[0][k];
+#pragma unroll
+    for (int a = 1; a < NP; ++a) chi[k] += h_new[a] * g.chi[a][k];
+  }
+  Real dmu[NM];
+  solve_small<NM>(chi, rhs, dmu);
+#pragma unroll
+  for (int i = 0; i < NM; ++i) mn[i] = mc[i] + dmu[i];
+}
+
 }  // namespace msgb

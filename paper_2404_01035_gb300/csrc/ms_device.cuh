@@ -50,6 +50,7 @@ struct StepArgs {
   // indices (z ny + y) segs + segment of the rows that are not bulk.
   unsigned int* iface;
   unsigned int iface_cap;
+  unsigned int* iface2;   // second list, same layout (rows left for the full update)
   // 1 when the output buffer holds the state one step before the input
   // (ping-pong stepping), so codes_out still describe it before they are
   // overwritten: bulk rows whose pure phase is unchanged then skip phi.

@@ -54,7 +54,8 @@ struct LaunchGeom {
   int tiles = 0;       // gridDim.x
   int zchunks = 1;     // gridDim.y
   int zchunk = 1;
-  unsigned int* iface = nullptr;   // work list of split kernels (see StepArgs)
+  unsigned int* iface = nullptr;   // work lists of split kernels (see StepArgs)
+  unsigned int* iface2 = nullptr;
   unsigned int iface_cap = 0;
   int iface_blocks = 0;            // SMs: the interface grid is this x resident CTAs per SM
   int reuse_prev = 1;              // output buffer = state one step before the input (see StepArgs)

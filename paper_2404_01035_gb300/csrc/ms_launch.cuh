@@ -125,6 +125,7 @@ void set_launch_args(StepArgs<Real, NP, NM>& g, const HostModel& m, double t, vo
   g.tz0 = (Real)temp_offset(m, t);
   g.zchunk = lg.zchunk;
   g.iface = lg.iface;
+  g.iface2 = lg.iface2;
   g.iface_cap = lg.iface_cap;
   g.reuse_prev = lg.reuse_prev;
 }
@@ -151,31 +152,37 @@ cudaError_t launch_step(const CUtensorMap* tm, const CUtensorMap*, void* blob, c
 // Split 3-D FP32 step: the bulk streaming kernel (tm = mu-only tile map),
 // then the interface kernel over the rows it listed (tmi = interface boxes).
 template <int NP, int NM, int TY>
-cudaError_t launch_split(const CUtensorMap* tm, const CUtensorMap* tmi, void* blob, const HostModel& m,
-                         double t, void* out, const uint8_t* codes_in, uint8_t* codes_out, const LaunchGeom& lg,
+cudaError_t launch_split(const CUtensorMap* tm, const CUtensorMap* tmi, void* blob, const HostModel& m, double t,
+                         void* out, const uint8_t* codes_in, uint8_t* codes_out, const LaunchGeom& lg,
                          cudaStream_t st) {
   using Ss = StreamShape<NP, NM, TY>;
   using Si = IfaceShape<NP, NM, float>;
-  if (!lg.iface || !tmi || lg.iface_blocks < 1) return cudaErrorInvalidValue;
+  constexpr bool two = NP > kSparseK;   // a second launch for rows with many phases
+  if (!lg.iface || !lg.iface2 || !tmi || lg.iface_blocks < 1) return cudaErrorInvalidValue;
   auto& g = *reinterpret_cast<StepArgs<float, NP, NM>*>(blob);
   set_launch_args(g, m, t, out, codes_in, codes_out, lg);
   auto ks = k_gp_stream<NP, NM, TY>;
-  auto ki = k_gp_iface<3, NP, NM, float>;
+  auto ki = k_gp_iface<3, NP, NM, float, 0>;
+  auto kf = k_gp_iface<3, NP, NM, float, 1>;
   static bool configured = false;   // attributes are per function, set once
-  static int iface_per_sm = 0;      // resident interface CTAs per SM
+  static int iface_per_sm = 0, full_per_sm = 0;   // resident CTAs per SM
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, Ss::SMEM_BYTES);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&iface_per_sm, ki, Si::THREADS, Si::SMEM_BYTES);
+    if (two && e == cudaSuccess)
+      e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
+    if (two && e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&full_per_sm, kf, Si::THREADS, Si::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    if (iface_per_sm < 1) iface_per_sm = 1;
+    iface_per_sm = iface_per_sm < 1 ? 1 : iface_per_sm;
+    full_per_sm = full_per_sm < 1 ? 1 : full_per_sm;
     configured = true;
   }
   ks<<<dim3(lg.tiles, lg.zchunks), Ss::NTHREADS, Ss::SMEM_BYTES, st>>>(*tm, g);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   ki<<<lg.iface_blocks * iface_per_sm, Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
+  if constexpr (two) kf<<<lg.iface_blocks * full_per_sm, Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
   return cudaGetLastError();
 }
 

@@ -435,14 +435,17 @@ int default_zchunk(const HostModel& m, const StepKernel& k) {
 ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk) {
   if (k->split && !c->iface) {
     // work list of the split step: count, ticket and one entry per warp row
+    // (two lists: the second takes the rows left for a second launch)
     const size_t cap = (size_t)segments(c->m) * c->m.ny * c->m.nz;
     if (cap > 0xFFFFFFF0ull) return fail(c, MS_ERR_UNSUPPORTED, "grid too large for the split step");
-    c->iface = static_cast<unsigned int*>(dev_alloc(c->hook, (cap + 2) * sizeof(unsigned int)));
+    c->iface = static_cast<unsigned int*>(dev_alloc(c->hook, 2 * (cap + 2) * sizeof(unsigned int)));
     if (!c->iface) return fail(c, MS_ERR_OOM, "interface work-list allocation failed");
-    cudaError_t e = cudaMemsetAsync(c->iface, 0, 2 * sizeof(unsigned int), c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "work-list reset");
     c->lg.iface = c->iface;
+    c->lg.iface2 = c->iface + cap + 2;
     c->lg.iface_cap = (unsigned int)cap;
+    cudaError_t e = cudaMemsetAsync(c->lg.iface, 0, 2 * sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->lg.iface2, 0, 2 * sizeof(unsigned int), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "work-list reset");
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

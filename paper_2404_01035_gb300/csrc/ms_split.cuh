@@ -34,7 +34,7 @@ struct StreamShape {
   static constexpr int FSTRIDE = SY * SX;         // elements per field in a stage
   static constexpr int STAGE_BYTES = NM * FSTRIDE * 4;
   static constexpr int STAGE_STRIDE = (STAGE_BYTES + 127) / 128 * 128;
-  static constexpr int NST_RAW = (52 * 1024) / STAGE_STRIDE;
+  static constexpr int NST_RAW = (44 * 1024) / STAGE_STRIDE;   // 4 CTAs per SM
   static constexpr int NST = NST_RAW < 4 ? 4 : (NST_RAW > 12 ? 12 : NST_RAW);
   static constexpr int NFL = SY * WCS;            // row flags per entry (one per producer lane)
   static constexpr int NWF = TY * WCS;            // combined flags per entry
@@ -51,7 +51,7 @@ struct StreamShape {
   static constexpr int OFF_BAR = OFF_COEF + (NP * NCOEF * 4 + 15) / 16 * 16;
   static constexpr int OFF_ABORT = OFF_BAR + 2 * NST * 8;
   static constexpr int SMEM_BYTES = OFF_ABORT + 16 + 128;
-  static constexpr int MIN_BLOCKS = 3;
+  static constexpr int MIN_BLOCKS = 4;
   static_assert(NFL <= 32, "the producer warp holds one row flag per lane");
 };
 
@@ -361,6 +361,10 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
   }
 }
 
+// Phases the compact update of the interface kernel handles (more phases
+// than this around a row take the full update).
+constexpr int kSparseK = 4;
+
 // Interface kernel of the split 3-D step (shape of its shared memory).  Each
 // warp owns two buffers of one TMA box: 32 + 2H cells x 3 rows x 3 planes x
 // all fields around one listed 32-cell row, so the next row is in flight
@@ -430,13 +434,18 @@ __device__ __forceinline__ uint32_t box_phase_mask(const Real* box, int lane) {
 // Interface kernel of the split 3-D step: the full cell update of every warp
 // row the streaming kernel listed (32 cells of one row of one plane per
 // warp), from a TMA box of the input state; writes phi, mu, their ghost
-// images and the row's segment code.  The last CTA to finish clears the list
-// for the next step (ticket in iface[1]), so the pair of launches can be
-// replayed from a CUDA graph.
-template <int DIM, int NP, int NM, class Real>
+// images and the row's segment code.  With more than kSparseK phases the
+// work is shared by two launches: MODE 0 takes the rows whose box holds at
+// most kSparseK phases (the compact update) and moves the others to a second
+// list, which MODE 1 updates with the full one (each kernel's registers then
+// fit its own path).  The last CTA to finish clears its list (ticket in
+// list[1]), so the launches can be replayed from a CUDA graph.
+template <int DIM, int NP, int NM, class Real, int MODE>
 __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<NP, NM, Real>::MIN_BLOCKS)
     k_gp_iface(const __grid_constant__ CUtensorMap tmi, const __grid_constant__ StepArgs<Real, NP, NM> g) {
   static_assert(DIM == 3, "the interface list is built by the 3-D streaming kernel");
+  constexpr bool kSparse = NP > kSparseK && MODE == 0;   // compact update, defer the rest
+  unsigned int* const list = MODE == 0 ? g.iface : g.iface2;
   using Sh = IfaceShape<NP, NM, Real>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
@@ -445,7 +454,7 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR) + 2 * wid;
   Real* buf0 = reinterpret_cast<Real*>(smem + (2 * wid) * Sh::BOX_STRIDE);
-  if (threadIdx.x == 0) s_count = min(*(volatile unsigned int*)&g.iface[0], g.iface_cap);
+  if (threadIdx.x == 0) s_count = min(*(volatile unsigned int*)&list[0], g.iface_cap);
   if (lane == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -462,7 +471,7 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
 
   // row r = (z ny + y) segs + segment  ->  box origin (x, y - 1, z - 1 in padded coordinates)
   auto issue = [&](unsigned int i, int b) {
-    const unsigned int r = g.iface[2 + i];
+    const unsigned int r = list[2 + i];
     const int sg = (int)(r % (unsigned int)g.segs);
     const unsigned int zy = r / (unsigned int)g.segs;
     const int y = (int)(zy % (unsigned int)g.ny), z = (int)(zy / (unsigned int)g.ny);
@@ -491,7 +500,7 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
     }
     pending[b] = false;
     phase[b] ^= 1u;
-    const unsigned int r = g.iface[2 + i];
+    const unsigned int r = list[2 + i];
     const int sg = (int)(r % (unsigned int)g.segs);
     const unsigned int zy = r / (unsigned int)g.segs;
     const int y = (int)(zy % (unsigned int)g.ny), z = (int)(zy / (unsigned int)g.ny);
@@ -499,6 +508,18 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
     const bool active = x < g.nx;
     const Real* box = reinterpret_cast<const Real*>(reinterpret_cast<unsigned char*>(buf0) + b * Sh::BOX_STRIDE);
     const uint32_t wmask = box_phase_mask<NP, NM, Real>(box, lane);
+    if constexpr (kSparse) {
+      if (__popc(wmask) > kSparseK) {   // for the MODE 1 launch
+        if (lane == 0) {
+          const unsigned int k = atomicAdd(&g.iface2[0], 1u);
+          if (k < g.iface_cap) g.iface2[2 + k] = r;
+        }
+        __syncwarp();
+        b ^= 1;
+        i = nxt;
+        continue;
+      }
+    }
     int code = 0;
     if (active) {
       BoxAcc<DIM, NP, NM, Real> acc;
@@ -507,7 +528,10 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
       acc.sidx = 3 * Sh::BX + Sh::BX + Sh::H + lane;
       acc.wmask = wmask;
       Real pn[NP], mn[NM];
-      gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, z + g.zorg, pn, mn);
+      if constexpr (kSparse)   // many phases, at most kSparseK of them around this row
+        gp_cell_sparse<DIM, NP, NM, kSparseK, Real>(acc, g, z + g.zorg, pn, mn);
+      else
+        gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, z + g.zorg, pn, mn);
       uint32_t nzm = 0, one = 0;
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
@@ -538,9 +562,9 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(&g.iface[1], 1u) == gridDim.x - 1) {
-      g.iface[0] = 0u;
-      g.iface[1] = 0u;
+    if (atomicAdd(&list[1], 1u) == gridDim.x - 1) {
+      list[0] = 0u;
+      list[1] = 0u;
     }
   }
 }

@@ -82,6 +82,37 @@ def test_3d_eight_phase_multigrain(dtype, steps, tol):
     assert max_err(g, o) <= tol
 
 
+def _split_tile(prob):
+    from paper_2404_01035_gb300 import Simulation
+    sim = Simulation(prob, dtype="f32")
+    tiles = sim.tiles()
+    sim.close()
+    return [i for i, t in enumerate(tiles) if t[2] == 1][0], tiles
+
+
+def test_3d_eight_phase_multigrain_split_variant():
+    # the split step with 8 phases: rows around a grain hold few phases and
+    # take the compact update (MODE 0 of the interface kernel)
+    p = W.cfg5(n=40, grains=7, R=5.0, min_sep=14.0, seed=3)
+    t, _ = _split_tile(p)
+    g = gpu_run(p, 300, "f32", set_launch=(t, 16))
+    o = oracle.run(p, p.phi0, p.mu0, 300)
+    assert max_err(g, o) <= FP32_TOL
+
+
+def test_3d_eight_phase_dense_split_matches_fused():
+    # every phase everywhere: rows whose box holds more than 4 phases go to
+    # the second interface launch (MODE 1); agreement with the fused kernel
+    # to FP32 rounding after 20 steps, bitwise across z-chunks
+    p = W.small_multiphase(n=20, dim=3, N=8, NM=1, nx=70, ny=37, nz=30)
+    t, tiles = _split_tile(p)
+    fused = gpu_run(p, 20, "f32", set_launch=(0, 0))
+    a = gpu_run(p, 20, "f32", set_launch=(t, 16))
+    b = gpu_run(p, 20, "f32", set_launch=(t, 5))
+    assert max_err(a, fused) <= 1e-6
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_2d_three_phase_ternary(dtype):
     p = W.small_multiphase(n=30, dim=2, N=3, NM=2, nx=70, ny=45, rotate=True, gamma3=0.3)
