@@ -301,6 +301,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_extras:
         extra["batched"] = bench_batched(stream)
         extra["adjoint"] = bench_adjoint(stream)
+        extra["multigrain"] = bench_multigrain(stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -368,6 +369,34 @@ def bench_batched(stream):
             "plain_step_mlups": plain, "plain_step": f"single {big.nx}^2 simulation, one launch per step",
             "vs_plain_step": batched / plain,
             "hbm_frac": batched * 1e6 * 24 / (measured_peaks()[0]["hbm_gbs"] * 1e9)}
+
+
+def bench_multigrain(stream):
+    """3-D 512^3 multigrain (8 phases: 7 rotated grains + liquid, binary, FP32,
+    periodic): the launch the tuner picks, 100 steps from the seeded state."""
+    import workloads
+    from paper_2404_01035_gb300 import Simulation
+    p = workloads.cfg5()
+    sim = Simulation(p, dtype="f32", stream=stream)
+    sim.set_fields(p.phi0, p.mu0)
+    sim.tune(None, steps_per_trial=10)
+    sim.set_fields(p.phi0, p.mu0)
+    sim.step(10)
+    steps = 100
+    ms = _events_ms(stream, lambda: sim.step(steps))
+    tiles = sim.tiles()
+    t, zc = sim.launch()
+    sim.close()
+    mlups = p.cells * steps / (ms / 1e3) / 1e6
+    bpc = algorithmic_bytes_per_cell(p, 4)
+    return {"workload": "3-D 512^3 multigrain: 8 phases (7 rotated grains + liquid), binary, FP32, "
+                        "periodic, 100 steps from the seeded state", "cells": int(p.cells),
+            "mlups": mlups, "ms_per_step": ms / steps,
+            "launch": {"tx": tiles[t][0], "ty": tiles[t][1], "split": tiles[t][2], "zchunk": zc},
+            "bytes_per_cell": bpc,
+            "algorithmic_hbm_frac": mlups * 1e6 * bpc / (measured_peaks()[0]["hbm_gbs"] * 1e9),
+            "note": "99.6% of the cells are bulk liquid, whose update moves mu only, so the "
+                    "algorithmic fraction (every field read and written once) can exceed 1"}
 
 
 def bench_adjoint(stream):

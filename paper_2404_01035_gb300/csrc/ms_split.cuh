@@ -293,35 +293,57 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
       const bool write_phi = sprev[(k * TY + ty) * Sh::WCS + wc] != flag;
       if (vec_ok) {
         float* p = out0 + k * plane;
+        const long long fs = g.fstride;
+        // the cell row
+        if (write_phi) {
+#pragma unroll
+          for (int a = 0; a < NP; ++a) {
+            const float v = a == l ? 1.0f : 0.0f;
+            stg4(p + a * fs, v, v, v, v);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < NM; ++i) stg4(p + (NP + i) * fs, mn[i][0], mn[i][1], mn[i][2], mn[i][3]);
+        // x ghost images of the row's first / last cell (lanes 0 and 31 of the
+        // tiles at the x ends)
+        if (oxl | oxr) {
+#pragma unroll
+          for (int a = 0; a < NP + NM; ++a) {
+            if (a < NP && !write_phi) continue;
+            const float v0 = a < NP ? (a == l ? 1.0f : 0.0f) : mn[a < NP ? 0 : a - NP][0];
+            const float v3 = a < NP ? (a == l ? 1.0f : 0.0f) : mn[a < NP ? 0 : a - NP][3];
+            if (oxl) p[oxl + a * fs] = v0;
+            if (oxr) p[3 + oxr + a * fs] = v3;
+          }
+        }
+        // rows at a y or z boundary (rare): their y / z images, with x images
         long long oz0 = 0, oz1 = 0;
         if (g.bc[2] != kBcHalo) {   // internal cuts get their ghost planes from the exchange
           if (z == 0) oz0 = (g.bc[2] == 3 ? g.nz : -1) * plane;
           if (z == g.nz - 1) oz1 = (g.bc[2] == 3 ? -g.nz : 1) * plane;
         }
-        const long long oy[3] = {0, oy0, oy1}, oz[3] = {0, oz0, oz1};
-        // the cell row and its y / z ghost images (at most 8 rows, corners included)
+        if ((oy0 | oy1 | oz0 | oz1) != 0) {
+          const long long oy[3] = {0, oy0, oy1}, oz[3] = {0, oz0, oz1};
+          for (int iz = 0; iz < 3; ++iz)
+            for (int iy = 0; iy < 3; ++iy) {
+              if ((iy | iz) == 0 || (iy && !oy[iy]) || (iz && !oz[iz])) continue;
+              float* q = p + oy[iy] + oz[iz];
+              for (int a = 0; a < NP + NM; ++a) {
+                if (a < NP && !write_phi) continue;
+                float c4[4];
+                if (a < NP) {
+                  const float v = a == l ? 1.0f : 0.0f;
+                  c4[0] = c4[1] = c4[2] = c4[3] = v;
+                } else {
 #pragma unroll
-        for (int iz = 0; iz < 3; ++iz)
-#pragma unroll
-          for (int iy = 0; iy < 3; ++iy) {
-            if ((iy && !oy[iy]) || (iz && !oz[iz])) continue;
-            float* q = p + oy[iy] + oz[iz];
-            if (write_phi) {
-#pragma unroll
-              for (int a = 0; a < NP; ++a) {
-                const float v = a == l ? 1.0f : 0.0f;
-                stg4(q + a * g.fstride, v, v, v, v);
-                if (oxl) q[oxl + a * g.fstride] = v;
-                if (oxr) q[3 + oxr + a * g.fstride] = v;
+                  for (int u = 0; u < 4; ++u) c4[u] = mn[a - NP][u];
+                }
+                stg4(q + a * fs, c4[0], c4[1], c4[2], c4[3]);
+                if (oxl) q[oxl + a * fs] = c4[0];
+                if (oxr) q[3 + oxr + a * fs] = c4[3];
               }
             }
-#pragma unroll
-            for (int i = 0; i < NM; ++i) {
-              stg4(q + (NP + i) * g.fstride, mn[i][0], mn[i][1], mn[i][2], mn[i][3]);
-              if (oxl) q[oxl + (NP + i) * g.fstride] = mn[i][0];
-              if (oxr) q[3 + oxr + (NP + i) * g.fstride] = mn[i][3];
-            }
-          }
+        }
       } else {
         // partial groups at the end of a ragged row: per cell, with every image
         float pn[NP];
