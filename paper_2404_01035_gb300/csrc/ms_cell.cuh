@@ -21,6 +21,8 @@
 // phi^{n+1} = phi^n there bit for bit; only the mu update is evaluated.
 #pragma once
 
+#include <type_traits>
+
 #include "ms_device.cuh"
 
 namespace msgb {
@@ -105,6 +107,49 @@ __device__ __forceinline__ S face_pair_flux(const S& pa, const S& pb, const S* g
   return gq[D];
 }
 
+// Normal (axis D) component of g_ab on the two faces of a cell along D at
+// once (low half: the face shared with the -D neighbour, high half: with the
+// +D neighbour) in paired FP32 arithmetic: face values pa, pb, their
+// negations, face gradients ga, gb.  Same forms as face_pair_flux.
+template <int DIM, int D>
+__device__ __forceinline__ F2 face_pair_flux2(F2 pa, F2 npb, const F2* ga, const F2* gb, float gam2, float del,
+                                              bool aniso, bool rotated, const float* R) {
+  const F2 qD = fma2(pa, gb[D], npb * ga[D]);
+  if (!aniso) return f2s(gam2) * qD;
+  F2 q[DIM];
+#pragma unroll
+  for (int t = 0; t < DIM; ++t) q[t] = t == D ? qD : fma2(pa, gb[t], npb * ga[t]);
+  if (rotated) {
+    float ql[DIM], qh[DIM], gl[DIM], gh[DIM];
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      ql[t] = f2lo(q[t]);
+      qh[t] = f2hi(q[t]);
+    }
+    pair_grad<DIM>(ql, gam2, del, true, true, R, gl);
+    pair_grad<DIM>(qh, gam2, del, true, true, R, gh);
+    return f2(gl[D], gh[D]);
+  }
+  F2 q2[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) q2[i] = q[i] * q[i];
+  F2 Q = q2[0], s4 = q2[0] * q2[0];
+#pragma unroll
+  for (int i = 1; i < DIM; ++i) {
+    Q = Q + q2[i];
+    s4 = fma2(q2[i], q2[i], s4);
+  }
+  const float Ql = f2lo(Q), Qh = f2hi(Q);
+  const bool tl = Ql < 1e-12f, th = Qh < 1e-12f;
+  if (tl && th) return f2s(0.0f);
+  const F2 invQ = f2(recip(tl ? 1.0f : Ql), recip(th ? 1.0f : Qh));
+  const F2 r = s4 * invQ * invQ;
+  const F2 ac = fma2(f2s(4.0f * del), r, f2s(1.0f - 3.0f * del));
+  const F2 t = q2[D] * invQ - r;
+  const F2 gD = (f2s(gam2) * ac) * qD * fma2(f2s(16.0f * del), t, ac);
+  return f2(tl ? 0.0f : f2lo(gD), th ? 0.0f : f2hi(gD));
+}
+
 template <class S, int P>
 struct DiffPrm {
   S mob;         // phase-field mobility 1/tau
@@ -177,6 +222,52 @@ __device__ __forceinline__ void face_flux(const Acc& A, const StepArgs<Real, NP,
   }
 }
 
+// Both faces along axis D at once in paired FP32 arithmetic (low half: the
+// face with the -D neighbour, high half: with the +D neighbour); the same
+// discretisation as face_flux, J[a] = (J_a on the low face, on the high face).
+template <int DIM, int D, int NP, int NM, class Acc>
+__device__ __forceinline__ void face_flux_pair(const Acc& A, const StepArgs<float, NP, NM>& g, uint32_t mask,
+                                               bool need_tan, F2* J) {
+  const Off<DIM> m = unit<DIM>(D, -1), p = unit<DIM>(D, 1);
+  F2 pf[NP], npf[NP], gr[NP][DIM];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    J[a] = f2s(0.0f);
+    if (!((mask >> a) & 1u)) continue;
+    const float vm = A.phi(a, m.x, m.y, m.z), v0 = A.phi(a, 0, 0, 0), vp = A.phi(a, p.x, p.y, p.z);
+    const F2 vl = f2(vm, v0), vr = f2(v0, vp);
+    pf[a] = f2s(0.5f) * (vl + vr);
+    npf[a] = f2s(-0.5f) * (vl + vr);
+    gr[a][D] = (vr - vl) * f2s(g.inv_dx);
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      if (t == D) continue;
+      if (need_tan) {
+        const Off<DIM> up = unit<DIM>(t, 1), dn = unit<DIM>(t, -1);
+        const Off<DIM> mu_ = add(m, up), md = add(m, dn), pu = add(p, up), pd = add(p, dn);
+        const float cu = A.phi(a, up.x, up.y, up.z), cd = A.phi(a, dn.x, dn.y, dn.z);
+        const F2 Lu = f2(A.phi(a, mu_.x, mu_.y, mu_.z), cu), Ru = f2(cu, A.phi(a, pu.x, pu.y, pu.z));
+        const F2 Ld = f2(A.phi(a, md.x, md.y, md.z), cd), Rd = f2(cd, A.phi(a, pd.x, pd.y, pd.z));
+        gr[a][t] = ((Lu + Ru) - (Ld + Rd)) * f2s(g.quarter_inv_dx);
+      } else {
+        gr[a][t] = f2s(0.0f);
+      }
+    }
+  }
+  int pi = 0;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int b = a + 1; b < NP; ++b, ++pi) {
+      if (!(((mask >> a) & (mask >> b)) & 1u)) continue;
+      const F2 gD = face_pair_flux2<DIM, D>(pf[a], npf[b], gr[a], gr[b], g.gam2[pi], g.delta[pi], g.aniso[pi] != 0,
+                                            g.rotated[pi] != 0, g.rot[pi]);
+      J[a] = fma2(npf[b], gD, J[a]);
+      J[b] = fma2(pf[a], gD, J[b]);
+    }
+  }
+}
+
 // psi^b(mu, T) = C^b(T) - 1/2 (mu - B^b)^T chi^b (mu - B^b), s = T - T_ref.
 template <int NP, int NM, class Real, class S>
 __device__ __forceinline__ S grand_potential(const StepArgs<Real, NP, NM>& g, int b, const S* mu,
@@ -238,25 +329,46 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
       }
       // S1-S3: divergence of the face fluxes
       {
-        S Jm[NP], Jp[NP];
-        face_flux<DIM, 0>(A, g, dp, mask, 0, need_tan, Jm);
-        face_flux<DIM, 0>(A, g, dp, mask, 1, need_tan, Jp);
+        if constexpr (std::is_same<S, float>::value) {
+          F2 J[NP];
+          face_flux_pair<DIM, 0>(A, g, mask, need_tan, J);
 #pragma unroll
-        for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+          for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
+        } else {
+          S Jm[NP], Jp[NP];
+          face_flux<DIM, 0>(A, g, dp, mask, 0, need_tan, Jm);
+          face_flux<DIM, 0>(A, g, dp, mask, 1, need_tan, Jp);
+#pragma unroll
+          for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+        }
       }
       {
-        S Jm[NP], Jp[NP];
-        face_flux<DIM, 1>(A, g, dp, mask, 0, need_tan, Jm);
-        face_flux<DIM, 1>(A, g, dp, mask, 1, need_tan, Jp);
+        if constexpr (std::is_same<S, float>::value) {
+          F2 J[NP];
+          face_flux_pair<DIM, 1>(A, g, mask, need_tan, J);
 #pragma unroll
-        for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+          for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
+        } else {
+          S Jm[NP], Jp[NP];
+          face_flux<DIM, 1>(A, g, dp, mask, 0, need_tan, Jm);
+          face_flux<DIM, 1>(A, g, dp, mask, 1, need_tan, Jp);
+#pragma unroll
+          for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+        }
       }
       if constexpr (DIM == 3) {
-        S Jm[NP], Jp[NP];
-        face_flux<DIM, 2>(A, g, dp, mask, 0, need_tan, Jm);
-        face_flux<DIM, 2>(A, g, dp, mask, 1, need_tan, Jp);
+        if constexpr (std::is_same<S, float>::value) {
+          F2 J[NP];
+          face_flux_pair<DIM, 2>(A, g, mask, need_tan, J);
 #pragma unroll
-        for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+          for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
+        } else {
+          S Jm[NP], Jp[NP];
+          face_flux<DIM, 2>(A, g, dp, mask, 0, need_tan, Jm);
+          face_flux<DIM, 2>(A, g, dp, mask, 1, need_tan, Jp);
+#pragma unroll
+          for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+        }
       }
       // centre term, central differences
       S gc[NP][DIM];

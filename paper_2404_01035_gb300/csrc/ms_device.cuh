@@ -295,6 +295,49 @@ __host__ __device__ constexpr int pair_index(int a, int b) {
 }
 
 // g = dA/dq for A(q) = gamma a_c(R q)^2 |q|^2 with the four-fold
+// Two FP32 values in one 64-bit register with the paired FP32 arithmetic of
+// sm_100-class GPUs (one add / sub / mul / fma instruction for both halves,
+// each rounded as the scalar operation).
+struct F2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ F2 f2(float lo, float hi) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ F2 f2s(float x) { return f2(x, x); }
+__device__ __forceinline__ float f2lo(F2 a) {
+  float l, h;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(a.v));
+  return l;
+}
+__device__ __forceinline__ float f2hi(F2 a) {
+  float l, h;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(a.v));
+  return h;
+}
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+  F2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+  F2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
+  F2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {   // a * b + c
+  F2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+
 // 1 / x: the hardware approximate reciprocal in FP32 (relative error of a
 // few ulp, far below the FP32 path's tolerance), an exact division otherwise.
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }

@@ -163,7 +163,7 @@ cudaError_t launch_split(const CUtensorMap* tm, const CUtensorMap* tmi, void* bl
   set_launch_args(g, m, t, out, codes_in, codes_out, lg);
   auto ks = k_gp_stream<NP, NM, TY>;
   auto ki = k_gp_iface<3, NP, NM, float, 0>;
-  auto kf = k_gp_iface<3, NP, NM, float, 1>;
+  auto kf = k_gp_iface<3, NP, NM, float, two ? 1 : 0>;   // only launched when two
   static bool configured = false;   // attributes are per function, set once
   static int iface_per_sm = 0, full_per_sm = 0;   // resident CTAs per SM
   if (!configured) {
