@@ -268,6 +268,31 @@ __device__ __forceinline__ void face_flux_pair(const Acc& A, const StepArgs<floa
   }
 }
 
+// Cell mobilities M = sum_a h_a D^a chi^a of the two neighbours along axis d
+// at once (low half: the -d neighbour, high half: the +d one), paired FP32.
+template <int DIM, int NP, int NM, class Acc>
+__device__ __forceinline__ void mobility_pair(const Acc& A, const StepArgs<float, NP, NM>& g, int d, F2* M) {
+  const Off<DIM> m = unit<DIM>(d, -1), p = unit<DIM>(d, 1);
+  F2 f[NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) f[a] = f2(A.phi(a, m.x, m.y, m.z), A.phi(a, p.x, p.y, p.z));
+  F2 e1 = f[0], e2 = f2s(0.0f), run = f[0];
+#pragma unroll
+  for (int a = 1; a < NP; ++a) {
+    e1 = e1 + f[a];
+    e2 = fma2(f[a], run, e2);
+    run = run + f[a];
+  }
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    const F2 rest = e2 - f[a] * (e1 - f[a]);
+    const F2 p2 = f[a] * f[a];
+    const F2 h = f2s(3.0f) * p2 - f2s(2.0f) * p2 * f[a] + f2s(2.0f) * f[a] * rest;
+#pragma unroll
+    for (int k = 0; k < NM * NM; ++k) M[k] = a == 0 ? h * f2s(g.DX[0][k]) : fma2(h, f2s(g.DX[a][k]), M[k]);
+  }
+}
+
 // psi^b(mu, T) = C^b(T) - 1/2 (mu - B^b)^T chi^b (mu - B^b), s = T - T_ref.
 template <int NP, int NM, class Real, class S>
 __device__ __forceinline__ S grand_potential(const StepArgs<Real, NP, NM>& g, int b, const S* mu,
@@ -463,19 +488,43 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
   S div[NM];
 #pragma unroll
   for (int i = 0; i < NM; ++i) div[i] = S(Real(0));
+  if constexpr (std::is_same<S, float>::value) {
+    // both neighbours along each axis at once (paired FP32)
+    F2 dv[NM];
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) {
+    for (int i = 0; i < NM; ++i) dv[i] = f2s(0.0f);
 #pragma unroll
-    for (int sd = -1; sd <= 1; sd += 2) {
-      const Off<DIM> o = unit<DIM>(d, sd);
-      S Mn[NM * NM];
-      A.mobility(o.x, o.y, o.z, Mn);
+    for (int d = 0; d < DIM; ++d) {
+      const Off<DIM> m = unit<DIM>(d, -1), p = unit<DIM>(d, 1);
+      F2 Mn[NM * NM];
+      mobility_pair<DIM, NP, NM>(A, g, d, Mn);
 #pragma unroll
       for (int i = 0; i < NM; ++i) {
 #pragma unroll
         for (int j = 0; j < NM; ++j) {
-          S Mf = Real(0.5) * (Mc[i * NM + j] + Mn[i * NM + j]);
-          div[i] += Mf * ((A.mu(j, o.x, o.y, o.z) - mc[j]) * g.inv_dx2);
+          const F2 Mf = f2s(0.5f) * (f2s(Mc[i * NM + j]) + Mn[i * NM + j]);
+          const F2 dm = f2(A.mu(j, m.x, m.y, m.z), A.mu(j, p.x, p.y, p.z)) - f2s(mc[j]);
+          dv[i] = fma2(Mf, dm * f2s(g.inv_dx2), dv[i]);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NM; ++i) div[i] = f2lo(dv[i]) + f2hi(dv[i]);
+  } else {
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+      for (int sd = -1; sd <= 1; sd += 2) {
+        const Off<DIM> o = unit<DIM>(d, sd);
+        S Mn[NM * NM];
+        A.mobility(o.x, o.y, o.z, Mn);
+#pragma unroll
+        for (int i = 0; i < NM; ++i) {
+#pragma unroll
+          for (int j = 0; j < NM; ++j) {
+            S Mf = Real(0.5) * (Mc[i * NM + j] + Mn[i * NM + j]);
+            div[i] += Mf * ((A.mu(j, o.x, o.y, o.z) - mc[j]) * g.inv_dx2);
+          }
         }
       }
     }
