@@ -80,9 +80,11 @@ typedef struct {
   int nx, ny, nz;   /* cells per axis; nz is ignored (taken as 1) for dim = 2 */
   double dx;        /* cell size (DELTA_X = DELTA_Y = DELTA_Z) */
   int bc[3];        /* MS_BC_* for the x, y, z axes (both faces of an axis) */
-  int z_origin;     /* global index of this grid's first z-plane when it is one
-                       slab of a larger domain (0 otherwise); the temperature
-                       field is evaluated at the global plane index */
+  int z_origin;     /* lab index of this grid's first cell along the last axis
+                       (z in 3-D, y in 2-D): the first plane of a slab of a
+                       larger domain, or the frame offset after ms_shift (0
+                       otherwise); the temperature field and the phi-noise
+                       counter use lab indices */
 } ms_grid;
 
 /* Model inputs, named after the paper's infile keys.  All pointers are host
@@ -107,6 +109,15 @@ typedef struct {
   double T0, G, z0, V;     /* Tempgrady: T(s,t) = T0 + G (s - z0 - V t), s the
                               cell-centre coordinate along the last axis */
   double t0;               /* physical time of the initial state */
+  double noise_amp;        /* Noise_phasefield / Amp_Noise_Phase: every step adds
+                              dt * noise_amp * xi to the phi rate of each phase a
+                              with 0 < phi_a < 1 at the cell, before the
+                              projection; xi uniform in [-1/2, 1/2) from the
+                              SplitMix64 finaliser (Steele, Lea, Flood 2014)
+                              applied to noise_seed, the step index and the lab
+                              cell index x + nx (y + ny z) times N plus a.  0 =
+                              off.  Not available with ms_grad or ms_batch_*. */
+  unsigned long long noise_seed;
 } ms_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  NULL in
@@ -185,6 +196,21 @@ ms_status ms_time(const ms_ctx* ctx, int64_t* step, double* t);
 size_t ms_checkpoint_bytes(const ms_ctx* ctx);
 ms_status ms_checkpoint(ms_ctx* ctx, void* host_buf, size_t bytes);
 ms_status ms_restore(ms_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Moving frame (the SHIFT key of the paper's input files, Sec. 4: a camera
+ * that follows the solidification front).  Drops the first `planes` cells
+ * along the last axis (z in 3-D, y in 2-D), moves the rest down, fills the far
+ * end with pure liquid (the last phase) at chemical potentials mu_fill[K-1]
+ * (host array, the original alloy's) and advances the grid's z_origin by
+ * `planes`, so the pulled temperature field and the phi-noise counter stay in
+ * lab coordinates.  0 <= planes <= extent of the last axis; checkpoints of
+ * the adjoint are dropped.  MS_ERR_UNSUPPORTED for a slab of a decomposed
+ * domain (MS_BC_HALO along z).  Asynchronous on the context's stream. */
+ms_status ms_shift(ms_ctx* ctx, int planes, const double* mu_fill);
+/* Highest index along the last axis holding a cell that is not pure liquid
+ * (phi of the last phase != 1), -1 if none: the position of the growth front
+ * for the moving-frame test.  Synchronises the context's stream. */
+ms_status ms_front(ms_ctx* ctx, int* last_plane);
 
 /* Launch shape: tile (index into ms_tile_shapes) and z-chunk (planes marched
  * per CTA, 3-D only; 0 = automatic; values above 64 are clamped to 64). */

@@ -59,6 +59,8 @@ class _Problem(ctypes.Structure):
         ("ceq", ctypes.c_void_p), ("slopes", ctypes.c_void_p), ("f0", ctypes.c_void_p),
         ("T_ref", ctypes.c_double), ("T0", ctypes.c_double), ("G", ctypes.c_double),
         ("z0", ctypes.c_double), ("V", ctypes.c_double), ("t0", ctypes.c_double),
+        ("z_origin", ctypes.c_int), ("noise_amp", ctypes.c_double), ("noise_seed", ctypes.c_ulonglong),
+        ("step0", ctypes.c_longlong),
     ]
 
 
@@ -83,6 +85,8 @@ def lib():
             L.oracle_interp.argtypes = [ctypes.c_int, dp, dp, dp]
             L.oracle_project.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
             L.oracle_thermo.argtypes = [P, ctypes.c_int, dp, ctypes.c_double, dp, dp, dp]
+            L.oracle_noise.argtypes = [ctypes.c_ulonglong, ctypes.c_longlong, ctypes.c_ulonglong]
+            L.oracle_noise.restype = ctypes.c_double
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_set_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -96,8 +100,9 @@ def _dp(a):
 class OracleProblem:
     """Marshals a problem description (duck-typed workloads.Problem) for the C oracle."""
 
-    def __init__(self, prob, t0: float = 0.0, **override):
+    def __init__(self, prob, t0: float = 0.0, step0: int = 0, **override):
         g = lambda k: override.get(k, getattr(prob, k))
+        opt = lambda k, d: override.get(k, getattr(prob, k, d))
         self.N = int(g("n_phases"))
         self.NM = int(g("n_components")) - 1
         self.dim = int(g("dim"))
@@ -133,6 +138,11 @@ class OracleProblem:
         s.T_ref, s.T0, s.G = float(g("T_ref")), float(g("T0")), float(g("G"))
         s.z0, s.V = float(g("z0")), float(g("V"))
         s.t0 = float(t0)
+        meta = getattr(prob, "meta", None) or {}
+        s.z_origin = int(override.get("z_origin", meta.get("z_origin", 0)))
+        s.noise_amp = float(opt("noise_amp", 0.0))
+        s.noise_seed = int(opt("noise_seed", 0)) & 0xFFFFFFFFFFFFFFFF
+        s.step0 = int(step0)
         self.s = s
 
     @property
@@ -146,9 +156,10 @@ class OracleProblem:
         return ctypes.byref(self.s)
 
 
-def run(prob, phi0, mu0, nsteps: int, t0: float = 0.0, **override):
-    """nsteps explicit steps in FP64; returns (phi, mu) shaped [F][nz][ny][nx]."""
-    op = OracleProblem(prob, t0, **override)
+def run(prob, phi0, mu0, nsteps: int, t0: float = 0.0, step0: int = 0, **override):
+    """nsteps explicit steps in FP64; returns (phi, mu) shaped [F][nz][ny][nx].
+    step0 = step index of the input state (the counter of the phi noise)."""
+    op = OracleProblem(prob, t0, step0, **override)
     phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(op.shape(op.N))
     mu0 = np.ascontiguousarray(mu0, dtype=np.float64).reshape(op.shape(op.NM))
     phi = np.empty_like(phi0)
@@ -157,6 +168,39 @@ def run(prob, phi0, mu0, nsteps: int, t0: float = 0.0, **override):
     if rc:
         raise ValueError("oracle_run rejected the problem")
     return phi, mu
+
+
+def noise(seed: int, step: int, counter: int) -> float:
+    """The phi-noise variate in [-1/2, 1/2) for (seed, step, counter), counter =
+    lab cell index x + nx (y + ny z) times N plus the phase."""
+    return lib().oracle_noise(int(seed) & 0xFFFFFFFFFFFFFFFF, int(step), int(counter) & 0xFFFFFFFFFFFFFFFF)
+
+
+def shift(dim, phi, mu, planes: int, mu_fill):
+    """Moving frame (the SHIFT key of Sec. 4, "moving camera"): drop the first
+    `planes` cells along the last axis (z in 3-D, y in 2-D), move the rest
+    down and fill the far end with pure liquid (the last phase) at the
+    chemical potential mu_fill of the original alloy.  Fields [F][nz][ny][nx]."""
+    ax = 1 if dim == 3 else 2
+    n = phi.shape[ax]
+    k = int(planes)
+    out = []
+    for f, fill in ((phi, None), (mu, mu_fill)):
+        g = np.empty_like(f)
+        src = [slice(None)] * 4
+        dst = [slice(None)] * 4
+        src[ax], dst[ax] = slice(k, n), slice(0, n - k)
+        g[tuple(dst)] = f[tuple(src)]
+        tail = [slice(None)] * 4
+        tail[ax] = slice(n - k, n)
+        if fill is None:
+            g[tuple(tail)] = 0.0
+            g[(-1,) + tuple(tail[1:])] = 1.0
+        else:
+            for i, v in enumerate(np.atleast_1d(fill)):
+                g[(i,) + tuple(tail[1:])] = float(v)
+        out.append(g)
+    return out[0], out[1]
 
 
 def run_tangent(prob, phi0, mu0, nsteps: int, dphi0=None, dmu0=None, ddelta=None,

@@ -96,6 +96,10 @@ typedef struct {
   const double* f0;      // [N] or NULL
   double T_ref, T0, G, z0, V;
   double t0;             // physical time of the input state
+  int z_origin;          // lab index of the first cell along the last axis
+  double noise_amp;      // phi noise amplitude (0 = off)
+  unsigned long long noise_seed;
+  long long step0;       // step index of the input state (noise counter)
 } oracle_problem;
 
 }  // extern "C"
@@ -381,11 +385,31 @@ S grand_potential(const oracle_problem& p, int a, const S* mu, double T) {
   return f - mc;
 }
 
-// Temperature at a cell centre (frozen, pulled gradient along the last axis).
+// Temperature at a cell centre (frozen, pulled gradient along the last axis,
+// in lab coordinates: the grid starts at lab index z_origin).
 double temperature(const oracle_problem& p, int y, int z, double t) {
-  int k = p.dim == 3 ? z : y;
+  int k = (p.dim == 3 ? z : y) + p.z_origin;
   double s = (k + 0.5) * p.dx;
   return p.T0 + p.G * (s - p.z0 - p.V * t);
+}
+
+// ------------------------------------------------------------------ noise
+// Counter-based uniform variate in [-1/2, 1/2): the SplitMix64 finaliser
+// (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+// OOPSLA 2014) applied in turn to the seed, the step index and the lab cell
+// index times N plus the phase; the top 24 bits of the last value.
+inline uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+inline double noise_variate(uint64_t seed, uint64_t step, uint64_t counter) {
+  uint64_t h = splitmix64(seed);
+  h = splitmix64(h ^ step);
+  h = splitmix64(h ^ counter);
+  return static_cast<double>(h >> 40) * (1.0 / 16777216.0) - 0.5;
 }
 
 // ------------------------------------------------------- simplex projection
@@ -529,7 +553,7 @@ void cell_mobility(const Ctx<S>& c, const S* phi, int64_t ic, S* M) {
 
 // One explicit step phi^n, mu^n (time t) -> phi^{n+1}, mu^{n+1}.
 template <class S>
-void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, double t) {
+void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, double t, int64_t nstep) {
   const oracle_problem& p = *c.p;
   const int N = p.N, NM = p.NM, dim = p.dim;
 #pragma omp parallel for collapse(2) schedule(dynamic, 1)
@@ -544,6 +568,14 @@ void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, dou
           ph[a] = phi[a * c.cells + ic];
           S r = c.q.mob * (p.eps * (divJ[a] - Gc[a]) - W[a] / p.eps - P[a]) / p.eps;
           v[a] = ph[a] + p.dt * r;
+          // phi noise on the cell's interface phases (0 < phi_a < 1): an
+          // additive dt * amplitude * xi on the rate, before the projection
+          if (p.noise_amp != 0.0 && val(ph[a]) > 0.0 && val(ph[a]) < 1.0) {
+            const int64_t ylab = dim == 3 ? y : y + p.z_origin;
+            const int64_t zlab = dim == 3 ? z + p.z_origin : 0;
+            const uint64_t gcell = static_cast<uint64_t>(x + (int64_t)c.n[0] * (ylab + (int64_t)c.n[1] * zlab));
+            v[a] += p.dt * p.noise_amp * noise_variate(p.noise_seed, (uint64_t)nstep, gcell * N + a);
+          }
         }
         if (p.potential == 1)
           project_simplex(N, v, pn);
@@ -657,7 +689,7 @@ int oracle_run(const oracle_problem* p, const double* phi0, const double* mu0, i
   std::vector<double> pa(phi0, phi0 + p->N * cells), pb(p->N * cells);
   std::vector<double> ma(mu0, mu0 + p->NM * cells), mb(p->NM * cells);
   for (int n = 0; n < nsteps; ++n) {
-    step(c, pa.data(), ma.data(), pb.data(), mb.data(), p->t0 + n * p->dt);
+    step(c, pa.data(), ma.data(), pb.data(), mb.data(), p->t0 + n * p->dt, p->step0 + n);
     pa.swap(pb);
     ma.swap(mb);
   }
@@ -688,7 +720,7 @@ int oracle_run_tangent(const oracle_problem* p, const double* phi0, const double
   for (int64_t i = 0; i < p->N * cells; ++i) pa[i] = Dual(phi0[i], dphi0 ? dphi0[i] : 0.0);
   for (int64_t i = 0; i < p->NM * cells; ++i) ma[i] = Dual(mu0[i], dmu0 ? dmu0[i] : 0.0);
   for (int n = 0; n < nsteps; ++n) {
-    step(c, pa.data(), ma.data(), pb.data(), mb.data(), p->t0 + n * p->dt);
+    step(c, pa.data(), ma.data(), pb.data(), mb.data(), p->t0 + n * p->dt, p->step0 + n);
     pa.swap(pb);
     ma.swap(mb);
   }
@@ -759,6 +791,11 @@ int oracle_diag(const oracle_problem* p, const double* phi, const double* mu, do
 }
 
 // ---- single-formula probes used by the pin tests
+// The phi-noise variate for (seed, step, counter) (see noise_variate).
+double oracle_noise(unsigned long long seed, long long step, unsigned long long counter) {
+  return noise_variate(seed, (uint64_t)step, counter);
+}
+
 double oracle_pair_energy(const oracle_problem* p, int a, int b, const double* q) {
   Ctx<double> c;
   init_ctx(c, p);

@@ -27,7 +27,8 @@ EXPORTS = [
     "ms_create", "ms_destroy", "ms_last_error", "ms_update_params", "ms_set_fields",
     "ms_get_fields", "ms_fields", "ms_step", "ms_diag", "ms_set_diag_every", "ms_sync",
     "ms_time", "ms_checkpoint_bytes", "ms_checkpoint", "ms_restore", "ms_set_launch",
-    "ms_tile_count", "ms_tile_shape", "ms_tile_split", "ms_get_launch", "ms_tune", "ms_diag_noalloc",
+    "ms_tile_count", "ms_tile_shape", "ms_tile_split", "ms_get_launch", "ms_tune",
+    "ms_shift", "ms_front", "ms_diag_noalloc",
     "ms_enable_checkpoints", "ms_grad_param_count", "ms_grad",
     "ms_batch_create", "ms_batch_destroy", "ms_batch_last_error", "ms_batch_set_fields",
     "ms_batch_get_fields", "ms_batch_step", "ms_batch_sync", "ms_batch_cells",
@@ -56,6 +57,7 @@ class Params(ctypes.Structure):
         ("ceq", ctypes.c_void_p), ("slopes", ctypes.c_void_p), ("f0", ctypes.c_void_p),
         ("T_ref", ctypes.c_double), ("T0", ctypes.c_double), ("G", ctypes.c_double),
         ("z0", ctypes.c_double), ("V", ctypes.c_double), ("t0", ctypes.c_double),
+        ("noise_amp", ctypes.c_double), ("noise_seed", ctypes.c_ulonglong),
     ]
 
 
@@ -108,6 +110,8 @@ def lib(build_if_missing: bool = True):
         L.ms_tile_count.argtypes = [vp]
         L.ms_tile_shape.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]
+        L.ms_shift.argtypes = [vp, ctypes.c_int, dp]
+        L.ms_front.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.ms_tile_split.argtypes = [vp, ctypes.c_int]
         L.ms_get_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.ms_tune.argtypes = [vp, ctypes.c_char_p, ctypes.c_int, dp]

@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(128) k_adjoint(const Real* __restrict__ st, co
             A.seed = seed;
             A.DX = &g.DX;
             DF pn[NP], mn[NM];
-            gp_cell<DIM, NP, NM, Real, DF>(A, g, dpf, DIM == 3 ? rz + g.zorg : ry, pn, mn);
+            gp_cell<DIM, NP, NM, Real, DF>(A, g, dpf, (DIM == 3 ? rz : ry) + g.zorg, lab_cell<DIM>(g, rx, ry, rz), pn,
+                                           mn);
             const long long ri = dense(rx, ry, rz);
 #pragma unroll
             for (int a = 0; a < NP; ++a) {
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(128) k_adjoint(const Real* __restrict__ st, co
       A.seed = -1;
       A.DX = &DXd;
       DPm pn[NP], mn[NM];
-      gp_cell<DIM, NP, NM, Real, DPm>(A, g, dpp, DIM == 3 ? z + g.zorg : y, pn, mn);
+      gp_cell<DIM, NP, NM, Real, DPm>(A, g, dpp, (DIM == 3 ? z : y) + g.zorg, lab_cell<DIM>(g, x, y, z), pn, mn);
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
         const Real l = lam_in[a * cells + j];
@@ -325,6 +326,8 @@ ms_status ms_enable_checkpoints(ms_ctx* c, int every) {
   if (!c || every < 0) return fail(c, MS_ERR_ARG, "bad argument");
   if (every > 0 && !find_adjoint(c->m))
     return fail(c, MS_ERR_UNSUPPORTED, "no compiled adjoint kernel for this (dim, N, K, dtype)");
+  if (every > 0 && c->m.noise_amp != 0.0)
+    return fail(c, MS_ERR_UNSUPPORTED, "the adjoint does not support phi noise (noise_amp != 0)");
   ms_reset_extra(c);
   c->adj.every = every;
   return MS_OK;
@@ -341,6 +344,7 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
   if (!c || !dphi_T) return fail(c, MS_ERR_ARG, "ctx and dphi_T are required");
   AdjointStore& A = c->adj;
   if (A.every <= 0) return fail(c, MS_ERR_STATE, "checkpoints are not enabled (ms_enable_checkpoints)");
+  if (c->m.noise_amp != 0.0) return fail(c, MS_ERR_UNSUPPORTED, "the adjoint does not support phi noise (noise_amp != 0)");
   const AdjKernel* ak = find_adjoint(c->m);
   if (!ak) return fail(c, MS_ERR_UNSUPPORTED, "no compiled adjoint kernel for this (dim, N, K, dtype)");
   const int64_t nsteps = c->step - A.first_step;

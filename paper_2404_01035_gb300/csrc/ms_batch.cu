@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(TX* TY + 32, 3)
             dp.mob = g.mob;
 #pragma unroll
             for (int p = 0; p < StepArgs<Real, NP, NM>::P; ++p) dp.delta[p] = g.delta[p];
-            gp_cell<2, NP, NM, Real, Real>(acc, g, dp, y, pn, mn);
+            gp_cell<2, NP, NM, Real, Real>(acc, g, dp, y + g.zorg, lab_cell<2>(g, x, y, 0), pn, mn);
           }
           store_cell<2>(g, x, y, 0, pn, mn);
         }
@@ -318,6 +318,10 @@ ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_c
     if (m.dim != 2 || m.N != 2 || m.NM != 1 || m.dtype != MS_F32) {
       batch_free(b);
       return bfail(nullptr, MS_ERR_UNSUPPORTED, "the batched kernel is compiled for 2-D, N=2, K=2, FP32");
+    }
+    if (m.noise_amp != 0.0) {
+      batch_free(b);
+      return bfail(nullptr, MS_ERR_UNSUPPORTED, "batched simulations do not support phi noise (noise_amp != 0)");
     }
     if (m.G * m.V != 0.0) {
       batch_free(b);

@@ -313,8 +313,8 @@ __device__ __forceinline__ S grand_potential(const StepArgs<Real, NP, NM>& g, in
 // The full cell update.  kz = cell index along the last axis (for T).
 template <int DIM, int NP, int NM, class Real, class S, class Acc>
 __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, NM>& g,
-                                        const DiffPrm<S, NP*(NP - 1) / 2>& dp, int kz, S* pn,
-                                        S* mn) {
+                                        const DiffPrm<S, NP*(NP - 1) / 2>& dp, int kz, unsigned long long gcell,
+                                        S* pn, S* mn) {
   S ph[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) ph[a] = A.phi(a, 0, 0, 0);
@@ -476,6 +476,9 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
       // S5: rate of Eq. (phi_eqn) / (tau eps), explicit Euler
       S r = dp.mob * ((g.eps * (divJ[a] - Gc[a]) - W[a] * g.inv_eps - P) * g.inv_eps);
       v[a] = ph[a] + g.dt * r;
+      // phi noise on the interface phases of the cell (0 < phi_a < 1)
+      if (g.noise_amp != Real(0) && val(ph[a]) > Real(0) && val(ph[a]) < Real(1))
+        v[a] = v[a] + g.dt * g.noise_amp * noise_variate<Real>(g.noise_seed, g.step, gcell * NP + a);
     }
     project<NP>(g.potential, v, pn);
   }
@@ -653,8 +656,8 @@ __device__ __forceinline__ void mobility_sparse(const Acc& A, const StepArgs<Rea
 }
 
 template <int DIM, int NP, int NM, int KP, class Real, class Acc>
-__device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real, NP, NM>& g, int kz, Real* pn,
-                                               Real* mn) {
+__device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real, NP, NM>& g, int kz,
+                                               unsigned long long gcell, Real* pn, Real* mn) {
   static_assert(!IsDual<Real>::value, "real arithmetic only");
   const uint32_t mask = A.mask();
   const int kn = __popc(mask);
@@ -802,6 +805,8 @@ __device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real
       // S5: rate of Eq. (phi_eqn) / (tau eps), explicit Euler
       Real r = g.mob * ((g.eps * d - W[a] * g.inv_eps - P) * g.inv_eps);
       v[a] = ph[a] + g.dt * r;
+      if (g.noise_amp != Real(0) && ph[a] > Real(0) && ph[a] < Real(1))
+        v[a] = v[a] + g.dt * g.noise_amp * noise_variate<Real>(g.noise_seed, g.step, gcell * NP + a);
     }
     project<NP>(g.potential, v, pn);
   }

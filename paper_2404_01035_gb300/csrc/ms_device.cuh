@@ -51,6 +51,9 @@ struct StepArgs {
   unsigned int* iface;
   unsigned int iface_cap;
   unsigned int* iface2;   // second list, same layout (rows left for the full update)
+  // phi noise: amplitude, seed, step index of the input state
+  Real noise_amp;
+  unsigned long long noise_seed, step;
   // 1 when the output buffer holds the state one step before the input
   // (ping-pong stepping), so codes_out still describe it before they are
   // overwritten: bulk rows whose pure phase is unchanged then skip phi.
@@ -336,6 +339,36 @@ __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {   // a * b + c
   F2 r;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
   return r;
+}
+
+// ------------------------------------------------------------- phi noise
+// Counter-based uniform variate in [-1/2, 1/2): the SplitMix64 finaliser
+// (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+// OOPSLA 2014) applied in turn to the seed, the step index and the counter;
+// the top 24 bits of the last value (exact in FP32 and FP64).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <class Real>
+__device__ __forceinline__ Real noise_variate(unsigned long long seed, unsigned long long step,
+                                              unsigned long long counter) {
+  unsigned long long h = splitmix64(seed);
+  h = splitmix64(h ^ step);
+  h = splitmix64(h ^ counter);
+  return Real(h >> 40) * Real(1.0 / 16777216.0) - Real(0.5);
+}
+
+// Lab index of cell (x, y, z): x + nx (y_lab + ny z_lab), the last axis
+// offset by the grid's origin (z in 3-D, y in 2-D).
+template <int DIM, class Real, int NP, int NM>
+__device__ __forceinline__ unsigned long long lab_cell(const StepArgs<Real, NP, NM>& g, int x, int y, int z) {
+  const long long yl = DIM == 3 ? y : y + g.zorg;
+  const long long zl = DIM == 3 ? z + g.zorg : 0;
+  return (unsigned long long)(x + (long long)g.nx * (yl + (long long)g.ny * zl));
 }
 
 // 1 / x: the hardware approximate reciprocal in FP32 (relative error of a

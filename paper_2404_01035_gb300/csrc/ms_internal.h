@@ -29,7 +29,7 @@ constexpr int kMaxZChunk = 64;
 struct HostModel {
   int dim = 2, N = 2, NM = 1, dtype = 0;
   int nx = 1, ny = 1, nz = 1, bc[3] = {3, 3, 3};
-  int zorg = 0;   // global index of the first z-plane (slab decomposition)
+  int zorg = 0;   // lab index of the first cell along the last axis (slabs, moving frame)
   // padded layout (elements)
   int pitch = 0, nyp = 0, nzp = 0, xoff = 0, zoff = 0;
   long long fstride = 0;
@@ -47,6 +47,8 @@ struct HostModel {
   double B0[kNMax][kKMax] = {}, B1[kNMax][kKMax] = {};
   double C0[kNMax] = {}, C1[kNMax] = {}, C2[kNMax] = {};
   double T0 = 0, G = 0, z0 = 0, V = 0, T_ref = 0, t0 = 0;
+  double noise_amp = 0;                    // phi noise (0 = off)
+  unsigned long long noise_seed = 0;
 };
 
 // Launch geometry of one step.
@@ -59,6 +61,7 @@ struct LaunchGeom {
   unsigned int iface_cap = 0;
   int iface_blocks = 0;            // SMs: the interface grid is this x resident CTAs per SM
   int reuse_prev = 1;              // output buffer = state one step before the input (see StepArgs)
+  long long step = 0;              // step index of the input state (phi-noise counter)
 };
 
 // One compiled forward-step instantiation.

@@ -29,6 +29,8 @@ void fill_args(void* blob, const HostModel& m, int zchunk, int* status) {
   g.zoff = m.zoff;
   g.zchunk = zchunk;
   g.zorg = m.zorg;
+  g.noise_amp = (Real)m.noise_amp;
+  g.noise_seed = m.noise_seed;
   for (int d = 0; d < 3; ++d) g.bc[d] = m.bc[d];
   g.status = status;
   g.dt = (Real)m.dt;
@@ -128,6 +130,7 @@ void set_launch_args(StepArgs<Real, NP, NM>& g, const HostModel& m, double t, vo
   g.iface2 = lg.iface2;
   g.iface_cap = lg.iface_cap;
   g.reuse_prev = lg.reuse_prev;
+  g.step = (unsigned long long)lg.step;
 }
 
 // Fused step: one kernel updates every cell.

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kNaThreads) k_diag_dense(
     acc[NM] = fmax(acc[NM], fabs(sum - 1.0));
     Real h[NP];
     interp_h<NP>(ph, h);
-    const Real s = (Real)(tz0 + tzg * ((DIM == 3 ? z + zorg : y) + 0.5));
+    const Real s = (Real)(tz0 + tzg * ((DIM == 3 ? z : y) + zorg + 0.5));
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
       Real ci = Real(0);

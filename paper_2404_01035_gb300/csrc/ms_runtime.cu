@@ -139,7 +139,7 @@ ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params
   m.ny = g->ny;
   m.nz = g->dim == 3 ? g->nz : 1;
   for (int d = 0; d < 3; ++d) m.bc[d] = g->bc[d];
-  m.zorg = g->dim == 3 ? g->z_origin : 0;
+  m.zorg = g->z_origin;
   if (m.zorg < 0) return fail(c, MS_ERR_ARG, "z_origin must be >= 0");
   m.dx = g->dx;
   m.dt = p->dt;
@@ -214,6 +214,9 @@ ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params
   m.V = p->V;
   m.T_ref = p->T_ref;
   m.t0 = p->t0;
+  if (!(p->noise_amp >= 0.0) || !std::isfinite(p->noise_amp)) return fail(c, MS_ERR_ARG, "noise_amp must be finite and >= 0");
+  m.noise_amp = p->noise_amp;
+  m.noise_seed = p->noise_seed;
   // explicit stability bound (FP64): (dx^2 / 2d) min(tau / (gamma (1 + 15 delta)), 1 / D_eff)
   double gmax = 0, dmax = 0, Dmax = 0;
   for (int a = 0; a < N; ++a)
@@ -465,6 +468,7 @@ ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk) {
 
 ms_status launch_one_step(ms_ctx* c) {
   const int src = c->cur, dst = 1 - c->cur;
+  c->lg.step = c->step;
   cudaError_t e = c->kern->launch(&c->tm[src], &c->tmi[src], c->args.data(), c->m, c->t, c->buf[dst], c->codes[src],
                                   c->codes[dst], c->lg, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step launch");

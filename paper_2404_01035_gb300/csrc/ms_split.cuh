@@ -551,9 +551,9 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
       acc.wmask = wmask;
       Real pn[NP], mn[NM];
       if constexpr (kSparse)   // many phases, at most kSparseK of them around this row
-        gp_cell_sparse<DIM, NP, NM, kSparseK, Real>(acc, g, z + g.zorg, pn, mn);
+        gp_cell_sparse<DIM, NP, NM, kSparseK, Real>(acc, g, z + g.zorg, lab_cell<DIM>(g, x, y, z), pn, mn);
       else
-        gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, z + g.zorg, pn, mn);
+        gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, z + g.zorg, lab_cell<DIM>(g, x, y, z), pn, mn);
       uint32_t nzm = 0, one = 0;
 #pragma unroll
       for (int a = 0; a < NP; ++a) {

@@ -431,7 +431,8 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
         dp.mob = g.mob;
 #pragma unroll
         for (int p = 0; p < StepArgs<Real, NP, NM>::P; ++p) dp.delta[p] = g.delta[p];
-        gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, DIM == 3 ? z + g.zorg : y, pn, mn);
+        gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, (DIM == 3 ? z : y) + g.zorg, lab_cell<DIM>(g, x, y, z), pn,
+                                         mn);
         uint32_t nzm = 0, one = 0;
 #pragma unroll
         for (int a = 0; a < NP; ++a) {

@@ -102,7 +102,7 @@ extern "C" ms_status ms_tune(ms_ctx* c, const char* cache_path, int steps, doubl
   cudaEventCreate(&ev1);
   std::vector<int> zcs;
   if (c->m.dim == 3) {
-    for (int z : {8, 16, 32, 64})
+    for (int z : {8, 12, 16, 24, 32, 64})
       if (z <= c->m.nz) zcs.push_back(z);
     if (zcs.empty()) zcs.push_back(c->m.nz);
   } else {

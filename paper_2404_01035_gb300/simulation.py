@@ -43,6 +43,8 @@ def make_params(prob, dtype: str, keep: list, **override) -> Params:
     p.T_ref, p.T0, p.G = float(g("T_ref")), float(g("T0")), float(g("G"))
     p.z0, p.V = float(g("z0")), float(g("V"))
     p.t0 = float(override.get("t0", 0.0))
+    p.noise_amp = float(override.get("noise_amp", getattr(prob, "noise_amp", 0.0)))
+    p.noise_seed = int(override.get("noise_seed", getattr(prob, "noise_seed", 0))) & 0xFFFFFFFFFFFFFFFF
     return p
 
 
@@ -53,7 +55,7 @@ def make_grid(prob) -> Grid:
     gr.dx = float(prob.dx)
     bc = list(prob.bc) + [3, 3, 3]
     gr.bc = (ctypes.c_int * 3)(*bc[:3])
-    gr.z_origin = int(getattr(prob, "meta", {}).get("z_origin", 0)) if prob.dim == 3 else 0
+    gr.z_origin = int(getattr(prob, "meta", {}).get("z_origin", 0))
     return gr
 
 
@@ -230,6 +232,32 @@ class Simulation:
     def restore(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         self._c(lib().ms_restore(self.h, buf, len(blob)))
+
+    # ------------------------------------------------------------ moving frame
+    def shift(self, planes: int, mu_fill):
+        """Moving frame: drop `planes` cells at the start of the last axis, fill
+        the far end with pure liquid at chemical potentials mu_fill (K-1
+        values), advance the lab origin (ms_shift)."""
+        mf = np.ascontiguousarray(np.atleast_1d(np.asarray(mu_fill, dtype=np.float64)))
+        self._c(lib().ms_shift(self.h, int(planes), mf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def front(self) -> int:
+        """Highest index along the last axis with a cell that is not pure liquid (-1 if none)."""
+        v = ctypes.c_int()
+        self._c(lib().ms_front(self.h, ctypes.byref(v)))
+        return v.value
+
+    def step_moving_frame(self, n: int, keep: int, mu_fill, check_every: int = 100):
+        """n steps in a frame that follows the growth front: every check_every
+        steps, when the front has passed index `keep`, shift it back to `keep`."""
+        done = 0
+        while done < n:
+            k = min(check_every, n - done)
+            self.step(k)
+            done += k
+            f = self.front()
+            if f > keep:
+                self.shift(f - keep, mu_fill)
 
     # ----------------------------------------------------------- launch shape
     def tiles(self):

@@ -102,6 +102,8 @@ class Problem:
     z0: float = 0.0
     V: float = 0.0
     steps: int = 1
+    noise_amp: float = 0.0         # phi noise amplitude (0 = off)
+    noise_seed: int = 0
     phi0: np.ndarray = None        # [N,nz,ny,nx]
     mu0: np.ndarray = None         # [K-1,nz,ny,nx]
     meta: dict = field(default_factory=dict)
