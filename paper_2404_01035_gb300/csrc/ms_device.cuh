@@ -40,8 +40,11 @@ struct StepArgs {
   Real* out;                // destination state (padded, NP + NM fields)
   int* status;              // sticky device status word
   // Segment codes: one byte per 32-cell x-segment of every row of every
-  // plane, [nz][ny][segs]; l + 1 when all its cells are exactly pure phase l,
-  // else 0.  Read for the input state, written for the output state.
+  // plane, [nz][ny][segs]; the low bits (kCodePhase) hold l + 1 when all its
+  // cells are exactly pure phase l, else 0; bit kCodeReuse is set by the
+  // split step when the state one step earlier held the same pure phase there
+  // (writers that do not know that state leave it clear).  Read for the input
+  // state, written for the output state.
   const uint8_t* codes_in;
   uint8_t* codes_out;
   int segs;
@@ -55,8 +58,9 @@ struct StepArgs {
   Real noise_amp;
   unsigned long long noise_seed, step;
   // 1 when the output buffer holds the state one step before the input
-  // (ping-pong stepping), so codes_out still describe it before they are
-  // overwritten: bulk rows whose pure phase is unchanged then skip phi.
+  // (ping-pong stepping): bulk rows whose pure phase is unchanged over the
+  // two steps then skip phi (fused step: codes_out still describe that state
+  // before they are overwritten; split step: the reuse bit of codes_in).
   int reuse_prev;
   // scalars
   Real dt, eps, inv_eps, mob, inv_dx, half_inv_dx, quarter_inv_dx, inv_dx2;

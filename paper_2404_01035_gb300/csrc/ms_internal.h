@@ -24,6 +24,10 @@ constexpr int kStatusLaunch = 4;   // launch geometry beyond a compiled limit (n
 // Planes marched by one CTA of the 3-D step at most (bounds the shared-memory
 // copy of the segment codes a CTA reads).
 constexpr int kMaxZChunk = 64;
+// Segment-code byte: pure phase + 1 in the low bits (phases <= kNMax), and a
+// bit saying that the state one step earlier held the same pure phase there.
+constexpr int kCodePhase = 0x7F;
+constexpr int kCodeReuse = 0x80;
 
 // Model constants derived in FP64 from the paper's inputs (Sec. 3).
 struct HostModel {

@@ -41,13 +41,10 @@ struct StreamShape {
   static constexpr int CSEG = WCS + 2;
   static constexpr int CODE_ENTRIES = (kMaxZChunk + 2) * SY * CSEG;
   static constexpr int CODE_ITERS = (CODE_ENTRIES + NTHREADS - 1) / NTHREADS;
-  static constexpr int PREV_ENTRIES = kMaxZChunk * TY * WCS;
-  static constexpr int PREV_ITERS = (PREV_ENTRIES + NTHREADS - 1) / NTHREADS;
   static constexpr int OFF_FLAG = NST * STAGE_STRIDE;
   static constexpr int OFF_CODE = OFF_FLAG + (NST * NWF + 15) / 16 * 16;
-  static constexpr int OFF_PREV = OFF_CODE + (CODE_ENTRIES + 15) / 16 * 16;
   static constexpr int NCOEF = NM * NM + NM;     // Kb_l and eb_l of one phase
-  static constexpr int OFF_COEF = OFF_PREV + (PREV_ENTRIES + 15) / 16 * 16;
+  static constexpr int OFF_COEF = OFF_CODE + (CODE_ENTRIES + 15) / 16 * 16;
   static constexpr int OFF_BAR = OFF_COEF + (NP * NCOEF * 4 + 15) / 16 * 16;
   static constexpr int OFF_ABORT = OFF_BAR + 2 * NST * 8;
   static constexpr int SMEM_BYTES = OFF_ABORT + 16 + 128;
@@ -107,7 +104,7 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
 
   // The producer starts the first ring entries (their flags are published by
   // a plain arrive later); every thread loads the segment codes the CTA needs
-  // (input state, with halo) and the previous-state codes of its own rows.
+  // (input state, with halo).
   const int npre = nplanes < NST ? nplanes : NST;
   if (tid == Sh::NT) {
     prefetch_tensormap(&tm);
@@ -129,30 +126,11 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
         v[it] = load_code(g, seg0 - 1 + k, y0 - 1 + ay, zb - 1 + j);
       }
     }
-    const int nprev = nk * TY * Sh::WCS;
-    uint8_t w[Sh::PREV_ITERS];
-#pragma unroll
-    for (int it = 0; it < Sh::PREV_ITERS; ++it) {
-      const int e = tid + it * Sh::NTHREADS;
-      w[it] = 0;
-      if (e < nprev && g.reuse_prev) {
-        const int wc = e % Sh::WCS, r = e / Sh::WCS;
-        const int ty = r % TY, k = r / TY;
-        const int y = y0 + ty, sg = seg0 + wc;
-        if (y < g.ny && sg < g.segs) w[it] = g.codes_out[((long long)(zb + k + g.zoff) * g.ny + y) * g.segs + sg];
-      }
-    }
     uint8_t* scode = smem + Sh::OFF_CODE;
-    uint8_t* sprev = smem + Sh::OFF_PREV;
 #pragma unroll
     for (int it = 0; it < Sh::CODE_ITERS; ++it) {
       const int e = tid + it * Sh::NTHREADS;
       if (e < ncode) scode[e] = v[it];
-    }
-#pragma unroll
-    for (int it = 0; it < Sh::PREV_ITERS; ++it) {
-      const int e = tid + it * Sh::NTHREADS;
-      if (e < nprev) sprev[e] = w[it];
     }
   }
   __syncthreads();   // the last CTA-wide barrier: roles split below
@@ -226,7 +204,10 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
   const long long oy1 = y == g.ny - 1 ? (long long)(g.bc[1] == 3 ? -g.ny : 1) * g.pitch : 0;
   const long long cplane = (long long)g.ny * g.segs;
   uint8_t* const code0 = g.codes_out + ((long long)(zb + g.zoff) * g.ny + y) * g.segs + seg;
-  const uint8_t* sprev = smem + Sh::OFF_PREV;
+  // input code of this thread's segment at plane k: entry k + 1, row ty + 1,
+  // segment wc + 1 of the shared copy
+  const uint8_t* const scentre = smem + Sh::OFF_CODE + (Sh::SY + ty + 1) * Sh::CSEG + wc + 1;
+  const int reuse = g.reuse_prev ? kCodeReuse : 0;
   const int sidx = (ty + 1) * Sh::SX + Sh::H + 4 * lane;
   bool ok = mbar_wait_bounded(&full[0], 0) && mbar_wait_bounded(&full[1], 0);
   int s0 = 0, s1 = 1, s2 = 2 % NST;
@@ -290,7 +271,9 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
           mn[i][q] = dd;
         }
       }
-      const bool write_phi = sprev[(k * TY + ty) * Sh::WCS + wc] != flag;
+      // a bulk flag implies that the input held phase l here; the output
+      // buffer (the state before it) also did when the input's reuse bit is set
+      const bool write_phi = (scentre[k * Sh::SY * Sh::CSEG] & reuse) == 0;
       if (vec_ok) {
         float* p = out0 + k * plane;
         const long long fs = g.fstride;
@@ -359,8 +342,9 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
         }
       }
     }
-    // segment codes of bulk segments; the others go to the interface list
-    if (leader && flag != 0) code0[k * cplane] = (uint8_t)flag;
+    // segment codes of bulk segments (input and output pure phase l: reuse
+    // bit set); the others go to the interface list
+    if (leader && flag != 0) code0[k * cplane] = (uint8_t)(flag | kCodeReuse);
     const unsigned int need = __ballot_sync(0xffffffffu, leader && flag == 0);
     if (need) {
       const int first = __ffs(need) - 1;
@@ -565,8 +549,12 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
     }
     const int ref = __shfl_sync(0xffffffffu, code, 0);
     const bool same = __all_sync(0xffffffffu, !active || code == ref);
-    if (lane == 0)
-      g.codes_out[((long long)(z + g.zoff) * g.ny + y) * g.segs + sg] = same ? (uint8_t)ref : (uint8_t)0;
+    if (lane == 0) {
+      const long long ci = ((long long)(z + g.zoff) * g.ny + y) * g.segs + sg;
+      int c = same ? ref : 0;
+      if (c != 0 && (g.codes_in[ci] & kCodePhase) == c) c |= kCodeReuse;   // pure before and after
+      g.codes_out[ci] = (uint8_t)c;
+    }
     __syncwarp();   // every lane is done with buffer b before it is refilled
     b ^= 1;
     i = nxt;

@@ -146,14 +146,11 @@ __device__ __forceinline__ uint8_t load_code(const StepArgs<Real, NP, NM>& g, in
   return __ldg(g.codes_in + ((long long)zz * g.ny + yy) * g.segs + ss);
 }
 
-// Row flag: the pure phase + 1 when three adjacent segments agree on it.
+// Row flag: the pure phase + 1 when three adjacent segments agree on it
+// (the reuse bit of each code is ignored).
 __device__ __forceinline__ int combine_codes(const uint8_t* c) {
-  return (c[0] == c[1] && c[1] == c[2]) ? (int)c[1] : 0;
-}
-// The same for three codes packed in the low bytes of a word.
-__device__ __forceinline__ int combine_packed_codes(uint32_t c3) {
-  const uint32_t a = c3 & 0xFF, b = (c3 >> 8) & 0xFF, c = (c3 >> 16) & 0xFF;
-  return (a == b && b == c) ? (int)b : 0;
+  const int a = c[0] & kCodePhase, b = c[1] & kCodePhase, d = c[2] & kCodePhase;
+  return (a == b && b == d) ? b : 0;
 }
 
 // Bulk cell (whole stencil is the pure phase l): phi unchanged, and
@@ -425,7 +422,7 @@ __global__ void __launch_bounds__(TX* TY + 32, MinBlocks<NP, TX * TY>::value)
       if (bulk) {
         bulk_cell<DIM, NP, NM, Real>(acc, g, flag - 1, pn, mn);
         code = flag;
-        write_phi = sprev[(k * TY + ty) * Sh::WC + wc] != flag;
+        write_phi = (sprev[(k * TY + ty) * Sh::WC + wc] & kCodePhase) != flag;
       } else {
         DiffPrm<Real, StepArgs<Real, NP, NM>::P> dp;
         dp.mob = g.mob;

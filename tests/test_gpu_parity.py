@@ -280,6 +280,29 @@ def test_bulk_phi_reuse_survives_state_loads_and_adjoint_recompute():
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+def test_switching_between_split_and_fused_steps_mid_run():
+    # The split step marks bulk rows whose pure phase held over two steps
+    # (phi is then kept from the ping-pong partner); the fused step reads the
+    # partner's codes instead.  Alternating the two on one context, without
+    # reloading the state, must still track the oracle.
+    from paper_2404_01035_gb300 import Simulation
+    p = W.cfg2(n=48, steps=10)
+    p.nz = 40
+    p.phi0, p.mu0 = p.phi0[:, :40], p.mu0[:, :40]
+    sim = Simulation(p, dtype="f32")
+    tiles = sim.tiles()
+    split = [i for i, t in enumerate(tiles) if t[2] == 1][0]
+    fused = [i for i, t in enumerate(tiles) if t[2] == 0][0]
+    sim.set_fields(p.phi0, p.mu0)
+    for r in range(8):
+        sim.set_launch(split if r % 2 == 0 else fused, 8 if r % 4 < 2 else 16)
+        sim.step(4 + r % 3)
+    g = sim.get_fields()
+    sim.close()
+    o = oracle.run(p, p.phi0, p.mu0, sum(4 + r % 3 for r in range(8)))
+    assert max_err(g, o) <= FP32_TOL
+
+
 def test_device_and_host_field_io_agree():
     from paper_2404_01035_gb300 import Simulation
     import torch
