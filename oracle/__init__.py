@@ -13,6 +13,8 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
     mu, mass conservation, sum(phi)=1, flat-interface equilibrium,
     Gibbs-Thomson direction, anisotropic profile width, tangent vs finite
     differences: pinned.
+  * The anti-trapping current (``tests/test_oracle_at.py``): closed-form face
+    values, direction, inertness, flux-form conservation, symmetries: pinned.
   * The full multiphase (N >= 3) anisotropic dendrite / eutectic / multigrain
     trajectories: parity unpinned beyond the identities above.
 """
@@ -60,7 +62,7 @@ class _Problem(ctypes.Structure):
         ("T_ref", ctypes.c_double), ("T0", ctypes.c_double), ("G", ctypes.c_double),
         ("z0", ctypes.c_double), ("V", ctypes.c_double), ("t0", ctypes.c_double),
         ("z_origin", ctypes.c_int), ("noise_amp", ctypes.c_double), ("noise_seed", ctypes.c_ulonglong),
-        ("step0", ctypes.c_longlong),
+        ("step0", ctypes.c_longlong), ("anti_trapping", ctypes.c_int),
     ]
 
 
@@ -85,6 +87,8 @@ def lib():
             L.oracle_interp.argtypes = [ctypes.c_int, dp, dp, dp]
             L.oracle_project.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
             L.oracle_thermo.argtypes = [P, ctypes.c_int, dp, ctypes.c_double, dp, dp, dp]
+            L.oracle_at_face_flux.argtypes = [P, dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_double, dp]
             L.oracle_noise.argtypes = [ctypes.c_ulonglong, ctypes.c_longlong, ctypes.c_ulonglong]
             L.oracle_noise.restype = ctypes.c_double
             L.oracle_num_threads.restype = ctypes.c_int
@@ -143,6 +147,7 @@ class OracleProblem:
         s.noise_amp = float(opt("noise_amp", 0.0))
         s.noise_seed = int(opt("noise_seed", 0)) & 0xFFFFFFFFFFFFFFFF
         s.step0 = int(step0)
+        s.anti_trapping = int(bool(opt("anti_trapping", 0)))
         self.s = s
 
     @property
@@ -168,6 +173,20 @@ def run(prob, phi0, mu0, nsteps: int, t0: float = 0.0, step0: int = 0, **overrid
     if rc:
         raise ValueError("oracle_run rejected the problem")
     return phi, mu
+
+
+def at_face_flux(prob, phi, phin, mu, x: int, y: int, z: int, d: int, t0: float = 0.0, **override):
+    """Normal component (along axis d) of the anti-trapping current j_at at the
+    face between cell (x, y, z) and its +d neighbour, per solute; phi = phi^n,
+    phin = phi^{n+1}, mu = mu^n at time t0 (Eq. jatr)."""
+    op = OracleProblem(prob, t0, **override)
+    phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(op.shape(op.N))
+    phin = np.ascontiguousarray(phin, dtype=np.float64).reshape(op.shape(op.N))
+    mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(op.shape(op.NM))
+    J = np.zeros(op.NM)
+    if lib().oracle_at_face_flux(op.ptr(), _dp(phi), _dp(phin), _dp(mu), x, y, z, d, float(t0), _dp(J)):
+        raise ValueError("oracle_at_face_flux rejected the problem")
+    return J
 
 
 def noise(seed: int, step: int, counter: int) -> float:

@@ -17,6 +17,9 @@
 //   * Eq. (Mu_explicit_temperature): dmu/dt = chi^-1 [div(M grad mu)
 //     - sum_a c^a dh_a/dt - dT/dt sum_a (dc^a/dT)_mu h_a].
 //   * Eq. (free_energy_density), Eqs. (Coeff_B), (Coeff_C): parabolic f^a.
+//   * Eq. (jatr) and the obstacle / well forms of j^{at,alpha} below it: the
+//     anti-trapping current, subtracted from M grad mu inside the divergence
+//     of Eq. (Mu_explicit_temperature) when enabled.
 //
 // Readings where the paper is silent or ambiguous (all listed in the design
 // notes): unit-spacing finite differences with face fluxes (normal difference,
@@ -73,6 +76,11 @@ inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
 inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
 inline double val(double x) { return x; }
 inline double val(const Dual& x) { return x.v; }
+inline double sqrt_s(double x) { return std::sqrt(x); }
+inline Dual sqrt_s(const Dual& x) {
+  const double r = std::sqrt(x.v);
+  return {r, x.d / (2.0 * r)};
+}
 
 }  // namespace
 
@@ -100,6 +108,7 @@ typedef struct {
   double noise_amp;      // phi noise amplitude (0 = off)
   unsigned long long noise_seed;
   long long step0;       // step index of the input state (noise counter)
+  int anti_trapping;     // 1 = anti-trapping current j_at in the mu update
 } oracle_problem;
 
 }  // extern "C"
@@ -551,6 +560,83 @@ void cell_mobility(const Ctx<S>& c, const S* phi, int64_t ic, S* M) {
   }
 }
 
+// ------------------------------------------------------ anti-trapping current
+// Coefficient of j^{at,alpha} (the two forms below Eq. jatr) at the local
+// value phi0 of phi_alpha, read as the equilibrium 1-D profile value there:
+// obstacle  pi eps phi0 (1 - h(phi0)) / (4 sqrt(phi0 (1 - phi0))), with h the
+//           two-phase restriction phi0^2 (3 - 2 phi0) of Eq. (hphi) (the 1-D
+//           profile holds two phases); 0 outside 0 < phi0 < 1;
+// well      eps / (2 sqrt 2).
+template <class S>
+S at_coefficient(const oracle_problem& p, S phi0) {
+  if (p.potential != 1) return S(p.eps / (2.0 * std::sqrt(2.0)));
+  if (!(val(phi0) > 0.0 && val(phi0) < 1.0)) return S(0.0);
+  const S h = phi0 * phi0 * (3.0 - 2.0 * phi0);
+  const double pi = 3.14159265358979323846;
+  return pi * p.eps * phi0 * (1.0 - h) / (4.0 * sqrt_s(phi0 * (1.0 - phi0)));
+}
+
+// Normal component (along axis d) of the anti-trapping current j_at_i
+// (Eq. jatr) at the face between cell (x,y,z) and its +d neighbour, for every
+// solute i.  phi = phi^n, phin = phi^{n+1}, mu = mu^n at time t.  Face values
+// as for the gradient-energy fluxes: the arithmetic mean of the two cells for
+// phi, mu and d phi/dt (each cell's forward difference over the step), the
+// normal difference and 4-point averaged tangential differences for grad phi;
+// the mean of the two cells' T.  The liquid is phase N-1; a phase whose face gradient
+// has |grad phi|^2 < 1e-12 has no normal and contributes nothing.
+template <class S>
+void at_face_flux(const Ctx<S>& c, const S* phi, const S* phin, const S* mu, int x, int y, int z, int d,
+                  double t, S* J) {
+  const oracle_problem& p = *c.p;
+  const int N = p.N, NM = p.NM, dim = p.dim, liq = N - 1;
+  int L[3] = {x, y, z}, R[3] = {x, y, z};
+  R[d] += 1;
+  auto at = [&](const S* f, int a, const int* pos, int tt, int sgn) {
+    int q[3] = {pos[0], pos[1], pos[2]};
+    if (tt >= 0) q[tt] += sgn;
+    return f[a * c.cells + cell_index(c, q[0], q[1], q[2])];
+  };
+  S pf[NMAX], rate[NMAX], nrm[NMAX][3];
+  bool has_n[NMAX];
+  for (int a = 0; a < N; ++a) {
+    const S vl = at(phi, a, L, -1, 0), vr = at(phi, a, R, -1, 0);
+    pf[a] = 0.5 * (vl + vr);
+    rate[a] = 0.5 * ((at(phin, a, L, -1, 0) - vl) + (at(phin, a, R, -1, 0) - vr)) / p.dt;
+    S gr[3] = {0.0, 0.0, 0.0}, g2 = 0.0;
+    for (int tt = 0; tt < dim; ++tt) {
+      if (tt == d)
+        gr[tt] = (vr - vl) / p.dx;
+      else
+        gr[tt] = ((at(phi, a, L, tt, +1) + at(phi, a, R, tt, +1)) - (at(phi, a, L, tt, -1) + at(phi, a, R, tt, -1))) /
+                 (4.0 * p.dx);
+      g2 += gr[tt] * gr[tt];
+    }
+    has_n[a] = val(g2) >= 1e-12;
+    const S inv = has_n[a] ? 1.0 / sqrt_s(g2) : S(0.0);
+    for (int tt = 0; tt < 3; ++tt) nrm[a][tt] = gr[tt] * inv;
+  }
+  S mf[KMAX];
+  for (int i = 0; i < NM; ++i) mf[i] = 0.5 * (at(mu, i, L, -1, 0) + at(mu, i, R, -1, 0));
+  // T: the mean of the two cells' temperatures (cells taken after the
+  // boundary mapping, so that a wrapped face has one value from either side)
+  const int yl = map_axis(L[1], c.n[1], p.bc[1]), yr = map_axis(R[1], c.n[1], p.bc[1]);
+  const int zl = map_axis(L[2], c.n[2], p.bc[2]), zr = map_axis(R[2], c.n[2], p.bc[2]);
+  const double Tf = 0.5 * (temperature(p, yl, zl, t) + temperature(p, yr, zr, t));
+  S cl[KMAX];
+  comp_of_mu(p, liq, mf, Tf, cl);
+  for (int i = 0; i < NM; ++i) J[i] = 0.0;
+  if (!has_n[liq]) return;
+  for (int al = 0; al < N - 1; ++al) {
+    if (!has_n[al]) continue;
+    S proj = 0.0;   // -n_alpha . n_liq
+    for (int tt = 0; tt < dim; ++tt) proj -= nrm[al][tt] * nrm[liq][tt];
+    S ca[KMAX];
+    comp_of_mu(p, al, mf, Tf, ca);
+    const S k = at_coefficient(p, pf[al]) * rate[al] * nrm[al][d] * proj;
+    for (int i = 0; i < NM; ++i) J[i] += k * (ca[i] - cl[i]);
+  }
+}
+
 // One explicit step phi^n, mu^n (time t) -> phi^{n+1}, mu^{n+1}.
 template <class S>
 void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, double t, int64_t nstep) {
@@ -582,8 +668,19 @@ void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, dou
         else
           project_hyperplane(N, v, pn);
         for (int a = 0; a < N; ++a) phi_out[a * c.cells + ic] = pn[a];
-
-        // ---- chemical-potential update
+      }
+  // ---- chemical-potential update (a second sweep: the anti-trapping current
+  // needs phi^{n+1} of the neighbours)
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+  for (int z = 0; z < c.n[2]; ++z)
+    for (int y = 0; y < c.n[1]; ++y)
+      for (int x = 0; x < c.n[0]; ++x) {
+        const int64_t ic = cell_index(c, x, y, z);
+        S ph[NMAX], pn[NMAX];
+        for (int a = 0; a < N; ++a) {
+          ph[a] = phi[a * c.cells + ic];
+          pn[a] = phi_out[a * c.cells + ic];
+        }
         S h_old[NMAX], h_new[NMAX];
         interp_h(N, ph, h_old);
         interp_h(N, pn, h_new);
@@ -605,6 +702,16 @@ void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, dou
                 div[i] += Mf * (mu[j * c.cells + in] - mc[j]) / (p.dx * p.dx);
               }
           }
+        if (p.anti_trapping) {   // - div j_at (Eq. Mu_explicit_temperature)
+          for (int d = 0; d < dim; ++d) {
+            S Jp[KMAX], Jm[KMAX];
+            at_face_flux(c, phi, phi_out, mu, x, y, z, d, t, Jp);
+            int q[3] = {x, y, z};
+            q[d] -= 1;
+            at_face_flux(c, phi, phi_out, mu, q[0], q[1], q[2], d, t, Jm);
+            for (int i = 0; i < NM; ++i) div[i] -= (Jp[i] - Jm[i]) / p.dx;
+          }
+        }
         const double Tn = temperature(p, y, z, t);
         const double Tn1 = temperature(p, y, z, t + p.dt);
         S rhs[KMAX];
@@ -791,6 +898,17 @@ int oracle_diag(const oracle_problem* p, const double* phi, const double* mu, do
 }
 
 // ---- single-formula probes used by the pin tests
+// The anti-trapping current's normal component at the +d face of cell
+// (x, y, z): J[NM] (see at_face_flux); phi, phin [N][cells], mu [NM][cells].
+int oracle_at_face_flux(const oracle_problem* p, const double* phi, const double* phin, const double* mu, int x,
+                        int y, int z, int d, double t, double* J) {
+  if (check(p)) return 1;
+  Ctx<double> c;
+  init_ctx(c, p);
+  at_face_flux(c, phi, phin, mu, x, y, z, d, t, J);
+  return 0;
+}
+
 // The phi-noise variate for (seed, step, counter) (see noise_variate).
 double oracle_noise(unsigned long long seed, long long step, unsigned long long counter) {
   return noise_variate(seed, (uint64_t)step, counter);
