@@ -118,6 +118,13 @@ typedef struct {
                               cell index x + nx (y + ny z) times N plus a.  0 =
                               off.  Not available with ms_grad or ms_batch_*. */
   unsigned long long noise_seed;
+  int anti_trapping;       /* 1 = anti-trapping current j_at (Sec. 2.1, Eq. jatr;
+                              obstacle or well form by `potential`) inside the
+                              divergence of the mu update, for the liquid =
+                              phase N-1; each step then runs a second kernel
+                              that corrects mu with phi^{n+1} of the
+                              neighbours.  0 = off.  Not available with
+                              ms_grad, ms_batch_* or MS_BC_HALO faces. */
 } ms_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  NULL in

@@ -53,6 +53,7 @@ struct HostModel {
   double T0 = 0, G = 0, z0 = 0, V = 0, T_ref = 0, t0 = 0;
   double noise_amp = 0;                    // phi noise (0 = off)
   unsigned long long noise_seed = 0;
+  int at = 0;                              // anti-trapping current in the mu update
 };
 
 // Launch geometry of one step.
@@ -85,6 +86,10 @@ struct StepKernel {
                         cudaStream_t st);
   // Recompute the segment codes of a state loaded from outside.
   cudaError_t (*codes)(const void* state, const HostModel& m, uint8_t* codes, cudaStream_t st);
+  // Anti-trapping correction of the mu just written by launch (same
+  // arguments; in = the input state).
+  cudaError_t (*at)(const void* in, void* blob, const HostModel& m, double t, void* out, const uint8_t* codes_in,
+                    uint8_t* codes_out, const LaunchGeom& lg, cudaStream_t st);
 };
 
 // Number of 32-cell segments per row.

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "ms_at.cuh"
 #include "ms_diag.cuh"
 #include "ms_internal.h"
 #include "ms_split.cuh"
@@ -173,9 +174,13 @@ cudaError_t launch_split(const CUtensorMap* tm, const CUtensorMap* tmi, void* bl
     cudaError_t e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, Ss::SMEM_BYTES);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
     if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(ki, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&iface_per_sm, ki, Si::THREADS, Si::SMEM_BYTES);
     if (two && e == cudaSuccess)
       e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
+    if (two && e == cudaSuccess)
+      e = cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (two && e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&full_per_sm, kf, Si::THREADS, Si::SMEM_BYTES);
     if (e != cudaSuccess) return e;
@@ -186,6 +191,17 @@ cudaError_t launch_split(const CUtensorMap* tm, const CUtensorMap* tmi, void* bl
   ks<<<dim3(lg.tiles, lg.zchunks), Ss::NTHREADS, Ss::SMEM_BYTES, st>>>(*tm, g);
   ki<<<lg.iface_blocks * iface_per_sm, Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
   if constexpr (two) kf<<<lg.iface_blocks * full_per_sm, Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
+  return cudaGetLastError();
+}
+
+template <int DIM, int NP, int NM, class Real>
+cudaError_t launch_at(const void* in, void* blob, const HostModel& m, double t, void* out, const uint8_t* codes_in,
+                      uint8_t* codes_out, const LaunchGeom& lg, cudaStream_t st) {
+  auto& g = *reinterpret_cast<StepArgs<Real, NP, NM>*>(blob);
+  set_launch_args(g, m, t, out, codes_in, codes_out, lg);
+  const long long warps = (long long)segments(m) * m.ny * (DIM == 3 ? m.nz : 1);
+  const int blocks = (int)((warps * 32 + 255) / 256);
+  k_at<DIM, NP, NM, Real><<<blocks, 256, 0, st>>>(g, reinterpret_cast<const Real*>(in));
   return cudaGetLastError();
 }
 
@@ -214,6 +230,7 @@ StepKernel make_step_kernel() {
   k.fill = &fill_args<DIM, NP, NM, Real>;
   k.launch = &launch_step<DIM, NP, NM, Real, TX, TY>;
   k.codes = &launch_codes<DIM, NP, Real>;
+  k.at = &launch_at<DIM, NP, NM, Real>;
   return k;
 }
 
@@ -233,6 +250,7 @@ StepKernel make_split_kernel() {
   k.fill = &fill_args<3, NP, NM, float>;
   k.launch = &launch_split<NP, NM, TY>;
   k.codes = &launch_codes<3, NP, float>;
+  k.at = &launch_at<3, NP, NM, float>;
   return k;
 }
 

@@ -217,6 +217,9 @@ ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params
   if (!(p->noise_amp >= 0.0) || !std::isfinite(p->noise_amp)) return fail(c, MS_ERR_ARG, "noise_amp must be finite and >= 0");
   m.noise_amp = p->noise_amp;
   m.noise_seed = p->noise_seed;
+  m.at = p->anti_trapping ? 1 : 0;
+  if (m.at && m.dim == 3 && m.bc[2] == kBcHalo)
+    return fail(c, MS_ERR_UNSUPPORTED, "the anti-trapping current is not available on slabs with halo faces");
   // explicit stability bound (FP64): (dx^2 / 2d) min(tau / (gamma (1 + 15 delta)), 1 / D_eff)
   double gmax = 0, dmax = 0, Dmax = 0;
   for (int a = 0; a < N; ++a)
@@ -471,6 +474,9 @@ ms_status launch_one_step(ms_ctx* c) {
   c->lg.step = c->step;
   cudaError_t e = c->kern->launch(&c->tm[src], &c->tmi[src], c->args.data(), c->m, c->t, c->buf[dst], c->codes[src],
                                   c->codes[dst], c->lg, c->stream);
+  if (e == cudaSuccess && c->m.at)
+    e = c->kern->at(c->buf[src], c->args.data(), c->m, c->t, c->buf[dst], c->codes[src], c->codes[dst], c->lg,
+                    c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
   c->cur = dst;
   c->step += 1;

@@ -127,11 +127,13 @@ __device__ __forceinline__ int bc_map(int i, int n, int bc) {
   return i < 0 ? 0 : n - 1;
 }
 
-// Segment code of (segment s, row y, plane z) of the input state, with the
-// boundary mapping of each axis (out-of-range indices give the periodic image
-// or the adjacent interior segment, row or plane).
+// Segment code of (segment s, row y, plane z) of a code array (the input
+// state's by default), with the boundary mapping of each axis (out-of-range
+// indices give the periodic image or the adjacent interior segment, row or
+// plane).
 template <class Real, int NP, int NM>
-__device__ __forceinline__ uint8_t load_code(const StepArgs<Real, NP, NM>& g, int s, int y, int z) {
+__device__ __forceinline__ uint8_t load_code_from(const uint8_t* codes, const StepArgs<Real, NP, NM>& g, int s, int y,
+                                                  int z) {
   const int ss = bc_map(s, g.segs, g.bc[0]);
   const int yy = bc_map(y, g.ny, g.bc[1]);
   // plane index in the code array (3-D arrays carry one ghost plane per side,
@@ -143,7 +145,11 @@ __device__ __forceinline__ uint8_t load_code(const StepArgs<Real, NP, NM>& g, in
     zz = z < 0 ? 0 : g.nz + 1;
   else
     zz = bc_map(z, g.nz, g.bc[2]) + g.zoff;
-  return __ldg(g.codes_in + ((long long)zz * g.ny + yy) * g.segs + ss);
+  return __ldg(codes + ((long long)zz * g.ny + yy) * g.segs + ss);
+}
+template <class Real, int NP, int NM>
+__device__ __forceinline__ uint8_t load_code(const StepArgs<Real, NP, NM>& g, int s, int y, int z) {
+  return load_code_from(g.codes_in, g, s, y, z);
 }
 
 // Row flag: the pure phase + 1 when three adjacent segments agree on it
