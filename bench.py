@@ -303,6 +303,7 @@ def run_ours(args, rank, world, local_rank):
         extra["adjoint"] = bench_adjoint(stream)
         extra["multigrain"] = bench_multigrain(stream)
         extra["frame_noise"] = bench_frame_noise(stream)
+        extra["anti_trapping"] = bench_anti_trapping(stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -424,6 +425,30 @@ def bench_frame_noise(stream):
                         "and an 8-plane shift", "mlups": p.cells * steps / (ms / 1e3) / 1e6,
             "ms_per_step": ms / steps, "front_plane": front, "front_ms_host": front_ms,
             "shift_8_planes_ms": shift_ms}
+
+
+def bench_anti_trapping(stream):
+    """The 256^3 eutectic with the anti-trapping current on, 200 steps from the
+    seeded state after 20 warm-up steps, against the same run without it (the
+    correction kernel's cost is the difference)."""
+    import workloads
+    from paper_2404_01035_gb300 import Simulation
+    out = {"workload": "3-D 256^3 eutectic with the anti-trapping current (obstacle form), 200 steps"}
+    steps = 200
+    for at in (1, 0):
+        p = workloads.cfg2()
+        p.anti_trapping = at
+        sim = Simulation(p, dtype="f32", stream=stream)
+        sim.set_fields(p.phi0, p.mu0)
+        sim.tune(None, steps_per_trial=10)
+        sim.set_fields(p.phi0, p.mu0)
+        sim.step(20)
+        ms = _events_ms(stream, lambda: sim.step(steps))
+        key = "with" if at else "without"
+        out[key] = {"mlups": p.cells * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps}
+        sim.close()
+    out["correction_ms_per_step"] = out["with"]["ms_per_step"] - out["without"]["ms_per_step"]
+    return out
 
 
 def bench_adjoint(stream):

@@ -54,6 +54,10 @@ struct StepArgs {
   unsigned int* iface;
   unsigned int iface_cap;
   unsigned int* iface2;   // second list, same layout (rows left for the full update)
+  // anti-trapping work list: [0] count, [1] ticket, [2..] row segments
+  // (z ny + y) segs + segment whose block of segments is not one pure phase
+  unsigned int* at_list;
+  unsigned int at_cap;
   // phi noise: amplitude, seed, step index of the input state
   Real noise_amp;
   unsigned long long noise_seed, step;

@@ -65,6 +65,9 @@ struct LaunchGeom {
   unsigned int* iface2 = nullptr;
   unsigned int iface_cap = 0;
   int iface_blocks = 0;            // SMs: the interface grid is this x resident CTAs per SM
+  int sms = 0;                     // multiprocessors of the device
+  unsigned int* at_list = nullptr; // anti-trapping work list (see StepArgs)
+  unsigned int at_cap = 0;
   int reuse_prev = 1;              // output buffer = state one step before the input (see StepArgs)
   long long step = 0;              // step index of the input state (phi-noise counter)
 };

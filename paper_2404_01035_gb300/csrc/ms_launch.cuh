@@ -132,6 +132,8 @@ void set_launch_args(StepArgs<Real, NP, NM>& g, const HostModel& m, double t, vo
   g.iface_cap = lg.iface_cap;
   g.reuse_prev = lg.reuse_prev;
   g.step = (unsigned long long)lg.step;
+  g.at_list = lg.at_list;
+  g.at_cap = lg.at_cap;
 }
 
 // Fused step: one kernel updates every cell.
@@ -197,11 +199,25 @@ cudaError_t launch_split(const CUtensorMap* tm, const CUtensorMap* tmi, void* bl
 template <int DIM, int NP, int NM, class Real>
 cudaError_t launch_at(const void* in, void* blob, const HostModel& m, double t, void* out, const uint8_t* codes_in,
                       uint8_t* codes_out, const LaunchGeom& lg, cudaStream_t st) {
+  using Sh = AtShape<DIM, NP, NM, Real>;
+  if (!lg.at_list || lg.sms < 1) return cudaErrorInvalidValue;
   auto& g = *reinterpret_cast<StepArgs<Real, NP, NM>*>(blob);
   set_launch_args(g, m, t, out, codes_in, codes_out, lg);
-  const long long warps = (long long)segments(m) * m.ny * (DIM == 3 ? m.nz : 1);
-  const int blocks = (int)((warps * 32 + 255) / 256);
-  k_at<DIM, NP, NM, Real><<<blocks, 256, 0, st>>>(g, reinterpret_cast<const Real*>(in));
+  auto kw = k_at_work<DIM, NP, NM, Real>;
+  static bool configured = false;   // attributes are per function, set once
+  static int per_sm = 1;            // resident CTAs per SM
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kw, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kw, Sh::THREADS, Sh::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    configured = true;
+  }
+  const long long nseg = (long long)segments(m) * m.ny * (DIM == 3 ? m.nz : 1);
+  k_at_list<DIM, NP, NM, Real><<<(int)((nseg + 255) / 256), 256, 0, st>>>(g);
+  kw<<<lg.sms * per_sm, Sh::THREADS, Sh::SMEM_BYTES, st>>>(g, reinterpret_cast<const Real*>(in));
   return cudaGetLastError();
 }
 

@@ -48,6 +48,7 @@ struct ms_ctx {
   void* buf[2] = {nullptr, nullptr};
   uint8_t* codes[2] = {nullptr, nullptr};   // segment codes of buf[0] / buf[1]
   unsigned int* iface = nullptr;            // work list of the split step (lazily allocated)
+  unsigned int* at_list = nullptr;          // anti-trapping work list (allocated while it is on)
   size_t state_bytes = 0;
   int cur = 0;
   int64_t step = 0;
@@ -70,6 +71,7 @@ ms_status fail(ms_ctx* c, ms_status s, const std::string& msg);
 ms_status cuda_fail(ms_ctx* c, cudaError_t e, const char* what);
 ms_status launch_one_step(ms_ctx* c);
 ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk);
+ms_status ensure_at_list(ms_ctx* c);   // the anti-trapping work list, when the current is on
 ms_status refresh_codes(ms_ctx* c);   // segment codes of the current state
 // Tiled map of a padded state: box of (tx + 2H) x (ty + 2) x bz planes x nf fields.
 bool encode_state_map(CUtensorMap* tm, void* base, const HostModel& m, int nf, int tx, int ty, int bz = 1);

@@ -438,7 +438,29 @@ int default_zchunk(const HostModel& m, const StepKernel& k) {
   return std::min(zc, m.nz);
 }
 
+ms_status ensure_at_list(ms_ctx* c) {
+  if (!c->m.at || c->at_list) return MS_OK;
+  // count, ticket and one entry per row segment
+  const size_t cap = (size_t)segments(c->m) * c->m.ny * (c->m.dim == 3 ? c->m.nz : 1);
+  if (cap > 0xFFFFFFF0ull) return fail(c, MS_ERR_UNSUPPORTED, "grid too large for the anti-trapping list");
+  c->at_list = static_cast<unsigned int*>(dev_alloc(c->hook, (cap + 2) * sizeof(unsigned int)));
+  if (!c->at_list) return fail(c, MS_ERR_OOM, "anti-trapping work-list allocation failed");
+  c->lg.at_list = c->at_list;
+  c->lg.at_cap = (unsigned int)cap;
+  cudaError_t e = cudaMemsetAsync(c->at_list, 0, 2 * sizeof(unsigned int), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "work-list reset");
+  return MS_OK;
+}
+
 ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk) {
+  if (c->lg.sms < 1) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->lg.sms = sms;
+  }
+  ms_status as = ensure_at_list(c);
+  if (as != MS_OK) return as;
   if (k->split && !c->iface) {
     // work list of the split step: count, ticket and one entry per warp row
     // (two lists: the second takes the rows left for a second launch)
@@ -595,6 +617,7 @@ void ms_destroy(ms_ctx* c) {
   }
   dev_free(c->hook, c->small);
   dev_free(c->hook, c->iface);
+  dev_free(c->hook, c->at_list);
   if (c->diag_host) cudaFreeHost(c->diag_host);
   delete c;
 }
@@ -618,7 +641,7 @@ ms_status ms_update_params(ms_ctx* c, const ms_params* p) {
   m2.t0 = c->m.t0;
   c->m = m2;
   c->kern->fill(c->args.data(), c->m, c->lg.zchunk, c->status);
-  return MS_OK;
+  return ensure_at_list(c);
 }
 
 ms_status ms_set_fields(ms_ctx* c, const void* phi, const void* mu, int on_device) {

@@ -4,6 +4,7 @@ import pytest
 
 import oracle
 import workloads as W
+from gpu_util import pick_cells, windowed_one_step
 
 pytestmark = pytest.mark.gpu
 
@@ -90,3 +91,28 @@ def test_refused_by_the_adjoint_the_batch_and_halo_faces():
     q = _at(W.small_multiphase(n=12, dim=3, N=3, NM=2, nx=16, ny=12, nz=10, bc=[3, 3, 16]))
     with pytest.raises(Exception):
         Simulation(q, dtype="f64")
+
+
+def test_cfg2_full_size_sampled_one_step_fp32():
+    # 256^3 eutectic in the tuned launch, 300 steps with the current, then one
+    # step checked at sampled cells (random, interface, corners) against the
+    # oracle on a window (radius 3: mu needs phi^{n+1} of the neighbours)
+    from paper_2404_01035_gb300 import Simulation
+    p = _at(W.cfg2())
+    rng = np.random.default_rng(5)
+    sim = Simulation(p, dtype="f32")
+    sim.set_fields(p.phi0, p.mu0)
+    sim.tune(None, steps_per_trial=5)
+    sim.set_fields(p.phi0, p.mu0)
+    sim.step(300)
+    phi_n, mu_n = sim.get_fields()
+    t_n = sim.time()[1]
+    sim.step(1)
+    phi_1, mu_1 = sim.get_fields()
+    sim.close()
+    cells = pick_cells(phi_n, rng)
+    ophi, omu = windowed_one_step(p, phi_n, mu_n, cells, t0=t_n, r=3)
+    gphi = np.array([phi_1[:, z, y, x] for (z, y, x) in cells])
+    gmu = np.array([mu_1[:, z, y, x] for (z, y, x) in cells])
+    assert np.abs(gphi - ophi).max() <= 2e-5
+    assert np.abs(gmu - omu).max() <= 2e-5
