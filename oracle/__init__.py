@@ -15,6 +15,8 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
     differences: pinned.
   * The anti-trapping current (``tests/test_oracle_at.py``): closed-form face
     values, direction, inertness, flux-form conservation, symmetries: pinned.
+  * Grain growth (``tests/test_oracle_gg.py``): frozen mu, stationary planar
+    boundary, the curvature-driven area loss rate of a circular grain: pinned.
   * The full multiphase (N >= 3) anisotropic dendrite / eutectic / multigrain
     trajectories: parity unpinned beyond the identities above.
 """
@@ -62,7 +64,7 @@ class _Problem(ctypes.Structure):
         ("T_ref", ctypes.c_double), ("T0", ctypes.c_double), ("G", ctypes.c_double),
         ("z0", ctypes.c_double), ("V", ctypes.c_double), ("t0", ctypes.c_double),
         ("z_origin", ctypes.c_int), ("noise_amp", ctypes.c_double), ("noise_seed", ctypes.c_ulonglong),
-        ("step0", ctypes.c_longlong), ("anti_trapping", ctypes.c_int),
+        ("step0", ctypes.c_longlong), ("anti_trapping", ctypes.c_int), ("grain_growth", ctypes.c_int),
     ]
 
 
@@ -148,6 +150,7 @@ class OracleProblem:
         s.noise_seed = int(opt("noise_seed", 0)) & 0xFFFFFFFFFFFFFFFF
         s.step0 = int(step0)
         s.anti_trapping = int(bool(opt("anti_trapping", 0)))
+        s.grain_growth = int(bool(opt("grain_growth", 0)))
         self.s = s
 
     @property

@@ -20,6 +20,8 @@
 //   * Eq. (jatr) and the obstacle / well forms of j^{at,alpha} below it: the
 //     anti-trapping current, subtracted from M grad mu inside the divergence
 //     of Eq. (Mu_explicit_temperature) when enabled.
+//   * Sec. 4 "Grain-growth" (GRAINGROWTH = 1): isotropic grain growth, read as
+//     the phi equation without the chemical term dpsi/dphi and with mu held.
 //
 // Readings where the paper is silent or ambiguous (all listed in the design
 // notes): unit-spacing finite differences with face fluxes (normal difference,
@@ -109,6 +111,7 @@ typedef struct {
   unsigned long long noise_seed;
   long long step0;       // step index of the input state (noise counter)
   int anti_trapping;     // 1 = anti-trapping current j_at in the mu update
+  int grain_growth;      // 1 = GRAINGROWTH: no chemical driving force, mu frozen
 } oracle_problem;
 
 }  // extern "C"
@@ -652,7 +655,10 @@ void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, dou
         S ph[NMAX], v[NMAX], pn[NMAX];
         for (int a = 0; a < N; ++a) {
           ph[a] = phi[a * c.cells + ic];
-          S r = c.q.mob * (p.eps * (divJ[a] - Gc[a]) - W[a] / p.eps - P[a]) / p.eps;
+          // grain growth (GRAINGROWTH = 1, Sec. 4 "Grain-growth"): the
+          // interfaces move by their curvature only, no dpsi/dphi term
+          const S Pa = p.grain_growth ? S(0.0) : P[a];
+          S r = c.q.mob * (p.eps * (divJ[a] - Gc[a]) - W[a] / p.eps - Pa) / p.eps;
           v[a] = ph[a] + p.dt * r;
           // phi noise on the cell's interface phases (0 < phi_a < 1): an
           // additive dt * amplitude * xi on the rate, before the projection
@@ -670,7 +676,11 @@ void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, dou
         for (int a = 0; a < N; ++a) phi_out[a * c.cells + ic] = pn[a];
       }
   // ---- chemical-potential update (a second sweep: the anti-trapping current
-  // needs phi^{n+1} of the neighbours)
+  // needs phi^{n+1} of the neighbours); grain growth keeps mu as it is
+  if (p.grain_growth) {
+    for (int64_t k = 0; k < (int64_t)NM * c.cells; ++k) mu_out[k] = mu[k];
+    return;
+  }
 #pragma omp parallel for collapse(2) schedule(dynamic, 1)
   for (int z = 0; z < c.n[2]; ++z)
     for (int y = 0; y < c.n[1]; ++y)

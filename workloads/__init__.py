@@ -105,6 +105,7 @@ class Problem:
     noise_amp: float = 0.0         # phi noise amplitude (0 = off)
     noise_seed: int = 0
     anti_trapping: int = 0         # 1 = anti-trapping current in the mu update
+    grain_growth: int = 0          # 1 = GRAINGROWTH: curvature-driven only, mu held
     phi0: np.ndarray = None        # [N,nz,ny,nx]
     mu0: np.ndarray = None         # [K-1,nz,ny,nx]
     meta: dict = field(default_factory=dict)
