@@ -304,6 +304,7 @@ def run_ours(args, rank, world, local_rank):
         extra["multigrain"] = bench_multigrain(stream)
         extra["frame_noise"] = bench_frame_noise(stream)
         extra["anti_trapping"] = bench_anti_trapping(stream)
+        extra["grain_growth"] = bench_grain_growth(stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -449,6 +450,27 @@ def bench_anti_trapping(stream):
         sim.close()
     out["correction_ms_per_step"] = out["with"]["ms_per_step"] - out["without"]["ms_per_step"]
     return out
+
+
+def bench_grain_growth(stream):
+    """Isotropic grain growth of 8 Voronoi grains in a periodic 256^3 box,
+    FP32, 200 steps after 20 warm-up steps, tuned launch."""
+    import workloads
+    from paper_2404_01035_gb300 import Simulation
+    p = workloads.grain_growth(n=256, dim=3, grains=8)
+    sim = Simulation(p, dtype="f32", stream=stream)
+    sim.set_fields(p.phi0, p.mu0)
+    sim.tune(None, steps_per_trial=10)
+    sim.set_fields(p.phi0, p.mu0)
+    sim.step(20)
+    steps = 200
+    ms = _events_ms(stream, lambda: sim.step(steps))
+    tile, zc = sim.launch()
+    tx, ty, split = sim.tiles()[tile]
+    sim.close()
+    return {"workload": "3-D 256^3 isotropic grain growth, 8 Voronoi grains, periodic, FP32, 200 steps",
+            "mlups": p.cells * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps,
+            "launch": {"tx": tx, "ty": ty, "split": split, "zchunk": zc}}
 
 
 def bench_adjoint(stream):

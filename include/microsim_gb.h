@@ -125,6 +125,12 @@ typedef struct {
                               that corrects mu with phi^{n+1} of the
                               neighbours.  0 = off.  Not available with
                               ms_grad, ms_batch_* or MS_BC_HALO faces. */
+  int grain_growth;        /* GRAINGROWTH = 1 (Sec. 4 "Grain-growth"): the phi
+                              equation without the chemical term dpsi/dphi, mu
+                              held (copied unchanged every step); the fields
+                              keep their layout (N grains, M >= 1 mu fields that
+                              stay constant).  Not available with
+                              anti_trapping, ms_grad or ms_batch_*. */
 } ms_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  NULL in

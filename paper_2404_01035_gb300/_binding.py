@@ -58,7 +58,7 @@ class Params(ctypes.Structure):
         ("T_ref", ctypes.c_double), ("T0", ctypes.c_double), ("G", ctypes.c_double),
         ("z0", ctypes.c_double), ("V", ctypes.c_double), ("t0", ctypes.c_double),
         ("noise_amp", ctypes.c_double), ("noise_seed", ctypes.c_ulonglong),
-        ("anti_trapping", ctypes.c_int),
+        ("anti_trapping", ctypes.c_int), ("grain_growth", ctypes.c_int),
     ]
 
 

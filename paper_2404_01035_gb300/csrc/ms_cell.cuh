@@ -450,7 +450,7 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
     // S4: driving force sum_b psi^b dh_b/dphi_a
     S psi[NP];
 #pragma unroll
-    for (int b = 0; b < NP; ++b) psi[b] = grand_potential<NP, NM, Real>(g, b, mc, s);
+    for (int b = 0; b < NP; ++b) psi[b] = g.gg ? S(Real(0)) : grand_potential<NP, NM, Real>(g, b, mc, s);
     S e1 = ph[0];
 #pragma unroll
     for (int a = 1; a < NP; ++a) e1 += ph[a];
@@ -481,6 +481,11 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
         v[a] = v[a] + g.dt * g.noise_amp * noise_variate<Real>(g.noise_seed, g.step, gcell * NP + a);
     }
     project<NP>(g.potential, v, pn);
+  }
+  if (g.gg) {   // grain growth: mu held
+#pragma unroll
+    for (int i = 0; i < NM; ++i) mn[i] = mc[i];
+    return;
   }
 
   // ---- S6/S7: chemical-potential update
@@ -774,7 +779,7 @@ __device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real
     // S4: driving force
     Real psi[NP];
 #pragma unroll
-    for (int b = 0; b < NP; ++b) psi[b] = grand_potential<NP, NM, Real>(g, b, mc, s);
+    for (int b = 0; b < NP; ++b) psi[b] = g.gg ? Real(0) : grand_potential<NP, NM, Real>(g, b, mc, s);
     Real e1 = ph[0];
 #pragma unroll
     for (int a = 1; a < NP; ++a) e1 += ph[a];
@@ -809,6 +814,11 @@ __device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real
         v[a] = v[a] + g.dt * g.noise_amp * noise_variate<Real>(g.noise_seed, g.step, gcell * NP + a);
     }
     project<NP>(g.potential, v, pn);
+  }
+  if (g.gg) {   // grain growth: mu held
+#pragma unroll
+    for (int i = 0; i < NM; ++i) mn[i] = mc[i];
+    return;
   }
 
   // ---- S6/S7: chemical-potential update (mobilities from the present phases)

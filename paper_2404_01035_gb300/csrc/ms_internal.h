@@ -54,6 +54,7 @@ struct HostModel {
   double noise_amp = 0;                    // phi noise (0 = off)
   unsigned long long noise_seed = 0;
   int at = 0;                              // anti-trapping current in the mu update
+  int gg = 0;                              // grain growth: no chemical driving force, mu held
 };
 
 // Launch geometry of one step.

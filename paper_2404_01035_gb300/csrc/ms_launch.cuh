@@ -43,6 +43,7 @@ void fill_args(void* blob, const HostModel& m, int zchunk, int* status) {
   g.quarter_inv_dx = (Real)(0.25 / m.dx);
   g.inv_dx2 = (Real)(1.0 / (m.dx * m.dx));
   g.potential = m.potential;
+  g.gg = m.gg;
   g.has_g3 = m.has_g3 ? 1 : 0;
   const double PI = 3.14159265358979323846;
   int p = 0;
@@ -98,11 +99,11 @@ void fill_args(void* blob, const HostModel& m, int zchunk, int* status) {
           for (int j = 0; j < NM; ++j) cb += m.chi[a][k * NM + j] * m.B1[a][j];
           e += Hm[i * NM + k] * cb * m.G * m.V * m.dt;
         }
-        g.eb[a][i] = (Real)e;
+        g.eb[a][i] = m.gg ? Real(0) : (Real)e;   // grain growth holds mu
         for (int j = 0; j < NM; ++j) {
           double kk = 0;
           for (int k = 0; k < NM; ++k) kk += Hm[i * NM + k] * m.DX[a][k * NM + j];
-          g.Kb[a][i * NM + j] = (Real)(scale * kk);
+          g.Kb[a][i * NM + j] = m.gg ? Real(0) : (Real)(scale * kk);
         }
       }
     }

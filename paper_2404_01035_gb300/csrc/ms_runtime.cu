@@ -218,6 +218,8 @@ ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params
   m.noise_amp = p->noise_amp;
   m.noise_seed = p->noise_seed;
   m.at = p->anti_trapping ? 1 : 0;
+  m.gg = p->grain_growth ? 1 : 0;
+  if (m.at && m.gg) return fail(c, MS_ERR_ARG, "grain growth holds mu: the anti-trapping current does not apply");
   if (m.at && m.dim == 3 && m.bc[2] == kBcHalo)
     return fail(c, MS_ERR_UNSUPPORTED, "the anti-trapping current is not available on slabs with halo faces");
   // explicit stability bound (FP64): (dx^2 / 2d) min(tau / (gamma (1 + 15 delta)), 1 / D_eff)

@@ -46,6 +46,7 @@ def make_params(prob, dtype: str, keep: list, **override) -> Params:
     p.noise_amp = float(override.get("noise_amp", getattr(prob, "noise_amp", 0.0)))
     p.noise_seed = int(override.get("noise_seed", getattr(prob, "noise_seed", 0))) & 0xFFFFFFFFFFFFFFFF
     p.anti_trapping = int(bool(override.get("anti_trapping", getattr(prob, "anti_trapping", 0))))
+    p.grain_growth = int(bool(override.get("grain_growth", getattr(prob, "grain_growth", 0))))
     return p
 
 
