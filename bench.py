@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / adjoint lines")
     ap.add_argument("--launch", default=None,
                     help="force a launch variant tx,ty,split,zchunk instead of tuning (e.g. 128,6,1,16)")
+    ap.add_argument("--anti-trapping", action="store_true",
+                    help="run the workload with the anti-trapping current (for profiling its kernels)")
     return ap.parse_args()
 
 
@@ -193,6 +195,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
     prob = workloads.cfg2(n=args.n)
+    prob.anti_trapping = int(args.anti_trapping)
     cells = prob.cells
     stream = torch.cuda.Stream(device=dev)
     sim = Simulation(prob, dtype="f32", stream=stream)
@@ -207,7 +210,7 @@ def run_ours(args, rank, world, local_rank):
     tiles = sim.tiles()
     cur_tile, cur_zchunk = sim.launch()
     tx, ty, split = tiles[cur_tile]
-    step_launches = 2 if split else 1   # kernels per time step
+    step_launches = (2 if split else 1) + (2 if args.anti_trapping else 0)   # kernels per time step
     sim.set_diag_every(DIAG_EVERY)
     sim.step(args.warmup)
     sim.sync()
@@ -262,12 +265,13 @@ def run_ours(args, rank, world, local_rank):
     per_step_s = kern_ms / max(1, kern_n) / 1e3
     achieved = bpc * cells / per_step_s / 1e9
     launch = {"tx": tx, "ty": ty, "split": split, "zchunk": cur_zchunk}
-    prof = committed_profile(launch, args.n)
+    prof = committed_profile(launch, args.n) if not args.anti_trapping else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"],
             "traffic": prof["dram_bytes_per_step"] if prof else None,
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)",
-            "scope": "one time step: " + ("k_gp_stream + k_gp_iface" if split else "k_gp_step"),
+            "scope": "one time step: " + ("k_gp_stream + k_gp_iface" if split else "k_gp_step")
+                     + (" + k_at_list + k_at_work" if args.anti_trapping else ""),
             "bytes_per_cell": bpc, "step_ms": per_step_s * 1e3,
             "kernel_shares": prof["kernel_shares"] if prof else None}
 
