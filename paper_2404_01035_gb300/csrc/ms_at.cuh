@@ -19,6 +19,12 @@
 
 namespace msgb {
 
+// 1 / sqrt(x): the hardware reciprocal square root in FP32 (rsqrtf, a few
+// ulp: the current is a correction far inside the FP32 tolerance), exact in
+// FP64.
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+
 // Coefficient A of j^{at,alpha} at the face value p of phi_alpha (read as the
 // 1-D equilibrium profile value there): obstacle pi eps p (1 - h(p)) /
 // (4 sqrt(p (1 - p))) with the two-phase h(p) = p^2 (3 - 2p), 0 outside
@@ -28,7 +34,7 @@ __device__ __forceinline__ Real at_coefficient(int potential, Real eps, Real p) 
   if (potential != 1) return eps * Real(0.35355339059327376220);   // 1 / (2 sqrt 2)
   if (!(p > Real(0) && p < Real(1))) return Real(0);
   const Real h = p * p * (Real(3) - Real(2) * p);
-  return Real(0.78539816339744830962) * eps * p * (Real(1) - h) / sqrt(p * (Real(1) - p));   // pi / 4
+  return Real(0.78539816339744830962) * eps * p * (Real(1) - h) * inv_sqrt(p * (Real(1) - p));   // pi / 4
 }
 
 // Shape of the staged block of one row segment: fields [phi^n (NP), mu^n
@@ -74,7 +80,8 @@ struct AtBox {
   __device__ __forceinline__ Real phin(int a, int dx, int dy, int dz) const { return at(NP + NM + a, dx, dy, dz); }
 };
 
-// Normal component along axis d of j_at_i at the face between the cell at
+// dt times the normal component along axis d of j_at_i (the rates are taken
+// as phi^{n+1} - phi^n) at the face between the cell at
 // offset (ox, oy, oz) from the lane's cell and its +d neighbour: face values
 // as for the gradient-energy fluxes (means of the two cells; normal
 // difference and 4-point averaged tangential differences of phi^n), T the
@@ -91,7 +98,7 @@ __device__ __forceinline__ void at_face(const StepArgs<Real, NP, NM>& g, const A
   for (int a = 0; a < NP; ++a) {
     const Real vl = A.phi(a, ox, oy, oz), vr = A.phi(a, rx, ry, rz);
     pf[a] = Real(0.5) * (vl + vr);
-    rate[a] = Real(0.5) * ((A.phin(a, ox, oy, oz) - vl) + (A.phin(a, rx, ry, rz) - vr));   // x dt
+    rate[a] = Real(0.5) * ((A.phin(a, ox, oy, oz) - vl) + (A.phin(a, rx, ry, rz) - vr));   // dt d phi/dt
     Real gr[DIM], g2 = Real(0);
 #pragma unroll
     for (int t = 0; t < DIM; ++t) {
@@ -106,7 +113,7 @@ __device__ __forceinline__ void at_face(const StepArgs<Real, NP, NM>& g, const A
       g2 += gr[t] * gr[t];
     }
     has_n[a] = g2 >= Real(1e-12);
-    const Real inv = has_n[a] ? Real(1) / sqrt(g2) : Real(0);
+    const Real inv = has_n[a] ? inv_sqrt(g2) : Real(0);
 #pragma unroll
     for (int t = 0; t < DIM; ++t) nrm[a][t] = gr[t] * inv;
   }
@@ -129,14 +136,13 @@ __device__ __forceinline__ void at_face(const StepArgs<Real, NP, NM>& g, const A
     for (int j = 0; j < NM; ++j) c += g.chi[L][i * NM + j] * (mf[j] - (g.B0[L][j] + g.B1[L][j] * sf));
     cl[i] = c;
   }
-  const Real inv_dt = Real(1) / g.dt;
 #pragma unroll
   for (int al = 0; al < L; ++al) {
     if (!has_n[al]) continue;
     Real proj = Real(0);   // -n_alpha . n_liq
 #pragma unroll
     for (int t = 0; t < DIM; ++t) proj -= nrm[al][t] * nrm[L][t];
-    const Real k = at_coefficient<Real>(g.potential, g.eps, pf[al]) * (rate[al] * inv_dt) * nrm[al][d] * proj;
+    const Real k = at_coefficient<Real>(g.potential, g.eps, pf[al]) * rate[al] * nrm[al][d] * proj;
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
       Real c = Real(0);
@@ -245,7 +251,7 @@ __global__ void __launch_bounds__(AtShape<DIM, NP, NM, Real>::THREADS)
         for (int a = 1; a < NP; ++a) chi[q] += h[a] * g.chi[a][q];
       }
 #pragma unroll
-      for (int q = 0; q < NM; ++q) rhs[q] = -g.dt * div[q];
+      for (int q = 0; q < NM; ++q) rhs[q] = -div[q];   // the rates above carry no 1/dt: dt div j_at
       solve_small<NM>(chi, rhs, dmu);
       const long long o = (long long)(DIM == 3 ? z + g.zoff : 0) * plane + (long long)(y + 1) * g.pitch + x + g.xoff;
 #pragma unroll
