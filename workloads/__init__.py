@@ -336,9 +336,10 @@ def grain_growth(n: int = 256, dim: int = 3, grains: int = 8, seed: int = BASE_S
                  nz: int = None, steps: int = 1000) -> Problem:
     """Isotropic grain growth (GRAINGROWTH = 1): `grains` grains (one phase
     each, equal isotropic boundary energies) filling a periodic box as the
-    Voronoi cells of seeded random centres, each boundary given the obstacle
-    profile across the bisector of its two nearest centres.  The solute field
-    (one, or two for 3 grains, to match the compiled (N, K) pairs) is held."""
+    Voronoi cells of seeded random centres (each cell pure in the grain of its
+    nearest centre; the boundaries take their diffuse profile in the first
+    steps).  The solute field (one, or two for 3 grains, to match the compiled
+    (N, K) pairs) is held."""
     N = grains
     NM = 2 if N == 3 else 1
     ny = n if ny is None else ny
@@ -352,26 +353,13 @@ def grain_growth(n: int = 256, dim: int = 3, grains: int = 8, seed: int = BASE_S
     # squared periodic distance of every cell centre to every grain centre
     grids = np.meshgrid(*[_centres(e, 1.0) for e in ext[::-1]], indexing="ij")   # z, y, x order
     d2 = np.zeros((N,) + grids[0].shape)
-    disp = np.zeros((N, dim) + grids[0].shape)
     for g, c in enumerate(centres):
         for k in range(dim):
             t = grids[dim - 1 - k] - c[k]
             t = t - ext[k] * np.round(t / ext[k])
-            disp[g, k] = t
             d2[g] += t * t
-    order = np.argsort(d2, axis=0)
-    first, second = order[0], order[1]
-    # distance to the bisector of the two nearest centres (positive inside the first)
-    take = lambda a, idx: np.take_along_axis(a, idx[None], axis=0)[0]
-    sep = np.zeros(grids[0].shape)
-    for k in range(dim):
-        sep += (take(disp[:, k], first) - take(disp[:, k], second)) ** 2
-    u = (take(d2, second) - take(d2, first)) / (2.0 * np.sqrt(np.maximum(sep, 1e-12)))
-    s = seed_profile(u / 4.0, "obstacle")
-    phi = np.zeros((N,) + grids[0].shape)
-    np.put_along_axis(phi, first[None], s[None], axis=0)
-    np.put_along_axis(phi, second[None], (1.0 - s)[None], axis=0)
-    phi = phi.reshape((N,) + shape)
+    nearest = np.argmin(d2, axis=0)
+    phi = np.stack([(nearest == g).astype(np.float64) for g in range(N)]).reshape((N,) + shape)
     mu0 = np.zeros((NM,) + shape)
     dt = 0.2 * dt_stab(dim, 1.0, 1.0, 1.0, 0.0, 0.0)
     return Problem(name=f"gg_{dim}d{n}_n{N}", dim=dim, nx=n, ny=ny, nz=nz, n_phases=N, n_components=NM + 1,
