@@ -437,6 +437,74 @@ __device__ __forceinline__ uint32_t box_phase_mask(const Real* box, int lane) {
   return __reduce_or_sync(0xffffffffu, m);
 }
 
+// Scan of an interface box by the warp: lane = column H + lane of the 3 x 3
+// rows; lanes 0..17 also take one cell of the halo column on either side
+// (lanes 0..8 the left one, 9..17 the right one, row lane % 9).  Returns the
+// phases present anywhere in the box (OR over the warp: a superset of every
+// cell's stencil) and sets `bulk` to l + 1 when every cell of the 3 x 3 x 3
+// block around the lane's cell is exactly pure phase l (phi_l = 1, all others
+// 0), else 0.  Called by all lanes of the warp.
+template <int NP, int NM, class Real>
+__device__ __forceinline__ uint32_t box_scan(const Real* box, int lane, int& bulk) {
+  using Sh = IfaceShape<NP, NM, Real>;
+  uint32_t m = 0;
+  // pure code of one box cell (l + 1 or 0); ORs its nonzero phases into nzm
+  auto code_of = [&](int r, int x, uint32_t& nzm) {
+    uint32_t nz = 0, one = 0;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const Real v = box[a * (9 * Sh::BX) + r * Sh::BX + x];
+      nz |= (v != Real(0) ? 1u : 0u) << a;
+      one |= (v == Real(1) ? 1u : 0u) << a;
+    }
+    nzm |= nz;
+    return (__popc(nz) == 1 && nz == one) ? __ffs(nz) : 0;
+  };
+  int col = code_of(0, Sh::H + lane, m);   // common code of the lane's 9 cells, or 0
+#pragma unroll
+  for (int r = 1; r < 9; ++r) {
+    const int c = code_of(r, Sh::H + lane, m);
+    col = c == col ? col : 0;
+  }
+  uint32_t hm = 0;
+  const int hc = code_of(lane % 9, lane < 9 ? Sh::H - 1 : Sh::H + 32, hm);
+  if (lane < 18) m |= hm;
+  const uint32_t wmask = __reduce_or_sync(0xffffffffu, m);
+  const int lc = __shfl_sync(0xffffffffu, hc, 0), rc = __shfl_sync(0xffffffffu, hc, 9);
+  const uint32_t lb = __ballot_sync(0xffffffffu, lane < 9 && hc == lc);
+  const uint32_t rb = __ballot_sync(0xffffffffu, lane >= 9 && lane < 18 && hc == rc);
+  int left = __shfl_up_sync(0xffffffffu, col, 1), right = __shfl_down_sync(0xffffffffu, col, 1);
+  if (lane == 0) left = lb == 0x1FFu ? lc : 0;
+  if (lane == 31) right = rb == (0x1FFu << 9) ? rc : 0;
+  bulk = (col != 0 && left == col && right == col) ? col : 0;
+  return wmask;
+}
+
+// Bulk update of one cell of an interface box whose 3 x 3 x 3 block is pure
+// phase l (c = the cell in field 0, cf = Kb_l then eb_l): phi unchanged and
+// mu + Kb_l Lap(mu) - eb_l, the form of the streaming kernel.
+template <int NP, int NM, class Real>
+__device__ __forceinline__ void box_bulk_mu(const Real* c, const Real* cf, Real* mn) {
+  using Sh = IfaceShape<NP, NM, Real>;
+  Real L[NM], mc[NM];
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    const Real* f = c + (NP + i) * (9 * Sh::BX);
+    const Real v = f[0];
+    Real sum = (f[-1] + f[1]) + (f[-Sh::BX] + f[Sh::BX]);
+    sum += f[-3 * Sh::BX] + f[3 * Sh::BX];
+    L[i] = sum - Real(6) * v;
+    mc[i] = v;
+  }
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    Real dd = mc[i] - cf[NM * NM + i];
+#pragma unroll
+    for (int j = 0; j < NM; ++j) dd += cf[i * NM + j] * L[j];
+    mn[i] = dd;
+  }
+}
+
 // Interface kernel of the split 3-D step: the full cell update of every warp
 // row the streaming kernel listed (32 cells of one row of one plane per
 // warp), from a TMA box of the input state; writes phi, mu, their ghost
@@ -513,7 +581,40 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
     const int x = 32 * sg + lane;
     const bool active = x < g.nx;
     const Real* box = reinterpret_cast<const Real*>(reinterpret_cast<unsigned char*>(buf0) + b * Sh::BOX_STRIDE);
-    const uint32_t wmask = box_phase_mask<NP, NM, Real>(box, lane);
+    uint32_t wmask;
+    if constexpr (kSparse) {
+      // many phases: rows whose cells all have a pure 3 x 3 x 3 block (listed
+      // only because a segment next to them is not pure) take the bulk update
+      int bk = 0;
+      wmask = box_scan<NP, NM, Real>(box, lane, bk);
+      if (__all_sync(0xffffffffu, !active || bk != 0)) {
+        if (active) {
+          Real pn[NP], mn[NM], cf[NM * NM + NM];
+#pragma unroll
+          for (int a = 0; a < NP; ++a) pn[a] = a == bk - 1 ? Real(1) : Real(0);
+#pragma unroll
+          for (int k = 0; k < NM * NM; ++k) cf[k] = g.Kb[bk - 1][k];
+#pragma unroll
+          for (int k = 0; k < NM; ++k) cf[NM * NM + k] = g.eb[bk - 1][k];
+          box_bulk_mu<NP, NM, Real>(box + 4 * Sh::BX + Sh::H + lane, cf, mn);
+          store_cell<DIM>(g, x, y, z, pn, mn);
+        }
+        const int ref = __shfl_sync(0xffffffffu, bk, 0);
+        const bool same = __all_sync(0xffffffffu, !active || bk == ref);
+        if (lane == 0) {
+          const long long ci = ((long long)(z + g.zoff) * g.ny + y) * g.segs + sg;
+          int c = same ? ref : 0;
+          if (c != 0 && (g.codes_in[ci] & kCodePhase) == c) c |= kCodeReuse;   // pure before and after
+          g.codes_out[ci] = (uint8_t)c;
+        }
+        __syncwarp();
+        b ^= 1;
+        i = nxt;
+        continue;
+      }
+    } else {
+      wmask = box_phase_mask<NP, NM, Real>(box, lane);
+    }
     if constexpr (kSparse) {
       if (__popc(wmask) > kSparseK) {   // for the MODE 1 launch
         if (lane == 0) {
