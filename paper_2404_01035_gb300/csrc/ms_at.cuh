@@ -212,10 +212,13 @@ __global__ void __launch_bounds__(AtShape<DIM, NP, NM, Real>::THREADS)
     const int x0 = 32 * s;
     // stage: rows (field, plane, row) of 34 cells x0 - 1 .. x0 + 32, all
     // copies in flight at once; cells past the +x ghost (x > nx) are never
-    // read by an active lane and stay unset
+    // read by an active lane and stay unset.  mu^n and phi^{n+1} are read
+    // only at the two cells of a face, never on the four corner rows (a
+    // y and a z offset together), which are left unset for them.
     const int xa = x0 - 1 + lane, xb = x0 + 31 + lane;
     for (int row = 0; row < Sh::ROWS; ++row) {
       const int f = row / (3 * Sh::NPL), pl = (row / 3) % Sh::NPL, ry = row % 3;
+      if (DIM == 3 && f >= NP && pl != 1 && ry != 1) continue;
       const int zz = DIM == 3 ? z + pl - 1 : 0, yy = y + ry - 1;
       const Real* src = f < NP + NM ? in + (long long)f * g.fstride : g.out + (long long)(f - NP - NM) * g.fstride;
       src += (long long)(DIM == 3 ? zz + g.zoff : 0) * plane + (long long)(yy + 1) * g.pitch + g.xoff;
