@@ -17,6 +17,8 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
     values, direction, inertness, flux-form conservation, symmetries: pinned.
   * Grain growth (``tests/test_oracle_gg.py``): frozen mu, stationary planar
     boundary, the curvature-driven area loss rate of a circular grain: pinned.
+  * Elasticity (``tests/test_oracle_elastic.py``): closed-form laminate,
+    Voigt shear factor, divergence-free stress: pinned.
   * The full multiphase (N >= 3) anisotropic dendrite / eutectic / multigrain
     trajectories: parity unpinned beyond the identities above.
 """
@@ -65,6 +67,7 @@ class _Problem(ctypes.Structure):
         ("z0", ctypes.c_double), ("V", ctypes.c_double), ("t0", ctypes.c_double),
         ("z_origin", ctypes.c_int), ("noise_amp", ctypes.c_double), ("noise_seed", ctypes.c_ulonglong),
         ("step0", ctypes.c_longlong), ("anti_trapping", ctypes.c_int), ("grain_growth", ctypes.c_int),
+        ("elw", ctypes.c_void_p),
     ]
 
 
@@ -151,6 +154,8 @@ class OracleProblem:
         s.step0 = int(step0)
         s.anti_trapping = int(bool(opt("anti_trapping", 0)))
         s.grain_growth = int(bool(opt("grain_growth", 0)))
+        elw = override.get("elw", None)
+        s.elw = arr(elw, (N, self.nx * self.ny * self.nz)) if elw is not None else None
         self.s = s
 
     @property
@@ -164,9 +169,105 @@ class OracleProblem:
         return ctypes.byref(self.s)
 
 
+# Voigt index of a symmetric pair (xx, yy, zz, yz, xz, xy)
+_VOIGT = {(0, 0): 0, (1, 1): 1, (2, 2): 2, (1, 2): 3, (2, 1): 3, (0, 2): 4, (2, 0): 4, (0, 1): 5, (1, 0): 5}
+
+
+def stiffness_tensor(Cv, dim):
+    """C_ijkl from the 6 x 6 Voigt matrix (sigma_v = C_v eps_v, engineering
+    shear), restricted to the first `dim` axes (plane strain in 2-D)."""
+    C = np.zeros((3, 3, 3, 3))
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                for l in range(3):
+                    C[i, j, k, l] = Cv[_VOIGT[i, j]][_VOIGT[k, l]]
+    return C[:dim, :dim, :dim, :dim]
+
+
+def interp_field(phi):
+    """h_a(phi) of Eq. (hphi) over whole fields [N][...]: 3 phi_a^2 - 2 phi_a^3
+    + 2 phi_a sum_{b<c; b, c != a} phi_b phi_c."""
+    N = phi.shape[0]
+    h = np.empty_like(phi)
+    for a in range(N):
+        pair = np.zeros_like(phi[0])
+        for b in range(N):
+            for c in range(b + 1, N):
+                if b != a and c != a:
+                    pair += phi[b] * phi[c]
+        h[a] = 3.0 * phi[a] ** 2 - 2.0 * phi[a] ** 3 + 2.0 * phi[a] * pair
+    return h
+
+
+def _wavenumbers(n, dx):
+    """2 pi m / (n dx) in FFT order, the Nyquist index of an even n taken as 0
+    (its sign is ambiguous; a zero keeps the solution Hermitian)."""
+    k = 2.0 * np.pi * np.fft.fftfreq(n, dx)
+    if n % 2 == 0:
+        k[n // 2] = 0.0
+    return k
+
+
+def elastic_fields(prob, phi):
+    """Mechanical equilibrium with a homogeneous stiffness (Sec. 2 "Elasticity
+    implementation": the homogeneous case of the Fourier-space solution, with
+    the eigenstrain sum_a eps*^a h_a(phi) of its Eq. for e_kl and no
+    homogeneous strain, i.e. a clamped periodic box).  In Fourier space
+    t_i = C_ijmn k_j eps*_mn, G = (C_ijkl k_j k_l)^-1, the displacement is
+    -i G t and the strain eps_kl = (k_k (G t)_l + k_l (G t)_k) / 2 (zero at
+    k = 0); k_j = 2 pi m_j / (n_j dx) in FFT order (the Nyquist index of an
+    even extent taken as 0).  Returns the stress
+    sigma = C (eps - eps*) [dim][dim][nz][ny][nx] and, per phase, the elastic
+    part of its potential w_b = -sigma : eps*^b [N][nz][ny][nx], whose
+    contraction with dh_b/dphi_a is d f_el / d phi_a."""
+    dim = prob.dim
+    N = prob.n_phases
+    nz = prob.nz if dim == 3 else 1
+    shape = (nz, prob.ny, prob.nx)
+    phi = np.asarray(phi, dtype=np.float64).reshape((N,) + shape)
+    C = stiffness_tensor(np.asarray(prob.elastic_C, dtype=np.float64), dim)
+    eig = np.asarray(prob.eigenstrain, dtype=np.float64).reshape(N, 3, 3)[:, :dim, :dim]
+    h = interp_field(phi)
+    E = np.einsum("amn,a...->mn...", eig, h)                      # eps*(x) [dim][dim][grid]
+    axes = (0, 1, 2) if dim == 3 else (1, 2)
+    Eh = np.fft.fftn(E, axes=tuple(a + 2 for a in axes))
+    ks = [_wavenumbers(n, prob.dx) for n in (prob.nx, prob.ny, nz)[:dim]]
+    K = np.zeros((dim,) + shape)
+    grids = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")   # z, y, x
+    for d in range(dim):
+        K[d] = ks[d][grids[2 - d]]
+    t = np.einsum("ijmn,j...,mn...->i...", C, K, Eh)
+    Ginv = np.einsum("ijkl,j...,l...->ik...", C, K, K)
+    Ginv = np.moveaxis(Ginv, (0, 1), (-2, -1))
+    zero = (K ** 2).sum(axis=0) == 0.0
+    Ginv[zero] = np.eye(dim)
+    G = np.linalg.inv(Ginv)
+    G[zero] = 0.0
+    Gt = np.einsum("...ki,i...->k...", G, t)
+    epsh = 0.5 * (np.einsum("k...,l...->kl...", K, Gt) + np.einsum("l...,k...->kl...", K, Gt))
+    eps = np.real(np.fft.ifftn(epsh, axes=tuple(a + 2 for a in axes)))
+    sigma = np.einsum("ijkl,kl...->ij...", C, eps - E)
+    w = -np.einsum("ij...,bij->b...", sigma, eig)
+    return sigma, w
+
+
+def _elastic(prob, override):
+    C = override.get("elastic_C", getattr(prob, "elastic_C", None))
+    return C is not None
+
+
 def run(prob, phi0, mu0, nsteps: int, t0: float = 0.0, step0: int = 0, **override):
     """nsteps explicit steps in FP64; returns (phi, mu) shaped [F][nz][ny][nx].
-    step0 = step index of the input state (the counter of the phi noise)."""
+    step0 = step index of the input state (the counter of the phi noise).
+    With a stiffness (`elastic_C`) the elastic potentials are solved from the
+    state before every step."""
+    if _elastic(prob, override) and "elw" not in override:
+        phi, mu = phi0, mu0
+        for n in range(int(nsteps)):
+            _, w = elastic_fields(prob, phi)
+            phi, mu = run(prob, phi, mu, 1, t0=t0 + n * prob.dt, step0=step0 + n, elw=w, **override)
+        return phi, mu
     op = OracleProblem(prob, t0, step0, **override)
     phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(op.shape(op.N))
     mu0 = np.ascontiguousarray(mu0, dtype=np.float64).reshape(op.shape(op.NM))

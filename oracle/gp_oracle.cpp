@@ -22,6 +22,9 @@
 //     of Eq. (Mu_explicit_temperature) when enabled.
 //   * Sec. 4 "Grain-growth" (GRAINGROWTH = 1): isotropic grain growth, read as
 //     the phi equation without the chemical term dpsi/dphi and with mu held.
+//   * Sec. 2 "Elasticity implementation" (homogeneous stiffness): the elastic
+//     driving force arrives as a per-phase field `elw` (computed by the Python
+//     side of the oracle with an FFT) and is added to the phase potentials.
 //
 // Readings where the paper is silent or ambiguous (all listed in the design
 // notes): unit-spacing finite differences with face fluxes (normal difference,
@@ -112,6 +115,7 @@ typedef struct {
   long long step0;       // step index of the input state (noise counter)
   int anti_trapping;     // 1 = anti-trapping current j_at in the mu update
   int grain_growth;      // 1 = GRAINGROWTH: no chemical driving force, mu frozen
+  const double* elw;     // [N][cells] elastic part of the potential of each phase, or NULL
 } oracle_problem;
 
 }  // extern "C"
@@ -534,7 +538,11 @@ void rate_parts(const Ctx<S>& c, const S* phi, const S* mu, int x, int y, int z,
   const double T = temperature(p, y, z, t);
   S psi[NMAX], mloc[KMAX], dh[NMAX * NMAX];
   for (int i = 0; i < p.NM; ++i) mloc[i] = mu[i * c.cells + ic];
-  for (int b = 0; b < N; ++b) psi[b] = grand_potential(p, b, mloc, T);
+  // the elastic energy enters like a phase potential: d f_el / d phi_a =
+  // sum_b (-sigma : eps*^b) dh_b / dphi_a (homogeneous stiffness, eigenstrain
+  // interpolated with h; the field comes from the FFT equilibrium solve)
+  for (int b = 0; b < N; ++b)
+    psi[b] = grand_potential(p, b, mloc, T) + (p.elw ? p.elw[b * c.cells + ic] : 0.0);
   interp_dh(N, ph, dh);
   for (int a = 0; a < N; ++a) {
     P[a] = 0.0;

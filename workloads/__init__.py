@@ -106,6 +106,8 @@ class Problem:
     noise_seed: int = 0
     anti_trapping: int = 0         # 1 = anti-trapping current in the mu update
     grain_growth: int = 0          # 1 = GRAINGROWTH: curvature-driven only, mu held
+    elastic_C: Optional[np.ndarray] = None   # [6,6] Voigt stiffness (homogeneous); None = no elasticity
+    eigenstrain: Optional[np.ndarray] = None # [N,3,3] eigenstrain of each phase (tensor components)
     phi0: np.ndarray = None        # [N,nz,ny,nx]
     mu0: np.ndarray = None         # [K-1,nz,ny,nx]
     meta: dict = field(default_factory=dict)
