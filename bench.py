@@ -309,6 +309,7 @@ def run_ours(args, rank, world, local_rank):
         extra["frame_noise"] = bench_frame_noise(stream)
         extra["anti_trapping"] = bench_anti_trapping(stream)
         extra["grain_growth"] = bench_grain_growth(stream)
+        extra["elasticity"] = bench_elasticity(stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -475,6 +476,39 @@ def bench_grain_growth(stream):
     return {"workload": "3-D 256^3 isotropic grain growth, 8 Voronoi grains, periodic, FP32, 200 steps",
             "mlups": p.cells * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps,
             "launch": {"tx": tx, "ty": ty, "split": split, "zchunk": zc}}
+
+
+def bench_elasticity(stream):
+    """The multigrain grid (7 grains + liquid, 8 phases) at 256^3 with a cubic
+    stiffness and a dilatational eigenstrain of 1% in every grain: the FFT
+    equilibrium before every step, against the same run without it."""
+    import numpy as np
+    import workloads
+    from paper_2404_01035_gb300 import Simulation
+    out = {"workload": "3-D 256^3 multigrain (8 phases), FP32, cubic stiffness, 1% dilatational eigenstrain "
+                       "in the grains, 100 steps"}
+    steps = 100
+    for el in (1, 0):
+        p = workloads.cfg5(n=256)
+        if el:
+            C = np.zeros((6, 6))
+            C[:3, :3] = 60.0
+            np.fill_diagonal(C[:3, :3], 150.0)
+            C[3, 3] = C[4, 4] = C[5, 5] = 75.0
+            eig = np.zeros((p.n_phases, 3, 3))
+            for g in range(p.n_phases - 1):
+                eig[g] = np.eye(3) * 0.01
+            p.elastic_C, p.eigenstrain = C, eig
+        sim = Simulation(p, dtype="f32", stream=stream)
+        sim.set_fields(p.phi0, p.mu0)
+        sim.tune(None, steps_per_trial=5)
+        sim.set_fields(p.phi0, p.mu0)
+        sim.step(10)
+        ms = _events_ms(stream, lambda: sim.step(steps))
+        out["with" if el else "without"] = {"mlups": p.cells * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps}
+        sim.close()
+    out["equilibrium_ms_per_step"] = out["with"]["ms_per_step"] - out["without"]["ms_per_step"]
+    return out
 
 
 def bench_adjoint(stream):

@@ -131,6 +131,19 @@ typedef struct {
                               keep their layout (N grains, M >= 1 mu fields that
                               stay constant).  Not available with
                               anti_trapping, ms_grad or ms_batch_*. */
+  const double* elastic_C; /* Elasticity (Sec. 2 "Elasticity implementation",
+                              homogeneous stiffness): 6 x 6 Voigt stiffness,
+                              order xx yy zz yz xz xy, engineering shear; NULL =
+                              off.  Before every step the periodic equilibrium
+                              strain of the eigenstrain sum_a eps*^a h_a(phi) is
+                              solved by FFT (cuFFT, opened at run time; zero
+                              mean strain), and -sigma : eps*^b joins each
+                              phase potential.  2-D grids use plane strain.
+                              Needs periodic boundaries and N in {2, 3, 8}; not
+                              available with grain_growth, ms_grad, ms_batch_*
+                              or MS_BC_HALO faces. */
+  const double* eigenstrain; /* [N][3][3] eigenstrain of each phase (symmetric
+                              tensor components), read with elastic_C. */
 } ms_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  NULL in

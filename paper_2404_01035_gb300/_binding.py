@@ -59,6 +59,7 @@ class Params(ctypes.Structure):
         ("z0", ctypes.c_double), ("V", ctypes.c_double), ("t0", ctypes.c_double),
         ("noise_amp", ctypes.c_double), ("noise_seed", ctypes.c_ulonglong),
         ("anti_trapping", ctypes.c_int), ("grain_growth", ctypes.c_int),
+        ("elastic_C", ctypes.c_void_p), ("eigenstrain", ctypes.c_void_p),
     ]
 
 

@@ -328,8 +328,9 @@ ms_status ms_enable_checkpoints(ms_ctx* c, int every) {
     return fail(c, MS_ERR_UNSUPPORTED, "no compiled adjoint kernel for this (dim, N, K, dtype)");
   if (every > 0 && c->m.noise_amp != 0.0)
     return fail(c, MS_ERR_UNSUPPORTED, "the adjoint does not support phi noise (noise_amp != 0)");
-  if (every > 0 && (c->m.at || c->m.gg))
-    return fail(c, MS_ERR_UNSUPPORTED, "the adjoint does not support the anti-trapping current or grain growth");
+  if (every > 0 && (c->m.at || c->m.gg || c->m.el))
+    return fail(c, MS_ERR_UNSUPPORTED,
+                "the adjoint does not support the anti-trapping current, grain growth or elasticity");
   ms_reset_extra(c);
   c->adj.every = every;
   return MS_OK;
@@ -347,8 +348,9 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
   AdjointStore& A = c->adj;
   if (A.every <= 0) return fail(c, MS_ERR_STATE, "checkpoints are not enabled (ms_enable_checkpoints)");
   if (c->m.noise_amp != 0.0) return fail(c, MS_ERR_UNSUPPORTED, "the adjoint does not support phi noise (noise_amp != 0)");
-  if (c->m.at || c->m.gg)
-    return fail(c, MS_ERR_UNSUPPORTED, "the adjoint does not support the anti-trapping current or grain growth");
+  if (c->m.at || c->m.gg || c->m.el)
+    return fail(c, MS_ERR_UNSUPPORTED,
+                "the adjoint does not support the anti-trapping current, grain growth or elasticity");
   const AdjKernel* ak = find_adjoint(c->m);
   if (!ak) return fail(c, MS_ERR_UNSUPPORTED, "no compiled adjoint kernel for this (dim, N, K, dtype)");
   const int64_t nsteps = c->step - A.first_step;

@@ -323,10 +323,10 @@ ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_c
       batch_free(b);
       return bfail(nullptr, MS_ERR_UNSUPPORTED, "batched simulations do not support phi noise (noise_amp != 0)");
     }
-    if (m.at || m.gg) {
+    if (m.at || m.gg || m.el) {
       batch_free(b);
       return bfail(nullptr, MS_ERR_UNSUPPORTED,
-                   "batched simulations do not support the anti-trapping current or grain growth");
+                   "batched simulations do not support the anti-trapping current, grain growth or elasticity");
     }
     if (m.G * m.V != 0.0) {
       batch_free(b);

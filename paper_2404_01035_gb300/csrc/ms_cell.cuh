@@ -451,6 +451,12 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
     S psi[NP];
 #pragma unroll
     for (int b = 0; b < NP; ++b) psi[b] = g.gg ? S(Real(0)) : grand_potential<NP, NM, Real>(g, b, mc, s);
+    if (g.elw) {   // elasticity: -sigma : eps*^b joins each phase potential
+      const unsigned long long cell = gcell - (unsigned long long)g.zorg * (DIM == 3 ? (unsigned long long)g.nx * g.ny : g.nx);
+      const unsigned long long cells = (unsigned long long)g.nx * g.ny * (DIM == 3 ? g.nz : 1);
+#pragma unroll
+      for (int b = 0; b < NP; ++b) psi[b] = psi[b] + g.elw[b * cells + cell];
+    }
     S e1 = ph[0];
 #pragma unroll
     for (int a = 1; a < NP; ++a) e1 += ph[a];
@@ -780,6 +786,12 @@ __device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real
     Real psi[NP];
 #pragma unroll
     for (int b = 0; b < NP; ++b) psi[b] = g.gg ? Real(0) : grand_potential<NP, NM, Real>(g, b, mc, s);
+    if (g.elw) {   // elasticity: -sigma : eps*^b joins each phase potential
+      const unsigned long long cell = gcell - (unsigned long long)g.zorg * (DIM == 3 ? (unsigned long long)g.nx * g.ny : g.nx);
+      const unsigned long long cells = (unsigned long long)g.nx * g.ny * (DIM == 3 ? g.nz : 1);
+#pragma unroll
+      for (int b = 0; b < NP; ++b) psi[b] += g.elw[b * cells + cell];
+    }
     Real e1 = ph[0];
 #pragma unroll
     for (int a = 1; a < NP; ++a) e1 += ph[a];

@@ -70,6 +70,9 @@ struct StepArgs {
   Real dt, eps, inv_eps, mob, inv_dx, half_inv_dx, quarter_inv_dx, inv_dx2;
   int potential;            // 1 obstacle, 2 well
   int gg;                   // grain growth: no chemical driving force, mu held
+  // elastic part of each phase potential, -sigma : eps*^b, dense
+  // [NP][nz][ny][nx] (grid cell index), or NULL without elasticity
+  const Real* elw;
   int has_g3;
   // pairs (a < b, row-major order)
   Real gam2[P];             // 2 gamma_ab

@@ -55,6 +55,9 @@ struct HostModel {
   unsigned long long noise_seed = 0;
   int at = 0;                              // anti-trapping current in the mu update
   int gg = 0;                              // grain growth: no chemical driving force, mu held
+  int el = 0;                              // elasticity (homogeneous stiffness)
+  double elC[3][3][3][3] = {};             // stiffness tensor
+  double eig[kNMax][3][3] = {};            // eigenstrain of each phase
 };
 
 // Launch geometry of one step.
@@ -68,6 +71,7 @@ struct LaunchGeom {
   int iface_blocks = 0;            // SMs: the interface grid is this x resident CTAs per SM
   int sms = 0;                     // multiprocessors of the device
   unsigned int* at_list = nullptr; // anti-trapping work list (see StepArgs)
+  const void* elw = nullptr;       // elastic part of the phase potentials (see StepArgs)
   unsigned int at_cap = 0;
   int reuse_prev = 1;              // output buffer = state one step before the input (see StepArgs)
   long long step = 0;              // step index of the input state (phi-noise counter)

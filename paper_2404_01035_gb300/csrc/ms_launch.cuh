@@ -135,6 +135,7 @@ void set_launch_args(StepArgs<Real, NP, NM>& g, const HostModel& m, double t, vo
   g.step = (unsigned long long)lg.step;
   g.at_list = lg.at_list;
   g.at_cap = lg.at_cap;
+  g.elw = reinterpret_cast<const Real*>(lg.elw);
 }
 
 // Fused step: one kernel updates every cell.

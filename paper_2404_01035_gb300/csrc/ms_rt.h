@@ -35,6 +35,15 @@ struct AdjointStore {
   double* gsum = nullptr;      // accumulated parameter gradients (device)
 };
 
+// Elasticity buffers and FFT plans (allocated while elasticity is on).
+struct ElasticState {
+  void* E = nullptr;      // eigenstrain components, dense
+  void* eps = nullptr;    // periodic strain components, dense
+  void* spec = nullptr;   // their half spectra
+  void* W = nullptr;      // -sigma : eps*^b per phase, dense [N][cells]
+  int plan_r2c = 0, plan_c2r = 0, ncomp = 0;
+};
+
 }  // namespace msgb
 
 struct ms_ctx {
@@ -64,6 +73,7 @@ struct ms_ctx {
   void* diag_host = nullptr;
   std::string err;
   msgb::AdjointStore adj;
+  msgb::ElasticState el;
 };
 
 namespace msgb {
@@ -73,6 +83,10 @@ ms_status launch_one_step(ms_ctx* c);
 ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk);
 ms_status ensure_at_list(ms_ctx* c);   // the anti-trapping work list, when the current is on
 ms_status refresh_codes(ms_ctx* c);   // segment codes of the current state
+bool elastic_available();                         // cuFFT could be opened
+ms_status elastic_setup(ms_ctx* c);               // buffers and plans, when elasticity is on
+ms_status elastic_solve(ms_ctx* c, const void* state);   // w per phase from the state's phi
+void elastic_free(ms_ctx* c);
 // Tiled map of a padded state: box of (tx + 2H) x (ty + 2) x bz planes x nf fields.
 bool encode_state_map(CUtensorMap* tm, void* base, const HostModel& m, int nf, int tx, int ty, int bz = 1);
 // Maps a step variant reads from a state buffer: tm = its tile map (mu only

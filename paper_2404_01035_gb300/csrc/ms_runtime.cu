@@ -220,6 +220,24 @@ ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params
   m.at = p->anti_trapping ? 1 : 0;
   m.gg = p->grain_growth ? 1 : 0;
   if (m.at && m.gg) return fail(c, MS_ERR_ARG, "grain growth holds mu: the anti-trapping current does not apply");
+  m.el = p->elastic_C ? 1 : 0;
+  if (m.el) {
+    if (!p->eigenstrain) return fail(c, MS_ERR_ARG, "elasticity needs eigenstrain with elastic_C");
+    if (m.gg) return fail(c, MS_ERR_UNSUPPORTED, "elasticity is not offered with grain growth");
+    if (m.dim == 3 && m.bc[2] == kBcHalo)
+      return fail(c, MS_ERR_UNSUPPORTED, "elasticity needs the whole periodic domain (no halo faces)");
+    for (int d = 0; d < m.dim; ++d)
+      if (m.bc[d] != 3) return fail(c, MS_ERR_UNSUPPORTED, "elasticity (FFT equilibrium) needs periodic boundaries");
+    // Voigt index of a symmetric pair (xx, yy, zz, yz, xz, xy)
+    const int v[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) m.elC[i][j][k][l] = p->elastic_C[v[i][j] * 6 + v[k][l]];
+    for (int a = 0; a < N; ++a)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) m.eig[a][i][j] = p->eigenstrain[(a * 3 + i) * 3 + j];
+  }
   if (m.at && m.dim == 3 && m.bc[2] == kBcHalo)
     return fail(c, MS_ERR_UNSUPPORTED, "the anti-trapping current is not available on slabs with halo faces");
   // explicit stability bound (FP64): (dx^2 / 2d) min(tau / (gamma (1 + 15 delta)), 1 / D_eff)
@@ -496,6 +514,10 @@ ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk) {
 ms_status launch_one_step(ms_ctx* c) {
   const int src = c->cur, dst = 1 - c->cur;
   c->lg.step = c->step;
+  if (c->m.el) {   // elastic potentials of phi^n before the step
+    ms_status es = elastic_solve(c, c->buf[src]);
+    if (es != MS_OK) return es;
+  }
   cudaError_t e = c->kern->launch(&c->tm[src], &c->tmi[src], c->args.data(), c->m, c->t, c->buf[dst], c->codes[src],
                                   c->codes[dst], c->lg, c->stream);
   if (e == cudaSuccess && c->m.at)
@@ -599,6 +621,7 @@ ms_status ms_create(const ms_grid* grid, int n_phases, int n_components, const m
     return r;
   }
   s = apply_launch(c, k, 0);
+  if (s == MS_OK) s = elastic_setup(c);
   if (s != MS_OK) {
     std::string m = c->err;
     ms_destroy(c);
@@ -613,6 +636,7 @@ void ms_destroy(ms_ctx* c) {
   if (!c) return;
   if (c->stream || true) cudaStreamSynchronize(c->stream);
   ms_release_extra(c);
+  elastic_free(c);
   for (int b = 0; b < 2; ++b) {
     dev_free(c->hook, c->buf[b]);
     dev_free(c->hook, c->codes[b]);
@@ -643,7 +667,8 @@ ms_status ms_update_params(ms_ctx* c, const ms_params* p) {
   m2.t0 = c->m.t0;
   c->m = m2;
   c->kern->fill(c->args.data(), c->m, c->lg.zchunk, c->status);
-  return ensure_at_list(c);
+  ms_status es = ensure_at_list(c);
+  return es == MS_OK ? elastic_setup(c) : es;
 }
 
 ms_status ms_set_fields(ms_ctx* c, const void* phi, const void* mu, int on_device) {

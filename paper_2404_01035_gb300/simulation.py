@@ -47,6 +47,10 @@ def make_params(prob, dtype: str, keep: list, **override) -> Params:
     p.noise_seed = int(override.get("noise_seed", getattr(prob, "noise_seed", 0))) & 0xFFFFFFFFFFFFFFFF
     p.anti_trapping = int(bool(override.get("anti_trapping", getattr(prob, "anti_trapping", 0))))
     p.grain_growth = int(bool(override.get("grain_growth", getattr(prob, "grain_growth", 0))))
+    C = override.get("elastic_C", getattr(prob, "elastic_C", None))
+    if C is not None:
+        p.elastic_C = _arr(keep, C, (6, 6))
+        p.eigenstrain = _arr(keep, override.get("eigenstrain", getattr(prob, "eigenstrain", None)), (N, 3, 3))
     return p
 
 
