@@ -95,3 +95,42 @@ def test_batch_create_rejects_unsupported_combinations():
     rc = L.ms_batch_create(1, grids, p.n_phases, p.n_components, params, None, None, ctypes.byref(h))
     assert rc == 9 and not h.value
     assert L.ms_batch_create(0, grids, 2, 2, params, None, None, ctypes.byref(h)) == 1
+
+
+def test_params_struct_layout_matches_the_header(tmp_path):
+    # the ctypes mirror of ms_params / ms_grid against the C compiler's layout
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in B.Params._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "microsim_gb.h"', "int main(void) {",
+             '  printf("%zu\\n", sizeof(ms_params));']
+    lines += [f'  printf("%zu\\n", offsetof(ms_params, {f}));' for f in fields]
+    lines += ['  printf("%zu\\n", sizeof(ms_grid));', "  return 0;", "}"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(B.Params)
+    assert out[1:1 + len(fields)] == [getattr(B.Params, f).offset for f in fields]
+    assert out[-1] == ctypes.sizeof(B.Grid)
+
+
+def test_create_rejects_inconsistent_options():
+    p = W.cfg1()
+    C = np.eye(6) * 100.0
+    eig = np.zeros((2, 3, 3))
+    # a stiffness without eigenstrains
+    assert _create(p, elastic_C=C, eigenstrain=None)[0] == 1
+    # the FFT equilibrium needs periodic boundaries; not with grain growth
+    assert _create(p.copy(bc=[3, 1, 1]), elastic_C=C, eigenstrain=eig)[0] == 9
+    assert _create(p, elastic_C=C, eigenstrain=eig, grain_growth=1)[0] == 9
+    # grain growth holds mu, so the anti-trapping current cannot apply
+    assert _create(p, anti_trapping=1, grain_growth=1)[0] == 1
+    # a slab with halo faces cannot take the anti-trapping current
+    q = W.small_multiphase(n=8, dim=3, N=3, NM=2, bc=[3, 3, 16])
+    rc, h, msg = _create(q, anti_trapping=1)
+    assert rc == 9 and "anti-trapping" in msg
