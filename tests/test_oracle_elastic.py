@@ -4,9 +4,11 @@ the CPU.
 
 A laminate (fields varying along x only) has a closed-form equilibrium: the
 normal stress along x is uniform, the mean strain is zero, and the in-plane
-stresses follow pointwise; a uniform phase carries sigma = -C eps*; and any
+stresses follow pointwise; a uniform phase carries sigma = -C eps*; any
 state's stress must be divergence-free (checked spectrally here, independently
-of how the oracle solves for it).
+of how the oracle solves for it); and with an isotropic stiffness the energy
+of a dilatational inclusion depends on its volume only (the classical
+shape independence), with a closed form in the volume fraction.
 """
 import numpy as np
 import pytest
@@ -102,3 +104,45 @@ def test_stress_is_divergence_free(dim):
     scale = np.abs(sh).max() * max(np.abs(k).max() for k in ks)
     assert np.abs(div).max() <= 1e-11 * scale
     assert np.abs(sigma).max() > 1e-3
+
+
+def _energy(w, phi):
+    # E = 1/2 int sigma:(eps - eps*) = -1/2 int sigma:eps* (int sigma:eps = 0 at
+    # equilibrium in a periodic box with zero mean strain) = 1/2 sum h_b w_b
+    h = np.where(phi > 0.5, 1.0, 0.0)             # sharp fields: h = phi
+    return 0.5 * float((h * w).sum())
+
+
+def test_isotropic_dilatational_energy_is_shape_independent():
+    # Homogeneous isotropic stiffness (lambda, mu) and a dilatational misfit
+    # e0 in a sharp inclusion of volume fraction f: with K = lambda + 2 mu / 3
+    # the equilibrium strain trace is 3 K e0 (chi - f) / (lambda + 2 mu), so
+    # E = (9 K e0^2 V / 2) [f - K (f - f^2) / (lambda + 2 mu)] whatever the
+    # inclusion's shape (odd extents: no Nyquist modes).
+    lam, mu, e0 = 80.0, 50.0, 0.01
+    C = np.zeros((6, 6))
+    C[:3, :3] = lam
+    np.fill_diagonal(C[:3, :3], lam + 2 * mu)
+    C[3, 3] = C[4, 4] = C[5, 5] = mu
+    n = 21
+    p = W.binary_problem("el_eshelby", n, dim=3, ny=n, nz=n)
+    p.elastic_C = C
+    eig = np.zeros((2, 3, 3))
+    eig[0] = np.eye(3) * e0
+    p.eigenstrain = eig
+    z, y, x = np.meshgrid(*[np.arange(n) - n // 2] * 3, indexing="ij")
+    ball = (x ** 2 + y ** 2 + z ** 2) <= 5.3 ** 2
+    cells = int(ball.sum())
+    slab = np.zeros(n ** 3, bool)
+    slab[:cells] = True                          # the same number of cells as planes and a partial row
+    slab = slab.reshape(n, n, n)
+    K = lam + 2 * mu / 3
+    V = float(n ** 3)
+    f = cells / V
+    expect = 4.5 * K * e0 ** 2 * V * (f - K * (f - f * f) / (lam + 2 * mu))
+    for shape in (ball, slab):
+        phi = np.zeros((2, n, n, n))
+        phi[0] = shape
+        phi[1] = 1.0 - phi[0]
+        _, w = oracle.elastic_fields(p, phi)
+        assert _energy(w, phi) == pytest.approx(expect, rel=1e-10)
