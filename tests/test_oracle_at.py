@@ -142,3 +142,25 @@ def test_mirror_and_axis_permutation_symmetry():
     # and the current matters on this state
     off = oracle.run(p, p.phi0, p.mu0, 2)
     assert np.abs(off[1] - ref[1]).max() > 1e-6
+
+
+def test_current_moves_solute_from_a_growing_poor_solid_into_the_liquid():
+    # one step with and without the current on a planar binary front (solid
+    # poorer in solute, growing): across the face the current carries solute
+    # out of the solid cell into the liquid cell, so chi dmu (the solute
+    # change) falls on the solid side and rises on the liquid side
+    p = W.binary_problem("at_sign", 16, dim=2, ny=1, Delta=0.4, bc=[1, 1, 1])
+    p.ceq = np.array([[0.60], [0.817]])
+    x = (np.arange(16) + 0.5)
+    s = W.seed_profile((8.0 - x) / p.eps, "obstacle")        # solid on the left
+    phi = np.zeros((2, 1, 1, 16))
+    phi[0, 0, 0] = s
+    phi[1] = 1.0 - phi[0]
+    mu = np.full((1, 1, 1, 16), 1.634)
+    a = oracle.run(p, phi, mu, 1)
+    b = oracle.run(p, phi, mu, 1, anti_trapping=1)
+    grow = a[0][0, 0, 0] - phi[0, 0, 0]
+    assert grow[7] > 0 and grow[8] > 0                      # the solid grows
+    d = (b[1] - a[1])[0, 0, 0]
+    # the two cells of the central face (x = 7.5 | 8.5); chi > 0
+    assert d[7] < 0 < d[8]
