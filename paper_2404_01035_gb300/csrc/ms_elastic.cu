@@ -310,6 +310,9 @@ bool elastic_available() { return fft_api().ok; }
 
 ms_status elastic_setup(ms_ctx* c) {
   const HostModel& m = c->m;
+  // the step kernels read the elastic potentials only while elasticity is on
+  // (ms_update_params may turn it on or off)
+  c->lg.elw = m.el ? c->el.W : nullptr;
   if (!m.el || c->el.W) return MS_OK;
   const FftApi& f = fft_api();
   if (!f.ok) return fail(c, MS_ERR_UNSUPPORTED, "elasticity needs cuFFT (libcufft.so.12), which could not be opened");

@@ -84,3 +84,21 @@ def test_refusals():
     sim.close()
     with pytest.raises(Exception):
         Batch([p])
+
+
+def test_turning_elasticity_off_and_on_mid_run():
+    from paper_2404_01035_gb300 import Simulation
+    p = _elastic(W.small_multiphase(n=16, dim=2, N=3, NM=2, nx=32, ny=24, bc=[3, 3, 3]))
+    sim = Simulation(p, dtype="f64")
+    sim.set_fields(p.phi0, p.mu0)
+    sim.step(5)
+    sim.update_params(elastic_C=None)      # off: the step must stop reading the potentials
+    sim.step(5)
+    sim.update_params()                     # on again
+    sim.step(5)
+    g = sim.get_fields()
+    sim.close()
+    a = oracle.run(p, p.phi0, p.mu0, 5)
+    a = oracle.run(p, a[0], a[1], 5, t0=5 * p.dt, step0=5, elastic_C=None)
+    o = oracle.run(p, a[0], a[1], 5, t0=10 * p.dt, step0=10)
+    assert _err(g, o) <= 1e-10
