@@ -321,6 +321,8 @@ ms_status elastic_setup(ms_ctx* c) {
   const int nz = m.dim == 3 ? m.nz : 1;
   const long long cells = (long long)m.nx * m.ny * nz;
   const long long ncplx = (long long)(m.nx / 2 + 1) * m.ny * nz;
+  if (cells > 0x7FFFFFFFll || (long long)(m.dim == 3 ? 6 : 3) * cells > 0x7FFFFFFFFFll)
+    return fail(c, MS_ERR_UNSUPPORTED, "grid too large for the FFT plans of the elasticity");
   s.ncomp = m.dim == 3 ? 6 : 3;
   const size_t real = m.dtype == MS_F64 ? 8 : 4;
   s.E = dev_alloc(c->hook, s.ncomp * cells * real);
