@@ -172,8 +172,15 @@ void ms_destroy(ms_ctx* ctx);
 /* Text of the last error on ctx (or of the calling thread when ctx is NULL). */
 const char* ms_last_error(const ms_ctx* ctx);
 
-/* Replace the model parameters (dt, eps, tau, delta, D, ...) without
- * reallocating; grid, N, K and dtype must be unchanged. */
+/* Replace the model parameters (dt, eps, tau, delta, D, ...); grid, N, K and
+ * dtype must be unchanged.  Turning on the anti-trapping current or
+ * elasticity allocates their buffers (and FFT plans) here; if that fails the
+ * call returns the error and the context keeps the parameters it had.  While
+ * adjoint checkpoints are recording, phi noise, the anti-trapping current,
+ * grain growth and elasticity cannot be turned on (MS_ERR_UNSUPPORTED), and
+ * a successful update drops the snapshots recorded so far: the recording
+ * restarts at the current step, so that ms_grad never mixes two parameter
+ * sets. */
 ms_status ms_update_params(ms_ctx* ctx, const ms_params* params);
 
 /* Copy the state in.  phi: N fields, mu: K-1 fields, dense [f][z][y][x] in
@@ -214,6 +221,26 @@ ms_status ms_set_diag_every(ms_ctx* ctx, int64_t k);
 /* Wait for the stream; returns the sticky device status (MS_OK,
  * MS_ERR_NONFINITE or MS_ERR_TIMEOUT). */
 ms_status ms_sync(ms_ctx* ctx);
+
+/* Failure-path self-test (the paper has no counterpart; a library service
+ * for callers that want to see the timeout path work).  Enqueues one small
+ * kernel whose single thread waits, through the same bounded mbarrier wait
+ * the step kernels use, on a barrier that nothing completes, with a limit of
+ * limit_ns nanoseconds of %globaltimer (1e3 <= limit_ns <= 1e9); the wait
+ * gives up, records the timeout in the context's sticky status word and the
+ * kernel returns (no copy is in flight).  ms_sync / ms_diag then return
+ * MS_ERR_TIMEOUT for the rest of the context's life; the CUDA context stays
+ * usable for other ms contexts.  The step kernels' own waits keep their
+ * fixed one-second limit.  MS_ERR_ARG for a limit outside the range. */
+ms_status ms_selftest_timeout(ms_ctx* ctx, int64_t limit_ns);
+
+/* Host-side fault injection: when the environment variable MS_FAULT reads
+ * "step:K,code:X" at ms_create (K >= 0, X a non-zero ms_status value), that
+ * context's ms_step returns X, without launching, once the context has
+ * reached step K, and every later ms_step / ms_sync / ms_diag returns X too
+ * (sticky).  Used to test the failure handling of drivers above the library
+ * without a device fault.  A malformed MS_FAULT makes ms_create return
+ * MS_ERR_ARG. */
 
 /* Step count and physical time of the current state. */
 ms_status ms_time(const ms_ctx* ctx, int64_t* step, double* t);

@@ -267,14 +267,15 @@ __device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t pa
 // Wait for phase `parity` of the barrier, giving up after kWaitLimitNs.
 // Retries suspend the waiting warp so that it leaves the issue slots to the
 // warps that have work.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (;;) {
 #pragma unroll 1
     for (int i = 0; i < 8; ++i)
       if (mbar_try_wait_suspend(bar, parity, 20000u)) return true;
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
 }
 

@@ -308,28 +308,53 @@ cudaError_t solve(const HostModel& m, const void* st, ElasticState& s, cudaStrea
 
 bool elastic_available() { return fft_api().ok; }
 
+namespace {
+void release_state(ms_ctx* c, ElasticState& s) {
+  const FftApi& f = fft_api();
+  if (f.ok) {
+    if (s.has_r2c) f.destroy(s.plan_r2c);
+    if (s.has_c2r) f.destroy(s.plan_c2r);
+  }
+  dev_free(c->hook, s.E);
+  dev_free(c->hook, s.eps);
+  dev_free(c->hook, s.spec);
+  dev_free(c->hook, s.W);
+  s = ElasticState{};
+}
+}  // namespace
+
+bool elastic_grid_fits(const HostModel& m) {
+  // the batched plans take the per-transform distance (cells) as an int
+  const long long cells = (long long)m.nx * m.ny * (m.dim == 3 ? m.nz : 1);
+  return cells <= 0x7FFFFFFFll;
+}
+
 ms_status elastic_setup(ms_ctx* c) {
   const HostModel& m = c->m;
   // the step kernels read the elastic potentials only while elasticity is on
   // (ms_update_params may turn it on or off)
-  c->lg.elw = m.el ? c->el.W : nullptr;
-  if (!m.el || c->el.W) return MS_OK;
+  c->lg.elw = m.el && c->el.ready ? c->el.W : nullptr;
+  if (!m.el || c->el.ready) return MS_OK;
   const FftApi& f = fft_api();
   if (!f.ok) return fail(c, MS_ERR_UNSUPPORTED, "elasticity needs cuFFT (libcufft.so.12), which could not be opened");
   if (m.N != 2 && m.N != 3 && m.N != 8) return fail(c, MS_ERR_UNSUPPORTED, "elasticity: phases must be 2, 3 or 8");
-  ElasticState& s = c->el;
+  if (!elastic_grid_fits(m)) return fail(c, MS_ERR_UNSUPPORTED, "grid too large for the FFT plans of the elasticity");
+  // everything is built in a local state and handed to the context only when
+  // every buffer and both plans exist; a failure part-way frees what was made
+  ElasticState s;
   const int nz = m.dim == 3 ? m.nz : 1;
   const long long cells = (long long)m.nx * m.ny * nz;
   const long long ncplx = (long long)(m.nx / 2 + 1) * m.ny * nz;
-  if (cells > 0x7FFFFFFFll || (long long)(m.dim == 3 ? 6 : 3) * cells > 0x7FFFFFFFFFll)
-    return fail(c, MS_ERR_UNSUPPORTED, "grid too large for the FFT plans of the elasticity");
   s.ncomp = m.dim == 3 ? 6 : 3;
   const size_t real = m.dtype == MS_F64 ? 8 : 4;
   s.E = dev_alloc(c->hook, s.ncomp * cells * real);
   s.eps = dev_alloc(c->hook, s.ncomp * cells * real);
   s.spec = dev_alloc(c->hook, s.ncomp * ncplx * 2 * real);
   s.W = dev_alloc(c->hook, (size_t)m.N * cells * real);
-  if (!s.E || !s.eps || !s.spec || !s.W) return fail(c, MS_ERR_OOM, "elasticity buffers");
+  if (!s.E || !s.eps || !s.spec || !s.W) {
+    release_state(c, s);
+    return fail(c, MS_ERR_OOM, "elasticity buffers");
+  }
   int n3[3] = {nz, m.ny, m.nx};
   int* n = m.dim == 3 ? n3 : n3 + 1;
   const int rank = m.dim;
@@ -339,13 +364,28 @@ ms_status elastic_setup(ms_ctx* c) {
   int* onb = m.dim == 3 ? onr : onr + 1;
   const bool dbl = m.dtype == MS_F64;
   cufftHandle p1 = 0, p2 = 0;
-  if (f.plan_many(&p1, rank, n, inb, 1, idist, onb, 1, odist, dbl ? CUFFT_D2Z : CUFFT_R2C, s.ncomp) != CUFFT_SUCCESS ||
-      f.plan_many(&p2, rank, n, onb, 1, odist, inb, 1, idist, dbl ? CUFFT_Z2D : CUFFT_C2R, s.ncomp) != CUFFT_SUCCESS)
+  const bool ok1 = f.plan_many(&p1, rank, n, inb, 1, idist, onb, 1, odist, dbl ? CUFFT_D2Z : CUFFT_R2C, s.ncomp) ==
+                   CUFFT_SUCCESS;
+  if (ok1) {
+    s.plan_r2c = p1;
+    s.has_r2c = true;
+  }
+  const bool ok2 = ok1 && f.plan_many(&p2, rank, n, onb, 1, odist, inb, 1, idist, dbl ? CUFFT_Z2D : CUFFT_C2R,
+                                      s.ncomp) == CUFFT_SUCCESS;
+  if (ok2) {
+    s.plan_c2r = p2;
+    s.has_c2r = true;
+  }
+  if (!ok1 || !ok2) {
+    release_state(c, s);
     return fail(c, MS_ERR_CUDA, "cuFFT plan creation failed");
-  s.plan_r2c = p1;
-  s.plan_c2r = p2;
-  if (f.set_stream(p1, c->stream) != CUFFT_SUCCESS || f.set_stream(p2, c->stream) != CUFFT_SUCCESS)
+  }
+  if (f.set_stream(p1, c->stream) != CUFFT_SUCCESS || f.set_stream(p2, c->stream) != CUFFT_SUCCESS) {
+    release_state(c, s);
     return fail(c, MS_ERR_CUDA, "cuFFT stream");
+  }
+  s.ready = true;
+  c->el = s;
   c->lg.elw = s.W;
   return MS_OK;
 }
@@ -357,18 +397,6 @@ ms_status elastic_solve(ms_ctx* c, const void* state) {
   return MS_OK;
 }
 
-void elastic_free(ms_ctx* c) {
-  ElasticState& s = c->el;
-  const FftApi& f = fft_api();
-  if (f.ok) {
-    if (s.plan_r2c) f.destroy(s.plan_r2c);
-    if (s.plan_c2r) f.destroy(s.plan_c2r);
-  }
-  dev_free(c->hook, s.E);
-  dev_free(c->hook, s.eps);
-  dev_free(c->hook, s.spec);
-  dev_free(c->hook, s.W);
-  s = ElasticState{};
-}
+void elastic_free(ms_ctx* c) { release_state(c, c->el); }
 
 }  // namespace msgb

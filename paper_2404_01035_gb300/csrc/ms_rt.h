@@ -42,6 +42,8 @@ struct ElasticState {
   void* spec = nullptr;   // their half spectra
   void* W = nullptr;      // -sigma : eps*^b per phase, dense [N][cells]
   int plan_r2c = 0, plan_c2r = 0, ncomp = 0;
+  bool has_r2c = false, has_c2r = false;   // the plan handles hold created plans
+  bool ready = false;   // every buffer and both plans exist (set only when complete)
 };
 
 }  // namespace msgb
@@ -74,6 +76,11 @@ struct ms_ctx {
   std::string err;
   msgb::AdjointStore adj;
   msgb::ElasticState el;
+  // host-side fault injection (MS_FAULT=step:K,code:X read at ms_create):
+  // ms_step fails with fault_code when the context reaches step fault_step
+  int64_t fault_step = -1;
+  int fault_code = 0;
+  int host_status = 0;   // sticky host-side status (an injected fault), 0 = none
 };
 
 namespace msgb {
@@ -83,8 +90,12 @@ ms_status launch_one_step(ms_ctx* c);
 ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk);
 ms_status ensure_at_list(ms_ctx* c);   // the anti-trapping work list, when the current is on
 ms_status refresh_codes(ms_ctx* c);   // segment codes of the current state
+// Parse a fault-injection spec "step:K,code:X" (K >= 0, X a non-zero
+// ms_status); false for a malformed one.  NULL or empty = no fault (step -1).
+bool parse_fault_spec(const char* spec, int64_t* step, int* code);
 bool elastic_available();                         // cuFFT could be opened
 ms_status elastic_setup(ms_ctx* c);               // buffers and plans, when elasticity is on
+bool elastic_grid_fits(const HostModel& m);       // the FFT plans take the grid's cell count
 ms_status elastic_solve(ms_ctx* c, const void* state);   // w per phase from the state's phi
 void elastic_free(ms_ctx* c);
 // Tiled map of a padded state: box of (tx + 2H) x (ty + 2) x bz planes x nf fields.

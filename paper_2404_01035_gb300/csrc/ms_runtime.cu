@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -228,6 +229,8 @@ ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params
       return fail(c, MS_ERR_UNSUPPORTED, "elasticity needs the whole periodic domain (no halo faces)");
     for (int d = 0; d < m.dim; ++d)
       if (m.bc[d] != 3) return fail(c, MS_ERR_UNSUPPORTED, "elasticity (FFT equilibrium) needs periodic boundaries");
+    if (!elastic_grid_fits(m))
+      return fail(c, MS_ERR_UNSUPPORTED, "grid too large for the FFT plans of the elasticity (more than 2^31-1 cells)");
     // Voigt index of a symmetric pair (xx, yy, zz, yz, xz, xy)
     const int v[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
     for (int i = 0; i < 3; ++i)
@@ -515,6 +518,7 @@ ms_status launch_one_step(ms_ctx* c) {
   const int src = c->cur, dst = 1 - c->cur;
   c->lg.step = c->step;
   if (c->m.el) {   // elastic potentials of phi^n before the step
+    if (!c->el.ready) return fail(c, MS_ERR_STATE, "elasticity is on but its buffers and FFT plans do not exist");
     ms_status es = elastic_solve(c, c->buf[src]);
     if (es != MS_OK) return es;
   }
@@ -538,6 +542,19 @@ ms_status refresh_codes(ms_ctx* c) {
   e = cudaMemsetAsync(c->codes[1 - c->cur], 0, code_bytes(c->m), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "segment codes");
   return MS_OK;
+}
+
+bool parse_fault_spec(const char* spec, int64_t* step, int* code) {
+  *step = -1;
+  *code = 0;
+  if (!spec || !*spec) return true;
+  long long k = -1;
+  int x = 0, used = 0;
+  if (std::sscanf(spec, "step:%lld,code:%d%n", &k, &x, &used) != 2 || spec[used] != '\0') return false;
+  if (k < 0 || x < MS_ERR_ARG || x > MS_ERR_UNSUPPORTED) return false;
+  *step = (int64_t)k;
+  *code = x;
+  return true;
 }
 
 ms_status launch_diag_now(ms_ctx* c) {
@@ -570,6 +587,10 @@ ms_status ms_create(const ms_grid* grid, int n_phases, int n_components, const m
     return s;
   }
   set_layout(c->m);
+  if (!parse_fault_spec(std::getenv("MS_FAULT"), &c->fault_step, &c->fault_code)) {
+    delete c;
+    return fail(nullptr, MS_ERR_ARG, "MS_FAULT must read step:K,code:X (K >= 0, X a non-zero ms_status)");
+  }
   const StepKernel* k = find_step(c->m.dim, c->m.N, c->m.NM, c->m.dtype, 32, 8);
   if (!k) k = find_step(c->m.dim, c->m.N, c->m.NM, c->m.dtype, 0, 0);
   c->diagk = find_diag(c->m.dim, c->m.N, c->m.NM, c->m.dtype);
@@ -662,13 +683,31 @@ ms_status ms_update_params(ms_ctx* c, const ms_params* p) {
   HostModel m2;
   ms_status s = build_model(c, &g, c->m.N, c->m.NM + 1, p, m2);
   if (s != MS_OK) return s;
+  if (c->adj.every > 0 && (m2.noise_amp != 0.0 || m2.at || m2.gg || m2.el))
+    return fail(c, MS_ERR_UNSUPPORTED,
+                "adjoint checkpoints are recording: phi noise, the anti-trapping current, grain growth and "
+                "elasticity cannot be turned on (ms_enable_checkpoints(ctx, 0) first)");
   set_layout(m2);
   // keep the time line of the current state
   m2.t0 = c->m.t0;
+  const HostModel before = c->m;
   c->m = m2;
-  c->kern->fill(c->args.data(), c->m, c->lg.zchunk, c->status);
   ms_status es = ensure_at_list(c);
-  return es == MS_OK ? elastic_setup(c) : es;
+  if (es == MS_OK) es = elastic_setup(c);
+  if (es != MS_OK) {
+    // the context keeps running with the parameters it had
+    const std::string msg = c->err;
+    c->m = before;
+    ensure_at_list(c);
+    elastic_setup(c);
+    c->kern->fill(c->args.data(), c->m, c->lg.zchunk, c->status);
+    return fail(c, es, msg);
+  }
+  c->kern->fill(c->args.data(), c->m, c->lg.zchunk, c->status);
+  // recorded adjoint snapshots belong to the old parameters: the recording
+  // restarts at the current step
+  if (c->adj.every > 0 && c->step > c->adj.first_step) ms_reset_extra(c);
+  return MS_OK;
 }
 
 ms_status ms_set_fields(ms_ctx* c, const void* phi, const void* mu, int on_device) {
@@ -712,6 +751,8 @@ ms_status ms_step(ms_ctx* c, int64_t n) {
   if (!c) return fail(nullptr, MS_ERR_ARG, "ctx is NULL");
   if (n < 0) return fail(c, MS_ERR_ARG, "n must be >= 0");
   for (int64_t i = 0; i < n; ++i) {
+    if (c->fault_step >= 0 && c->step == c->fault_step) c->host_status = c->fault_code;
+    if (c->host_status) return fail(c, (ms_status)c->host_status, "injected fault (MS_FAULT)");
     ms_status s = ms_before_step(c);
     if (s != MS_OK) return s;
     s = launch_one_step(c);
@@ -731,6 +772,7 @@ ms_status ms_set_diag_every(ms_ctx* c, int64_t k) {
 }
 
 static ms_status read_status(ms_ctx* c) {
+  if (c->host_status) return fail(c, (ms_status)c->host_status, "injected fault (MS_FAULT)");
   int st = 0;
   MS_CUDA(c, cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   MS_CUDA(c, cudaStreamSynchronize(c->stream));

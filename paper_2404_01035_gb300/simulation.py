@@ -69,7 +69,7 @@ class Simulation:
     """One grand-potential simulation living on the GPU."""
 
     def __init__(self, prob, dtype: str = "f32", stream=None, torch_alloc: bool = True,
-                 **override):
+                 allocator=None, **override):
         import torch
         self._torch = torch
         L = lib()
@@ -86,7 +86,9 @@ class Simulation:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        self._alloc = TorchAllocator() if torch_alloc else None
+        # allocator: any object with a ctypes `struct` (an ms_allocator), e.g. a
+        # TorchAllocator subclass; default torch's caching allocator
+        self._alloc = allocator if allocator is not None else (TorchAllocator() if torch_alloc else None)
         h = ctypes.c_void_p()
         _check(L.ms_create(ctypes.byref(grid), self.N, int(prob.n_components),
                                 ctypes.byref(params), ctypes.c_void_p(stream.cuda_stream),
@@ -173,6 +175,10 @@ class Simulation:
     # --------------------------------------------------------------- stepping
     def step(self, n: int = 1):
         self._c(lib().ms_step(self.h, int(n)))
+
+    def selftest_timeout(self, limit_ns: int = 1_000_000):
+        """Enqueue the bounded-wait self-test (include/microsim_gb.h)."""
+        self._c(lib().ms_selftest_timeout(self.h, int(limit_ns)))
 
     def sync(self):
         self._c(lib().ms_sync(self.h))

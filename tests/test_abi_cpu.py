@@ -134,3 +134,20 @@ def test_create_rejects_inconsistent_options():
     q = W.small_multiphase(n=8, dim=3, N=3, NM=2, bc=[3, 3, 16])
     rc, h, msg = _create(q, anti_trapping=1)
     assert rc == 9 and "anti-trapping" in msg
+
+
+def test_create_refuses_grids_beyond_the_fft_plans():
+    # the elasticity's batched FFT plans take the cell count as an int: a
+    # 2048 x 1024 x 1024 grid (2^31 cells) is refused before any allocation
+    q = W.small_multiphase(n=8, dim=3, N=3, NM=2, bc=[3, 3, 3]).copy(nx=2048, ny=1024, nz=1024)
+    rc, h, msg = _create(q, elastic_C=np.eye(6) * 100.0, eigenstrain=np.zeros((3, 3, 3)))
+    assert rc == 9 and "too large" in msg and not h.value
+
+
+@pytest.mark.parametrize("spec", ["step:3", "step:-1,code:6", "step:2,code:0", "step:2,code:42",
+                                  "step:2,code:6,extra", "bogus"])
+def test_create_rejects_a_malformed_fault_spec(monkeypatch, spec):
+    # MS_FAULT is parsed before any device work, so a bad spec fails on CPU
+    monkeypatch.setenv("MS_FAULT", spec)
+    rc, h, msg = _create(W.cfg1())
+    assert rc == 1 and "MS_FAULT" in msg and not h.value
