@@ -234,6 +234,15 @@ ms_status ms_sync(ms_ctx* ctx);
  * fixed one-second limit.  MS_ERR_ARG for a limit outside the range. */
 ms_status ms_selftest_timeout(ms_ctx* ctx, int64_t limit_ns);
 
+/* FP32 arithmetic peak of the current device in TFLOP/s, measured (the paper
+ * has no counterpart; a measurement service for the ALU roof of the step's
+ * roofline): a grid of 64 warps per SM, each thread 8 independent chains of
+ * fused multiply-adds, scalar (paired = 0) or two-lane fma.rn.f32x2
+ * (paired = 1), 2 flops per FMA, best of five timed launches on `stream`
+ * (a cudaStream_t, NULL = legacy default).  Synchronous; allocates and frees
+ * 4 bytes with the stream-ordered allocator.  MS_ERR_CUDA on failure. */
+ms_status ms_peak_fp32(void* stream, int paired, double* tflops);
+
 /* Host-side fault injection: when the environment variable MS_FAULT reads
  * "step:K,code:X" at ms_create (K >= 0, X a non-zero ms_status value), that
  * context's ms_step returns X, without launching, once the context has

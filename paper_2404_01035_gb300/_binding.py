@@ -32,7 +32,7 @@ EXPORTS = [
     "ms_enable_checkpoints", "ms_grad_param_count", "ms_grad",
     "ms_batch_create", "ms_batch_destroy", "ms_batch_last_error", "ms_batch_set_fields",
     "ms_batch_get_fields", "ms_batch_step", "ms_batch_sync", "ms_batch_cells",
-    "ms_halo_exchange", "ms_halo_mirror", "ms_selftest_timeout",
+    "ms_halo_exchange", "ms_halo_mirror", "ms_selftest_timeout", "ms_peak_fp32",
 ]
 
 
@@ -133,6 +133,7 @@ def lib(build_if_missing: bool = True):
         L.ms_halo_exchange.argtypes = [vp, vp]
         L.ms_halo_mirror.argtypes = [vp, ctypes.c_int]
         L.ms_selftest_timeout.argtypes = [vp, i64]
+        L.ms_peak_fp32.argtypes = [vp, ctypes.c_int, dp]
         L.ms_enable_checkpoints.argtypes = [vp, ctypes.c_int]
         L.ms_grad_param_count.argtypes = [vp]
         L.ms_grad.argtypes = [vp, vp, vp, dp, vp, vp]

@@ -296,3 +296,13 @@ class Simulation:
         self._c(lib().ms_tune(self.h, cache_path.encode() if cache_path else None,
                               int(steps_per_trial), ctypes.byref(best)))
         return best.value
+
+
+def peak_fp32(paired: bool = False, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device in TFLOP/s
+    (ms_peak_fp32: scalar or paired f32x2 fused multiply-adds)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double(0.0)
+    _check(lib().ms_peak_fp32(ctypes.c_void_p(st.cuda_stream), int(bool(paired)), ctypes.byref(out)))
+    return out.value
