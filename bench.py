@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256, help="grid edge (256 = the benchmark workload)")
+    ap.add_argument("--pre-steps", type=int, default=1000,
+                    help="untimed steps from the seeded state before the warm-up (1000 = the middle of "
+                         "the 2000-step workload)")
+    ap.add_argument("--no-alu-roof", action="store_true", help="skip the FP32 peak and flop count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
@@ -211,6 +215,8 @@ def run_ours(args, rank, world, local_rank):
     cur_tile, cur_zchunk = sim.launch()
     tx, ty, split = tiles[cur_tile]
     step_launches = (2 if split else 1) + (2 if args.anti_trapping else 0)   # kernels per time step
+    if args.pre_steps > 0:   # a representative state: interfaces developed, not the sharp seed
+        sim.step(args.pre_steps)
     sim.set_diag_every(DIAG_EVERY)
     sim.step(args.warmup)
     sim.sync()
@@ -275,6 +281,12 @@ def run_ours(args, rank, world, local_rank):
             "bytes_per_cell": bpc, "step_ms": per_step_s * 1e3,
             "kernel_shares": prof["kernel_shares"] if prof else None}
 
+    if not args.no_alu_roof:
+        phi_h, mu_h = sim.get_fields()
+        roof["alu"] = alu_roof(prob, phi_h, mu_h, sim.time()[1], per_step_s, bpc * cells / (peaks["hbm_gbs"] * 1e9),
+                               stream)
+        del phi_h, mu_h
+
     # ---- e2e through the public API with host (pinned) buffers, continuing
     # from the evolved state of the timed run
     e2e = None
@@ -324,11 +336,92 @@ def run_ours(args, rank, world, local_rank):
                 "config": {"workload": WORKLOAD, "cells_per_gpu": cells, "grid": [args.n] * 3,
                            "phases": prob.n_phases, "components": prob.n_components,
                            "diag_every": DIAG_EVERY,
+                           "state": f"evolved {args.pre_steps} steps from the seeded initial state before "
+                                    f"the {args.warmup} warm-up steps",
                            "l2": "inputs larger than L2 (state 671 MB per buffer)",
                            "tuned_ms_per_step": tuned_ms, **launch_info},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches, **extra}
         print(json.dumps(line), flush=True)
+
+
+def pure_stencil_mask(phi, bc):
+    """Cells whose 19-point stencil (the 3x3x3 block without its corners,
+    after the boundary mapping) is one pure phase: phi_l = 1 on all of it."""
+    N = phi.shape[0]
+    out = np.zeros(phi.shape[1:], dtype=bool)
+    offs = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+            if abs(dz) + abs(dy) + abs(dx) < 3]
+
+    def shifted(a, dz, dy, dx):
+        for axis, d, b in ((0, dz, bc[2]), (1, dy, bc[1]), (2, dx, bc[0])):
+            if d == 0:
+                continue
+            if b == 3:
+                a = np.roll(a, -d, axis=axis)
+            else:   # no-flux: the ghost is the adjacent interior cell
+                idx = np.clip(np.arange(a.shape[axis]) + d, 0, a.shape[axis] - 1)
+                a = np.take(a, idx, axis=axis)
+        return a
+
+    for l in range(N):
+        one = phi[l] == 1.0
+        acc = one.copy()
+        for o in offs:
+            if o != (0, 0, 0):
+                acc &= shifted(one, *o)
+        out |= acc
+    return out
+
+
+def alu_roof(prob, phi, mu, t, step_s, hbm_s, stream, samples=256, seed=20240401):
+    """FP32 roof of one step: the measured FMA peak of the device and the
+    step's algorithmic flops.  A cell whose 19-point stencil is one pure phase
+    keeps phi exactly and its mu update reduces to the constant-coefficient
+    Laplacian update (NM (2 dim + 2 + 2 NM) flops, counted by hand); every
+    other cell costs the full update, counted by the oracle's op-counting
+    scalar on a window around each of `samples` random such cells (mean)."""
+    import oracle
+    from paper_2404_01035_gb300.simulation import peak_fp32
+
+    def _axis_index(c, n, bc, r):   # window indices with the boundary mapping
+        idx = np.arange(c - r, c + r + 1)
+        return idx % n if bc == 3 else np.clip(idx, 0, n - 1)
+    peak_s = peak_fp32(False, stream)
+    peak_p = peak_fp32(True, stream)
+    phi = np.asarray(phi, dtype=np.float64)
+    mu = np.asarray(mu, dtype=np.float64)
+    pure = pure_stencil_mask(phi, prob.bc)
+    n_iface = int((~pure).sum())
+    n_bulk = int(pure.sum())
+    NM, dim = prob.n_components - 1, prob.dim
+    f_bulk = NM * (2 * dim + 2 + 2 * NM)
+    rng = np.random.default_rng(seed)
+    cand = np.argwhere(~pure)
+    f_cells = []
+    r = 2
+    for k in rng.choice(len(cand), size=min(samples, len(cand)), replace=False):
+        z, y, x = (int(v) for v in cand[k])
+        ix, iy, iz = (_axis_index(x, prob.nx, prob.bc[0], r), _axis_index(y, prob.ny, prob.bc[1], r),
+                      _axis_index(z, prob.nz, prob.bc[2], r))
+        wp = phi[:, iz][:, :, iy][:, :, :, ix]
+        wm = mu[:, iz][:, :, iy][:, :, :, ix]
+        w = 2 * r + 1
+        wprob = prob.copy(nx=w, ny=w, nz=w, bc=[3, 3, 3], z0=prob.z0 - (z - r) * prob.dx)
+        a, b = oracle.count_flops(wprob, wp, wm, t0=t)
+        f_cells.append(a[r, r, r] + b[r, r, r])
+    f_iface = float(np.mean(f_cells)) if f_cells else 0.0
+    flops = n_iface * f_iface + n_bulk * f_bulk
+    peak = max(peak_s, peak_p)
+    alu_s = flops / (peak * 1e12)
+    roof_s = max(alu_s, hbm_s)
+    return {"fp32_peak_tflops": peak, "fp32_peak_scalar_tflops": peak_s, "fp32_peak_paired_tflops": peak_p,
+            "peak_source": "measured on this device (ms_peak_fp32: FMA chains, 64 warps per SM)",
+            "flops_per_step": flops, "flops_per_interface_cell": f_iface, "flops_per_bulk_cell": f_bulk,
+            "interface_cells": n_iface, "bulk_cells": n_bulk, "sampled_cells": len(f_cells),
+            "alu_ms": alu_s * 1e3, "hbm_ms": hbm_s * 1e3, "roof_ms": roof_s * 1e3,
+            "binding": "alu" if alu_s > hbm_s else "hbm", "frac_of_roof": roof_s / step_s,
+            "achieved_tflops": flops / step_s / 1e12}
 
 
 def _events_ms(stream, fn):
@@ -362,48 +455,78 @@ def bench_batched(stream):
     ms = _events_ms(stream, lambda: b.step(steps))
     b.sync()
     cells = b.cells
+    tile = b.tile_height() if hasattr(b, "tile_height") else None
     b.close()
+    batched = cells * steps / (ms / 1e3) / 1e6
+    # the same 512 simulations stepped one after another through ms_step
+    sims = []
+    for p in probs:
+        sim = Simulation(p, dtype="f32", stream=stream)
+        sim.set_fields(p.phi0, p.mu0)
+        sims.append(sim)
+    for sim in sims:
+        sim.step(2)
+
+    def seq():
+        for sim in sims:
+            sim.step(steps)
+
+    sms = _events_ms(stream, seq)
+    for sim in sims:
+        sim.close()
+    seq_mlups = cells * steps / (sms / 1e3) / 1e6
+    # one plain grid with the same number of cells (a 2-D dendrite, the
+    # largest simulation's parameters)
     big = max(probs, key=lambda q: q.cells)
-    sim = Simulation(big, dtype="f32", stream=stream)
-    sim.set_fields(big.phi0, big.mu0)
-    sim.step(20)
+    ny = int(round(cells / 7488))
+    one = workloads.binary_problem("batched_equiv", 7488, ny=ny, delta=big.delta[0, 1],
+                                   Delta=big.meta.get("Delta", 0.2), R=6.0, dt=big.dt)
+    sim = Simulation(one, dtype="f32", stream=stream)
+    sim.set_fields(one.phi0, one.mu0)
+    sim.step(5)
     pms = _events_ms(stream, lambda: sim.step(steps))
     sim.close()
-    batched = cells * steps / (ms / 1e3) / 1e6
-    plain = big.cells * steps / (pms / 1e3) / 1e6
+    plain = one.cells * steps / (pms / 1e3) / 1e6
     return {"workload": "512 independent 2-D N=2 K=2 FP32 sims, edges 64..512, 500 steps, one "
-                        "graph-captured persistent launch", "cells": int(cells),
+                        "graph-captured persistent launch", "cells": int(cells), "tile_height": tile,
             "mlups": batched, "ms_per_step": ms / steps,
-            "plain_step_mlups": plain, "plain_step": f"single {big.nx}^2 simulation, one launch per step",
+            "sequential_mlups": seq_mlups,
+            "sequential": "the same 512 simulations, each stepped 500 steps by ms_step, one after another",
+            "vs_sequential": batched / seq_mlups,
+            "plain_step_mlups": plain,
+            "plain_step": f"one {one.nx}x{one.ny} simulation ({one.cells} cells, about the batch's total), "
+                          "one launch per step",
             "vs_plain_step": batched / plain,
             "hbm_frac": batched * 1e6 * 24 / (measured_peaks()[0]["hbm_gbs"] * 1e9)}
 
 
-def bench_multigrain(stream):
+def bench_multigrain(stream, pre_steps=1000, steps=1000):
     """3-D 512^3 multigrain (8 phases: 7 rotated grains + liquid, binary, FP32,
-    periodic): the launch the tuner picks, 100 steps from the seeded state."""
+    periodic): the launch the tuner picks, `steps` steps (the workload's 1000)
+    timed after `pre_steps` untimed ones from the seeded state."""
     import workloads
     from paper_2404_01035_gb300 import Simulation
     p = workloads.cfg5()
     sim = Simulation(p, dtype="f32", stream=stream)
     sim.set_fields(p.phi0, p.mu0)
-    sim.tune(None, steps_per_trial=10)
-    sim.set_fields(p.phi0, p.mu0)
+    sim.step(pre_steps)
+    sim.tune(None, steps_per_trial=10)   # trials on the evolved state, which is kept
     sim.step(10)
-    steps = 100
     ms = _events_ms(stream, lambda: sim.step(steps))
     tiles = sim.tiles()
     t, zc = sim.launch()
+    phi, _ = sim.get_fields()
     sim.close()
+    bulk = float(pure_stencil_mask(phi, p.bc).mean())
     mlups = p.cells * steps / (ms / 1e3) / 1e6
     bpc = algorithmic_bytes_per_cell(p, 4)
-    return {"workload": "3-D 512^3 multigrain: 8 phases (7 rotated grains + liquid), binary, FP32, "
-                        "periodic, 100 steps from the seeded state", "cells": int(p.cells),
-            "mlups": mlups, "ms_per_step": ms / steps,
+    return {"workload": f"3-D 512^3 multigrain: 8 phases (7 rotated grains + liquid), binary, FP32, "
+                        f"periodic, {steps} steps timed after {pre_steps} untimed from the seeded state",
+            "cells": int(p.cells), "mlups": mlups, "ms_per_step": ms / steps,
             "launch": {"tx": tiles[t][0], "ty": tiles[t][1], "split": tiles[t][2], "zchunk": zc},
-            "bytes_per_cell": bpc,
+            "bytes_per_cell": bpc, "pure_stencil_fraction": bulk,
             "algorithmic_hbm_frac": mlups * 1e6 * bpc / (measured_peaks()[0]["hbm_gbs"] * 1e9),
-            "note": "99.6% of the cells are bulk liquid, whose update moves mu only, so the "
+            "note": "cells whose stencil is one pure phase keep phi and move mu only, so the "
                     "algorithmic fraction (every field read and written once) can exceed 1"}
 
 

@@ -19,6 +19,11 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
     boundary, the curvature-driven area loss rate of a circular grain: pinned.
   * Elasticity (``tests/test_oracle_elastic.py``): closed-form laminate,
     Voigt shear factor, divergence-free stress: pinned.
+  * The chemical mobility inside interfaces, M = sum_a h_a D^a chi^a with
+    phi^n (``tests/test_oracle_mobility.py``): exact one-step and frozen-phi
+    mode decay, two-solute matrix order: pinned.
+  * count_flops (the op-counting scalar, ``tests/test_oracle_flops.py``):
+    exact counts of hand-countable updates: pinned.
   * The full multiphase (N >= 3) anisotropic dendrite / eutectic / multigrain
     trajectories: parity unpinned beyond the identities above.
 """
@@ -84,6 +89,7 @@ def lib():
                                              ctypes.c_int, dp, dp, dp, dp]
             L.oracle_rate_parts.argtypes = [P, dp, dp, dp, dp, dp, dp]
             L.oracle_diag.argtypes = [P, dp, dp, dp]
+            L.oracle_count_flops.argtypes = [P, dp, dp, dp, dp]
             L.oracle_pair_energy.argtypes = [P, ctypes.c_int, ctypes.c_int, dp]
             L.oracle_pair_energy.restype = ctypes.c_double
             L.oracle_pair_energy_grad.argtypes = [P, ctypes.c_int, ctypes.c_int, dp, dp]
@@ -357,6 +363,20 @@ def rate_parts(prob, phi, mu, t0: float = 0.0, **override):
     if rc:
         raise ValueError("oracle_rate_parts rejected the problem")
     return tuple(outs)
+
+
+def count_flops(prob, phi, mu, t0: float = 0.0, step0: int = 0, **override):
+    """Arithmetic operations of one step per cell, counted by running the
+    oracle's step with an op-counting scalar: (ops_phi, ops_mu), each
+    [nz][ny][nx] (the phi sweep and the mu sweep).  Single-threaded."""
+    op = OracleProblem(prob, t0, step0, **override)
+    phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(op.shape(op.N))
+    mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(op.shape(op.NM))
+    ops_phi = np.zeros(op.shape(1)[1:])
+    ops_mu = np.zeros(op.shape(1)[1:])
+    if lib().oracle_count_flops(op.ptr(), _dp(phi), _dp(mu), _dp(ops_phi), _dp(ops_mu)):
+        raise ValueError("oracle_count_flops rejected the problem")
+    return ops_phi, ops_mu
 
 
 def diag(prob, phi, mu, t0: float = 0.0, **override):

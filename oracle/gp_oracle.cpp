@@ -87,6 +87,28 @@ inline Dual sqrt_s(const Dual& x) {
   return {r, x.d / (2.0 * r)};
 }
 
+// ------------------------------------------------------- op-counting scalar
+// A double that counts the arithmetic done on it: every binary +, -, *, / and
+// every square root with at least one counted operand adds one to g_ops
+// (negation is a sign flip and counts nothing).  Arithmetic on parameters
+// alone (plain doubles) is not counted: it does not depend on the state.
+// Used only by oracle_count_flops, which runs single-threaded.
+uint64_t g_ops = 0;
+struct Cnt {
+  double v = 0.0;
+  Cnt() = default;
+  Cnt(double x) : v(x) {}
+};
+inline Cnt operator+(Cnt a, Cnt b) { ++g_ops; return {a.v + b.v}; }
+inline Cnt operator-(Cnt a, Cnt b) { ++g_ops; return {a.v - b.v}; }
+inline Cnt operator-(Cnt a) { return {-a.v}; }
+inline Cnt operator*(Cnt a, Cnt b) { ++g_ops; return {a.v * b.v}; }
+inline Cnt operator/(Cnt a, Cnt b) { ++g_ops; return {a.v / b.v}; }
+inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline Cnt& operator-=(Cnt& a, Cnt b) { a = a - b; return a; }
+inline double val(const Cnt& x) { return x.v; }
+inline Cnt sqrt_s(const Cnt& x) { ++g_ops; return {std::sqrt(x.v)}; }
+
 }  // namespace
 
 extern "C" {
@@ -649,114 +671,130 @@ void at_face_flux(const Ctx<S>& c, const S* phi, const S* phin, const S* mu, int
 }
 
 // One explicit step phi^n, mu^n (time t) -> phi^{n+1}, mu^{n+1}.
+// phi^{n+1} of cell (x, y, z): Eq. (phi_eqn) explicit Euler and the
+// projection (first sweep of a step).
+template <class S>
+void phi_cell(const Ctx<S>& c, const S* phi, const S* mu, int x, int y, int z, double t, int64_t nstep,
+              S* phi_out) {
+  const oracle_problem& p = *c.p;
+  const int N = p.N, dim = p.dim;
+  const int64_t ic = cell_index(c, x, y, z);
+  S divJ[NMAX], Gc[NMAX], W[NMAX], P[NMAX];
+  rate_parts(c, phi, mu, x, y, z, t, divJ, Gc, W, P);
+  S ph[NMAX], v[NMAX], pn[NMAX];
+  for (int a = 0; a < N; ++a) {
+    ph[a] = phi[a * c.cells + ic];
+    // grain growth (GRAINGROWTH = 1, Sec. 4 "Grain-growth"): the
+    // interfaces move by their curvature only, no dpsi/dphi term
+    const S Pa = p.grain_growth ? S(0.0) : P[a];
+    S r = c.q.mob * (p.eps * (divJ[a] - Gc[a]) - W[a] / p.eps - Pa) / p.eps;
+    v[a] = ph[a] + p.dt * r;
+    // phi noise on the cell's interface phases (0 < phi_a < 1): an
+    // additive dt * amplitude * xi on the rate, before the projection
+    if (p.noise_amp != 0.0 && val(ph[a]) > 0.0 && val(ph[a]) < 1.0) {
+      const int64_t ylab = dim == 3 ? y : y + p.z_origin;
+      const int64_t zlab = dim == 3 ? z + p.z_origin : 0;
+      const uint64_t gcell = static_cast<uint64_t>(x + (int64_t)c.n[0] * (ylab + (int64_t)c.n[1] * zlab));
+      v[a] += p.dt * p.noise_amp * noise_variate(p.noise_seed, (uint64_t)nstep, gcell * N + a);
+    }
+  }
+  if (p.potential == 1)
+    project_simplex(N, v, pn);
+  else
+    project_hyperplane(N, v, pn);
+  for (int a = 0; a < N; ++a) phi_out[a * c.cells + ic] = pn[a];
+}
+
+// mu^{n+1} of cell (x, y, z): Eq. (Mu_explicit_temperature) with the
+// mobility of Eq. (Mass_conservation) (second sweep of a step; phi_out holds
+// phi^{n+1} of every cell, which the anti-trapping current reads).
+template <class S>
+void mu_cell(const Ctx<S>& c, const S* phi, const S* mu, const S* phi_out, int x, int y, int z, double t,
+             S* mu_out) {
+  const oracle_problem& p = *c.p;
+  const int N = p.N, NM = p.NM, dim = p.dim;
+  const int64_t ic = cell_index(c, x, y, z);
+  S ph[NMAX], pn[NMAX];
+  for (int a = 0; a < N; ++a) {
+    ph[a] = phi[a * c.cells + ic];
+    pn[a] = phi_out[a * c.cells + ic];
+  }
+  S h_old[NMAX], h_new[NMAX];
+  interp_h(N, ph, h_old);
+  interp_h(N, pn, h_new);
+  S Mc[KMAX * KMAX], mc[KMAX];
+  cell_mobility(c, phi, ic, Mc);
+  for (int i = 0; i < NM; ++i) mc[i] = mu[i * c.cells + ic];
+  S div[KMAX];
+  for (int i = 0; i < NM; ++i) div[i] = 0.0;
+  for (int d = 0; d < dim; ++d)
+    for (int s = -1; s <= 1; s += 2) {
+      int u[3] = {x, y, z};
+      u[d] += s;
+      const int64_t in = cell_index(c, u[0], u[1], u[2]);
+      S Mn[KMAX * KMAX];
+      cell_mobility(c, phi, in, Mn);
+      for (int i = 0; i < NM; ++i)
+        for (int j = 0; j < NM; ++j) {
+          S Mf = 0.5 * (Mc[i * NM + j] + Mn[i * NM + j]);
+          div[i] += Mf * (mu[j * c.cells + in] - mc[j]) / (p.dx * p.dx);
+        }
+    }
+  if (p.anti_trapping) {   // - div j_at (Eq. Mu_explicit_temperature)
+    for (int d = 0; d < dim; ++d) {
+      S Jp[KMAX], Jm[KMAX];
+      at_face_flux(c, phi, phi_out, mu, x, y, z, d, t, Jp);
+      int q[3] = {x, y, z};
+      q[d] -= 1;
+      at_face_flux(c, phi, phi_out, mu, q[0], q[1], q[2], d, t, Jm);
+      for (int i = 0; i < NM; ++i) div[i] -= (Jp[i] - Jm[i]) / p.dx;
+    }
+  }
+  const double Tn = temperature(p, y, z, t);
+  const double Tn1 = temperature(p, y, z, t + p.dt);
+  S rhs[KMAX];
+  for (int i = 0; i < NM; ++i) rhs[i] = p.dt * div[i];
+  for (int a = 0; a < N; ++a) {
+    S c_now[KMAX], c_next[KMAX];
+    comp_of_mu(p, a, mc, Tn, c_now);
+    comp_of_mu(p, a, mc, Tn1, c_next);
+    for (int i = 0; i < NM; ++i) {
+      rhs[i] -= c_now[i] * (h_new[a] - h_old[a]);
+      rhs[i] -= h_new[a] * (c_next[i] - c_now[i]);
+    }
+  }
+  S chi[KMAX * KMAX], chinv[KMAX * KMAX];
+  for (int i = 0; i < NM * NM; ++i) chi[i] = 0.0;
+  for (int a = 0; a < N; ++a) {
+    double ca[KMAX * KMAX];
+    chi_phase(p, a, ca);
+    for (int i = 0; i < NM * NM; ++i) chi[i] += h_new[a] * ca[i];
+  }
+  invert<S>(NM, chi, chinv);
+  for (int i = 0; i < NM; ++i) {
+    S dmu = 0.0;
+    for (int j = 0; j < NM; ++j) dmu += chinv[i * NM + j] * rhs[j];
+    mu_out[i * c.cells + ic] = mc[i] + dmu;
+  }
+}
+
 template <class S>
 void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, double t, int64_t nstep) {
   const oracle_problem& p = *c.p;
-  const int N = p.N, NM = p.NM, dim = p.dim;
 #pragma omp parallel for collapse(2) schedule(dynamic, 1)
   for (int z = 0; z < c.n[2]; ++z)
     for (int y = 0; y < c.n[1]; ++y)
-      for (int x = 0; x < c.n[0]; ++x) {
-        const int64_t ic = cell_index(c, x, y, z);
-        S divJ[NMAX], Gc[NMAX], W[NMAX], P[NMAX];
-        rate_parts(c, phi, mu, x, y, z, t, divJ, Gc, W, P);
-        S ph[NMAX], v[NMAX], pn[NMAX];
-        for (int a = 0; a < N; ++a) {
-          ph[a] = phi[a * c.cells + ic];
-          // grain growth (GRAINGROWTH = 1, Sec. 4 "Grain-growth"): the
-          // interfaces move by their curvature only, no dpsi/dphi term
-          const S Pa = p.grain_growth ? S(0.0) : P[a];
-          S r = c.q.mob * (p.eps * (divJ[a] - Gc[a]) - W[a] / p.eps - Pa) / p.eps;
-          v[a] = ph[a] + p.dt * r;
-          // phi noise on the cell's interface phases (0 < phi_a < 1): an
-          // additive dt * amplitude * xi on the rate, before the projection
-          if (p.noise_amp != 0.0 && val(ph[a]) > 0.0 && val(ph[a]) < 1.0) {
-            const int64_t ylab = dim == 3 ? y : y + p.z_origin;
-            const int64_t zlab = dim == 3 ? z + p.z_origin : 0;
-            const uint64_t gcell = static_cast<uint64_t>(x + (int64_t)c.n[0] * (ylab + (int64_t)c.n[1] * zlab));
-            v[a] += p.dt * p.noise_amp * noise_variate(p.noise_seed, (uint64_t)nstep, gcell * N + a);
-          }
-        }
-        if (p.potential == 1)
-          project_simplex(N, v, pn);
-        else
-          project_hyperplane(N, v, pn);
-        for (int a = 0; a < N; ++a) phi_out[a * c.cells + ic] = pn[a];
-      }
+      for (int x = 0; x < c.n[0]; ++x) phi_cell(c, phi, mu, x, y, z, t, nstep, phi_out);
   // ---- chemical-potential update (a second sweep: the anti-trapping current
   // needs phi^{n+1} of the neighbours); grain growth keeps mu as it is
   if (p.grain_growth) {
-    for (int64_t k = 0; k < (int64_t)NM * c.cells; ++k) mu_out[k] = mu[k];
+    for (int64_t k = 0; k < (int64_t)p.NM * c.cells; ++k) mu_out[k] = mu[k];
     return;
   }
 #pragma omp parallel for collapse(2) schedule(dynamic, 1)
   for (int z = 0; z < c.n[2]; ++z)
     for (int y = 0; y < c.n[1]; ++y)
-      for (int x = 0; x < c.n[0]; ++x) {
-        const int64_t ic = cell_index(c, x, y, z);
-        S ph[NMAX], pn[NMAX];
-        for (int a = 0; a < N; ++a) {
-          ph[a] = phi[a * c.cells + ic];
-          pn[a] = phi_out[a * c.cells + ic];
-        }
-        S h_old[NMAX], h_new[NMAX];
-        interp_h(N, ph, h_old);
-        interp_h(N, pn, h_new);
-        S Mc[KMAX * KMAX], mc[KMAX];
-        cell_mobility(c, phi, ic, Mc);
-        for (int i = 0; i < NM; ++i) mc[i] = mu[i * c.cells + ic];
-        S div[KMAX];
-        for (int i = 0; i < NM; ++i) div[i] = 0.0;
-        for (int d = 0; d < dim; ++d)
-          for (int s = -1; s <= 1; s += 2) {
-            int u[3] = {x, y, z};
-            u[d] += s;
-            const int64_t in = cell_index(c, u[0], u[1], u[2]);
-            S Mn[KMAX * KMAX];
-            cell_mobility(c, phi, in, Mn);
-            for (int i = 0; i < NM; ++i)
-              for (int j = 0; j < NM; ++j) {
-                S Mf = 0.5 * (Mc[i * NM + j] + Mn[i * NM + j]);
-                div[i] += Mf * (mu[j * c.cells + in] - mc[j]) / (p.dx * p.dx);
-              }
-          }
-        if (p.anti_trapping) {   // - div j_at (Eq. Mu_explicit_temperature)
-          for (int d = 0; d < dim; ++d) {
-            S Jp[KMAX], Jm[KMAX];
-            at_face_flux(c, phi, phi_out, mu, x, y, z, d, t, Jp);
-            int q[3] = {x, y, z};
-            q[d] -= 1;
-            at_face_flux(c, phi, phi_out, mu, q[0], q[1], q[2], d, t, Jm);
-            for (int i = 0; i < NM; ++i) div[i] -= (Jp[i] - Jm[i]) / p.dx;
-          }
-        }
-        const double Tn = temperature(p, y, z, t);
-        const double Tn1 = temperature(p, y, z, t + p.dt);
-        S rhs[KMAX];
-        for (int i = 0; i < NM; ++i) rhs[i] = p.dt * div[i];
-        for (int a = 0; a < N; ++a) {
-          S c_now[KMAX], c_next[KMAX];
-          comp_of_mu(p, a, mc, Tn, c_now);
-          comp_of_mu(p, a, mc, Tn1, c_next);
-          for (int i = 0; i < NM; ++i) {
-            rhs[i] -= c_now[i] * (h_new[a] - h_old[a]);
-            rhs[i] -= h_new[a] * (c_next[i] - c_now[i]);
-          }
-        }
-        S chi[KMAX * KMAX], chinv[KMAX * KMAX];
-        for (int i = 0; i < NM * NM; ++i) chi[i] = 0.0;
-        for (int a = 0; a < N; ++a) {
-          double ca[KMAX * KMAX];
-          chi_phase(p, a, ca);
-          for (int i = 0; i < NM * NM; ++i) chi[i] += h_new[a] * ca[i];
-        }
-        invert<S>(NM, chi, chinv);
-        for (int i = 0; i < NM; ++i) {
-          S dmu = 0.0;
-          for (int j = 0; j < NM; ++j) dmu += chinv[i * NM + j] * rhs[j];
-          mu_out[i * c.cells + ic] = mc[i] + dmu;
-        }
-      }
+      for (int x = 0; x < c.n[0]; ++x) mu_cell(c, phi, mu, phi_out, x, y, z, t, mu_out);
 }
 
 template <class S>
@@ -857,6 +895,37 @@ int oracle_run_tangent(const oracle_problem* p, const double* phi0, const double
     mu[i] = ma[i].v;
     dmu[i] = ma[i].d;
   }
+  return 0;
+}
+
+// Arithmetic operations of one step, per cell, counted with the op-counting
+// scalar (single-threaded): ops_phi[cells] for the phi sweep (Eq. phi_eqn,
+// the projection), ops_mu[cells] for the mu sweep (Eq.
+// Mu_explicit_temperature); the state is advanced as by oracle_run with one
+// step, the new state is discarded.
+int oracle_count_flops(const oracle_problem* p, const double* phi, const double* mu, double* ops_phi,
+                       double* ops_mu) {
+  if (check(p)) return 1;
+  Ctx<Cnt> c;
+  init_ctx(c, p);
+  const int64_t cells = c.cells;
+  std::vector<Cnt> pa(p->N * cells), pb(p->N * cells), ma(p->NM * cells), mb(p->NM * cells);
+  for (int64_t i = 0; i < p->N * cells; ++i) pa[i] = Cnt(phi[i]);
+  for (int64_t i = 0; i < p->NM * cells; ++i) ma[i] = Cnt(mu[i]);
+  for (int z = 0; z < c.n[2]; ++z)
+    for (int y = 0; y < c.n[1]; ++y)
+      for (int x = 0; x < c.n[0]; ++x) {
+        const uint64_t before = g_ops;
+        phi_cell(c, pa.data(), ma.data(), x, y, z, p->t0, p->step0, pb.data());
+        ops_phi[cell_index(c, x, y, z)] = static_cast<double>(g_ops - before);
+      }
+  for (int z = 0; z < c.n[2]; ++z)
+    for (int y = 0; y < c.n[1]; ++y)
+      for (int x = 0; x < c.n[0]; ++x) {
+        const uint64_t before = g_ops;
+        if (!p->grain_growth) mu_cell(c, pa.data(), ma.data(), pb.data(), x, y, z, p->t0, mb.data());
+        ops_mu[cell_index(c, x, y, z)] = static_cast<double>(g_ops - before);
+      }
   return 0;
 }
 
