@@ -39,6 +39,16 @@ struct IsDual<Dual<R, W>> {
   static constexpr bool value = true;
 };
 
+// Optional parts of the cell update, as a compile-time mask: a kernel
+// instantiated without one of them never takes that path (its model does not
+// use it), which keeps the code and the registers of the common case small.
+constexpr int kFeatRot = 1;      // rotated anisotropic pairs (Rotation_matrix)
+constexpr int kFeatG3 = 2;       // the triple-junction term gamma_abc of the obstacle
+constexpr int kFeatNoise = 4;    // phi noise
+constexpr int kFeatElastic = 8;  // elastic potentials added to psi
+constexpr int kFeatGG = 16;      // grain growth (no chemical driving force, mu held)
+constexpr int kFeatAll = 31;
+
 // g = dA/dq of the unrotated anisotropic pair, evaluated in real arithmetic
 // through the factorisation g_i = 2 gamma a_c q_i (a_c + 16 delta (q_i^2 /
 // |q|^2 - r)), r = sum_j q_j^4 / |q|^4, a_c = (1 - 3 delta) + 4 delta r (the
@@ -178,7 +188,7 @@ __device__ __forceinline__ Off<DIM> add(Off<DIM> a, Off<DIM> b) {
 
 // Normal component (axis D) of J_a on one face of the cell: side 0 = the
 // face shared with the -D neighbour, side 1 = with the +D neighbour.
-template <int DIM, int D, int NP, int NM, class Real, class S, class Acc>
+template <int DIM, int D, int NP, int NM, class Real, class S, class Acc, int FEAT = kFeatAll>
 __device__ __forceinline__ void face_flux(const Acc& A, const StepArgs<Real, NP, NM>& g,
                                           const DiffPrm<S, NP*(NP - 1) / 2>& dp, uint32_t mask,
                                           int side, bool need_tan, S* Jn) {
@@ -215,7 +225,7 @@ __device__ __forceinline__ void face_flux(const Acc& A, const StepArgs<Real, NP,
     for (int b = a + 1; b < NP; ++b, ++p) {
       if (!(((mask >> a) & (mask >> b)) & 1u)) continue;
       const S gD = face_pair_flux<DIM, D>(pf[a], pf[b], gr[a], gr[b], g.gam2[p], dp.delta[p], g.aniso[p] != 0,
-                                          g.rotated[p] != 0, g.rot[p]);
+                                          (FEAT & kFeatRot) && g.rotated[p] != 0, g.rot[p]);
       Jn[a] -= pf[b] * gD;
       Jn[b] += pf[a] * gD;
     }
@@ -225,7 +235,7 @@ __device__ __forceinline__ void face_flux(const Acc& A, const StepArgs<Real, NP,
 // Both faces along axis D at once in paired FP32 arithmetic (low half: the
 // face with the -D neighbour, high half: with the +D neighbour); the same
 // discretisation as face_flux, J[a] = (J_a on the low face, on the high face).
-template <int DIM, int D, int NP, int NM, class Acc>
+template <int DIM, int D, int NP, int NM, class Acc, int FEAT = kFeatAll>
 __device__ __forceinline__ void face_flux_pair(const Acc& A, const StepArgs<float, NP, NM>& g, uint32_t mask,
                                                bool need_tan, F2* J) {
   const Off<DIM> m = unit<DIM>(D, -1), p = unit<DIM>(D, 1);
@@ -261,7 +271,7 @@ __device__ __forceinline__ void face_flux_pair(const Acc& A, const StepArgs<floa
     for (int b = a + 1; b < NP; ++b, ++pi) {
       if (!(((mask >> a) & (mask >> b)) & 1u)) continue;
       const F2 gD = face_pair_flux2<DIM, D>(pf[a], npf[b], gr[a], gr[b], g.gam2[pi], g.delta[pi], g.aniso[pi] != 0,
-                                            g.rotated[pi] != 0, g.rot[pi]);
+                                            (FEAT & kFeatRot) && g.rotated[pi] != 0, g.rot[pi]);
       J[a] = fma2(npf[b], gD, J[a]);
       J[b] = fma2(pf[a], gD, J[b]);
     }
@@ -311,10 +321,11 @@ __device__ __forceinline__ S grand_potential(const StepArgs<Real, NP, NM>& g, in
 }
 
 // The full cell update.  kz = cell index along the last axis (for T).
-template <int DIM, int NP, int NM, class Real, class S, class Acc>
+template <int DIM, int NP, int NM, class Real, class S, class Acc, int FEAT = kFeatAll>
 __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, NM>& g,
                                         const DiffPrm<S, NP*(NP - 1) / 2>& dp, int kz, unsigned long long gcell,
                                         S* pn, S* mn) {
+  const bool gg = (FEAT & kFeatGG) && g.gg;
   S ph[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) ph[a] = A.phi(a, 0, 0, 0);
@@ -356,13 +367,13 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
       {
         if constexpr (std::is_same<S, float>::value) {
           F2 J[NP];
-          face_flux_pair<DIM, 0>(A, g, mask, need_tan, J);
+          face_flux_pair<DIM, 0, NP, NM, Acc, FEAT>(A, g, mask, need_tan, J);
 #pragma unroll
           for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
         } else {
           S Jm[NP], Jp[NP];
-          face_flux<DIM, 0>(A, g, dp, mask, 0, need_tan, Jm);
-          face_flux<DIM, 0>(A, g, dp, mask, 1, need_tan, Jp);
+          face_flux<DIM, 0, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 0, need_tan, Jm);
+          face_flux<DIM, 0, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 1, need_tan, Jp);
 #pragma unroll
           for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
         }
@@ -370,13 +381,13 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
       {
         if constexpr (std::is_same<S, float>::value) {
           F2 J[NP];
-          face_flux_pair<DIM, 1>(A, g, mask, need_tan, J);
+          face_flux_pair<DIM, 1, NP, NM, Acc, FEAT>(A, g, mask, need_tan, J);
 #pragma unroll
           for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
         } else {
           S Jm[NP], Jp[NP];
-          face_flux<DIM, 1>(A, g, dp, mask, 0, need_tan, Jm);
-          face_flux<DIM, 1>(A, g, dp, mask, 1, need_tan, Jp);
+          face_flux<DIM, 1, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 0, need_tan, Jm);
+          face_flux<DIM, 1, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 1, need_tan, Jp);
 #pragma unroll
           for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
         }
@@ -384,13 +395,13 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
       if constexpr (DIM == 3) {
         if constexpr (std::is_same<S, float>::value) {
           F2 J[NP];
-          face_flux_pair<DIM, 2>(A, g, mask, need_tan, J);
+          face_flux_pair<DIM, 2, NP, NM, Acc, FEAT>(A, g, mask, need_tan, J);
 #pragma unroll
           for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
         } else {
           S Jm[NP], Jp[NP];
-          face_flux<DIM, 2>(A, g, dp, mask, 0, need_tan, Jm);
-          face_flux<DIM, 2>(A, g, dp, mask, 1, need_tan, Jp);
+          face_flux<DIM, 2, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 0, need_tan, Jm);
+          face_flux<DIM, 2, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 1, need_tan, Jp);
 #pragma unroll
           for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
         }
@@ -417,7 +428,8 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
           S q[DIM], gq[DIM];
 #pragma unroll
           for (int d = 0; d < DIM; ++d) q[d] = ph[a] * gc[b][d] - ph[b] * gc[a][d];
-          pair_grad_fwd<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, g.rotated[p] != 0, g.rot[p], gq);
+          pair_grad_fwd<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, (FEAT & kFeatRot) && g.rotated[p] != 0,
+                             g.rot[p], gq);
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
             Gc[a] += gq[d] * gc[b][d];
@@ -439,7 +451,7 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
         else
           W[a] += g.cw[a][b] * (ph[a] * (ph[b] * ph[b]));
       }
-      if (g.has_g3) {
+      if ((FEAT & kFeatG3) && g.has_g3) {
 #pragma unroll
         for (int b = 0; b < NP; ++b)
 #pragma unroll
@@ -450,8 +462,8 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
     // S4: driving force sum_b psi^b dh_b/dphi_a
     S psi[NP];
 #pragma unroll
-    for (int b = 0; b < NP; ++b) psi[b] = g.gg ? S(Real(0)) : grand_potential<NP, NM, Real>(g, b, mc, s);
-    if (g.elw) {   // elasticity: -sigma : eps*^b joins each phase potential
+    for (int b = 0; b < NP; ++b) psi[b] = gg ? S(Real(0)) : grand_potential<NP, NM, Real>(g, b, mc, s);
+    if ((FEAT & kFeatElastic) && g.elw) {   // elasticity: -sigma : eps*^b joins each phase potential
       const unsigned long long cell = gcell - (unsigned long long)g.zorg * (DIM == 3 ? (unsigned long long)g.nx * g.ny : g.nx);
       const unsigned long long cells = (unsigned long long)g.nx * g.ny * (DIM == 3 ? g.nz : 1);
 #pragma unroll
@@ -483,12 +495,12 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
       S r = dp.mob * ((g.eps * (divJ[a] - Gc[a]) - W[a] * g.inv_eps - P) * g.inv_eps);
       v[a] = ph[a] + g.dt * r;
       // phi noise on the interface phases of the cell (0 < phi_a < 1)
-      if (g.noise_amp != Real(0) && val(ph[a]) > Real(0) && val(ph[a]) < Real(1))
+      if ((FEAT & kFeatNoise) && g.noise_amp != Real(0) && val(ph[a]) > Real(0) && val(ph[a]) < Real(1))
         v[a] = v[a] + g.dt * g.noise_amp * noise_variate<Real>(g.noise_seed, g.step, gcell * NP + a);
     }
     project<NP>(g.potential, v, pn);
   }
-  if (g.gg) {   // grain growth: mu held
+  if (gg) {   // grain growth: mu held
 #pragma unroll
     for (int i = 0; i < NM; ++i) mn[i] = mc[i];
     return;
@@ -592,7 +604,7 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
 // Real arithmetic only (the adjoint's dual numbers use gp_cell).
 
 // Normal face fluxes of the present phases on one face (compact index k).
-template <int DIM, int D, int NP, int NM, int KP, class Real, class Acc>
+template <int DIM, int D, int NP, int NM, int KP, class Real, class Acc, int FEAT = kFeatAll>
 __device__ __forceinline__ void face_flux_sparse(const Acc& A, const StepArgs<Real, NP, NM>& g, const int* map,
                                                  int kn, int side, bool need_tan, Real* Jk) {
   const Off<DIM> L = unit<DIM>(D, side ? 0 : -1);
@@ -627,7 +639,7 @@ __device__ __forceinline__ void face_flux_sparse(const Acc& A, const StepArgs<Re
       if (l >= kn) continue;
       const int p = pair_index<NP>(map[k], map[l]);
       const Real gD = face_pair_flux<DIM, D>(pf[k], pf[l], gr[k], gr[l], g.gam2[p], g.delta[p], g.aniso[p] != 0,
-                                             g.rotated[p] != 0, g.rot[p]);
+                                             (FEAT & kFeatRot) && g.rotated[p] != 0, g.rot[p]);
       Jk[k] -= pf[l] * gD;
       Jk[l] += pf[k] * gD;
     }
@@ -666,9 +678,10 @@ __device__ __forceinline__ void mobility_sparse(const Acc& A, const StepArgs<Rea
   }
 }
 
-template <int DIM, int NP, int NM, int KP, class Real, class Acc>
+template <int DIM, int NP, int NM, int KP, class Real, class Acc, int FEAT = kFeatAll>
 __device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real, NP, NM>& g, int kz,
                                                unsigned long long gcell, Real* pn, Real* mn) {
+  const bool gg = (FEAT & kFeatGG) && g.gg;
   static_assert(!IsDual<Real>::value, "real arithmetic only");
   const uint32_t mask = A.mask();
   const int kn = __popc(mask);
@@ -709,22 +722,22 @@ __device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real
       for (int k = 0; k < KP; ++k) divJ[k] = Real(0);
       {
         Real Jm[KP], Jp[KP];
-        face_flux_sparse<DIM, 0, NP, NM, KP>(A, g, map, kn, 0, need_tan, Jm);
-        face_flux_sparse<DIM, 0, NP, NM, KP>(A, g, map, kn, 1, need_tan, Jp);
+        face_flux_sparse<DIM, 0, NP, NM, KP, Real, Acc, FEAT>(A, g, map, kn, 0, need_tan, Jm);
+        face_flux_sparse<DIM, 0, NP, NM, KP, Real, Acc, FEAT>(A, g, map, kn, 1, need_tan, Jp);
 #pragma unroll
         for (int k = 0; k < KP; ++k) divJ[k] += (Jp[k] - Jm[k]) * g.inv_dx;
       }
       {
         Real Jm[KP], Jp[KP];
-        face_flux_sparse<DIM, 1, NP, NM, KP>(A, g, map, kn, 0, need_tan, Jm);
-        face_flux_sparse<DIM, 1, NP, NM, KP>(A, g, map, kn, 1, need_tan, Jp);
+        face_flux_sparse<DIM, 1, NP, NM, KP, Real, Acc, FEAT>(A, g, map, kn, 0, need_tan, Jm);
+        face_flux_sparse<DIM, 1, NP, NM, KP, Real, Acc, FEAT>(A, g, map, kn, 1, need_tan, Jp);
 #pragma unroll
         for (int k = 0; k < KP; ++k) divJ[k] += (Jp[k] - Jm[k]) * g.inv_dx;
       }
       if constexpr (DIM == 3) {
         Real Jm[KP], Jp[KP];
-        face_flux_sparse<DIM, 2, NP, NM, KP>(A, g, map, kn, 0, need_tan, Jm);
-        face_flux_sparse<DIM, 2, NP, NM, KP>(A, g, map, kn, 1, need_tan, Jp);
+        face_flux_sparse<DIM, 2, NP, NM, KP, Real, Acc, FEAT>(A, g, map, kn, 0, need_tan, Jm);
+        face_flux_sparse<DIM, 2, NP, NM, KP, Real, Acc, FEAT>(A, g, map, kn, 1, need_tan, Jp);
 #pragma unroll
         for (int k = 0; k < KP; ++k) divJ[k] += (Jp[k] - Jm[k]) * g.inv_dx;
       }
@@ -749,7 +762,8 @@ __device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real
           Real q[DIM], gq[DIM];
 #pragma unroll
           for (int d = 0; d < DIM; ++d) q[d] = phk[k] * gc[l][d] - phk[l] * gc[k][d];
-          pair_grad_fwd<DIM>(q, g.gam2[p], g.delta[p], g.aniso[p] != 0, g.rotated[p] != 0, g.rot[p], gq);
+          pair_grad_fwd<DIM>(q, g.gam2[p], g.delta[p], g.aniso[p] != 0, (FEAT & kFeatRot) && g.rotated[p] != 0,
+                             g.rot[p], gq);
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
             Gc[k] += gq[d] * gc[l][d];
@@ -774,7 +788,7 @@ __device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real
         else
           W[a] += g.cw[a][b] * (ph[a] * (ph[b] * ph[b]));
       }
-      if (g.has_g3) {
+      if ((FEAT & kFeatG3) && g.has_g3) {
 #pragma unroll
         for (int k = 0; k < KP; ++k)
 #pragma unroll
@@ -785,8 +799,8 @@ __device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real
     // S4: driving force
     Real psi[NP];
 #pragma unroll
-    for (int b = 0; b < NP; ++b) psi[b] = g.gg ? Real(0) : grand_potential<NP, NM, Real>(g, b, mc, s);
-    if (g.elw) {   // elasticity: -sigma : eps*^b joins each phase potential
+    for (int b = 0; b < NP; ++b) psi[b] = gg ? Real(0) : grand_potential<NP, NM, Real>(g, b, mc, s);
+    if ((FEAT & kFeatElastic) && g.elw) {   // elasticity: -sigma : eps*^b joins each phase potential
       const unsigned long long cell = gcell - (unsigned long long)g.zorg * (DIM == 3 ? (unsigned long long)g.nx * g.ny : g.nx);
       const unsigned long long cells = (unsigned long long)g.nx * g.ny * (DIM == 3 ? g.nz : 1);
 #pragma unroll
@@ -822,12 +836,12 @@ __device__ __forceinline__ void gp_cell_sparse(const Acc& A, const StepArgs<Real
       // S5: rate of Eq. (phi_eqn) / (tau eps), explicit Euler
       Real r = g.mob * ((g.eps * d - W[a] * g.inv_eps - P) * g.inv_eps);
       v[a] = ph[a] + g.dt * r;
-      if (g.noise_amp != Real(0) && ph[a] > Real(0) && ph[a] < Real(1))
+      if ((FEAT & kFeatNoise) && g.noise_amp != Real(0) && ph[a] > Real(0) && ph[a] < Real(1))
         v[a] = v[a] + g.dt * g.noise_amp * noise_variate<Real>(g.noise_seed, g.step, gcell * NP + a);
     }
     project<NP>(g.potential, v, pn);
   }
-  if (g.gg) {   // grain growth: mu held
+  if (gg) {   // grain growth: mu held
 #pragma unroll
     for (int i = 0; i < NM; ++i) mn[i] = mc[i];
     return;

@@ -138,6 +138,15 @@ void set_launch_args(StepArgs<Real, NP, NM>& g, const HostModel& m, double t, vo
   g.elw = reinterpret_cast<const Real*>(lg.elw);
 }
 
+// A model that uses none of the optional paths of the cell update (rotated
+// pairs, gamma_abc, phi noise, elasticity, grain growth).
+inline bool plain_model(const HostModel& m) {
+  for (int a = 0; a < m.N; ++a)
+    for (int b = 0; b < m.N; ++b)
+      if (a != b && m.rotated[a][b]) return false;
+  return !m.has_g3 && m.noise_amp == 0.0 && !m.el && !m.gg;
+}
+
 // Fused step: one kernel updates every cell.
 template <int DIM, int NP, int NM, class Real, int TX, int TY>
 cudaError_t launch_step(const CUtensorMap* tm, const CUtensorMap*, void* blob, const HostModel& m, double t,
@@ -169,32 +178,41 @@ cudaError_t launch_split(const CUtensorMap* tm, const CUtensorMap* tmi, void* bl
   if (!lg.iface || !lg.iface2 || !tmi || lg.iface_blocks < 1) return cudaErrorInvalidValue;
   auto& g = *reinterpret_cast<StepArgs<float, NP, NM>*>(blob);
   set_launch_args(g, m, t, out, codes_in, codes_out, lg);
+  // the interface kernels in two builds: every optional path of the cell
+  // update, and none of them (when the model uses none: the common case)
+  const bool plain = plain_model(m);
   auto ks = k_gp_stream<NP, NM, TY>;
-  auto ki = k_gp_iface<3, NP, NM, float, 0>;
-  auto kf = k_gp_iface<3, NP, NM, float, two ? 1 : 0>;   // only launched when two
+  auto ki = plain ? k_gp_iface<3, NP, NM, float, 0, 0> : k_gp_iface<3, NP, NM, float, 0, kFeatAll>;
+  auto kf = plain ? k_gp_iface<3, NP, NM, float, two ? 1 : 0, 0>   // only launched when two
+                  : k_gp_iface<3, NP, NM, float, two ? 1 : 0, kFeatAll>;
   static bool configured = false;   // attributes are per function, set once
-  static int iface_per_sm = 0, full_per_sm = 0;   // resident CTAs per SM
+  static int iface_per_sm[2] = {0, 0}, full_per_sm[2] = {0, 0};   // resident CTAs per SM (all, plain)
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, Ss::SMEM_BYTES);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(ki, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&iface_per_sm, ki, Si::THREADS, Si::SMEM_BYTES);
-    if (two && e == cudaSuccess)
-      e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
-    if (two && e == cudaSuccess)
-      e = cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (two && e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&full_per_sm, kf, Si::THREADS, Si::SMEM_BYTES);
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+      auto vi = v ? k_gp_iface<3, NP, NM, float, 0, 0> : k_gp_iface<3, NP, NM, float, 0, kFeatAll>;
+      auto vf = v ? k_gp_iface<3, NP, NM, float, two ? 1 : 0, 0> : k_gp_iface<3, NP, NM, float, two ? 1 : 0, kFeatAll>;
+      e = cudaFuncSetAttribute(vi, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(vi, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&iface_per_sm[v], vi, Si::THREADS, Si::SMEM_BYTES);
+      if (two && e == cudaSuccess)
+        e = cudaFuncSetAttribute(vf, cudaFuncAttributeMaxDynamicSharedMemorySize, Si::SMEM_BYTES);
+      if (two && e == cudaSuccess)
+        e = cudaFuncSetAttribute(vf, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+      if (two && e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&full_per_sm[v], vf, Si::THREADS, Si::SMEM_BYTES);
+      iface_per_sm[v] = iface_per_sm[v] < 1 ? 1 : iface_per_sm[v];
+      full_per_sm[v] = full_per_sm[v] < 1 ? 1 : full_per_sm[v];
+    }
     if (e != cudaSuccess) return e;
-    iface_per_sm = iface_per_sm < 1 ? 1 : iface_per_sm;
-    full_per_sm = full_per_sm < 1 ? 1 : full_per_sm;
     configured = true;
   }
+  const int v = plain ? 1 : 0;
   ks<<<dim3(lg.tiles, lg.zchunks), Ss::NTHREADS, Ss::SMEM_BYTES, st>>>(*tm, g);
-  ki<<<lg.iface_blocks * iface_per_sm, Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
-  if constexpr (two) kf<<<lg.iface_blocks * full_per_sm, Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
+  ki<<<lg.iface_blocks * iface_per_sm[v], Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
+  if constexpr (two) kf<<<lg.iface_blocks * full_per_sm[v], Si::THREADS, Si::SMEM_BYTES, st>>>(*tmi, g);
   return cudaGetLastError();
 }
 

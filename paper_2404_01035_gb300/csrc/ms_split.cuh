@@ -306,11 +306,16 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
           if (z == g.nz - 1) oz1 = (g.bc[2] == 3 ? -g.nz : 1) * plane;
         }
         if ((oy0 | oy1 | oz0 | oz1) != 0) {
+          // (the loops are unrolled so that every array index is a constant
+          // and nothing lives in local memory)
           const long long oy[3] = {0, oy0, oy1}, oz[3] = {0, oz0, oz1};
+#pragma unroll
           for (int iz = 0; iz < 3; ++iz)
+#pragma unroll
             for (int iy = 0; iy < 3; ++iy) {
               if ((iy | iz) == 0 || (iy && !oy[iy]) || (iz && !oz[iz])) continue;
               float* q = p + oy[iy] + oz[iz];
+#pragma unroll
               for (int a = 0; a < NP + NM; ++a) {
                 if (a < NP && !write_phi) continue;
                 float c4[4];
@@ -514,7 +519,7 @@ __device__ __forceinline__ void box_bulk_mu(const Real* c, const Real* cf, Real*
 // list, which MODE 1 updates with the full one (each kernel's registers then
 // fit its own path).  The last CTA to finish clears its list (ticket in
 // list[1]), so the launches can be replayed from a CUDA graph.
-template <int DIM, int NP, int NM, class Real, int MODE>
+template <int DIM, int NP, int NM, class Real, int MODE, int FEAT = kFeatAll>
 __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<NP, NM, Real>::MIN_BLOCKS)
     k_gp_iface(const __grid_constant__ CUtensorMap tmi, const __grid_constant__ StepArgs<Real, NP, NM> g) {
   static_assert(DIM == 3, "the interface list is built by the 3-D streaming kernel");
@@ -554,26 +559,28 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
     tma_load_4d(reinterpret_cast<unsigned char*>(buf0) + b * Sh::BOX_STRIDE, &tmi, &bar[b],
                 32 * sg + g.xoff - Sh::H, y, z + g.zoff - 1, 0);
   };
-  bool pending[2] = {false, false};
-  uint32_t phase[2] = {0u, 0u};
+  // bit b of `pending` / `phase`: buffer b has a copy in flight / the
+  // parity its barrier completes next (bits, not arrays: a runtime index
+  // would put them in local memory)
+  uint32_t pending = 0u, phase = 0u;
   bool aborted = false;
   unsigned int i = blockIdx.x * Sh::WARPS + wid;
   if (i < count && lane == 0) issue(i, 0);
-  pending[0] = i < count;
+  if (i < count) pending = 1u;
   int b = 0;
   while (i < count) {
     const unsigned int nxt = i + stride;
     if (nxt < count) {
       if (lane == 0) issue(nxt, b ^ 1);
-      pending[b ^ 1] = true;
+      pending |= 1u << (b ^ 1);
     }
-    const bool ok = mbar_wait_bounded(&bar[b], phase[b]);
+    const bool ok = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
     if (!__all_sync(0xffffffffu, ok)) {
       aborted = true;
       break;
     }
-    pending[b] = false;
-    phase[b] ^= 1u;
+    pending &= ~(1u << b);
+    phase ^= 1u << b;
     const unsigned int r = list[2 + i];
     const int sg = (int)(r % (unsigned int)g.segs);
     const unsigned int zy = r / (unsigned int)g.segs;
@@ -636,9 +643,11 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
       acc.wmask = wmask;
       Real pn[NP], mn[NM];
       if constexpr (kSparse)   // many phases, at most kSparseK of them around this row
-        gp_cell_sparse<DIM, NP, NM, kSparseK, Real>(acc, g, z + g.zorg, lab_cell<DIM>(g, x, y, z), pn, mn);
+        gp_cell_sparse<DIM, NP, NM, kSparseK, Real, BoxAcc<DIM, NP, NM, Real>, FEAT>(acc, g, z + g.zorg,
+                                                                                   lab_cell<DIM>(g, x, y, z), pn, mn);
       else
-        gp_cell<DIM, NP, NM, Real, Real>(acc, g, dp, z + g.zorg, lab_cell<DIM>(g, x, y, z), pn, mn);
+        gp_cell<DIM, NP, NM, Real, Real, BoxAcc<DIM, NP, NM, Real>, FEAT>(acc, g, dp, z + g.zorg,
+                                                                         lab_cell<DIM>(g, x, y, z), pn, mn);
       uint32_t nzm = 0, one = 0;
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
@@ -666,7 +675,7 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
     if (lane == 0) {
       atomicOr(g.status, kStatusTimeout);
       for (int k = 0; k < 2; ++k)
-        if (pending[k]) mbar_wait_bounded(&bar[k], phase[k]);
+        if ((pending >> k) & 1u) mbar_wait_bounded(&bar[k], (phase >> k) & 1u);
     }
   }
   // every CTA read the count before taking its ticket

@@ -186,6 +186,19 @@ __device__ __forceinline__ void bulk_cell(const Acc& A, const StepArgs<Real, NP,
 
 // Store the NF outputs of cell (x, y, z), plus ghost images on the boundary;
 // with write_phi false only mu (the output buffer already holds phi^{n+1}).
+// Coordinate of variant v of cell c along an axis of n cells with boundary
+// code bc: v = 0 the cell itself, v = 1 its ghost image when c is the first
+// cell (c + n periodic, -1 mirrored), v = 2 when c is the last (-1 periodic,
+// n mirrored); kNoImage when that variant does not exist (or `cut`: the
+// axis' ghosts are filled by a halo exchange).
+constexpr int kNoImage = -0x40000000;
+__device__ __forceinline__ int image_coord(int v, int c, int n, int bc, bool cut) {
+  if (v == 0) return c;
+  if (cut) return kNoImage;
+  if (v == 1) return c == 0 ? (bc == 3 ? n : -1) : kNoImage;
+  return c == n - 1 ? (bc == 3 ? -1 : n) : kNoImage;
+}
+
 template <int DIM, int NP, int NM, class Real>
 __device__ __forceinline__ void store_cell(const StepArgs<Real, NP, NM>& g, int x, int y, int z,
                                            const Real* pn, const Real* mn, bool write_phi = true) {
@@ -200,26 +213,21 @@ __device__ __forceinline__ void store_cell(const StepArgs<Real, NP, NM>& g, int 
   const bool edge = x == 0 || x == g.nx - 1 || y == 0 || y == g.ny - 1 ||
                     (DIM == 3 && (z == 0 || z == g.nz - 1));
   if (!edge) return;
-  int xs[3], ys[3], zs[3];
-  int nxs = 1, nys = 1, nzs = 1;
-  xs[0] = x;
-  ys[0] = y;
-  zs[0] = z;
-  if (x == 0) xs[nxs++] = g.bc[0] == 3 ? g.nx : -1;
-  if (x == g.nx - 1) xs[nxs++] = g.bc[0] == 3 ? -1 : g.nx;
-  if (y == 0) ys[nys++] = g.bc[1] == 3 ? g.ny : -1;
-  if (y == g.ny - 1) ys[nys++] = g.bc[1] == 3 ? -1 : g.ny;
-  if constexpr (DIM == 3) {
-    // internal cuts (halo faces) get their ghost planes from the exchange
-    if (z == 0 && g.bc[2] != kBcHalo) zs[nzs++] = g.bc[2] == 3 ? g.nz : -1;
-    if (z == g.nz - 1 && g.bc[2] != kBcHalo) zs[nzs++] = g.bc[2] == 3 ? -1 : g.nz;
-  }
-  for (int iz = 0; iz < nzs; ++iz)
-    for (int iy = 0; iy < nys; ++iy)
-      for (int ix = 0; ix < nxs; ++ix) {
-        if (ix == 0 && iy == 0 && iz == 0) continue;
-        Real* p = g.out + (long long)(zs[iz] + g.zoff) * plane + (long long)(ys[iy] + 1) * g.pitch +
-                  xs[ix] + g.xoff;
+  // every combination of the cell and its ghost images along each axis
+  // (variant 0 = the cell, 1 = its image when it is the first cell, 2 = when
+  // it is the last; scalars, so that nothing lives in local memory)
+  const bool zcut = DIM != 3 || g.bc[2] == kBcHalo;   // halo faces: the exchange fills them
+  for (int iz = 0; iz < (DIM == 3 ? 3 : 1); ++iz) {
+    const int zi = image_coord(iz, z, g.nz, g.bc[2], zcut);
+    if (zi == kNoImage) continue;
+    for (int iy = 0; iy < 3; ++iy) {
+      const int yi = image_coord(iy, y, g.ny, g.bc[1], false);
+      if (yi == kNoImage) continue;
+      for (int ix = 0; ix < 3; ++ix) {
+        if ((ix | iy | iz) == 0) continue;
+        const int xi = image_coord(ix, x, g.nx, g.bc[0], false);
+        if (xi == kNoImage) continue;
+        Real* p = g.out + (long long)(zi + g.zoff) * plane + (long long)(yi + 1) * g.pitch + xi + g.xoff;
         if (write_phi) {
 #pragma unroll
           for (int a = 0; a < NP; ++a) p[a * g.fstride] = pn[a];
@@ -227,6 +235,8 @@ __device__ __forceinline__ void store_cell(const StepArgs<Real, NP, NM>& g, int 
 #pragma unroll
         for (int i = 0; i < NM; ++i) p[(NP + i) * g.fstride] = mn[i];
       }
+    }
+  }
 }
 
 // Minimum CTAs per SM the register allocation must allow: two for the
