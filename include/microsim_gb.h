@@ -370,6 +370,30 @@ int64_t ms_batch_cells(const ms_batch* b);   /* total cells over all simulations
 ms_status ms_halo_exchange(ms_ctx* lower, ms_ctx* upper);
 ms_status ms_halo_mirror(ms_ctx* ctx, int face);
 
+/* The same exchange between processes (slabs held by different ranks: the
+ * domain decomposition with buffer layers of the paper's Sec. "CPU (MPI)
+ * implementation" and the GPU subdomains of Sec. "CUDA implementation"):
+ * a boundary plane travels through a flat device buffer that the caller
+ * moves between ranks (e.g. with torch.distributed or NCCL).
+ * ms_halo_plane_bytes: bytes of one packed plane, 0 for a 2-D context:
+ *   one padded z-plane of every field ([field][nyp][pitch] elements in the
+ *   context dtype, x/y ghost cells included) followed by the plane's
+ *   segment codes ([ny][segs] bytes).
+ * ms_halo_pack(ctx, face, dst): face 0 = the bottom interior plane (z = 0),
+ *   face 1 = the top interior plane (z = nz - 1) -> dst (device, at least
+ *   ms_halo_plane_bytes).
+ * ms_halo_unpack(ctx, face, src): a packed plane from the neighbour ->
+ *   the ghost plane on that face (0 = below z = 0, 1 = above z = nz - 1).
+ * After every step (and once after ms_set_fields), each rank packs both
+ * faces, sends face 1 up and face 0 down, and unpacks what it receives into
+ * the matching ghost planes (outer no-flux faces: ms_halo_mirror).  Both are
+ * asynchronous on the context's stream (synchronise it before handing dst to
+ * another stream or rank).  MS_ERR_ARG for a context without MS_BC_HALO z
+ * faces. */
+size_t ms_halo_plane_bytes(const ms_ctx* ctx);
+ms_status ms_halo_pack(ms_ctx* ctx, int face, void* dst);
+ms_status ms_halo_unpack(ms_ctx* ctx, int face, const void* src);
+
 /* Allocation-free diagnostics (the paper has no counterpart; this is a
  * library service).  For callers that cannot allocate device memory while
  * they run -- a host application that gives this library a fixed memory

@@ -33,6 +33,7 @@ EXPORTS = [
     "ms_batch_create", "ms_batch_destroy", "ms_batch_last_error", "ms_batch_set_fields",
     "ms_batch_get_fields", "ms_batch_step", "ms_batch_sync", "ms_batch_cells",
     "ms_halo_exchange", "ms_halo_mirror", "ms_selftest_timeout", "ms_peak_fp32",
+    "ms_halo_plane_bytes", "ms_halo_pack", "ms_halo_unpack",
 ]
 
 
@@ -132,6 +133,10 @@ def lib(build_if_missing: bool = True):
         L.ms_batch_cells.restype = ctypes.c_int64
         L.ms_halo_exchange.argtypes = [vp, vp]
         L.ms_halo_mirror.argtypes = [vp, ctypes.c_int]
+        L.ms_halo_plane_bytes.argtypes = [vp]
+        L.ms_halo_plane_bytes.restype = ctypes.c_size_t
+        L.ms_halo_pack.argtypes = [vp, ctypes.c_int, vp]
+        L.ms_halo_unpack.argtypes = [vp, ctypes.c_int, vp]
         L.ms_selftest_timeout.argtypes = [vp, i64]
         L.ms_peak_fp32.argtypes = [vp, ctypes.c_int, dp]
         L.ms_enable_checkpoints.argtypes = [vp, ctypes.c_int]
@@ -141,7 +146,7 @@ def lib(build_if_missing: bool = True):
                                       ctypes.POINTER(Params), ctypes.c_double, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("ms_destroy", "ms_last_error", "ms_checkpoint_bytes", "ms_batch_destroy",
-                            "ms_batch_last_error", "ms_batch_cells"):
+                            "ms_batch_last_error", "ms_batch_cells", "ms_halo_plane_bytes"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return _lib

@@ -114,3 +114,53 @@ def test_slab_partition_covers_the_domain():
         assert max(n for _, n in parts) - min(n for _, n in parts) <= 1
     with pytest.raises(ValueError):
         slab_partition(4, 5)
+
+
+def _packed_worker(rank, world, port, periodic, q):
+    sys.path.insert(0, ROOT)
+    import datetime
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2404_01035_gb300.decomp import exchange_packed, slab_partition
+    try:
+        dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                                world_size=world, timeout=datetime.timedelta(seconds=30))
+        F, nz, ny, nx = 2, 9, 3, 4
+        g = torch.arange(F * nz * ny * nx, dtype=torch.float64).reshape(F, nz, ny, nx)
+        z0, n = slab_partition(nz, world)[rank]
+        slab = torch.full((F, n + 2, ny, nx), float("nan"), dtype=torch.float64)
+        slab[:, 1:-1] = g[:, z0:z0 + n]
+        # a flat packed plane as the library lays it out: every field's plane
+        pack = lambda face: slab[:, 1 if face == 0 else n].reshape(-1).clone()
+
+        def unpack(face, t):
+            slab[:, 0 if face == 0 else n + 1] = t.reshape(F, ny, nx)
+
+        def mirror(face):
+            slab[:, 0 if face == 0 else n + 1] = slab[:, 1 if face == 0 else n]
+
+        for step in range(3):   # repeated exchanges reuse the tags safely
+            exchange_packed(pack, unpack, mirror, rank, world, periodic, step=step)
+        below = (z0 - 1) % nz if periodic else max(z0 - 1, 0)
+        above = (z0 + n) % nz if periodic else min(z0 + n, nz - 1)
+        ok = torch.equal(slab[:, 0], g[:, below]) and torch.equal(slab[:, -1], g[:, above])
+        dist.destroy_process_group()
+        q.put((rank, bool(ok), ""))
+    except Exception as e:  # pragma: no cover - reported to the parent
+        q.put((rank, False, repr(e)))
+
+
+@pytest.mark.parametrize("world,periodic", [(1, True), (1, False), (2, True), (2, False), (3, True), (3, False)])
+def test_packed_plane_exchange_between_ranks(world, periodic):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _port()
+    procs = [ctx.Process(target=_packed_worker, args=(r, world, port, periodic, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+    assert all(ok for _, ok, _ in res), res
