@@ -47,7 +47,8 @@ constexpr int kFeatG3 = 2;       // the triple-junction term gamma_abc of the ob
 constexpr int kFeatNoise = 4;    // phi noise
 constexpr int kFeatElastic = 8;  // elastic potentials added to psi
 constexpr int kFeatGG = 16;      // grain growth (no chemical driving force, mu held)
-constexpr int kFeatAll = 31;
+constexpr int kFeatSolidD = 32;  // phases other than the liquid diffuse (else M = h_l D^l chi^l)
+constexpr int kFeatAll = 63;
 
 // g = dA/dq of the unrotated anisotropic pair, evaluated in real arithmetic
 // through the factorisation g_i = 2 gamma a_c q_i (a_c + 16 delta (q_i^2 /
@@ -237,7 +238,7 @@ __device__ __forceinline__ void face_flux(const Acc& A, const StepArgs<Real, NP,
 // discretisation as face_flux, J[a] = (J_a on the low face, on the high face).
 template <int DIM, int D, int NP, int NM, class Acc, int FEAT = kFeatAll>
 __device__ __forceinline__ void face_flux_pair(const Acc& A, const StepArgs<float, NP, NM>& g, uint32_t mask,
-                                               bool need_tan, F2* J) {
+                                               bool need_tan, const float (*gcr)[DIM], F2* J) {
   const Off<DIM> m = unit<DIM>(D, -1), p = unit<DIM>(D, 1);
   F2 pf[NP], npf[NP], gr[NP][DIM];
 #pragma unroll
@@ -253,12 +254,15 @@ __device__ __forceinline__ void face_flux_pair(const Acc& A, const StepArgs<floa
     for (int t = 0; t < DIM; ++t) {
       if (t == D) continue;
       if (need_tan) {
+        // the 4-point average (1/4)[(L+t) + (R+t) - (L-t) - (R-t)] written as
+        // the sum of the two cells' central differences along t: the
+        // neighbours' from the edge values, the cell's own (gcr) shared with
+        // the centre term
         const Off<DIM> up = unit<DIM>(t, 1), dn = unit<DIM>(t, -1);
         const Off<DIM> mu_ = add(m, up), md = add(m, dn), pu = add(p, up), pd = add(p, dn);
-        const float cu = A.phi(a, up.x, up.y, up.z), cd = A.phi(a, dn.x, dn.y, dn.z);
-        const F2 Lu = f2(A.phi(a, mu_.x, mu_.y, mu_.z), cu), Ru = f2(cu, A.phi(a, pu.x, pu.y, pu.z));
-        const F2 Ld = f2(A.phi(a, md.x, md.y, md.z), cd), Rd = f2(cd, A.phi(a, pd.x, pd.y, pd.z));
-        gr[a][t] = ((Lu + Ru) - (Ld + Rd)) * f2s(g.quarter_inv_dx);
+        const F2 nb = f2(A.phi(a, mu_.x, mu_.y, mu_.z), A.phi(a, pu.x, pu.y, pu.z)) -
+                      f2(A.phi(a, md.x, md.y, md.z), A.phi(a, pd.x, pd.y, pd.z));
+        gr[a][t] = (nb + f2s(gcr[a][t])) * f2s(g.quarter_inv_dx);
       } else {
         gr[a][t] = f2s(0.0f);
       }
@@ -301,6 +305,43 @@ __device__ __forceinline__ void mobility_pair(const Acc& A, const StepArgs<float
 #pragma unroll
     for (int k = 0; k < NM * NM; ++k) M[k] = a == 0 ? h * f2s(g.DX[0][k]) : fma2(h, f2s(g.DX[a][k]), M[k]);
   }
+}
+
+// As mobility_pair when only the liquid (phase NP-1) diffuses: M = h_l D^l
+// chi^l, h_l = phi_l^2 (3 - 2 phi_l) + 2 phi_l sum_{b<c<l} phi_b phi_c.
+template <int DIM, int NP, int NM, class Acc>
+__device__ __forceinline__ void mobility_pair_liquid(const Acc& A, const StepArgs<float, NP, NM>& g, int d, F2* M) {
+  const Off<DIM> m = unit<DIM>(d, -1), p = unit<DIM>(d, 1);
+  constexpr int L = NP - 1;
+  F2 f[NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) f[a] = f2(A.phi(a, m.x, m.y, m.z), A.phi(a, p.x, p.y, p.z));
+  F2 rest = f2s(0.0f), run = f[0];
+#pragma unroll
+  for (int b = 1; b < L; ++b) {
+    rest = fma2(f[b], run, rest);
+    run = run + f[b];
+  }
+  const F2 p2 = f[L] * f[L];
+  const F2 h = f2s(3.0f) * p2 - f2s(2.0f) * p2 * f[L] + f2s(2.0f) * f[L] * rest;
+#pragma unroll
+  for (int k = 0; k < NM * NM; ++k) M[k] = h * f2s(g.DX[L][k]);
+}
+
+// The cell's own mobility when only the liquid diffuses (scalar).
+template <int NP, int NM, class Real>
+__device__ __forceinline__ void mobility_liquid(const Real* ph, const StepArgs<Real, NP, NM>& g, Real* M) {
+  constexpr int L = NP - 1;
+  Real rest = Real(0), run = ph[0];
+#pragma unroll
+  for (int b = 1; b < L; ++b) {
+    rest += ph[b] * run;
+    run += ph[b];
+  }
+  const Real p2 = ph[L] * ph[L];
+  const Real h = Real(3) * p2 - Real(2) * p2 * ph[L] + Real(2) * ph[L] * rest;
+#pragma unroll
+  for (int k = 0; k < NM * NM; ++k) M[k] = h * g.DX[L][k];
 }
 
 // psi^b(mu, T) = C^b(T) - 1/2 (mu - B^b)^T chi^b (mu - B^b), s = T - T_ref.
@@ -363,11 +404,25 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
           for (int b = a + 1; b < NP; ++b, ++p)
             if ((((mask >> a) & (mask >> b)) & 1u) && g.aniso[p]) need_tan = true;
       }
+      // central differences (unscaled) of the present phases: the centre
+      // term and, in FP32, the tangential face gradients
+      S gcr[NP][DIM];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        if (!((mask >> a) & 1u)) {
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) gcr[a][d] = S(Real(0));
+          continue;
+        }
+        gcr[a][0] = A.phi(a, 1, 0, 0) - A.phi(a, -1, 0, 0);
+        gcr[a][1] = A.phi(a, 0, 1, 0) - A.phi(a, 0, -1, 0);
+        if constexpr (DIM == 3) gcr[a][2] = A.phi(a, 0, 0, 1) - A.phi(a, 0, 0, -1);
+      }
       // S1-S3: divergence of the face fluxes
       {
         if constexpr (std::is_same<S, float>::value) {
           F2 J[NP];
-          face_flux_pair<DIM, 0, NP, NM, Acc, FEAT>(A, g, mask, need_tan, J);
+          face_flux_pair<DIM, 0, NP, NM, Acc, FEAT>(A, g, mask, need_tan, gcr, J);
 #pragma unroll
           for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
         } else {
@@ -381,7 +436,7 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
       {
         if constexpr (std::is_same<S, float>::value) {
           F2 J[NP];
-          face_flux_pair<DIM, 1, NP, NM, Acc, FEAT>(A, g, mask, need_tan, J);
+          face_flux_pair<DIM, 1, NP, NM, Acc, FEAT>(A, g, mask, need_tan, gcr, J);
 #pragma unroll
           for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
         } else {
@@ -395,7 +450,7 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
       if constexpr (DIM == 3) {
         if constexpr (std::is_same<S, float>::value) {
           F2 J[NP];
-          face_flux_pair<DIM, 2, NP, NM, Acc, FEAT>(A, g, mask, need_tan, J);
+          face_flux_pair<DIM, 2, NP, NM, Acc, FEAT>(A, g, mask, need_tan, gcr, J);
 #pragma unroll
           for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
         } else {
@@ -415,9 +470,8 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
           for (int d = 0; d < DIM; ++d) gc[a][d] = S(Real(0));
           continue;
         }
-        gc[a][0] = (A.phi(a, 1, 0, 0) - A.phi(a, -1, 0, 0)) * g.half_inv_dx;
-        gc[a][1] = (A.phi(a, 0, 1, 0) - A.phi(a, 0, -1, 0)) * g.half_inv_dx;
-        if constexpr (DIM == 3) gc[a][2] = (A.phi(a, 0, 0, 1) - A.phi(a, 0, 0, -1)) * g.half_inv_dx;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) gc[a][d] = gcr[a][d] * g.half_inv_dx;
       }
       int p = 0;
 #pragma unroll
@@ -510,7 +564,14 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
   S h_new[NP];
   interp_h<NP>(pn, h_new);
   S Mc[NM * NM];
-  A.mobility(0, 0, 0, Mc);
+  if constexpr (!(FEAT & kFeatSolidD) && std::is_same<S, Real>::value) {
+    S phc[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) phc[a] = A.phi(a, 0, 0, 0);
+    mobility_liquid<NP, NM, Real>(phc, g, Mc);
+  } else {
+    A.mobility(0, 0, 0, Mc);
+  }
   S div[NM];
 #pragma unroll
   for (int i = 0; i < NM; ++i) div[i] = S(Real(0));
@@ -523,7 +584,10 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
     for (int d = 0; d < DIM; ++d) {
       const Off<DIM> m = unit<DIM>(d, -1), p = unit<DIM>(d, 1);
       F2 Mn[NM * NM];
-      mobility_pair<DIM, NP, NM>(A, g, d, Mn);
+      if constexpr (FEAT & kFeatSolidD)
+        mobility_pair<DIM, NP, NM>(A, g, d, Mn);
+      else
+        mobility_pair_liquid<DIM, NP, NM>(A, g, d, Mn);
 #pragma unroll
       for (int i = 0; i < NM; ++i) {
 #pragma unroll

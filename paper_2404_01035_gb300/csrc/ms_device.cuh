@@ -49,9 +49,11 @@ struct StepArgs {
   uint8_t* codes_out;
   int segs;
   // Interface work list of the split 3-D step: [0] = number of listed warp
-  // rows, [1] = completion ticket of the interface kernel, [2..] = row
-  // indices (z ny + y) segs + segment of the rows that are not bulk.
+  // rows, [1] = completion ticket of the interface kernel, [2..] = the rows
+  // that are not bulk, each (z << (seg_bits + y_bits)) | (y << seg_bits) |
+  // segment (bit fields: decoding needs no division).
   unsigned int* iface;
+  int seg_bits, y_bits;   // widths of the segment and y fields of a list entry
   unsigned int iface_cap;
   unsigned int* iface2;   // second list, same layout (rows left for the full update)
   // anti-trapping work list: [0] count, [1] ticket, [2..] row segments

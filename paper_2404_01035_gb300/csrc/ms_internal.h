@@ -102,6 +102,17 @@ struct StepKernel {
 
 // Number of 32-cell segments per row.
 inline int segments(const HostModel& m) { return (m.nx + 31) / 32; }
+// Bits that hold the values 0 .. n - 1.
+inline int bits_for(int n) {
+  int b = 0;
+  while ((1ll << b) < n) ++b;
+  return b;
+}
+// An interface-list entry (z, y, segment) packs into 31 bits (every shift
+// of its fields stays below 32).
+inline bool list_entry_fits(const HostModel& m) {
+  return bits_for(segments(m)) + bits_for(m.ny) + bits_for(m.nz) <= 31;
+}
 // Bytes of one segment-code array (3-D arrays carry a ghost plane per side).
 inline size_t code_bytes(const HostModel& m) { return (size_t)segments(m) * m.ny * m.nzp; }
 

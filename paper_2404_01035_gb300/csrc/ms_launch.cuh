@@ -113,6 +113,8 @@ void fill_args(void* blob, const HostModel& m, int zchunk, int* status) {
   }
   g.tzg = (Real)(m.G * m.dx);
   g.segs = segments(m);
+  g.seg_bits = bits_for(g.segs);
+  g.y_bits = bits_for(m.ny);
 }
 
 // T^n - T_ref at the first cell centre along the last axis, minus G dx / 2.
@@ -139,11 +141,15 @@ void set_launch_args(StepArgs<Real, NP, NM>& g, const HostModel& m, double t, vo
 }
 
 // A model that uses none of the optional paths of the cell update (rotated
-// pairs, gamma_abc, phi noise, elasticity, grain growth).
+// pairs, gamma_abc, phi noise, elasticity, grain growth) and in which only
+// the liquid diffuses (the one-sided model: D = 0 in every other phase).
 inline bool plain_model(const HostModel& m) {
   for (int a = 0; a < m.N; ++a)
     for (int b = 0; b < m.N; ++b)
       if (a != b && m.rotated[a][b]) return false;
+  for (int a = 0; a + 1 < m.N; ++a)
+    for (int k = 0; k < m.NM * m.NM; ++k)
+      if (m.DX[a][k] != 0.0) return false;
   return !m.has_g3 && m.noise_amp == 0.0 && !m.el && !m.gg;
 }
 

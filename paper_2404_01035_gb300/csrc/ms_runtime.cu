@@ -488,7 +488,8 @@ ms_status apply_launch(ms_ctx* c, const StepKernel* k, int zchunk) {
     // work list of the split step: count, ticket and one entry per warp row
     // (two lists: the second takes the rows left for a second launch)
     const size_t cap = (size_t)segments(c->m) * c->m.ny * c->m.nz;
-    if (cap > 0xFFFFFFF0ull) return fail(c, MS_ERR_UNSUPPORTED, "grid too large for the split step");
+    if (cap > 0xFFFFFFF0ull || !list_entry_fits(c->m))
+      return fail(c, MS_ERR_UNSUPPORTED, "grid too large for the split step");
     c->iface = static_cast<unsigned int*>(dev_alloc(c->hook, 2 * (cap + 2) * sizeof(unsigned int)));
     if (!c->iface) return fail(c, MS_ERR_OOM, "interface work-list allocation failed");
     c->lg.iface = c->iface;

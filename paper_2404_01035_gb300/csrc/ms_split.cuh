@@ -358,7 +358,9 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
       base = __shfl_sync(0xffffffffu, base, first);
       if ((need >> lane) & 1u) {
         const unsigned int i = base + __popc(need & ((1u << lane) - 1u));
-        if (i < g.iface_cap) g.iface[2 + i] = (unsigned int)(((long long)z * g.ny + y) * g.segs + seg);
+        if (i < g.iface_cap)
+          g.iface[2 + i] = ((unsigned int)z << (g.seg_bits + g.y_bits)) | ((unsigned int)y << g.seg_bits) |
+                           (unsigned int)seg;
       }
     }
     __syncwarp();
@@ -548,12 +550,14 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
 #pragma unroll
   for (int p = 0; p < StepArgs<Real, NP, NM>::P; ++p) dp.delta[p] = g.delta[p];
 
-  // row r = (z ny + y) segs + segment  ->  box origin (x, y - 1, z - 1 in padded coordinates)
+  // list entry r -> (segment, y, z) (bit fields)
+  const unsigned int seg_mask = (1u << g.seg_bits) - 1u, y_mask = (1u << g.y_bits) - 1u;
+  const int zshift = g.seg_bits + g.y_bits;
+  // row -> box origin (x, y - 1, z - 1 in padded coordinates)
   auto issue = [&](unsigned int i, int b) {
     const unsigned int r = list[2 + i];
-    const int sg = (int)(r % (unsigned int)g.segs);
-    const unsigned int zy = r / (unsigned int)g.segs;
-    const int y = (int)(zy % (unsigned int)g.ny), z = (int)(zy / (unsigned int)g.ny);
+    const int sg = (int)(r & seg_mask);
+    const int y = (int)((r >> g.seg_bits) & y_mask), z = (int)(r >> zshift);
     fence_proxy_async_shared();
     mbar_expect_tx(&bar[b], Sh::BOX_BYTES);
     tma_load_4d(reinterpret_cast<unsigned char*>(buf0) + b * Sh::BOX_STRIDE, &tmi, &bar[b],
@@ -582,9 +586,8 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
     pending &= ~(1u << b);
     phase ^= 1u << b;
     const unsigned int r = list[2 + i];
-    const int sg = (int)(r % (unsigned int)g.segs);
-    const unsigned int zy = r / (unsigned int)g.segs;
-    const int y = (int)(zy % (unsigned int)g.ny), z = (int)(zy / (unsigned int)g.ny);
+    const int sg = (int)(r & seg_mask);
+    const int y = (int)((r >> g.seg_bits) & y_mask), z = (int)(r >> zshift);
     const int x = 32 * sg + lane;
     const bool active = x < g.nx;
     const Real* box = reinterpret_cast<const Real*>(reinterpret_cast<unsigned char*>(buf0) + b * Sh::BOX_STRIDE);
