@@ -429,17 +429,36 @@ template <int NP, int NM, class Real>
 __device__ __forceinline__ uint32_t box_phase_mask(const Real* box, int lane) {
   using Sh = IfaceShape<NP, NM, Real>;
   uint32_t m = 0;
+  if constexpr (sizeof(Real) == 4) {
+    // phase fractions are never negative: the OR of the bit patterns is
+    // non-zero exactly when some value is (a -0.0 could only mark a phase
+    // present, which costs work, never correctness)
+    const unsigned int* bx = reinterpret_cast<const unsigned int*>(box);
+    const int xh = lane == 0 ? Sh::H - 1 : Sh::H + 32;
 #pragma unroll
-  for (int a = 0; a < NP; ++a) {
-    bool any = false;
+    for (int a = 0; a < NP; ++a) {
+      unsigned int any = 0u;
 #pragma unroll
-    for (int r = 0; r < 9; ++r) any = any || box[a * (9 * Sh::BX) + r * Sh::BX + Sh::H + lane] != Real(0);
-    if (lane == 0 || lane == 31) {
-      const int xh = lane == 0 ? Sh::H - 1 : Sh::H + 32;
+      for (int r = 0; r < 9; ++r) any |= bx[a * (9 * Sh::BX) + r * Sh::BX + Sh::H + lane];
+      if (lane == 0 || lane == 31) {
 #pragma unroll
-      for (int r = 0; r < 9; ++r) any = any || box[a * (9 * Sh::BX) + r * Sh::BX + xh] != Real(0);
+        for (int r = 0; r < 9; ++r) any |= bx[a * (9 * Sh::BX) + r * Sh::BX + xh];
+      }
+      m |= (any != 0u ? 1u : 0u) << a;
     }
-    m |= (any ? 1u : 0u) << a;
+  } else {
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      bool any = false;
+#pragma unroll
+      for (int r = 0; r < 9; ++r) any = any || box[a * (9 * Sh::BX) + r * Sh::BX + Sh::H + lane] != Real(0);
+      if (lane == 0 || lane == 31) {
+        const int xh = lane == 0 ? Sh::H - 1 : Sh::H + 32;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) any = any || box[a * (9 * Sh::BX) + r * Sh::BX + xh] != Real(0);
+      }
+      m |= (any ? 1u : 0u) << a;
+    }
   }
   return __reduce_or_sync(0xffffffffu, m);
 }
