@@ -447,6 +447,7 @@ def bench_batched(stream):
         b.set_fields(i, p.phi0, p.mu0)
     b.step(20)            # warm-up launch (graph capture for n = 20)
     b.sync()
+    tuned = b.tune(steps_per_trial=50)   # tile height on the evolved states (restored)
     steps = 500
     b.step(steps)         # capture for n = 500, then time a replay
     b.sync()
@@ -455,7 +456,7 @@ def bench_batched(stream):
     ms = _events_ms(stream, lambda: b.step(steps))
     b.sync()
     cells = b.cells
-    tile = b.tile_height() if hasattr(b, "tile_height") else None
+    tile = b.tile_height()
     b.close()
     batched = cells * steps / (ms / 1e3) / 1e6
     # the same 512 simulations stepped one after another through ms_step
@@ -489,6 +490,7 @@ def bench_batched(stream):
     plain = one.cells * steps / (pms / 1e3) / 1e6
     return {"workload": "512 independent 2-D N=2 K=2 FP32 sims, edges 64..512, 500 steps, one "
                         "graph-captured persistent launch", "cells": int(cells), "tile_height": tile,
+            "tuned_ms_per_step": tuned,
             "mlups": batched, "ms_per_step": ms / steps,
             "sequential_mlups": seq_mlups,
             "sequential": "the same 512 simulations, each stepped 500 steps by ms_step, one after another",

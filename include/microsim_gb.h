@@ -352,6 +352,18 @@ ms_status ms_batch_get_fields(ms_batch* b, int sim, void* phi, void* mu, int on_
 ms_status ms_batch_step(ms_batch* b, int64_t n);
 ms_status ms_batch_sync(ms_batch* b);
 int64_t ms_batch_cells(const ms_batch* b);   /* total cells over all simulations */
+/* Tile height of the batched work list: the persistent kernel is compiled for
+ * 32 x 4, 32 x 8 (the default) and 32 x 16 tiles; a change rebuilds the work
+ * list and the tensor maps (synchronous) and recaptures the graph at the next
+ * ms_batch_step.  MS_ERR_ARG for another height. */
+ms_status ms_batch_set_tile(ms_batch* b, int tile_height);
+int ms_batch_tile(const ms_batch* b);        /* current tile height, 0 for NULL */
+/* Autotuner of the batched form: times steps_per_trial steps (after one
+ * warm-up launch of the same length) with every compiled tile height on the
+ * current states, restores the states (a device copy of all of them is held
+ * during the call) and keeps the fastest height; best_ms_per_step (may be
+ * NULL) receives its time per step.  Synchronous. */
+ms_status ms_batch_tune(ms_batch* b, int steps_per_trial, double* best_ms_per_step);
 
 /* ---- Slab decomposition along z (3-D) ---------------------------------------
  * A domain split into contexts that each own a contiguous range of z-planes

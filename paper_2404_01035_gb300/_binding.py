@@ -34,6 +34,7 @@ EXPORTS = [
     "ms_batch_get_fields", "ms_batch_step", "ms_batch_sync", "ms_batch_cells",
     "ms_halo_exchange", "ms_halo_mirror", "ms_selftest_timeout", "ms_peak_fp32",
     "ms_halo_plane_bytes", "ms_halo_pack", "ms_halo_unpack",
+    "ms_batch_set_tile", "ms_batch_tile", "ms_batch_tune",
 ]
 
 
@@ -131,6 +132,9 @@ def lib(build_if_missing: bool = True):
         L.ms_batch_sync.argtypes = [vp]
         L.ms_batch_cells.argtypes = [vp]
         L.ms_batch_cells.restype = ctypes.c_int64
+        L.ms_batch_set_tile.argtypes = [vp, ctypes.c_int]
+        L.ms_batch_tile.argtypes = [vp]
+        L.ms_batch_tune.argtypes = [vp, ctypes.c_int, dp]
         L.ms_halo_exchange.argtypes = [vp, vp]
         L.ms_halo_mirror.argtypes = [vp, ctypes.c_int]
         L.ms_halo_plane_bytes.argtypes = [vp]

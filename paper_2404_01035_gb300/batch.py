@@ -75,3 +75,17 @@ class Batch:
     @property
     def cells(self) -> int:
         return lib().ms_batch_cells(self.h)
+
+    def set_tile(self, tile_height: int):
+        """Tile height of the work list (4, 8 or 16 rows of 32 cells)."""
+        self._c(lib().ms_batch_set_tile(self.h, int(tile_height)))
+
+    def tile_height(self) -> int:
+        return lib().ms_batch_tile(self.h)
+
+    def tune(self, steps_per_trial: int = 50) -> float:
+        """Time every compiled tile height on the current states (restored
+        afterwards) and keep the fastest; returns its ms per step."""
+        out = ctypes.c_double(0.0)
+        self._c(lib().ms_batch_tune(self.h, int(steps_per_trial), ctypes.byref(out)))
+        return out.value

@@ -57,7 +57,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int
 }
 
 template <int NP, int NM, class Real, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY + 32, 3)
+__global__ void __launch_bounds__(TX* TY + 32, TY <= 8 ? 3 : 1)
     k_batch(const BatchSim<Real, NP, NM>* __restrict__ sims, const CUtensorMap* __restrict__ maps,
             const BatchItem* __restrict__ items, int nitems, int nsteps, int parity0,
             unsigned int* barrier, int* status) {
@@ -248,6 +248,7 @@ struct ms_batch {
   cudaStream_t stream = nullptr;
   AllocHook hook;
   int grid = 0, smem = 0;
+  int ty = 0;                           // tile height of the work list (kBTYs)
   cudaGraphExec_t graph = nullptr;
   int64_t graph_n = -1;
   std::string err;
@@ -255,8 +256,23 @@ struct ms_batch {
 
 namespace {
 
+// Tiles are 32 cells (one warp row) wide; their height is chosen at run time
+// among the compiled ones (ms_batch_set_tile / ms_batch_tune).
 constexpr int kBTX = 32, kBTY = 8;
-using BF = BatchShape<2, 1, float, kBTX, kBTY>;
+constexpr int kBTYs[] = {4, 8, 16};
+constexpr int kNBTY = 3;
+
+template <int TY>
+void* batch_kernel() {
+  return reinterpret_cast<void*>(k_batch<2, 1, float, kBTX, TY>);
+}
+void* batch_kernel_for(int ty) {
+  return ty == 4 ? batch_kernel<4>() : ty == 16 ? batch_kernel<16>() : batch_kernel<8>();
+}
+int batch_smem_for(int ty) {
+  return ty == 4 ? BatchShape<2, 1, float, kBTX, 4>::SMEM
+                 : ty == 16 ? BatchShape<2, 1, float, kBTX, 16>::SMEM : BatchShape<2, 1, float, kBTX, 8>::SMEM;
+}
 
 ms_status bfail(ms_batch* b, ms_status s, const std::string& m) {
   if (b) b->err = m;
@@ -276,12 +292,11 @@ void batch_free(ms_batch* b) {
 }
 
 cudaError_t launch_batch(ms_batch* b, int64_t n) {
-  auto kern = k_batch<2, 1, float, kBTX, kBTY>;
   cudaError_t e = cudaMemsetAsync(b->barrier, 0, sizeof(unsigned int), b->stream);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->grid);
-  cfg.blockDim = dim3(kBTX * kBTY + 32);
+  cfg.blockDim = dim3(kBTX * b->ty + 32);
   cfg.dynamicSmemBytes = b->smem;
   cfg.stream = b->stream;
   cudaLaunchAttribute attr[1];
@@ -289,8 +304,63 @@ cudaError_t launch_batch(ms_batch* b, int64_t n) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, (const BatchSim<float, 2, 1>*)b->sims, (const CUtensorMap*)b->maps,
-                            (const BatchItem*)b->items, b->nitems, (int)n, b->parity, b->barrier, b->status);
+  const BatchSim<float, 2, 1>* sims = (const BatchSim<float, 2, 1>*)b->sims;
+  const CUtensorMap* maps = (const CUtensorMap*)b->maps;
+  const BatchItem* items = (const BatchItem*)b->items;
+  if (b->ty == 4)
+    return cudaLaunchKernelEx(&cfg, k_batch<2, 1, float, kBTX, 4>, sims, maps, items, b->nitems, (int)n, b->parity,
+                              b->barrier, b->status);
+  if (b->ty == 16)
+    return cudaLaunchKernelEx(&cfg, k_batch<2, 1, float, kBTX, 16>, sims, maps, items, b->nitems, (int)n, b->parity,
+                              b->barrier, b->status);
+  return cudaLaunchKernelEx(&cfg, k_batch<2, 1, float, kBTX, 8>, sims, maps, items, b->nitems, (int)n, b->parity,
+                            b->barrier, b->status);
+}
+
+// Work list, tensor maps and persistent grid for tile height ty (one of
+// kBTYs): items are (simulation, 32 x ty tile) pairs in simulation order,
+// the maps' boxes are the tiles with their halo.  Drops the captured graph.
+cudaError_t batch_set_tiles(ms_batch* b, int ty) {
+  std::vector<CUtensorMap> hm(2 * b->nsims);
+  std::vector<BatchItem> items;
+  for (int i = 0; i < b->nsims; ++i) {
+    const HostModel& m = b->models[i];
+    const size_t half = (b->sbytes[i] + 255) / 256 * 256;
+    char* base = static_cast<char*>(b->state) + b->off[i];
+    for (int par = 0; par < 2; ++par)
+      if (!encode_state_map(&hm[2 * i + par], base + par * half, m, 3, kBTX, ty)) return cudaErrorInvalidValue;
+    for (int y0 = 0; y0 < m.ny; y0 += ty)
+      for (int x0 = 0; x0 < m.nx; x0 += kBTX) items.push_back(BatchItem{i, x0, y0, x0 + m.xoff - 16 / 4});
+  }
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return e;
+  dev_free(b->hook, b->items);
+  b->items = static_cast<BatchItem*>(dev_alloc(b->hook, sizeof(BatchItem) * items.size()));
+  if (!b->items) return cudaErrorMemoryAllocation;
+  b->nitems = (int)items.size();
+  e = cudaMemcpyAsync(b->items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->maps, hm.data(), sizeof(CUtensorMap) * hm.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  void* kern = batch_kernel_for(ty);
+  const int smem = batch_smem_for(ty);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBTX * ty + 32, smem);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  b->ty = ty;
+  b->smem = smem;
+  b->grid = std::max(1, per_sm) * sms;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->graph_n = -1;
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -357,10 +427,8 @@ ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_c
   b->status = reinterpret_cast<int*>(reinterpret_cast<char*>(b->barrier) + 128);
   cudaError_t e = cudaMemsetAsync(b->state, 0, tot, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->barrier, 0, 256, b->stream);
-  // per-simulation constants and tensor maps
+  // per-simulation constants
   std::vector<BatchSim<float, 2, 1>> hs(nsims);
-  std::vector<CUtensorMap> hm(2 * nsims);
-  std::vector<BatchItem> items;
   const StepKernel* k = nullptr;
   for (auto& sk : step_registry())
     if (sk.dim == 2 && sk.np == 2 && sk.nm == 1 && sk.dtype == 0 && sk.tx == kBTX && sk.ty == kBTY) k = &sk;
@@ -373,43 +441,16 @@ ms_status ms_batch_create(int nsims, const ms_grid* grids, int n_phases, int n_c
       k->fill(&g, m, 1, b->status);
       g.out = reinterpret_cast<float*>(base + (1 - par) * half);
       g.tz0 = (float)temp_offset(m, m.t0);
-      if (!encode_state_map(&hm[2 * i + par], base + par * half, m, 3, kBTX, kBTY)) {
-        batch_free(b);
-        return bfail(nullptr, MS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-      }
     }
-    for (int y0 = 0; y0 < m.ny; y0 += kBTY)
-      for (int x0 = 0; x0 < m.nx; x0 += kBTX) items.push_back(BatchItem{i, x0, y0, x0 + m.xoff - 16 / 4});
-  }
-  // items in simulation order: each CTA takes a contiguous range of them
-  std::vector<BatchItem>& mixed = items;
-  b->nitems = (int)mixed.size();
-  b->items = static_cast<BatchItem*>(dev_alloc(b->hook, sizeof(BatchItem) * mixed.size()));
-  if (!b->items) {
-    batch_free(b);
-    return bfail(nullptr, MS_ERR_OOM, "batch work list allocation failed");
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->sims, hs.data(), sizeof(hs[0]) * nsims, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->maps, hm.data(), sizeof(CUtensorMap) * hm.size(), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->items, mixed.data(), sizeof(BatchItem) * mixed.size(), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  // persistent grid: every CTA resident at once
-  auto kern = k_batch<2, 1, float, kBTX, kBTY>;
-  b->smem = BF::SMEM;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, b->smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  int per_sm = 0, dev = 0, sms = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBTX * kBTY + 32, b->smem);
-  if (e == cudaSuccess) e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // work list, tensor maps and persistent grid (every CTA resident at once)
+  if (e == cudaSuccess) e = batch_set_tiles(b, kBTY);
   if (e != cudaSuccess) {
     std::string m = std::string("batch set-up: ") + cudaGetErrorString(e);
     batch_free(b);
-    return bfail(nullptr, MS_ERR_CUDA, m);
+    return bfail(nullptr, e == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA, m);
   }
-  b->grid = std::max(1, per_sm) * sms;
   *out = b;
   return MS_OK;
 }
@@ -494,6 +535,66 @@ ms_status ms_batch_sync(ms_batch* b) {
   if (e != cudaSuccess) return bfail(b, MS_ERR_CUDA, std::string("batch sync: ") + cudaGetErrorString(e));
   if (st & kStatusTimeout) return bfail(b, MS_ERR_TIMEOUT, "a bounded device wait timed out");
   return MS_OK;
+}
+
+ms_status ms_batch_set_tile(ms_batch* b, int ty) {
+  if (!b) return bfail(nullptr, MS_ERR_ARG, "batch is NULL");
+  bool ok = false;
+  for (int k = 0; k < kNBTY; ++k) ok = ok || kBTYs[k] == ty;
+  if (!ok) return bfail(b, MS_ERR_ARG, "tile height must be one of 4, 8, 16");
+  if (ty == b->ty) return MS_OK;
+  cudaError_t e = batch_set_tiles(b, ty);
+  if (e != cudaSuccess) return bfail(b, MS_ERR_CUDA, std::string("batch tiles: ") + cudaGetErrorString(e));
+  return MS_OK;
+}
+
+int ms_batch_tile(const ms_batch* b) { return b ? b->ty : 0; }
+
+ms_status ms_batch_tune(ms_batch* b, int steps_per_trial, double* best_ms_per_step) {
+  if (!b || steps_per_trial < 1) return bfail(b, MS_ERR_ARG, "bad argument");
+  size_t tot = 0;
+  for (int i = 0; i < b->nsims; ++i) tot = std::max(tot, b->off[i] + 2 * ((b->sbytes[i] + 255) / 256 * 256));
+  void* save = dev_alloc(b->hook, tot);
+  if (!save) return bfail(b, MS_ERR_OOM, "batch tuner: state copy allocation failed");
+  const int parity0 = b->parity;
+  const int64_t done0 = b->steps_done;
+  cudaError_t e = cudaMemcpyAsync(save, b->state, tot, cudaMemcpyDeviceToDevice, b->stream);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  int best = b->ty;
+  float best_ms = 0.0f;
+  for (int k = 0; k < kNBTY && e == cudaSuccess; ++k) {
+    e = batch_set_tiles(b, kBTYs[k]);
+    if (e != cudaSuccess) break;
+    // a warm-up launch captures the graph for this step count
+    if (ms_batch_step(b, steps_per_trial) != MS_OK) {
+      e = cudaErrorUnknown;
+      break;
+    }
+    e = cudaEventRecord(t0, b->stream);
+    if (e == cudaSuccess && ms_batch_step(b, steps_per_trial) != MS_OK) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e == cudaSuccess && (k == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = kBTYs[k];
+    }
+    // back to the saved state
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->state, save, tot, cudaMemcpyDeviceToDevice, b->stream);
+    b->parity = parity0;
+    b->steps_done = done0;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  dev_free(b->hook, save);
+  if (e == cudaSuccess) e = batch_set_tiles(b, best);
+  if (e != cudaSuccess) return bfail(b, MS_ERR_CUDA, std::string("batch tuner: ") + cudaGetErrorString(e));
+  if (best_ms_per_step) *best_ms_per_step = best_ms / steps_per_trial;
+  return ms_batch_sync(b);
 }
 
 int64_t ms_batch_cells(const ms_batch* b) {

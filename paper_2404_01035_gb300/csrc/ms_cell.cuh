@@ -151,8 +151,7 @@ __device__ __forceinline__ F2 face_pair_flux2(F2 pa, F2 npb, const F2* ga, const
     s4 = fma2(q2[i], q2[i], s4);
   }
   const float Ql = f2lo(Q), Qh = f2hi(Q);
-  const bool tl = Ql < 1e-12f, th = Qh < 1e-12f;
-  if (tl && th) return f2s(0.0f);
+  const bool tl = Ql < 1e-12f, th = Qh < 1e-12f;   // g := 0 there (selected below)
   const F2 invQ = f2(recip(tl ? 1.0f : Ql), recip(th ? 1.0f : Qh));
   const F2 r = s4 * invQ * invQ;
   const F2 ac = fma2(f2s(4.0f * del), r, f2s(1.0f - 3.0f * del));
@@ -236,7 +235,7 @@ __device__ __forceinline__ void face_flux(const Acc& A, const StepArgs<Real, NP,
 // Both faces along axis D at once in paired FP32 arithmetic (low half: the
 // face with the -D neighbour, high half: with the +D neighbour); the same
 // discretisation as face_flux, J[a] = (J_a on the low face, on the high face).
-template <int DIM, int D, int NP, int NM, class Acc, int FEAT = kFeatAll>
+template <int DIM, int D, int NP, int NM, class Acc, int FEAT = kFeatAll, bool ALL = false>
 __device__ __forceinline__ void face_flux_pair(const Acc& A, const StepArgs<float, NP, NM>& g, uint32_t mask,
                                                bool need_tan, const float (*gcr)[DIM], F2* J) {
   const Off<DIM> m = unit<DIM>(D, -1), p = unit<DIM>(D, 1);
@@ -244,7 +243,7 @@ __device__ __forceinline__ void face_flux_pair(const Acc& A, const StepArgs<floa
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
     J[a] = f2s(0.0f);
-    if (!((mask >> a) & 1u)) continue;
+    if (!ALL && !((mask >> a) & 1u)) continue;
     const float vm = A.phi(a, m.x, m.y, m.z), v0 = A.phi(a, 0, 0, 0), vp = A.phi(a, p.x, p.y, p.z);
     const F2 vl = f2(vm, v0), vr = f2(v0, vp);
     pf[a] = f2s(0.5f) * (vl + vr);
@@ -253,7 +252,7 @@ __device__ __forceinline__ void face_flux_pair(const Acc& A, const StepArgs<floa
 #pragma unroll
     for (int t = 0; t < DIM; ++t) {
       if (t == D) continue;
-      if (need_tan) {
+      if (ALL || need_tan) {
         // the 4-point average (1/4)[(L+t) + (R+t) - (L-t) - (R-t)] written as
         // the sum of the two cells' central differences along t: the
         // neighbours' from the edge values, the cell's own (gcr) shared with
@@ -273,7 +272,7 @@ __device__ __forceinline__ void face_flux_pair(const Acc& A, const StepArgs<floa
   for (int a = 0; a < NP; ++a) {
 #pragma unroll
     for (int b = a + 1; b < NP; ++b, ++pi) {
-      if (!(((mask >> a) & (mask >> b)) & 1u)) continue;
+      if (!ALL && !(((mask >> a) & (mask >> b)) & 1u)) continue;
       const F2 gD = face_pair_flux2<DIM, D>(pf[a], npf[b], gr[a], gr[b], g.gam2[pi], g.delta[pi], g.aniso[pi] != 0,
                                             (FEAT & kFeatRot) && g.rotated[pi] != 0, g.rot[pi]);
       J[a] = fma2(npf[b], gD, J[a]);
@@ -361,6 +360,103 @@ __device__ __forceinline__ S grand_potential(const StepArgs<Real, NP, NM>& g, in
   return C - Real(0.5) * quad;
 }
 
+// S1-S3 of the cell update: divergence of the face fluxes and the centre
+// term.  ALL: every phase is present in the stencil region and some present
+// pair is anisotropic (the row's mask says so), so no per-phase or per-pair
+// test is needed and the code is straight-line.
+template <int DIM, int NP, int NM, class Real, class S, class Acc, int FEAT, bool ALL>
+__device__ __forceinline__ void gradient_terms(const Acc& A, const StepArgs<Real, NP, NM>& g,
+                                               const DiffPrm<S, NP*(NP - 1) / 2>& dp, const S* ph, uint32_t mask,
+                                               bool need_tan, S* divJ, S* Gc) {
+  // central differences (unscaled) of the present phases: the centre
+  // term and, in FP32, the tangential face gradients
+  S gcr[NP][DIM];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    if (!ALL && !((mask >> a) & 1u)) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) gcr[a][d] = S(Real(0));
+      continue;
+    }
+    gcr[a][0] = A.phi(a, 1, 0, 0) - A.phi(a, -1, 0, 0);
+    gcr[a][1] = A.phi(a, 0, 1, 0) - A.phi(a, 0, -1, 0);
+    if constexpr (DIM == 3) gcr[a][2] = A.phi(a, 0, 0, 1) - A.phi(a, 0, 0, -1);
+  }
+  // S1-S3: divergence of the face fluxes
+  {
+    if constexpr (std::is_same<S, float>::value) {
+      F2 J[NP];
+      face_flux_pair<DIM, 0, NP, NM, Acc, FEAT, ALL>(A, g, mask, need_tan, gcr, J);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
+    } else {
+      S Jm[NP], Jp[NP];
+      face_flux<DIM, 0, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 0, need_tan, Jm);
+      face_flux<DIM, 0, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 1, need_tan, Jp);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+    }
+  }
+  {
+    if constexpr (std::is_same<S, float>::value) {
+      F2 J[NP];
+      face_flux_pair<DIM, 1, NP, NM, Acc, FEAT, ALL>(A, g, mask, need_tan, gcr, J);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
+    } else {
+      S Jm[NP], Jp[NP];
+      face_flux<DIM, 1, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 0, need_tan, Jm);
+      face_flux<DIM, 1, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 1, need_tan, Jp);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+    }
+  }
+  if constexpr (DIM == 3) {
+    if constexpr (std::is_same<S, float>::value) {
+      F2 J[NP];
+      face_flux_pair<DIM, 2, NP, NM, Acc, FEAT, ALL>(A, g, mask, need_tan, gcr, J);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
+    } else {
+      S Jm[NP], Jp[NP];
+      face_flux<DIM, 2, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 0, need_tan, Jm);
+      face_flux<DIM, 2, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 1, need_tan, Jp);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
+    }
+  }
+  // centre term, central differences
+  S gc[NP][DIM];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    if (!ALL && !((mask >> a) & 1u)) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) gc[a][d] = S(Real(0));
+      continue;
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) gc[a][d] = gcr[a][d] * g.half_inv_dx;
+  }
+  int p = 0;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int b = a + 1; b < NP; ++b, ++p) {
+      if (!ALL && !(((mask >> a) & (mask >> b)) & 1u)) continue;
+      S q[DIM], gq[DIM];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) q[d] = ph[a] * gc[b][d] - ph[b] * gc[a][d];
+      pair_grad_fwd<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, (FEAT & kFeatRot) && g.rotated[p] != 0,
+                         g.rot[p], gq);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        Gc[a] += gq[d] * gc[b][d];
+        Gc[b] -= gq[d] * gc[a][d];
+      }
+    }
+  }
+}
+
 // The full cell update.  kz = cell index along the last axis (for T).
 template <int DIM, int NP, int NM, class Real, class S, class Acc, int FEAT = kFeatAll>
 __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, NM>& g,
@@ -404,92 +500,13 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
           for (int b = a + 1; b < NP; ++b, ++p)
             if ((((mask >> a) & (mask >> b)) & 1u) && g.aniso[p]) need_tan = true;
       }
-      // central differences (unscaled) of the present phases: the centre
-      // term and, in FP32, the tangential face gradients
-      S gcr[NP][DIM];
-#pragma unroll
-      for (int a = 0; a < NP; ++a) {
-        if (!((mask >> a) & 1u)) {
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) gcr[a][d] = S(Real(0));
-          continue;
-        }
-        gcr[a][0] = A.phi(a, 1, 0, 0) - A.phi(a, -1, 0, 0);
-        gcr[a][1] = A.phi(a, 0, 1, 0) - A.phi(a, 0, -1, 0);
-        if constexpr (DIM == 3) gcr[a][2] = A.phi(a, 0, 0, 1) - A.phi(a, 0, 0, -1);
-      }
-      // S1-S3: divergence of the face fluxes
-      {
-        if constexpr (std::is_same<S, float>::value) {
-          F2 J[NP];
-          face_flux_pair<DIM, 0, NP, NM, Acc, FEAT>(A, g, mask, need_tan, gcr, J);
-#pragma unroll
-          for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
-        } else {
-          S Jm[NP], Jp[NP];
-          face_flux<DIM, 0, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 0, need_tan, Jm);
-          face_flux<DIM, 0, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 1, need_tan, Jp);
-#pragma unroll
-          for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
-        }
-      }
-      {
-        if constexpr (std::is_same<S, float>::value) {
-          F2 J[NP];
-          face_flux_pair<DIM, 1, NP, NM, Acc, FEAT>(A, g, mask, need_tan, gcr, J);
-#pragma unroll
-          for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
-        } else {
-          S Jm[NP], Jp[NP];
-          face_flux<DIM, 1, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 0, need_tan, Jm);
-          face_flux<DIM, 1, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 1, need_tan, Jp);
-#pragma unroll
-          for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
-        }
-      }
-      if constexpr (DIM == 3) {
-        if constexpr (std::is_same<S, float>::value) {
-          F2 J[NP];
-          face_flux_pair<DIM, 2, NP, NM, Acc, FEAT>(A, g, mask, need_tan, gcr, J);
-#pragma unroll
-          for (int a = 0; a < NP; ++a) divJ[a] += (f2hi(J[a]) - f2lo(J[a])) * g.inv_dx;
-        } else {
-          S Jm[NP], Jp[NP];
-          face_flux<DIM, 2, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 0, need_tan, Jm);
-          face_flux<DIM, 2, NP, NM, Real, S, Acc, FEAT>(A, g, dp, mask, 1, need_tan, Jp);
-#pragma unroll
-          for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
-        }
-      }
-      // centre term, central differences
-      S gc[NP][DIM];
-#pragma unroll
-      for (int a = 0; a < NP; ++a) {
-        if (!((mask >> a) & 1u)) {
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) gc[a][d] = S(Real(0));
-          continue;
-        }
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) gc[a][d] = gcr[a][d] * g.half_inv_dx;
-      }
-      int p = 0;
-#pragma unroll
-      for (int a = 0; a < NP; ++a) {
-#pragma unroll
-        for (int b = a + 1; b < NP; ++b, ++p) {
-          if (!(((mask >> a) & (mask >> b)) & 1u)) continue;
-          S q[DIM], gq[DIM];
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) q[d] = ph[a] * gc[b][d] - ph[b] * gc[a][d];
-          pair_grad_fwd<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, (FEAT & kFeatRot) && g.rotated[p] != 0,
-                             g.rot[p], gq);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            Gc[a] += gq[d] * gc[b][d];
-            Gc[b] -= gq[d] * gc[a][d];
-          }
-        }
+      if constexpr (std::is_same<S, float>::value) {
+        if (mask == (1u << NP) - 1u && need_tan)
+          gradient_terms<DIM, NP, NM, Real, S, Acc, FEAT, true>(A, g, dp, ph, mask, need_tan, divJ, Gc);
+        else
+          gradient_terms<DIM, NP, NM, Real, S, Acc, FEAT, false>(A, g, dp, ph, mask, need_tan, divJ, Gc);
+      } else {
+        gradient_terms<DIM, NP, NM, Real, S, Acc, FEAT, false>(A, g, dp, ph, mask, need_tan, divJ, Gc);
       }
     }
     // S4: potential derivative

@@ -68,3 +68,46 @@ def test_cfg3_batch_of_512_runs_500_steps():
         assert np.abs(phi - sphi).max() <= 1e-5 and np.abs(mu - smu).max() <= 1e-5, i
         assert np.abs(phi.sum(axis=0) - 1).max() < 1e-5
     b.close()
+
+
+@pytest.mark.parametrize("ty", [4, 16])
+def test_every_tile_height_matches_standalone_runs(ty):
+    from paper_2404_01035_gb300.batch import Batch
+    probs = _mixed_batch()
+    b = Batch(probs)
+    assert b.tile_height() == 8
+    b.set_tile(ty)
+    assert b.tile_height() == ty
+    for i, p in enumerate(probs):
+        b.set_fields(i, p.phi0, p.mu0)
+    b.step(120)
+    b.sync()
+    for i, p in enumerate(probs):
+        phi, mu = b.get_fields(i)
+        sphi, smu = _standalone(p, 120)
+        assert np.abs(phi - sphi).max() <= 1e-5 and np.abs(mu - smu).max() <= 1e-5, (ty, i)
+    with pytest.raises(Exception):
+        b.set_tile(12)
+    b.close()
+
+
+def test_tuner_restores_the_states_and_keeps_a_compiled_height():
+    from paper_2404_01035_gb300.batch import Batch
+    probs = _mixed_batch()
+    b = Batch(probs)
+    for i, p in enumerate(probs):
+        b.set_fields(i, p.phi0, p.mu0)
+    b.step(40)
+    before = [b.get_fields(i) for i in range(len(probs))]
+    ms = b.tune(steps_per_trial=30)
+    assert ms > 0 and b.tile_height() in (4, 8, 16)
+    for i in range(len(probs)):   # the trials left the states as they were
+        phi, mu = b.get_fields(i)
+        assert np.array_equal(phi, before[i][0]) and np.array_equal(mu, before[i][1])
+    b.step(60)                    # and stepping continues from them
+    b.sync()
+    for i, p in enumerate(probs):
+        phi, mu = b.get_fields(i)
+        sphi, smu = _standalone(p, 100)
+        assert np.abs(phi - sphi).max() <= 1e-5 and np.abs(mu - smu).max() <= 1e-5, i
+    b.close()

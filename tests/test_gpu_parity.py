@@ -203,7 +203,9 @@ def test_tile_shapes_and_zchunks_agree():
         phi, mu = sim.get_fields()
         if ref is None:
             ref = (phi, mu)
-        assert max(np.abs(phi - ref[0]).max(), np.abs(mu - ref[1]).max()) <= 1e-6, (t, z)
+        # (separately compiled instantiations contract FMAs differently; after
+        # 20 steps that is a few ulp of |mu| ~ 1.2, hence 5e-6)
+        assert max(np.abs(phi - ref[0]).max(), np.abs(mu - ref[1]).max()) <= 5e-6, (t, z)
         if t in per_tile:
             assert np.array_equal(phi, per_tile[t][0]) and np.array_equal(mu, per_tile[t][1]), (t, z)
         per_tile[t] = (phi, mu)
