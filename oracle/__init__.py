@@ -72,7 +72,7 @@ class _Problem(ctypes.Structure):
         ("z0", ctypes.c_double), ("V", ctypes.c_double), ("t0", ctypes.c_double),
         ("z_origin", ctypes.c_int), ("noise_amp", ctypes.c_double), ("noise_seed", ctypes.c_ulonglong),
         ("step0", ctypes.c_longlong), ("anti_trapping", ctypes.c_int), ("grain_growth", ctypes.c_int),
-        ("elw", ctypes.c_void_p),
+        ("elw", ctypes.c_void_p), ("active_set", ctypes.c_int),
     ]
 
 
@@ -162,6 +162,7 @@ class OracleProblem:
         s.grain_growth = int(bool(opt("grain_growth", 0)))
         elw = override.get("elw", None)
         s.elw = arr(elw, (N, self.nx * self.ny * self.nz)) if elw is not None else None
+        s.active_set = int(bool(opt("active_set", 0)))
         self.s = s
 
     @property

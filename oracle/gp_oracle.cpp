@@ -59,7 +59,7 @@
 
 namespace {
 
-constexpr int NMAX = 8;   // phases
+constexpr int NMAX = 64;   // phases (the dense CUDA path takes at most 8; sparse grain growth more)
 constexpr int KMAX = 3;   // independent solutes
 constexpr double PI = 3.14159265358979323846;
 
@@ -138,6 +138,7 @@ typedef struct {
   int anti_trapping;     // 1 = anti-trapping current j_at in the mu update
   int grain_growth;      // 1 = GRAINGROWTH: no chemical driving force, mu frozen
   const double* elw;     // [N][cells] elastic part of the potential of each phase, or NULL
+  int active_set;        // 1 = the projection acts on the locally active phases only (see phi_cell)
 } oracle_problem;
 
 }  // extern "C"
@@ -698,10 +699,35 @@ void phi_cell(const Ctx<S>& c, const S* phi, const S* mu, int x, int y, int z, d
       v[a] += p.dt * p.noise_amp * noise_variate(p.noise_seed, (uint64_t)nstep, gcell * N + a);
     }
   }
-  if (p.potential == 1)
+  if (p.active_set) {
+    // locally active phases (the multiphase-field form of the Lagrange
+    // multiplier over the phases present at a point): those non-zero at the
+    // cell or at one of its 2 dim face neighbours; the projection acts on
+    // them alone and every other phase stays 0
+    bool act[NMAX];
+    for (int a = 0; a < N; ++a) act[a] = val(ph[a]) > 0.0;
+    for (int d = 0; d < dim; ++d)
+      for (int s = -1; s <= 1; s += 2) {
+        int u[3] = {x, y, z};
+        u[d] += s;
+        const int64_t in = cell_index(c, u[0], u[1], u[2]);
+        for (int a = 0; a < N; ++a) act[a] = act[a] || val(phi[a * c.cells + in]) > 0.0;
+      }
+    S va[NMAX], pa[NMAX];
+    int na = 0;
+    for (int a = 0; a < N; ++a)
+      if (act[a]) va[na++] = v[a];
+    if (p.potential == 1)
+      project_simplex(na, va, pa);
+    else
+      project_hyperplane(na, va, pa);
+    na = 0;
+    for (int a = 0; a < N; ++a) pn[a] = act[a] ? pa[na++] : S(0.0);
+  } else if (p.potential == 1) {
     project_simplex(N, v, pn);
-  else
+  } else {
     project_hyperplane(N, v, pn);
+  }
   for (int a = 0; a < N; ++a) phi_out[a * c.cells + ic] = pn[a];
 }
 

@@ -106,6 +106,7 @@ class Problem:
     noise_seed: int = 0
     anti_trapping: int = 0         # 1 = anti-trapping current in the mu update
     grain_growth: int = 0          # 1 = GRAINGROWTH: curvature-driven only, mu held
+    active_set: int = 0            # 1 = projection over the locally active phases (sparse grain growth)
     elastic_C: Optional[np.ndarray] = None   # [6,6] Voigt stiffness (homogeneous); None = no elasticity
     eigenstrain: Optional[np.ndarray] = None # [N,3,3] eigenstrain of each phase (tensor components)
     phi0: np.ndarray = None        # [N,nz,ny,nx]
@@ -332,6 +333,27 @@ def cfg5(n: int = 512, steps: int = 1000, grains: int = 7, R: float = 8.0,
     if make_fields:
         p.phi0, p.mu0 = grain_fields(p, np.float64)
     return p
+
+
+def uniform_gamma3(N: int, value: float) -> np.ndarray:
+    """Gamma_abc = value for every triple of distinct phases, 0 otherwise."""
+    G = np.full((N, N, N), float(value))
+    for k in range(N):
+        G[k, k, :] = 0.0
+        G[k, :, k] = 0.0
+        G[:, k, k] = 0.0
+    return G
+
+
+def sparse_grain_growth(n: int = 256, dim: int = 3, grains: int = 8, gamma3: float = 15.0,
+                        seed: int = BASE_SEED, ny: int = None, nz: int = None, steps: int = 1000) -> Problem:
+    """Grain growth for the sparse (locally active) path: the Voronoi grains
+    of grain_growth, a uniform triple term Gamma_abc = gamma3 (above
+    96 gamma / pi^2, so that two-grain boundaries hold no third grain) and the
+    projection over the locally active phases."""
+    p = grain_growth(n=n, dim=dim, grains=grains, seed=seed, ny=ny, nz=nz, steps=steps)
+    return p.copy(gamma3=uniform_gamma3(grains, gamma3), active_set=1, name=p.name + "_sparse",
+                  meta={**p.meta, "gamma3": gamma3})
 
 
 def grain_growth(n: int = 256, dim: int = 3, grains: int = 8, seed: int = BASE_SEED, ny: int = None,
