@@ -406,6 +406,47 @@ size_t ms_halo_plane_bytes(const ms_ctx* ctx);
 ms_status ms_halo_pack(ms_ctx* ctx, int face, void* dst);
 ms_status ms_halo_unpack(ms_ctx* ctx, int face, const void* src);
 
+/* ---- Sparse grain growth: many grains, few per cell ------------------------
+ * Isotropic grain growth (GRAINGROWTH = 1, Sec. 4 "Grain-growth": the phi
+ * equation of Sec. 2.1 without the chemical driving force) with up to 64
+ * grains, every cell storing only the grains non-zero there (at most 8: a
+ * grain index and a value each).  The Lagrange multiplier is taken over the
+ * locally active grains -- those non-zero at the cell or at one of its face
+ * neighbours: the projection onto the simplex runs over them alone and every
+ * other grain stays 0 -- so a grain appears only next to where it is.  The
+ * obstacle potential (Eq. Obstacle) with a uniform triple term Gamma_abc
+ * (gamma3, the same value for every triple of distinct grains; a value above
+ * 96 gamma / pi^2 keeps third grains out of two-grain boundaries) and
+ * isotropic pairs (delta = 0); no mu field.
+ * ms_ggs_create(grid, n_grains, params, stream, alloc, out): params as for
+ *   ms_create (dtype, eps, tau, dt, gamma [N][N], gamma3 [N][N][N] or NULL;
+ *   potential MS_POT_OBSTACLE; noise, anti-trapping, elasticity off); the
+ *   whole domain (no MS_BC_HALO).  dt is checked against the explicit bound
+ *   (dx^2 / 2 dim) tau / gamma_max (MS_ERR_DT_UNSTABLE).  MS_ERR_ARG /
+ *   MS_ERR_UNSUPPORTED for other settings.
+ * ms_ggs_set_fields(ctx, phi, on_device): phi dense [N][z][y][x] in the
+ *   context dtype; a cell with more than 8 non-zero grains, or a negative or
+ *   non-finite value, gives MS_ERR_BOUNDS.  Resets the step counter.
+ * ms_ggs_get_fields(ctx, phi, on_device): the dense fields (zeros where a
+ *   grain is absent); synchronous.
+ * ms_ggs_step(ctx, n): n steps (two launches each: the cells whose 7-point
+ *   stencil is one grain keep it, the others are listed and updated).
+ *   Asynchronous on the context's stream.
+ * ms_ggs_sync(ctx): waits; MS_ERR_BOUNDS (sticky) when a step needed more than
+ *   8 grains in a cell or in a cell's stencil.
+ * ms_ggs_stats(ctx, listed_cells, step): cells updated by the last step's
+ *   list and the step count (synchronises). */
+typedef struct ms_ggs ms_ggs;
+ms_status ms_ggs_create(const ms_grid* grid, int n_grains, const ms_params* params, void* stream,
+                        const ms_allocator* alloc, ms_ggs** out);
+void ms_ggs_destroy(ms_ggs* ctx);
+const char* ms_ggs_last_error(const ms_ggs* ctx);
+ms_status ms_ggs_set_fields(ms_ggs* ctx, const void* phi, int on_device);
+ms_status ms_ggs_get_fields(ms_ggs* ctx, void* phi, int on_device);
+ms_status ms_ggs_step(ms_ggs* ctx, int64_t n);
+ms_status ms_ggs_sync(ms_ggs* ctx);
+ms_status ms_ggs_stats(ms_ggs* ctx, int64_t* listed_cells, int64_t* step);
+
 /* Allocation-free diagnostics (the paper has no counterpart; this is a
  * library service).  For callers that cannot allocate device memory while
  * they run -- a host application that gives this library a fixed memory

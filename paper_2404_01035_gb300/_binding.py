@@ -35,6 +35,8 @@ EXPORTS = [
     "ms_halo_exchange", "ms_halo_mirror", "ms_selftest_timeout", "ms_peak_fp32",
     "ms_halo_plane_bytes", "ms_halo_pack", "ms_halo_unpack",
     "ms_batch_set_tile", "ms_batch_tile", "ms_batch_tune",
+    "ms_ggs_create", "ms_ggs_destroy", "ms_ggs_last_error", "ms_ggs_set_fields", "ms_ggs_get_fields",
+    "ms_ggs_step", "ms_ggs_sync", "ms_ggs_stats",
 ]
 
 
@@ -135,6 +137,17 @@ def lib(build_if_missing: bool = True):
         L.ms_batch_set_tile.argtypes = [vp, ctypes.c_int]
         L.ms_batch_tile.argtypes = [vp]
         L.ms_batch_tune.argtypes = [vp, ctypes.c_int, dp]
+        L.ms_ggs_create.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(Params), vp,
+                                    ctypes.POINTER(Allocator), ctypes.POINTER(vp)]
+        L.ms_ggs_destroy.argtypes = [vp]
+        L.ms_ggs_destroy.restype = None
+        L.ms_ggs_last_error.argtypes = [vp]
+        L.ms_ggs_last_error.restype = ctypes.c_char_p
+        L.ms_ggs_set_fields.argtypes = [vp, vp, ctypes.c_int]
+        L.ms_ggs_get_fields.argtypes = [vp, vp, ctypes.c_int]
+        L.ms_ggs_step.argtypes = [vp, i64]
+        L.ms_ggs_sync.argtypes = [vp]
+        L.ms_ggs_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.ms_halo_exchange.argtypes = [vp, vp]
         L.ms_halo_mirror.argtypes = [vp, ctypes.c_int]
         L.ms_halo_plane_bytes.argtypes = [vp]
@@ -150,7 +163,8 @@ def lib(build_if_missing: bool = True):
                                       ctypes.POINTER(Params), ctypes.c_double, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("ms_destroy", "ms_last_error", "ms_checkpoint_bytes", "ms_batch_destroy",
-                            "ms_batch_last_error", "ms_batch_cells", "ms_halo_plane_bytes"):
+                            "ms_batch_last_error", "ms_batch_cells", "ms_halo_plane_bytes",
+                            "ms_ggs_destroy", "ms_ggs_last_error"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
         return _lib

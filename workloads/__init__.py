@@ -348,12 +348,15 @@ def uniform_gamma3(N: int, value: float) -> np.ndarray:
 def sparse_grain_growth(n: int = 256, dim: int = 3, grains: int = 8, gamma3: float = 15.0,
                         seed: int = BASE_SEED, ny: int = None, nz: int = None, steps: int = 1000) -> Problem:
     """Grain growth for the sparse (locally active) path: the Voronoi grains
-    of grain_growth, a uniform triple term Gamma_abc = gamma3 (above
-    96 gamma / pi^2, so that two-grain boundaries hold no third grain) and the
-    projection over the locally active phases."""
+    of grain_growth with diffuse boundaries (diffuse_voronoi: a sharp start
+    makes transient stencils of 10 and more grains), a uniform triple term
+    Gamma_abc = gamma3 (above 96 gamma / pi^2, so that two-grain boundaries
+    hold no third grain) and the projection over the locally active phases."""
     p = grain_growth(n=n, dim=dim, grains=grains, seed=seed, ny=ny, nz=nz, steps=steps)
-    return p.copy(gamma3=uniform_gamma3(grains, gamma3), active_set=1, name=p.name + "_sparse",
-                  meta={**p.meta, "gamma3": gamma3})
+    p = p.copy(gamma3=uniform_gamma3(grains, gamma3), active_set=1, name=p.name + "_sparse",
+               meta={**p.meta, "gamma3": gamma3})
+    p.phi0 = diffuse_voronoi(p)
+    return p
 
 
 def grain_growth(n: int = 256, dim: int = 3, grains: int = 8, seed: int = BASE_SEED, ny: int = None,
@@ -500,3 +503,32 @@ def small_multiphase(n: int = 24, dim: int = 3, N: int = 3, NM: int = 2, seed: i
                    D=D, A=A, ceq=ceq, slopes=slopes, f0=np.zeros(N) - 0.05 * np.eye(N)[0],
                    T_ref=0.0, T0=0.0, G=2e-3, z0=(nz if dim == 3 else ny) / 2.0, V=0.05, steps=10,
                    phi0=phi0, mu0=mu0, meta={"seed": seed})
+
+
+def diffuse_voronoi(p: Problem) -> np.ndarray:
+    """Voronoi grains of p.meta['centres'] (periodic) with diffuse boundaries:
+    each cell shares the obstacle profile S(s / eps) between its nearest and
+    second-nearest grain, s the distance to their bisecting plane (pure in the
+    nearest grain farther than pi^2 eps / 8 from it)."""
+    n, ny, nz, N, dim = p.nx, p.ny, p.nz, p.n_phases, p.dim
+    ext = np.array([n, ny, nz][:dim], dtype=np.float64)
+    cen = np.array(p.meta["centres"], dtype=np.float64)
+    grids = np.meshgrid(*[_centres(int(e), 1.0) for e in ext[::-1]], indexing="ij")
+    pos = np.stack([grids[dim - 1 - k] for k in range(dim)], axis=-1)
+    d2 = np.zeros((N,) + grids[0].shape)
+    for g in range(N):
+        t = pos - cen[g]
+        t = t - ext * np.round(t / ext)
+        d2[g] = (t * t).sum(-1)
+    order = np.argsort(d2, axis=0)
+    g1, g2 = order[0], order[1]
+    d1 = np.take_along_axis(d2, g1[None], 0)[0]
+    dd2 = np.take_along_axis(d2, g2[None], 0)[0]
+    dc = cen[g2] - cen[g1]
+    dc = dc - ext * np.round(dc / ext)
+    s = (dd2 - d1) / (2.0 * np.sqrt((dc * dc).sum(-1)))
+    f = seed_profile(s / p.eps, p.potential)
+    phi = np.zeros((N,) + grids[0].shape)
+    np.put_along_axis(phi, g1[None], f[None], 0)
+    np.put_along_axis(phi, g2[None], (1.0 - f)[None], 0)
+    return phi.reshape((N,) + p.phi0.shape[1:])
