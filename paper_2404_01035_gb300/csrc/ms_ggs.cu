@@ -19,7 +19,8 @@
 //     keeps it (written only when the destination buffer, which holds the
 //     state one step back, does not already hold it); the others are appended
 //     to a work list (warp-aggregated).
-//   k_ggs_update: grid-stride over the list; the grains of the 7 stencil cells
+//   k_ggs_update: grid-stride over the list (a build for unions of up to 4
+//     grains, which defers larger ones to a second list and build); the grains of the 7 stencil cells
 //     (a 64-bit union mask), their values gathered into per-thread shared
 //     memory, the face fluxes, centre term, potential derivative and rate over
 //     that union in increasing grain order (the order of the dense sums, whose
@@ -49,6 +50,7 @@ namespace {
 
 constexpr int kSlots = 8;        // grains stored per cell
 constexpr int kUnion = 8;        // grains in a 7-point stencil at most
+constexpr int kUnionSmall = 4;   // the union size of the first update build
 constexpr int kMaxGrains = 64;   // union masks are 64-bit
 constexpr int kStatusOverflow = 8;
 
@@ -71,6 +73,7 @@ struct GgsArgs {
   uint8_t* idx_out;
   Real* val_out;
   unsigned int* list;      // [0] count, [1..] cell indices
+  unsigned int* list2;     // the cells whose stencil holds more than kUnionSmall grains
   unsigned int list_cap;
   int* status;
 };
@@ -128,14 +131,14 @@ __global__ void __launch_bounds__(256) k_ggs_classify(const GgsArgs<Real> g) {
 
 // Simplex projection (Held-Wolfe-Crowder 1974; Duchi et al. 2008) of the
 // first n <= kUnion values: the threshold theta (phi = max(v - theta, 0)).
-template <class Real>
+template <class Real, int K>
 __device__ __forceinline__ Real simplex_theta(const Real* v, int n) {
-  Real u[kUnion];
+  Real u[K];
 #pragma unroll
-  for (int a = 0; a < kUnion; ++a) u[a] = a < n ? v[a] : Real(-INFINITY);
-  // insertion sort, descending (a fixed network over kUnion entries)
+  for (int a = 0; a < K; ++a) u[a] = a < n ? v[a] : Real(-INFINITY);
+  // insertion sort, descending (a fixed network over K entries)
 #pragma unroll
-  for (int i = 1; i < kUnion; ++i)
+  for (int i = 1; i < K; ++i)
 #pragma unroll
     for (int j = i; j > 0; --j)
       if (u[j] > u[j - 1]) {
@@ -145,7 +148,7 @@ __device__ __forceinline__ Real simplex_theta(const Real* v, int n) {
       }
   Real csum = Real(0), theta = Real(0);
 #pragma unroll
-  for (int j = 0; j < kUnion; ++j) {
+  for (int j = 0; j < K; ++j) {
     if (j >= n) break;
     csum += u[j];
     const Real t = (csum - Real(1)) / Real(j + 1);
@@ -154,26 +157,34 @@ __device__ __forceinline__ Real simplex_theta(const Real* v, int n) {
   return theta;
 }
 
-// Threads per block of the update kernel: its shared memory holds 7 x kUnion
+// Threads per block of the update kernel: its shared memory holds 7 x KU
 // values per thread.
-template <class Real>
+template <class Real, int KU>
 struct UpdShape {
-  static constexpr int THREADS = sizeof(Real) == 8 ? 64 : 128;
+  static constexpr int THREADS = sizeof(Real) * KU > 16 ? 64 : 128;
+  static constexpr int MIN_BLOCKS = sizeof(Real) * KU > 16 ? 4 : 4;   // registers for 16 warps per SM (8 for the large builds)
 };
 
-template <class Real>
-__global__ void __launch_bounds__(UpdShape<Real>::THREADS) k_ggs_update(const GgsArgs<Real> g) {
-  constexpr int T = UpdShape<Real>::THREADS;
+// Two builds: KU = kUnionSmall takes the cells of the first list whose
+// stencil holds at most that many grains (nearly all) and moves the others to
+// the second list, which the KU = kUnion build then updates (each build's
+// registers fit its own union size).
+template <class Real, int KU>
+__global__ void __launch_bounds__(UpdShape<Real, KU>::THREADS, UpdShape<Real, KU>::MIN_BLOCKS)
+    k_ggs_update(const GgsArgs<Real> g) {
+  constexpr int T = UpdShape<Real, KU>::THREADS;
+  constexpr bool kFirst = KU < kUnion;
+  const unsigned int* list = kFirst ? g.list : g.list2;
   // per thread: the union's values at the 7 stencil cells ([cell][grain]) and
   // the union's grain ids (increasing)
-  __shared__ Real s_val[T][7][kUnion];
-  __shared__ uint8_t s_uid[T][kUnion];
-  Real (*sv)[kUnion] = s_val[threadIdx.x];
+  __shared__ Real s_val[T][7][KU];
+  __shared__ uint8_t s_uid[T][KU];
+  Real (*sv)[KU] = s_val[threadIdx.x];
   uint8_t* uid = s_uid[threadIdx.x];
-  const unsigned int count = min(*(volatile unsigned int*)&g.list[0], g.list_cap);
+  const unsigned int count = min(*(volatile const unsigned int*)&list[0], g.list_cap);
   const int nst = 2 * g.dim + 1;   // stencil cells: 0 the centre, 1 + 2d the -d and 2 + 2d the +d neighbour
   for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < count; w += gridDim.x * blockDim.x) {
-    const long long i = g.list[1 + w];
+    const long long i = list[1 + w];
     const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
     long long ci[7];
     ci[0] = i;
@@ -183,23 +194,31 @@ __global__ void __launch_bounds__(UpdShape<Real>::THREADS) k_ggs_update(const Gg
       ci[1 + 2 * d] = nb_index(g, x, y, z, d, -1);
       ci[2 + 2 * d] = nb_index(g, x, y, z, d, 1);
     }
-    // union of the grains present on the stencil
+    // union of the grains present on the stencil (every load independent:
+    // the counts first, then all slots, predicated)
+    int cntc[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) cntc[c] = c < nst ? (int)g.cnt_in[ci[c]] : 0;
     unsigned long long mask = 0ull;
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      if (c >= nst) break;
-      const int n = g.cnt_in[ci[c]];
-      for (int k = 0; k < n; ++k) mask |= 1ull << g.idx_in[k * g.cells + ci[c]];
-    }
+    for (int c = 0; c < 7; ++c)
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k)
+        if (k < cntc[c]) mask |= 1ull << g.idx_in[k * g.cells + ci[c]];
     const int nu = __popcll(mask);
-    if (nu > kUnion) {
-      atomicOr(g.status, kStatusOverflow);
+    if (nu > KU) {
+      if constexpr (kFirst) {
+        const unsigned int k2 = atomicAdd(&g.list2[0], 1u);
+        if (k2 < g.list_cap) g.list2[1 + k2] = (unsigned int)i;
+      } else {
+        atomicOr(g.status, kStatusOverflow);
+      }
       continue;
     }
     {
       unsigned long long m = mask;
 #pragma unroll
-      for (int u = 0; u < kUnion; ++u) {
+      for (int u = 0; u < KU; ++u) {
         uid[u] = m ? (uint8_t)(__ffsll((long long)m) - 1) : (uint8_t)0;
         m &= m - 1ull;
       }
@@ -207,38 +226,37 @@ __global__ void __launch_bounds__(UpdShape<Real>::THREADS) k_ggs_update(const Gg
 #pragma unroll
     for (int c = 0; c < 7; ++c)
 #pragma unroll
-      for (int u = 0; u < kUnion; ++u) sv[c][u] = Real(0);
+      for (int u = 0; u < KU; ++u) sv[c][u] = Real(0);
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      if (c >= nst) break;
-      const int n = g.cnt_in[ci[c]];
-      for (int k = 0; k < n; ++k) {
-        const int a = g.idx_in[k * g.cells + ci[c]];
-        sv[c][__popcll(mask & ((1ull << a) - 1ull))] = g.val_in[k * g.cells + ci[c]];
-      }
-    }
+    for (int c = 0; c < 7; ++c)
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k)
+        if (k < cntc[c]) {
+          const int a = g.idx_in[k * g.cells + ci[c]];
+          sv[c][__popcll(mask & ((1ull << a) - 1ull))] = g.val_in[k * g.cells + ci[c]];
+        }
     // S1-S3: divergence of the face fluxes (isotropic: the normal component
     // of g = 2 gamma q needs the normal differences only), in the order of
     // the dense sums restricted to the present grains
-    Real divJ[kUnion], Gc[kUnion];
+    Real divJ[KU], Gc[KU];
 #pragma unroll
-    for (int u = 0; u < kUnion; ++u) {
+    for (int u = 0; u < KU; ++u) {
       divJ[u] = Real(0);
       Gc[u] = Real(0);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (d >= g.dim) break;
-      Real Jm[kUnion], Jp[kUnion];
+      Real Jm[KU], Jp[KU];
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         // side 0: the face with the -d neighbour (left = it, right = the
         // cell); side 1: with the +d neighbour (left = the cell)
         const int cl = side ? 0 : 1 + 2 * d, cr = side ? 2 + 2 * d : 0;
         Real* J = side ? Jp : Jm;
-        Real pf[kUnion], gr[kUnion];
+        Real pf[KU], gr[KU];
 #pragma unroll
-        for (int a = 0; a < kUnion; ++a) {
+        for (int a = 0; a < KU; ++a) {
           J[a] = Real(0);
           if (a >= nu) continue;
           const Real vl = sv[cl][a], vr = sv[cr][a];
@@ -246,10 +264,10 @@ __global__ void __launch_bounds__(UpdShape<Real>::THREADS) k_ggs_update(const Gg
           gr[a] = (vr - vl) * g.inv_dx;
         }
 #pragma unroll
-        for (int a = 0; a < kUnion; ++a) {
+        for (int a = 0; a < KU; ++a) {
           if (a >= nu) break;
 #pragma unroll
-          for (int b = a + 1; b < kUnion; ++b) {
+          for (int b = a + 1; b < KU; ++b) {
             if (b >= nu) break;
             const Real q = pf[a] * gr[b] - pf[b] * gr[a];
             const Real gq = g.gam2[uid[a] * g.N + uid[b]] * q;
@@ -259,20 +277,20 @@ __global__ void __launch_bounds__(UpdShape<Real>::THREADS) k_ggs_update(const Gg
         }
       }
 #pragma unroll
-      for (int a = 0; a < kUnion; ++a)
+      for (int a = 0; a < KU; ++a)
         if (a < nu) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
     }
     // centre term, central differences
-    Real gc[kUnion][3];
+    Real gc[KU][3];
 #pragma unroll
-    for (int a = 0; a < kUnion; ++a)
+    for (int a = 0; a < KU; ++a)
 #pragma unroll
       for (int d = 0; d < 3; ++d) gc[a][d] = d < g.dim ? (sv[2 + 2 * d][a] - sv[1 + 2 * d][a]) * g.half_inv_dx : Real(0);
 #pragma unroll
-    for (int a = 0; a < kUnion; ++a) {
+    for (int a = 0; a < KU; ++a) {
       if (a >= nu) break;
 #pragma unroll
-      for (int b = a + 1; b < kUnion; ++b) {
+      for (int b = a + 1; b < KU; ++b) {
         if (b >= nu) break;
         const Real gm = g.gam2[uid[a] * g.N + uid[b]];
         Real gq[3];
@@ -288,31 +306,31 @@ __global__ void __launch_bounds__(UpdShape<Real>::THREADS) k_ggs_update(const Gg
     }
     // S4 potential derivative (obstacle, with the triple term), S5 rate and
     // explicit Euler (no chemical driving force in grain growth)
-    Real v[kUnion];
+    Real v[KU];
 #pragma unroll
-    for (int a = 0; a < kUnion; ++a) {
+    for (int a = 0; a < KU; ++a) {
       v[a] = Real(0);
       if (a >= nu) continue;
       Real W = Real(0);
 #pragma unroll
-      for (int b = 0; b < kUnion; ++b)
+      for (int b = 0; b < KU; ++b)
         if (b < nu && b != a) W += g.cw[uid[a] * g.N + uid[b]] * sv[0][b];
       if (g.has_g3) {
 #pragma unroll
-        for (int b = 0; b < kUnion; ++b)
+        for (int b = 0; b < KU; ++b)
 #pragma unroll
-          for (int e = b + 1; e < kUnion; ++e)
+          for (int e = b + 1; e < KU; ++e)
             if (e < nu && b != a && e != a) W += g.g3 * sv[0][b] * sv[0][e];
       }
       const Real r = g.mob * (g.eps * (divJ[a] - Gc[a]) - W * g.inv_eps) * g.inv_eps;
       v[a] = sv[0][a] + g.dt * r;
     }
     // projection over the locally active grains (the union)
-    const Real theta = simplex_theta<Real>(v, nu);
+    const Real theta = simplex_theta<Real, KU>(v, nu);
     int n_out = 0;
     uint8_t code = 0;
 #pragma unroll
-    for (int a = 0; a < kUnion; ++a) {
+    for (int a = 0; a < KU; ++a) {
       if (a >= nu) break;
       const Real dd = v[a] - theta;
       const Real pn = dd > Real(0) ? dd : Real(0);
@@ -382,6 +400,7 @@ struct ms_ggs {
   void* buf[2] = {nullptr, nullptr};   // cnt | code | idx | val per buffer
   void* tables = nullptr;              // gam2 [N][N], cw [N][N]
   unsigned int* list = nullptr;
+  unsigned int* list2 = nullptr;
   int* status = nullptr;
   int cur = 0;
   int64_t step = 0;
@@ -444,6 +463,7 @@ GgsArgs<Real> make_args(const ms_ggs* s, int src) {
   g.idx_out = idx_of(s, 1 - src);
   g.val_out = static_cast<Real*>(val_of(s, 1 - src));
   g.list = s->list;
+  g.list2 = s->list2;
   g.list_cap = (unsigned int)s->cells;
   g.status = s->status;
   return g;
@@ -453,9 +473,11 @@ template <class Real>
 cudaError_t step_once(ms_ggs* s) {
   const GgsArgs<Real> g = make_args<Real>(s, s->cur);
   cudaError_t e = cudaMemsetAsync(s->list, 0, sizeof(unsigned int), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->list2, 0, sizeof(unsigned int), s->stream);
   if (e != cudaSuccess) return e;
   k_ggs_classify<Real><<<(unsigned int)((s->cells + 255) / 256), 256, 0, s->stream>>>(g);
-  k_ggs_update<Real><<<s->upd_blocks, UpdShape<Real>::THREADS, 0, s->stream>>>(g);
+  k_ggs_update<Real, kUnionSmall><<<s->upd_blocks, UpdShape<Real, kUnionSmall>::THREADS, 0, s->stream>>>(g);
+  k_ggs_update<Real, kUnion><<<s->upd_blocks, UpdShape<Real, kUnion>::THREADS, 0, s->stream>>>(g);
   return cudaGetLastError();
 }
 
@@ -586,12 +608,13 @@ ms_status ms_ggs_create(const ms_grid* grid, int n_grains, const ms_params* p, v
   if (alloc) s->hook = AllocHook{alloc->alloc, alloc->release, alloc->user};
   for (int b = 0; b < 2; ++b) s->buf[b] = dev_alloc(s->hook, buf_bytes(s));
   s->tables = dev_alloc(s->hook, 2 * (size_t)N * N * s->s);
-  s->list = static_cast<unsigned int*>(dev_alloc(s->hook, (size_t)(s->cells + 1) * sizeof(unsigned int) + 256));
+  s->list = static_cast<unsigned int*>(dev_alloc(s->hook, 2 * (size_t)(s->cells + 1) * sizeof(unsigned int) + 256));
   if (!s->buf[0] || !s->buf[1] || !s->tables || !s->list) {
     ms_ggs_destroy(s);
     return gfail(nullptr, MS_ERR_OOM, "sparse grain-growth allocation failed");
   }
-  s->status = reinterpret_cast<int*>(reinterpret_cast<char*>(s->list) + (s->cells + 1) * sizeof(unsigned int));
+  s->list2 = s->list + (s->cells + 1);
+  s->status = reinterpret_cast<int*>(s->list2 + (s->cells + 1));
   const double PI = 3.14159265358979323846;
   std::vector<double> tab(2 * (size_t)N * N);
   for (int a = 0; a < N; ++a)
