@@ -22,6 +22,8 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   * The chemical mobility inside interfaces, M = sum_a h_a D^a chi^a with
     phi^n (``tests/test_oracle_mobility.py``): exact one-step and frozen-phi
     mode decay, two-solute matrix order: pinned.
+  * run_adjoint (the reverse sweep by a tape, ``tests/test_oracle_adjoint.py``):
+    equal to the forward-mode tangent in a dot-product test: pinned.
   * count_flops (the op-counting scalar, ``tests/test_oracle_flops.py``):
     exact counts of hand-countable updates: pinned.
   * The full multiphase (N >= 3) anisotropic dendrite / eutectic / multigrain
@@ -90,6 +92,7 @@ def lib():
             L.oracle_rate_parts.argtypes = [P, dp, dp, dp, dp, dp, dp]
             L.oracle_diag.argtypes = [P, dp, dp, dp]
             L.oracle_count_flops.argtypes = [P, dp, dp, dp, dp]
+            L.oracle_run_adjoint.argtypes = [P, dp, dp, ctypes.c_int, dp, dp, dp, dp, dp]
             L.oracle_pair_energy.argtypes = [P, ctypes.c_int, ctypes.c_int, dp]
             L.oracle_pair_energy.restype = ctypes.c_double
             L.oracle_pair_energy_grad.argtypes = [P, ctypes.c_int, ctypes.c_int, dp, dp]
@@ -364,6 +367,26 @@ def rate_parts(prob, phi, mu, t0: float = 0.0, **override):
     if rc:
         raise ValueError("oracle_rate_parts rejected the problem")
     return tuple(outs)
+
+
+def run_adjoint(prob, phi0, mu0, nsteps: int, lam_phi, lam_mu, t0: float = 0.0, step0: int = 0, **override):
+    """Reverse adjoint of nsteps steps by the oracle's tape: for a loss with
+    dL/dphi = lam_phi and dL/dmu = lam_mu at the final state, returns
+    (dL/dphi0, dL/dmu0, dL/dtheta), theta = (delta_ab for pairs a < b, the
+    phase mobility 1/tau, D^a_ij).  Single-threaded; small grids only."""
+    op = OracleProblem(prob, t0, step0, **override)
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64).reshape(op.shape(op.N))
+    mu0 = np.ascontiguousarray(mu0, dtype=np.float64).reshape(op.shape(op.NM))
+    lp = np.ascontiguousarray(lam_phi, dtype=np.float64).reshape(op.shape(op.N))
+    lm = np.ascontiguousarray(lam_mu, dtype=np.float64).reshape(op.shape(op.NM))
+    dphi0 = np.empty_like(phi0)
+    dmu0 = np.empty_like(mu0)
+    nprm = op.N * (op.N - 1) // 2 + 1 + op.N * op.NM * op.NM
+    dtheta = np.zeros(nprm)
+    if lib().oracle_run_adjoint(op.ptr(), _dp(phi0), _dp(mu0), int(nsteps), _dp(lp), _dp(lm), _dp(dphi0),
+                                _dp(dmu0), _dp(dtheta)):
+        raise ValueError("oracle_run_adjoint rejected the problem")
+    return dphi0, dmu0, dtheta
 
 
 def count_flops(prob, phi, mu, t0: float = 0.0, step0: int = 0, **override):

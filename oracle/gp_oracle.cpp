@@ -109,6 +109,56 @@ inline Cnt& operator-=(Cnt& a, Cnt b) { a = a - b; return a; }
 inline double val(const Cnt& x) { return x.v; }
 inline Cnt sqrt_s(const Cnt& x) { ++g_ops; return {std::sqrt(x.v)}; }
 
+// ------------------------------------------------------- reverse-mode tape
+// A minimal tape for the reverse adjoint: every operation with a recorded
+// operand appends a node holding its (at most two) operands and the partial
+// derivatives with respect to them; a constant (no operand recorded) carries
+// id -1.  The tape is global, so a step taped with Rev runs single-threaded
+// (see taped<S> below).  Sweeping the nodes backwards accumulates adjoints.
+struct TapeNode {
+  int a, b;
+  double da, db;
+};
+std::vector<TapeNode> g_tape;
+struct Rev {
+  double v = 0.0;
+  int id = -1;
+  Rev() = default;
+  Rev(double x) : v(x), id(-1) {}
+  Rev(double x, int i) : v(x), id(i) {}
+};
+inline Rev rev_node(double v, int a, double da, int b, double db) {
+  if (a < 0 && b < 0) return Rev(v);
+  g_tape.push_back({a, b, da, db});
+  return Rev(v, (int)g_tape.size() - 1);
+}
+inline Rev rev_leaf(double v) {   // an independent input
+  g_tape.push_back({-1, -1, 0.0, 0.0});
+  return Rev(v, (int)g_tape.size() - 1);
+}
+inline Rev operator+(Rev x, Rev y) { return rev_node(x.v + y.v, x.id, 1.0, y.id, 1.0); }
+inline Rev operator-(Rev x, Rev y) { return rev_node(x.v - y.v, x.id, 1.0, y.id, -1.0); }
+inline Rev operator-(Rev x) { return rev_node(-x.v, x.id, -1.0, -1, 0.0); }
+inline Rev operator*(Rev x, Rev y) { return rev_node(x.v * y.v, x.id, y.v, y.id, x.v); }
+inline Rev operator/(Rev x, Rev y) {
+  const double q = x.v / y.v;
+  return rev_node(q, x.id, 1.0 / y.v, y.id, -q / y.v);
+}
+inline Rev& operator+=(Rev& x, Rev y) { x = x + y; return x; }
+inline Rev& operator-=(Rev& x, Rev y) { x = x - y; return x; }
+inline double val(const Rev& x) { return x.v; }
+inline Rev sqrt_s(const Rev& x) {
+  const double r = std::sqrt(x.v);
+  return rev_node(r, x.id, 0.5 / r, -1, 0.0);
+}
+
+// A step may run its cell loops in parallel unless its scalar records onto
+// the global tape.
+template <class S>
+constexpr bool taped() { return false; }
+template <>
+constexpr bool taped<Rev>() { return true; }
+
 }  // namespace
 
 extern "C" {
@@ -807,7 +857,7 @@ void mu_cell(const Ctx<S>& c, const S* phi, const S* mu, const S* phi_out, int x
 template <class S>
 void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, double t, int64_t nstep) {
   const oracle_problem& p = *c.p;
-#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) if (!taped<S>())
   for (int z = 0; z < c.n[2]; ++z)
     for (int y = 0; y < c.n[1]; ++y)
       for (int x = 0; x < c.n[0]; ++x) phi_cell(c, phi, mu, x, y, z, t, nstep, phi_out);
@@ -817,7 +867,7 @@ void step(const Ctx<S>& c, const S* phi, const S* mu, S* phi_out, S* mu_out, dou
     for (int64_t k = 0; k < (int64_t)p.NM * c.cells; ++k) mu_out[k] = mu[k];
     return;
   }
-#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+#pragma omp parallel for collapse(2) schedule(dynamic, 1) if (!taped<S>())
   for (int z = 0; z < c.n[2]; ++z)
     for (int y = 0; y < c.n[1]; ++y)
       for (int x = 0; x < c.n[0]; ++x) mu_cell(c, phi, mu, phi_out, x, y, z, t, mu_out);
@@ -952,6 +1002,81 @@ int oracle_count_flops(const oracle_problem* p, const double* phi, const double*
         if (!p->grain_growth) mu_cell(c, pa.data(), ma.data(), pb.data(), x, y, z, p->t0, mb.data());
         ops_mu[cell_index(c, x, y, z)] = static_cast<double>(g_ops - before);
       }
+  return 0;
+}
+
+// Reverse (adjoint) sweep of nsteps steps by the tape: given lam_phi / lam_mu
+// = dL/dphi, dL/dmu of the final state, returns dL/dphi0, dL/dmu0 of the
+// initial state and dL/dtheta for theta = (delta_ab for pairs a < b in
+// row-major order, the phase mobility 1/tau, the entries D^a_ij), accumulated
+// over the steps.  The forward states are kept; each step is taped from its
+// own input (recorded leaves) and swept back on its own.
+int oracle_run_adjoint(const oracle_problem* p, const double* phi0, const double* mu0, int nsteps,
+                       const double* lam_phi, const double* lam_mu, double* dphi0, double* dmu0, double* dtheta) {
+  if (check(p)) return 1;
+  Ctx<double> c;
+  init_ctx(c, p);
+  const int64_t cells = c.cells;
+  const int N = p->N, NM = p->NM;
+  const int64_t nphi = N * cells, nmu = NM * cells;
+  std::vector<double> st((int64_t)(nsteps + 1) * (nphi + nmu));
+  std::memcpy(st.data(), phi0, sizeof(double) * nphi);
+  std::memcpy(st.data() + nphi, mu0, sizeof(double) * nmu);
+  for (int n = 0; n < nsteps; ++n) {
+    double* a = st.data() + (int64_t)n * (nphi + nmu);
+    double* b = a + (nphi + nmu);
+    step(c, a, a + nphi, b, b + nphi, p->t0 + n * p->dt, p->step0 + n);
+  }
+  const int P = N * (N - 1) / 2;
+  const int NPRM = P + 1 + N * NM * NM;
+  for (int k = 0; k < NPRM; ++k) dtheta[k] = 0.0;
+  std::vector<double> lp(lam_phi, lam_phi + nphi), lm(lam_mu, lam_mu + nmu);
+  for (int n = nsteps - 1; n >= 0; --n) {
+    g_tape.clear();
+    Ctx<Rev> r;
+    init_ctx(r, p);
+    // the differentiable parameters as recorded leaves
+    int pid[NMAX * NMAX], mid, did[NMAX * KMAX * KMAX];
+    for (int a = 0, k = 0; a < N; ++a)
+      for (int b = a + 1; b < N; ++b, ++k) {
+        r.q.delta[a][b] = rev_leaf(p->delta[a * N + b]);
+        r.q.delta[b][a] = r.q.delta[a][b];
+        pid[k] = r.q.delta[a][b].id;
+      }
+    r.q.mob = rev_leaf(1.0 / p->tau);
+    mid = r.q.mob.id;
+    for (int a = 0; a < N; ++a)
+      for (int i = 0; i < NM; ++i)
+        for (int j = 0; j < NM; ++j) {
+          r.q.D[a][i][j] = rev_leaf(p->D[(a * NM + i) * NM + j]);
+          did[(a * NM + i) * NM + j] = r.q.D[a][i][j].id;
+        }
+    const double* in = st.data() + (int64_t)n * (nphi + nmu);
+    std::vector<Rev> pa(nphi), ma(nmu), pb(nphi), mb(nmu);
+    for (int64_t i = 0; i < nphi; ++i) pa[i] = rev_leaf(in[i]);
+    for (int64_t i = 0; i < nmu; ++i) ma[i] = rev_leaf(in[nphi + i]);
+    step(r, pa.data(), ma.data(), pb.data(), mb.data(), p->t0 + n * p->dt, p->step0 + n);
+    std::vector<double> adj(g_tape.size(), 0.0);
+    for (int64_t i = 0; i < nphi; ++i)
+      if (pb[i].id >= 0) adj[pb[i].id] += lp[i];
+    for (int64_t i = 0; i < nmu; ++i)
+      if (mb[i].id >= 0) adj[mb[i].id] += lm[i];
+    for (int64_t k = (int64_t)g_tape.size() - 1; k >= 0; --k) {
+      const TapeNode& t = g_tape[k];
+      if (adj[k] == 0.0) continue;
+      if (t.a >= 0) adj[t.a] += t.da * adj[k];
+      if (t.b >= 0) adj[t.b] += t.db * adj[k];
+    }
+    for (int64_t i = 0; i < nphi; ++i) lp[i] = adj[pa[i].id];
+    for (int64_t i = 0; i < nmu; ++i) lm[i] = adj[ma[i].id];
+    for (int k = 0; k < P; ++k) dtheta[k] += adj[pid[k]];
+    dtheta[P] += adj[mid];
+    for (int k = 0; k < N * NM * NM; ++k) dtheta[P + 1 + k] += adj[did[k]];
+  }
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  std::memcpy(dphi0, lp.data(), sizeof(double) * nphi);
+  std::memcpy(dmu0, lm.data(), sizeof(double) * nmu);
   return 0;
 }
 

@@ -155,3 +155,23 @@ def test_cfg4_gradients_match_central_differences_and_fp32():
     g32, _ = _cfg4_grad(prob, phi_hat, steps, "f32")
     for k in (0, 1, 3):
         assert g32[k] == pytest.approx(g64[k], rel=1e-2)
+
+
+@pytest.mark.parametrize("case", ["well2d", "ternary2d"])
+def test_gradients_equal_the_oracle_reverse_sweep(case):
+    # ms_grad (FP64) against the oracle's own reverse adjoint, element by element
+    if case == "well2d":
+        p = W.binary_problem("adjr", 40, delta=0.02, Delta=0.2, R=8.0, potential="well", ny=36,
+                             tau=1.25, dt=0.2 * 0.25 / 1.45)
+        steps, every = 60, 25
+    else:
+        p = W.small_multiphase(n=16, dim=2, N=3, NM=2, nx=18, ny=16, rotate=True)
+        steps, every = 16, 6
+    rng = np.random.default_rng(21)
+    lam_phi = rng.normal(size=p.phi0.shape)
+    lam_mu = rng.normal(size=p.mu0.shape)
+    dparams, dphi0, dmu0, _ = _adjoint(p, steps, every, lam_phi, lam_mu)
+    ophi0, omu0, oth = oracle.run_adjoint(p, p.phi0, p.mu0, steps, lam_phi, lam_mu)
+    np.testing.assert_allclose(dparams, oth, rtol=1e-9, atol=1e-12 * np.abs(oth).max())
+    assert np.abs(dphi0 - ophi0).max() <= 1e-9 * np.abs(ophi0).max()
+    assert np.abs(dmu0 - omu0).max() <= 1e-9 * np.abs(omu0).max()
