@@ -138,7 +138,9 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
   if (tid >= Sh::NT) {
     // ---------------- producer warp: TMA loads + bulk flags of every entry
     const int f_ay = lane / Sh::WCS, f_wc = lane % Sh::WCS;
-    const bool fl = lane < Sh::NFL && seg0 + f_wc < g.segs;
+    // a segment cut by the end of a ragged row is never bulk: it goes to the
+    // interface list, so that bulk groups are always 4 whole cells
+    const bool fl = lane < Sh::NFL && (seg0 + f_wc + 1) * 32 <= g.nx;
     const uint8_t* scode = smem + Sh::OFF_CODE;
     int issued = npre, arrived = 0;
     bool ok = true;
@@ -192,9 +194,8 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
   const int xs = x0 + 4 * lane;          // first of this thread's cells
   const int y = y0 + ty;
   const bool have = y < g.ny && xs < g.nx;
-  // vector path: all 4 cells exist (x ghost images of the first / last cell
-  // of the row are added as single stores)
-  const bool vec_ok = xs + 3 < g.nx;
+  // a bulk flag implies 4 whole cells (x ghost images of the first / last
+  // cell of the row are added as single stores)
   const long long oxl = xs == 0 ? (g.bc[0] == 3 ? g.nx : -1) : 0;                // image of cell q = 0
   const long long oxr = xs + 3 == g.nx - 1 ? (g.bc[0] == 3 ? -g.nx : 1) : 0;     // image of cell q = 3
   const bool leader = (lane & 7) == 0 && y < g.ny && seg < g.segs;
@@ -274,77 +275,62 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
       // a bulk flag implies that the input held phase l here; the output
       // buffer (the state before it) also did when the input's reuse bit is set
       const bool write_phi = (scentre[k * Sh::SY * Sh::CSEG] & reuse) == 0;
-      if (vec_ok) {
-        float* p = out0 + k * plane;
-        const long long fs = g.fstride;
-        // the cell row
-        if (write_phi) {
+      float* p = out0 + k * plane;
+      const long long fs = g.fstride;
+      // the cell row
+      if (write_phi) {
 #pragma unroll
-          for (int a = 0; a < NP; ++a) {
-            const float v = a == l ? 1.0f : 0.0f;
-            stg4(p + a * fs, v, v, v, v);
-          }
+        for (int a = 0; a < NP; ++a) {
+          const float v = a == l ? 1.0f : 0.0f;
+          stg4(p + a * fs, v, v, v, v);
         }
+      }
 #pragma unroll
-        for (int i = 0; i < NM; ++i) stg4(p + (NP + i) * fs, mn[i][0], mn[i][1], mn[i][2], mn[i][3]);
-        // x ghost images of the row's first / last cell (lanes 0 and 31 of the
-        // tiles at the x ends)
-        if (oxl | oxr) {
+      for (int i = 0; i < NM; ++i) stg4(p + (NP + i) * fs, mn[i][0], mn[i][1], mn[i][2], mn[i][3]);
+      // x ghost images of the row's first / last cell (lanes 0 and 31 of the
+      // tiles at the x ends)
+      if (oxl | oxr) {
 #pragma unroll
-          for (int a = 0; a < NP + NM; ++a) {
-            if (a < NP && !write_phi) continue;
-            const float v0 = a < NP ? (a == l ? 1.0f : 0.0f) : mn[a < NP ? 0 : a - NP][0];
-            const float v3 = a < NP ? (a == l ? 1.0f : 0.0f) : mn[a < NP ? 0 : a - NP][3];
-            if (oxl) p[oxl + a * fs] = v0;
-            if (oxr) p[3 + oxr + a * fs] = v3;
-          }
+        for (int a = 0; a < NP + NM; ++a) {
+          if (a < NP && !write_phi) continue;
+          const float v0 = a < NP ? (a == l ? 1.0f : 0.0f) : mn[a < NP ? 0 : a - NP][0];
+          const float v3 = a < NP ? (a == l ? 1.0f : 0.0f) : mn[a < NP ? 0 : a - NP][3];
+          if (oxl) p[oxl + a * fs] = v0;
+          if (oxr) p[3 + oxr + a * fs] = v3;
         }
-        // rows at a y or z boundary (rare): their y / z images, with x images
-        long long oz0 = 0, oz1 = 0;
-        if (g.bc[2] != kBcHalo) {   // internal cuts get their ghost planes from the exchange
-          if (z == 0) oz0 = (g.bc[2] == 3 ? g.nz : -1) * plane;
-          if (z == g.nz - 1) oz1 = (g.bc[2] == 3 ? -g.nz : 1) * plane;
-        }
-        if ((oy0 | oy1 | oz0 | oz1) != 0) {
-          // (the loops are unrolled so that every array index is a constant
-          // and nothing lives in local memory)
-          const long long oy[3] = {0, oy0, oy1}, oz[3] = {0, oz0, oz1};
+      }
+      // rows at a y or z boundary (rare): their y / z images, with x images
+      long long oz0 = 0, oz1 = 0;
+      if (g.bc[2] != kBcHalo) {   // internal cuts get their ghost planes from the exchange
+        if (z == 0) oz0 = (g.bc[2] == 3 ? g.nz : -1) * plane;
+        if (z == g.nz - 1) oz1 = (g.bc[2] == 3 ? -g.nz : 1) * plane;
+      }
+      if ((oy0 | oy1 | oz0 | oz1) != 0) {
+        // (the loops are unrolled so that every array index is a constant
+        // and nothing lives in local memory)
+        const long long oy[3] = {0, oy0, oy1}, oz[3] = {0, oz0, oz1};
 #pragma unroll
-          for (int iz = 0; iz < 3; ++iz)
+        for (int iz = 0; iz < 3; ++iz)
 #pragma unroll
-            for (int iy = 0; iy < 3; ++iy) {
-              if ((iy | iz) == 0 || (iy && !oy[iy]) || (iz && !oz[iz])) continue;
-              float* q = p + oy[iy] + oz[iz];
+          for (int iy = 0; iy < 3; ++iy) {
+            if ((iy | iz) == 0 || (iy && !oy[iy]) || (iz && !oz[iz])) continue;
+            float* q = p + oy[iy] + oz[iz];
 #pragma unroll
-              for (int a = 0; a < NP + NM; ++a) {
-                if (a < NP && !write_phi) continue;
-                float c4[4];
-                if (a < NP) {
-                  const float v = a == l ? 1.0f : 0.0f;
-                  c4[0] = c4[1] = c4[2] = c4[3] = v;
-                } else {
+            for (int a = 0; a < NP + NM; ++a) {
+              if (a < NP && !write_phi) continue;
+              float c4[4];
+              if (a < NP) {
+                const float v = a == l ? 1.0f : 0.0f;
+                c4[0] = c4[1] = c4[2] = c4[3] = v;
+              } else {
 #pragma unroll
-                  for (int u = 0; u < 4; ++u) c4[u] = mn[a - NP][u];
-                }
-                stg4(q + a * fs, c4[0], c4[1], c4[2], c4[3]);
-                if (oxl) q[oxl + a * fs] = c4[0];
-                if (oxr) q[3 + oxr + a * fs] = c4[3];
+                for (int u = 0; u < 4; ++u) c4[u] = mn[a - NP][u];
               }
+              stg4(q + a * fs, c4[0], c4[1], c4[2], c4[3]);
+              if (oxl) q[oxl + a * fs] = c4[0];
+              if (oxr) q[3 + oxr + a * fs] = c4[3];
             }
-        }
-      } else {
-        // partial groups at the end of a ragged row: per cell, with every image
-        float pn[NP];
-#pragma unroll
-        for (int a = 0; a < NP; ++a) pn[a] = a == l ? 1.0f : 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (xs + q >= g.nx) break;
-          float m1[NM];
-#pragma unroll
-          for (int i = 0; i < NM; ++i) m1[i] = mn[i][q];
-          store_cell<3>(g, xs + q, y, z, pn, m1, write_phi);
-        }
+          }
       }
     }
     // segment codes of bulk segments (input and output pure phase l: reuse
