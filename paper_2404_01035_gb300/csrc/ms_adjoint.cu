@@ -6,15 +6,27 @@
 // adds lambda^{n+1} . d(step)/d(theta) to the parameter gradients, theta =
 // (delta_ab per pair, phase mobility 1/tau, D^a entries).
 //
-// J_n^T is applied as a gather, one thread per input cell j, with no atomics:
-// cell j's value is read by every cell i whose stencil covers one of j's
-// positions p (j itself, or a ghost image of j across a periodic / no-flux
-// face).  For each such (p, i) the thread re-evaluates cell i's update with
-// forward-mode dual numbers seeded on all fields at position p, and contracts
-// the result with lambda_i^{n+1}.  Each (i, p) pair is evaluated once over the
-// grid, so the cost is (stencil size) dual evaluations per cell.  The
-// parameter derivative is one more dual evaluation per cell, seeded on theta,
-// reduced per block in FP64 and summed in a fixed order (deterministic).
+// The step of cell i is a stencil part -- the face-flux divergence divJ_i,
+// the centre term Gc_i, the mu flux divergence div_i -- followed by a tail
+// that is local to the cell (potential, driving force, rate, projection, mu
+// update).  The reverse step runs in two passes:
+//   1. k_adj_cell, one thread per cell i: the tail is evaluated once in
+//      forward mode with one derivative slot per tail input (phi_i, mu_i,
+//      divJ_i, Gc_i, div_i, 1/tau) and contracted with lambda_i, which gives
+//      the adjoints of those inputs (tbar_i).  The stencil part is evaluated
+//      with derivative slots on delta (divJ, Gc) and on D (div), so the
+//      parameter gradient of the cell follows from tbar_i at once.
+//   2. k_adj_gather, one thread per input cell j: lambda_j^n is tbar_j's
+//      direct part plus, for every position p holding j's value (j and its
+//      ghost images), the transpose of each stencil part that reads p: every
+//      face whose stencil contains p (its flux adjoint is
+//      (tbar_divJ(L) - tbar_divJ(R)) / dx for the cells L, R it separates),
+//      every centre term reading p, and the mu flux terms (hand-written: div
+//      is linear in mu and in the cell mobilities M(phi)).  The face fluxes and
+//      centre terms are differentiated in forward mode with one slot per phase
+//      at the seeded position; nothing is accumulated with atomics, so the
+//      result is deterministic.
+// Parameter partials are reduced per block in FP64 and summed in block order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,172 +50,218 @@ struct AdjExtra {
   Real D[NP][NM * NM];
 };
 
-// Stencil accessor over the padded state in global memory, yielding duals.
-// SEED: derivative slot a (phase) / NP + i (solute) is 1 at padded index
-// `seed`; otherwise all derivatives are zero.
-template <int DIM, int NP, int NM, class R, int W, bool SEED, class DXT>
-struct GAcc {
-  using D = Dual<R, W>;
-  const R* st;
-  long long fstride, plane, base, seed;
-  int pitch;
-  const DXT* DX;
-
-  __device__ __forceinline__ D load(int f, int dx, int dy, int dz) const {
-    const long long idx = base + dz * plane + (long long)dy * pitch + dx;
-    D v(st[f * fstride + idx]);
-    if constexpr (SEED) {
-      if (idx == seed) v.d[f] = R(1);
-    }
-    return v;
-  }
-  __device__ __forceinline__ D phi(int a, int dx, int dy, int dz) const { return load(a, dx, dy, dz); }
-  __device__ __forceinline__ D mu(int i, int dx, int dy, int dz) const { return load(NP + i, dx, dy, dz); }
-  __device__ __forceinline__ uint32_t mask() const { return (1u << NP) - 1u; }
-  __device__ __forceinline__ void mobility(int dx, int dy, int dz, D* M) const {
-    D ph[NP];
-#pragma unroll
-    for (int a = 0; a < NP; ++a) ph[a] = phi(a, dx, dy, dz);
-    cell_mobility<NP, NM>(ph, *DX, M);
-  }
+// Tail inputs of one cell, in the order of the derivative slots of pass 1
+// (the first TB of them are stored per cell for pass 2).
+template <int NP, int NM>
+struct TailSlots {
+  static constexpr int PH = 0, MC = NP, DJ = NP + NM, GC = 2 * NP + NM, DIV = 3 * NP + NM;
+  static constexpr int TB = 3 * NP + 2 * NM;   // stored adjoints per cell
+  static constexpr int MOB = TB;               // the mobility slot (pass 1 only)
+  static constexpr int T = TB + 1;
 };
 
+// Stencil accessor yielding plain values as the scalar S (no derivative).
+template <int NP, int NM, class Real, class S>
+struct ValAcc {
+  const Real* st;
+  long long fstride, plane, base;
+  int pitch;
+  __device__ __forceinline__ S ld(int f, int dx, int dy, int dz) const {
+    return S(st[f * fstride + base + dz * plane + (long long)dy * pitch + dx]);
+  }
+  __device__ __forceinline__ S phi(int a, int dx, int dy, int dz) const { return ld(a, dx, dy, dz); }
+  __device__ __forceinline__ S mu(int i, int dx, int dy, int dz) const { return ld(NP + i, dx, dy, dz); }
+  __device__ __forceinline__ uint32_t mask() const { return (1u << NP) - 1u; }
+};
+
+// Stencil accessor yielding phases as Dual<Real, NP> with slot a = 1 for
+// phase a at the padded index `seed`.
+template <int NP, int NM, class Real>
+struct SeedAcc {
+  using D = Dual<Real, NP>;
+  const Real* st;
+  long long fstride, plane, base, seed;
+  int pitch;
+  __device__ __forceinline__ D phi(int a, int dx, int dy, int dz) const {
+    const long long idx = base + dz * plane + (long long)dy * pitch + dx;
+    D v(st[a * fstride + idx]);
+    if (idx == seed) v.d[a] = Real(1);
+    return v;
+  }
+  __device__ __forceinline__ uint32_t mask() const { return (1u << NP) - 1u; }
+};
+
+template <int DIM, class Real, int NP, int NM>
+__device__ __forceinline__ bool in_grid(const StepArgs<Real, NP, NM>& g, int x, int y, int z) {
+  return x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < (DIM == 3 ? g.nz : 1);
+}
+
+template <int DIM, class Real, int NP, int NM>
+__device__ __forceinline__ long long padded_index(const StepArgs<Real, NP, NM>& g, int x, int y, int z) {
+  return (long long)(z + g.zoff) * ((long long)g.nyp * g.pitch) + (long long)(y + 1) * g.pitch + x + g.xoff;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool any_aniso(const unsigned char* aniso, int P) {
+  bool r = false;
+  for (int p = 0; p < P; ++p) r = r || aniso[p] != 0;
+  return r;
+}
+
+// Pass 1 (see the file comment).  tbar: [TB][cells], dense cell order.
 template <int DIM, int NP, int NM, class Real>
-__global__ void __launch_bounds__(128) k_adjoint(const Real* __restrict__ st, const Real* __restrict__ lam_in,
-                                                 Real* __restrict__ lam_out,
-                                                 const __grid_constant__ StepArgs<Real, NP, NM> g,
-                                                 const __grid_constant__ AdjExtra<Real, NP, NM> ex,
-                                                 double* __restrict__ partials) {
-  constexpr int NF = NP + NM;
+__global__ void __launch_bounds__(128) k_adj_cell(const Real* __restrict__ st, const Real* __restrict__ lam_in,
+                                                  Real* __restrict__ tbar,
+                                                  const __grid_constant__ StepArgs<Real, NP, NM> g,
+                                                  const __grid_constant__ AdjExtra<Real, NP, NM> ex,
+                                                  double* __restrict__ partials) {
   constexpr int P = NP * (NP - 1) / 2;
+  constexpr int ND = NP * NM * NM;
   constexpr int NPRM = ParamCount<NP, NM>::value;
-  using DF = Dual<Real, NF>;
-  using DPm = Dual<Real, NPRM>;
+  using TS = TailSlots<NP, NM>;
+  using DP = Dual<Real, P>;
+  using DD = Dual<Real, ND>;
+  using DT = Dual<Real, TS::T>;
   const long long cells = (long long)g.nx * g.ny * g.nz;
   const long long plane = (long long)g.nyp * g.pitch;
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool live = j < cells;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double gpar[NPRM];
 #pragma unroll
   for (int k = 0; k < NPRM; ++k) gpar[k] = 0.0;
-  if (live) {
-    const int x = (int)(j % g.nx), y = (int)((j / g.nx) % g.ny), z = (int)(j / ((long long)g.nx * g.ny));
-    auto padded = [&](int px, int py, int pz) {
-      return (long long)(pz + g.zoff) * plane + (long long)(py + 1) * g.pitch + px + g.xoff;
-    };
-    auto dense = [&](int px, int py, int pz) { return ((long long)pz * g.ny + py) * g.nx + px; };
-    // positions holding cell j's value: itself and its ghost images
-    int xs[3], ys[3], zs[3], nxs = 1, nys = 1, nzs = 1;
-    xs[0] = x;
-    ys[0] = y;
-    zs[0] = z;
-    if (x == 0) xs[nxs++] = g.bc[0] == 3 ? g.nx : -1;
-    if (x == g.nx - 1) xs[nxs++] = g.bc[0] == 3 ? -1 : g.nx;
-    if (y == 0) ys[nys++] = g.bc[1] == 3 ? g.ny : -1;
-    if (y == g.ny - 1) ys[nys++] = g.bc[1] == 3 ? -1 : g.ny;
-    if (DIM == 3) {
-      if (z == 0) zs[nzs++] = g.bc[2] == 3 ? g.nz : -1;
-      if (z == g.nz - 1) zs[nzs++] = g.bc[2] == 3 ? -1 : g.nz;
-    }
-    DiffPrm<DF, P> dpf;
-    dpf.mob = DF(g.mob);
-#pragma unroll
-    for (int p = 0; p < P; ++p) dpf.delta[p] = DF(g.delta[p]);
-    Real acc[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) acc[f] = Real(0);
-#pragma unroll 1
-    for (int iz = 0; iz < nzs; ++iz)
-#pragma unroll 1
-      for (int iy = 0; iy < nys; ++iy)
-#pragma unroll 1
-        for (int ix = 0; ix < nxs; ++ix) {
-          const int px = xs[ix], py = ys[iy], pz = zs[iz];
-          const long long seed = padded(px, py, pz);
-#pragma unroll 1
-          for (int o = 0; o < (DIM == 3 ? 27 : 9); ++o) {
-            const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = DIM == 3 ? o / 9 - 1 : 0;
-            if (DIM == 3 && dx != 0 && dy != 0 && dz != 0) continue;   // corners: not in the stencil
-            const int rx = px - dx, ry = py - dy, rz = pz - dz;       // reader cell
-            if (rx < 0 || rx >= g.nx || ry < 0 || ry >= g.ny || rz < 0 || rz >= (DIM == 3 ? g.nz : 1))
-              continue;
-            GAcc<DIM, NP, NM, Real, NF, true, Real[NP][NM * NM]> A;
-            A.st = st;
-            A.fstride = g.fstride;
-            A.plane = plane;
-            A.pitch = g.pitch;
-            A.base = padded(rx, ry, rz);
-            A.seed = seed;
-            A.DX = &g.DX;
-            DF pn[NP], mn[NM];
-            gp_cell<DIM, NP, NM, Real, DF>(A, g, dpf, (DIM == 3 ? rz : ry) + g.zorg, lab_cell<DIM>(g, rx, ry, rz), pn,
-                                           mn);
-            const long long ri = dense(rx, ry, rz);
-#pragma unroll
-            for (int a = 0; a < NP; ++a) {
-              const Real l = lam_in[a * cells + ri];
-#pragma unroll
-              for (int f = 0; f < NF; ++f) acc[f] += l * pn[a].d[f];
-            }
-#pragma unroll
-            for (int i = 0; i < NM; ++i) {
-              const Real l = lam_in[(NP + i) * cells + ri];
-#pragma unroll
-              for (int f = 0; f < NF; ++f) acc[f] += l * mn[i].d[f];
-            }
-          }
-        }
-#pragma unroll
-    for (int f = 0; f < NF; ++f) lam_out[f * cells + j] = acc[f];
-
-    if (partials) {
-      // parameter derivative of cell j's own update
-      DiffPrm<DPm, P> dpp;
-      dpp.mob = DPm(g.mob);
-      dpp.mob.d[P] = Real(1);
+  if (i < cells) {
+    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
+    const long long base = padded_index<DIM>(g, x, y, z);
+    // stencil part: divJ, Gc with delta slots
+    DP divJ[NP], Gc[NP];
+    {
+      ValAcc<NP, NM, Real, DP> A{st, g.fstride, plane, base, g.pitch};
+      DiffPrm<DP, P> dp;
+      dp.mob = DP(g.mob);
 #pragma unroll
       for (int p = 0; p < P; ++p) {
-        dpp.delta[p] = DPm(g.delta[p]);
-        dpp.delta[p].d[p] = Real(1);
+        dp.delta[p] = DP(g.delta[p]);
+        dp.delta[p].d[p] = Real(1);
       }
-      DPm DXd[NP][NM * NM];
+      DP ph[NP];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        ph[a] = A.phi(a, 0, 0, 0);
+        divJ[a] = DP(Real(0));
+        Gc[a] = DP(Real(0));
+      }
+      gradient_terms<DIM, NP, NM, Real, DP, ValAcc<NP, NM, Real, DP>, kFeatAll, false>(
+          A, g, dp, ph, A.mask(), any_aniso<DIM>(g.aniso, P), divJ, Gc);
+    }
+    // stencil part: div with D slots (M = sum_a h_a D^a chi^a)
+    DD div[NM];
+    {
+      ValAcc<NP, NM, Real, DD> B{st, g.fstride, plane, base, g.pitch};
+      DD DXd[NP][NM * NM];
 #pragma unroll
       for (int a = 0; a < NP; ++a)
 #pragma unroll
         for (int r = 0; r < NM; ++r)
 #pragma unroll
           for (int c = 0; c < NM; ++c) {
-            DPm s(Real(0));
+            DD sum(Real(0));
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
-              DPm Dm(ex.D[a][r * NM + m]);
-              Dm.d[P + 1 + (a * NM + r) * NM + m] = Real(1);
-              s += Dm * DPm(g.chi[a][m * NM + c]);
+              DD Dm(ex.D[a][r * NM + m]);
+              Dm.d[(a * NM + r) * NM + m] = Real(1);
+              sum += Dm * DD(g.chi[a][m * NM + c]);
             }
-            DXd[a][r * NM + c] = s;
+            DXd[a][r * NM + c] = sum;
           }
-      GAcc<DIM, NP, NM, Real, NPRM, false, DPm[NP][NM * NM]> A;
-      A.st = st;
-      A.fstride = g.fstride;
-      A.plane = plane;
-      A.pitch = g.pitch;
-      A.base = padded(x, y, z);
-      A.seed = -1;
-      A.DX = &DXd;
-      DPm pn[NP], mn[NM];
-      gp_cell<DIM, NP, NM, Real, DPm>(A, g, dpp, (DIM == 3 ? z : y) + g.zorg, lab_cell<DIM>(g, x, y, z), pn, mn);
+      DD ph[NP], mc[NM], Mc[NM * NM];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) ph[a] = B.phi(a, 0, 0, 0);
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        mc[k] = B.mu(k, 0, 0, 0);
+        div[k] = DD(Real(0));
+      }
+      cell_mobility<NP, NM>(ph, DXd, Mc);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+        for (int sd = -1; sd <= 1; sd += 2) {
+          const Off<DIM> o = unit<DIM>(d, sd);
+          DD pn[NP], Mn[NM * NM];
+#pragma unroll
+          for (int a = 0; a < NP; ++a) pn[a] = B.phi(a, o.x, o.y, o.z);
+          cell_mobility<NP, NM>(pn, DXd, Mn);
+#pragma unroll
+          for (int r = 0; r < NM; ++r)
+#pragma unroll
+            for (int c = 0; c < NM; ++c) {
+              DD Mf = Real(0.5) * (Mc[r * NM + c] + Mn[r * NM + c]);
+              div[r] += Mf * ((B.mu(c, o.x, o.y, o.z) - mc[c]) * g.inv_dx2);
+            }
+        }
+      }
+    }
+    // the tail, one slot per input
+    Real tb[TS::T];
+    {
+      DT in[TS::T];
+#pragma unroll
+      for (int k = 0; k < TS::T; ++k) in[k] = DT(Real(0));
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
-        const Real l = lam_in[a * cells + j];
-#pragma unroll
-        for (int k = 0; k < NPRM; ++k) gpar[k] += (double)(l * pn[a].d[k]);
+        in[TS::PH + a] = DT(st[a * g.fstride + base]);
+        in[TS::DJ + a] = DT(divJ[a].v);
+        in[TS::GC + a] = DT(Gc[a].v);
       }
 #pragma unroll
-      for (int i = 0; i < NM; ++i) {
-        const Real l = lam_in[(NP + i) * cells + j];
-#pragma unroll
-        for (int k = 0; k < NPRM; ++k) gpar[k] += (double)(l * mn[i].d[k]);
+      for (int k = 0; k < NM; ++k) {
+        in[TS::MC + k] = DT(st[(NP + k) * g.fstride + base]);
+        in[TS::DIV + k] = DT(div[k].v);
       }
+      in[TS::MOB] = DT(g.mob);
+#pragma unroll
+      for (int k = 0; k < TS::T; ++k) in[k].d[k] = Real(1);
+      DiffPrm<DT, P> dp;
+      dp.mob = in[TS::MOB];
+#pragma unroll
+      for (int p = 0; p < P; ++p) dp.delta[p] = DT(g.delta[p]);
+      const int kz = (DIM == 3 ? z : y) + g.zorg;
+      const Real s = g.tz0 + g.tzg * (Real(kz) + Real(0.5));
+      DT pn[NP], mn[NM];
+      phase_update<DIM, NP, NM, Real, DT, kFeatAll>(g, dp, in + TS::PH, in + TS::MC, in + TS::DJ, in + TS::GC, s,
+                                                    lab_cell<DIM>(g, x, y, z), pn);
+      mu_update<NP, NM, Real, DT>(g, in + TS::PH, pn, in + TS::MC, in + TS::DIV, s, false, mn);
+#pragma unroll
+      for (int k = 0; k < TS::T; ++k) tb[k] = Real(0);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        const Real l = lam_in[a * cells + i];
+#pragma unroll
+        for (int k = 0; k < TS::T; ++k) tb[k] += l * pn[a].d[k];
+      }
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        const Real l = lam_in[(NP + m) * cells + i];
+#pragma unroll
+        for (int k = 0; k < TS::T; ++k) tb[k] += l * mn[m].d[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < TS::TB; ++k) tbar[k * cells + i] = tb[k];
+    // parameter gradient of cell i's update
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      Real sp = Real(0);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) sp += tb[TS::DJ + a] * divJ[a].d[p] + tb[TS::GC + a] * Gc[a].d[p];
+      gpar[p] += (double)sp;
+    }
+    gpar[P] += (double)tb[TS::MOB];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      Real sd = Real(0);
+#pragma unroll
+      for (int m = 0; m < NM; ++m) sd += tb[TS::DIV + m] * div[m].d[k];
+      gpar[P + 1 + k] += (double)sd;
     }
   }
   if (partials) {
@@ -221,6 +279,214 @@ __global__ void __launch_bounds__(128) k_adjoint(const Real* __restrict__ st, co
   }
 }
 
+// Face fluxes along axis D whose stencil contains position (px, py, pz):
+// acc[a'] += sum_a Jbar_f[a] dJ_f[a]/dphi_a'(p).  A face is named by its
+// lower cell L (upper R = L + e_D); its stencil is L, R and, with
+// anisotropy, L +- e_t, R +- e_t for t != D.
+template <int DIM, int D, int NP, int NM, class Real>
+__device__ __forceinline__ void gather_faces(const Real* __restrict__ st, const Real* __restrict__ tbar,
+                                             const StepArgs<Real, NP, NM>& g, bool need_tan, int px, int py, int pz,
+                                             long long seed, Real* acc) {
+  constexpr int P = NP * (NP - 1) / 2;
+  using TS = TailSlots<NP, NM>;
+  using DN = Dual<Real, NP>;
+  const long long cells = (long long)g.nx * g.ny * g.nz;
+  const long long plane = (long long)g.nyp * g.pitch;
+  DiffPrm<DN, P> dp;
+  dp.mob = DN(g.mob);
+#pragma unroll
+  for (int p = 0; p < P; ++p) dp.delta[p] = DN(g.delta[p]);
+  const int ncand = 2 + (need_tan ? 4 * (DIM - 1) : 0);
+#pragma unroll 1
+  for (int c = 0; c < ncand; ++c) {
+    // offset of L from p
+    int o[3] = {0, 0, 0};
+    if (c == 0) {
+      o[D] = -1;   // p is R
+    } else if (c > 1) {
+      const int k = c - 2;
+      const int t = DIM == 2 ? 1 - D : (D + 1 + (k >> 2)) % 3;   // a tangential axis of D
+      const int sgn = (k & 1) ? 1 : -1;
+      o[t] = -sgn;                  // p = L + sgn e_t, or
+      if ((k >> 1) & 1) o[D] = -1;  // p = R + sgn e_t
+    }
+    const int lx = px + o[0], ly = py + o[1], lz = pz + o[2];
+    const int rx = lx + (D == 0), ry = ly + (D == 1), rz = lz + (D == 2);
+    const bool inL = in_grid<DIM>(g, lx, ly, lz), inR = in_grid<DIM>(g, rx, ry, rz);
+    if (!inL && !inR) continue;
+    Real Jbar[NP];
+    const long long li = ((long long)lz * g.ny + ly) * g.nx + lx, ri = ((long long)rz * g.ny + ry) * g.nx + rx;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const Real bl = inL ? tbar[(TS::DJ + a) * cells + li] : Real(0);
+      const Real br = inR ? tbar[(TS::DJ + a) * cells + ri] : Real(0);
+      Jbar[a] = (bl - br) * g.inv_dx;
+    }
+    SeedAcc<NP, NM, Real> A{st, g.fstride, plane, padded_index<DIM>(g, lx, ly, lz), seed, g.pitch};
+    DN J[NP];
+    face_flux<DIM, D, NP, NM, Real, DN, SeedAcc<NP, NM, Real>, kFeatAll>(A, g, dp, A.mask(), 1, need_tan, J);
+#pragma unroll
+    for (int a = 0; a < NP; ++a)
+#pragma unroll
+      for (int b = 0; b < NP; ++b) acc[b] += Jbar[a] * J[a].d[b];
+  }
+}
+
+// Pass 2 (see the file comment).
+template <int DIM, int NP, int NM, class Real>
+__global__ void __launch_bounds__(128) k_adj_gather(const Real* __restrict__ st, const Real* __restrict__ tbar,
+                                                    Real* __restrict__ lam_out,
+                                                    const __grid_constant__ StepArgs<Real, NP, NM> g) {
+  constexpr int NF = NP + NM;
+  constexpr int P = NP * (NP - 1) / 2;
+  using TS = TailSlots<NP, NM>;
+  using DN = Dual<Real, NP>;
+  const long long cells = (long long)g.nx * g.ny * g.nz;
+  const long long plane = (long long)g.nyp * g.pitch;
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= cells) return;
+  const int x = (int)(j % g.nx), y = (int)((j / g.nx) % g.ny), z = (int)(j / ((long long)g.nx * g.ny));
+  const long long jb = padded_index<DIM>(g, x, y, z);
+  auto dense = [&](int px, int py, int pz) { return ((long long)pz * g.ny + py) * g.nx + px; };
+  const bool need_tan = any_aniso<DIM>(g.aniso, P);
+  Real acc[NF];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) acc[a] = tbar[(TS::PH + a) * cells + j];
+#pragma unroll
+  for (int k = 0; k < NM; ++k) acc[NP + k] = tbar[(TS::MC + k) * cells + j];
+  Real phj[NP], muj[NM], Mj[NM * NM], Mbar[NM * NM];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) phj[a] = st[a * g.fstride + jb];
+#pragma unroll
+  for (int k = 0; k < NM; ++k) muj[k] = st[(NP + k) * g.fstride + jb];
+  cell_mobility<NP, NM>(phj, g.DX, Mj);
+#pragma unroll
+  for (int k = 0; k < NM * NM; ++k) Mbar[k] = Real(0);
+  DiffPrm<DN, P> dpn;
+  dpn.mob = DN(g.mob);
+#pragma unroll
+  for (int p = 0; p < P; ++p) dpn.delta[p] = DN(g.delta[p]);
+
+  // positions holding cell j's value: itself and its ghost images
+  int xs[3], ys[3], zs[3], nxs = 1, nys = 1, nzs = 1;
+  xs[0] = x;
+  ys[0] = y;
+  zs[0] = z;
+  if (x == 0) xs[nxs++] = g.bc[0] == 3 ? g.nx : -1;
+  if (x == g.nx - 1) xs[nxs++] = g.bc[0] == 3 ? -1 : g.nx;
+  if (y == 0) ys[nys++] = g.bc[1] == 3 ? g.ny : -1;
+  if (y == g.ny - 1) ys[nys++] = g.bc[1] == 3 ? -1 : g.ny;
+  if (DIM == 3) {
+    if (z == 0) zs[nzs++] = g.bc[2] == 3 ? g.nz : -1;
+    if (z == g.nz - 1) zs[nzs++] = g.bc[2] == 3 ? -1 : g.nz;
+  }
+#pragma unroll 1
+  for (int iz = 0; iz < nzs; ++iz)
+#pragma unroll 1
+    for (int iy = 0; iy < nys; ++iy)
+#pragma unroll 1
+      for (int ix = 0; ix < nxs; ++ix) {
+        const int px = xs[ix], py = ys[iy], pz = zs[iz];
+        const long long seed = padded_index<DIM>(g, px, py, pz);
+        // face fluxes
+        gather_faces<DIM, 0, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
+        gather_faces<DIM, 1, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
+        if constexpr (DIM == 3) gather_faces<DIM, 2, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
+        // centre terms of the cells whose central differences (or own phi) read p
+#pragma unroll 1
+        for (int c = 0; c < 1 + 2 * DIM; ++c) {
+          int cx = px, cy = py, cz = pz;
+          if (c > 0) {
+            const int d = (c - 1) >> 1, sgn = (c & 1) ? 1 : -1;
+            if (d == 0) cx += sgn;
+            if (d == 1) cy += sgn;
+            if (d == 2) cz += sgn;
+          }
+          if (!in_grid<DIM>(g, cx, cy, cz)) continue;
+          const long long ci = dense(cx, cy, cz);
+          SeedAcc<NP, NM, Real> A{st, g.fstride, plane, padded_index<DIM>(g, cx, cy, cz), seed, g.pitch};
+          DN ph[NP], gcr[NP][DIM], Gc[NP];
+#pragma unroll
+          for (int a = 0; a < NP; ++a) {
+            ph[a] = A.phi(a, 0, 0, 0);
+            gcr[a][0] = A.phi(a, 1, 0, 0) - A.phi(a, -1, 0, 0);
+            gcr[a][1] = A.phi(a, 0, 1, 0) - A.phi(a, 0, -1, 0);
+            if constexpr (DIM == 3) gcr[a][2] = A.phi(a, 0, 0, 1) - A.phi(a, 0, 0, -1);
+            Gc[a] = DN(Real(0));
+          }
+          centre_term<DIM, NP, NM, Real, DN, kFeatAll, false>(g, dpn, ph, gcr, A.mask(), Gc);
+#pragma unroll
+          for (int a = 0; a < NP; ++a) {
+            const Real gb = tbar[(TS::GC + a) * cells + ci];
+#pragma unroll
+            for (int b = 0; b < NP; ++b) acc[b] += gb * Gc[a].d[b];
+          }
+        }
+        // mu flux of the in-grid neighbours i = p - o: p is their neighbour at o
+#pragma unroll 1
+        for (int c = 0; c < 2 * DIM; ++c) {
+          const int d = c >> 1, sgn = (c & 1) ? 1 : -1;
+          const int ix2 = px - (d == 0 ? sgn : 0), iy2 = py - (d == 1 ? sgn : 0), iz2 = pz - (d == 2 ? sgn : 0);
+          if (!in_grid<DIM>(g, ix2, iy2, iz2)) continue;
+          const long long ii = dense(ix2, iy2, iz2), ib = padded_index<DIM>(g, ix2, iy2, iz2);
+          Real phi_i[NP], Mi[NM * NM];
+#pragma unroll
+          for (int a = 0; a < NP; ++a) phi_i[a] = st[a * g.fstride + ib];
+          cell_mobility<NP, NM>(phi_i, g.DX, Mi);
+#pragma unroll
+          for (int r = 0; r < NM; ++r) {
+            const Real db = tbar[(TS::DIV + r) * cells + ii];
+#pragma unroll
+            for (int q = 0; q < NM; ++q) {
+              const Real mci = st[(NP + q) * g.fstride + ib];
+              acc[NP + q] += db * (Real(0.5) * (Mi[r * NM + q] + Mj[r * NM + q])) * g.inv_dx2;
+              Mbar[r * NM + q] += db * (Real(0.5) * (muj[q] - mci)) * g.inv_dx2;
+            }
+          }
+        }
+      }
+  // mu flux of cell j itself (its own mu and mobility at the centre)
+  {
+    Real db[NM];
+#pragma unroll
+    for (int r = 0; r < NM; ++r) db[r] = tbar[(TS::DIV + r) * cells + j];
+#pragma unroll 1
+    for (int c = 0; c < 2 * DIM; ++c) {
+      const int d = c >> 1, sgn = (c & 1) ? 1 : -1;
+      const long long nb = jb + (d == 0 ? sgn : 0) + (d == 1 ? (long long)sgn * g.pitch : 0) +
+                           (d == 2 ? (long long)sgn * plane : 0);
+      Real phn[NP], Mn[NM * NM];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) phn[a] = st[a * g.fstride + nb];
+      cell_mobility<NP, NM>(phn, g.DX, Mn);
+#pragma unroll
+      for (int r = 0; r < NM; ++r)
+#pragma unroll
+        for (int q = 0; q < NM; ++q) {
+          const Real mun = st[(NP + q) * g.fstride + nb];
+          acc[NP + q] -= db[r] * (Real(0.5) * (Mj[r * NM + q] + Mn[r * NM + q])) * g.inv_dx2;
+          Mbar[r * NM + q] += db[r] * (Real(0.5) * (mun - muj[q])) * g.inv_dx2;
+        }
+    }
+  }
+  // M(phi_j): chain the mobility adjoint to the phases
+  {
+    DN ph[NP], M[NM * NM];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      ph[a] = DN(phj[a]);
+      ph[a].d[a] = Real(1);
+    }
+    cell_mobility<NP, NM>(ph, g.DX, M);
+#pragma unroll
+    for (int k = 0; k < NM * NM; ++k)
+#pragma unroll
+      for (int b = 0; b < NP; ++b) acc[b] += Mbar[k] * M[k].d[b];
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) lam_out[f * cells + j] = acc[f];
+}
+
 // gsum[k] += sum over blocks of partials[b][k], in block order (deterministic).
 __global__ void k_accumulate_params(const double* __restrict__ partials, int nblocks, int nprm,
                                     double* __restrict__ gsum) {
@@ -233,12 +499,15 @@ __global__ void k_accumulate_params(const double* __restrict__ partials, int nbl
 
 struct AdjKernel {
   int dim, np, nm, dtype, nprm;
-  cudaError_t (*launch)(const void* state, const void* lam_in, void* lam_out, const void* blob,
+  cudaError_t (*launch)(const void* state, const void* lam_in, void* lam_out, void* tbar, const void* blob,
                         const HostModel& m, double t, double* partials, cudaStream_t st);
 };
 
+// Stored tail adjoints per cell of the reverse step (pass 1 -> pass 2).
+inline int tail_slots(const HostModel& m) { return 3 * m.N + 2 * m.NM; }
+
 template <int DIM, int NP, int NM, class Real>
-cudaError_t launch_adjoint(const void* state, const void* lam_in, void* lam_out, const void* blob,
+cudaError_t launch_adjoint(const void* state, const void* lam_in, void* lam_out, void* tbar, const void* blob,
                            const HostModel& m, double t, double* partials, cudaStream_t st) {
   StepArgs<Real, NP, NM> g = *reinterpret_cast<const StepArgs<Real, NP, NM>*>(blob);
   g.tz0 = (Real)temp_offset(m, t);
@@ -247,9 +516,13 @@ cudaError_t launch_adjoint(const void* state, const void* lam_in, void* lam_out,
     for (int k = 0; k < NM * NM; ++k) ex.D[a][k] = (Real)m.D[a][k];
   const long long cells = (long long)m.nx * m.ny * m.nz;
   const int blocks = (int)((cells + 127) / 128);
-  k_adjoint<DIM, NP, NM, Real><<<blocks, 128, 0, st>>>(
-      reinterpret_cast<const Real*>(state), reinterpret_cast<const Real*>(lam_in),
-      reinterpret_cast<Real*>(lam_out), g, ex, partials);
+  const Real* s = reinterpret_cast<const Real*>(state);
+  k_adj_cell<DIM, NP, NM, Real><<<blocks, 128, 0, st>>>(s, reinterpret_cast<const Real*>(lam_in),
+                                                        reinterpret_cast<Real*>(tbar), g, ex, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_adj_gather<DIM, NP, NM, Real><<<blocks, 128, 0, st>>>(s, reinterpret_cast<const Real*>(tbar),
+                                                          reinterpret_cast<Real*>(lam_out), g);
   return cudaGetLastError();
 }
 
@@ -286,6 +559,8 @@ void free_adjoint(ms_ctx* c) {
     dev_free(c->hook, a.adj[b]);
     a.adj[b] = nullptr;
   }
+  dev_free(c->hook, a.tbar);
+  a.tbar = nullptr;
   dev_free(c->hook, a.gpart);
   a.gpart = nullptr;
   dev_free(c->hook, a.gsum);
@@ -370,6 +645,10 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
       if (!A.adj[b]) return fail(c, MS_ERR_OOM, "adjoint state allocation failed");
     }
   }
+  if (!A.tbar) {
+    A.tbar = dev_alloc(c->hook, (size_t)tail_slots(m) * cells * s);
+    if (!A.tbar) return fail(c, MS_ERR_OOM, "adjoint tail buffer allocation failed");
+  }
   if (!A.gpart) {
     A.gpart = static_cast<double*>(dev_alloc(c->hook, sizeof(double) * (size_t)blocks * nprm));
     A.gsum = static_cast<double*>(dev_alloc(c->hook, sizeof(double) * 64));
@@ -420,8 +699,8 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
     }
     for (int k = len - 1; k >= 0; --k) {
       const double t = m.t0 + (double)(s0 + k) * m.dt;
-      e = ak->launch(slots + (size_t)k * c->state_bytes, A.adj[cur], A.adj[1 - cur], c->args.data(), m, t,
-                     A.gpart, st);
+      e = ak->launch(slots + (size_t)k * c->state_bytes, A.adj[cur], A.adj[1 - cur], A.tbar, c->args.data(), m,
+                     t, A.gpart, st);
       if (e != cudaSuccess) return cuda_fail(c, e, "adjoint step");
       k_accumulate_params<<<1, 64, 0, st>>>(A.gpart, blocks, nprm, A.gsum);
       cur = 1 - cur;

@@ -360,6 +360,43 @@ __device__ __forceinline__ S grand_potential(const StepArgs<Real, NP, NM>& g, in
   return C - Real(0.5) * quad;
 }
 
+// Centre term of S3, Gc_a = sum_b g_ab . grad phi_b (with the opposite sign
+// for b), from the unscaled central differences gcr of the phases and the
+// cell's own phi.
+template <int DIM, int NP, int NM, class Real, class S, int FEAT, bool ALL>
+__device__ __forceinline__ void centre_term(const StepArgs<Real, NP, NM>& g, const DiffPrm<S, NP*(NP - 1) / 2>& dp,
+                                            const S* ph, const S (*gcr)[DIM], uint32_t mask, S* Gc) {
+  S gc[NP][DIM];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    if (!ALL && !((mask >> a) & 1u)) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) gc[a][d] = S(Real(0));
+      continue;
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) gc[a][d] = gcr[a][d] * g.half_inv_dx;
+  }
+  int p = 0;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int b = a + 1; b < NP; ++b, ++p) {
+      if (!ALL && !(((mask >> a) & (mask >> b)) & 1u)) continue;
+      S q[DIM], gq[DIM];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) q[d] = ph[a] * gc[b][d] - ph[b] * gc[a][d];
+      pair_grad_fwd<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, (FEAT & kFeatRot) && g.rotated[p] != 0,
+                         g.rot[p], gq);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        Gc[a] += gq[d] * gc[b][d];
+        Gc[b] -= gq[d] * gc[a][d];
+      }
+    }
+  }
+}
+
 // S1-S3 of the cell update: divergence of the face fluxes and the centre
 // term.  ALL: every phase is present in the stencil region and some present
 // pair is anisotropic (the row's mask says so), so no per-phase or per-pair
@@ -425,36 +462,126 @@ __device__ __forceinline__ void gradient_terms(const Acc& A, const StepArgs<Real
       for (int a = 0; a < NP; ++a) divJ[a] += (Jp[a] - Jm[a]) * g.inv_dx;
     }
   }
-  // centre term, central differences
-  S gc[NP][DIM];
+  centre_term<DIM, NP, NM, Real, S, FEAT, ALL>(g, dp, ph, gcr, mask, Gc);
+}
+
+// S4-S5 of the cell update from the gradient terms: the potential
+// derivative, the driving force, the rate of Eq. (phi_eqn) / (tau eps), the
+// explicit Euler step and the projection.  ph, mc: the cell's phi^n and mu^n;
+// divJ, Gc: divergence of the face fluxes and the centre term; s = T - T_ref.
+template <int DIM, int NP, int NM, class Real, class S, int FEAT = kFeatAll>
+__device__ __forceinline__ void phase_update(const StepArgs<Real, NP, NM>& g, const DiffPrm<S, NP*(NP - 1) / 2>& dp,
+                                             const S* ph, const S* mc, const S* divJ, const S* Gc, Real s,
+                                             unsigned long long gcell, S* pn) {
+  const bool gg = (FEAT & kFeatGG) && g.gg;
+  // S4: potential derivative
+  S W[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
-    if (!ALL && !((mask >> a) & 1u)) {
+    W[a] = S(Real(0));
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) gc[a][d] = S(Real(0));
-      continue;
+    for (int b = 0; b < NP; ++b) {
+      if (b == a) continue;
+      if (g.potential == 1)
+        W[a] += g.cw[a][b] * ph[b];
+      else
+        W[a] += g.cw[a][b] * (ph[a] * (ph[b] * ph[b]));
     }
+    if ((FEAT & kFeatG3) && g.has_g3) {
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) gc[a][d] = gcr[a][d] * g.half_inv_dx;
+      for (int b = 0; b < NP; ++b)
+#pragma unroll
+        for (int e = b + 1; e < NP; ++e)
+          if (b != a && e != a) W[a] += g.g3[a][b][e] * (ph[b] * ph[e]);
+    }
   }
-  int p = 0;
+  // S4: driving force sum_b psi^b dh_b/dphi_a
+  S psi[NP];
+#pragma unroll
+  for (int b = 0; b < NP; ++b) psi[b] = gg ? S(Real(0)) : grand_potential<NP, NM, Real>(g, b, mc, s);
+  if ((FEAT & kFeatElastic) && g.elw) {   // elasticity: -sigma : eps*^b joins each phase potential
+    const unsigned long long cell = gcell - (unsigned long long)g.zorg * (DIM == 3 ? (unsigned long long)g.nx * g.ny : g.nx);
+    const unsigned long long cells = (unsigned long long)g.nx * g.ny * (DIM == 3 ? g.nz : 1);
+#pragma unroll
+    for (int b = 0; b < NP; ++b) psi[b] = psi[b] + g.elw[b * cells + cell];
+  }
+  S e1 = ph[0];
+#pragma unroll
+  for (int a = 1; a < NP; ++a) e1 += ph[a];
+  S e2 = S(Real(0));
+  {
+    S run = ph[0];
+#pragma unroll
+    for (int a = 1; a < NP; ++a) {
+      e2 += ph[a] * run;
+      run += ph[a];
+    }
+  }
+  S v[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
+    S rest = e2 - ph[a] * (e1 - ph[a]);
+    S P = psi[a] * (Real(6) * ph[a] - Real(6) * (ph[a] * ph[a]) + Real(2) * rest);
 #pragma unroll
-    for (int b = a + 1; b < NP; ++b, ++p) {
-      if (!ALL && !(((mask >> a) & (mask >> b)) & 1u)) continue;
-      S q[DIM], gq[DIM];
+    for (int b = 0; b < NP; ++b) {
+      if (b == a) continue;
+      P += psi[b] * (Real(2) * ph[b] * ((e1 - ph[a]) - ph[b]));
+    }
+    // S5: rate of Eq. (phi_eqn) / (tau eps), explicit Euler
+    S r = dp.mob * ((g.eps * (divJ[a] - Gc[a]) - W[a] * g.inv_eps - P) * g.inv_eps);
+    v[a] = ph[a] + g.dt * r;
+    // phi noise on the interface phases of the cell (0 < phi_a < 1)
+    if ((FEAT & kFeatNoise) && g.noise_amp != Real(0) && val(ph[a]) > Real(0) && val(ph[a]) < Real(1))
+      v[a] = v[a] + g.dt * g.noise_amp * noise_variate<Real>(g.noise_seed, g.step, gcell * NP + a);
+  }
+  project<NP>(g.potential, v, pn);
+}
+
+// S7 of the cell update from the flux divergence div = sum_faces M_f grad mu:
+// the mu step of Eq. (Mu_explicit_temperature) with chi(h(phi^{n+1})),
+// c^a(mu^n) and dh/dt, dT/dt as one-step differences.  bulk: phi^{n+1} =
+// phi^n (no dh term).
+template <int NP, int NM, class Real, class S>
+__device__ __forceinline__ void mu_update(const StepArgs<Real, NP, NM>& g, const S* ph, const S* pn, const S* mc,
+                                          const S* div, Real s, bool bulk, S* mn) {
+  S h_new[NP];
+  interp_h<NP>(pn, h_new);
+  S rhs[NM];
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) q[d] = ph[a] * gc[b][d] - ph[b] * gc[a][d];
-      pair_grad_fwd<DIM>(q, g.gam2[p], dp.delta[p], g.aniso[p] != 0, (FEAT & kFeatRot) && g.rotated[p] != 0,
-                         g.rot[p], gq);
+  for (int i = 0; i < NM; ++i) rhs[i] = g.dt * div[i];
+  if (!bulk) {
+    S h_old[NP];
+    interp_h<NP>(ph, h_old);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        Gc[a] += gq[d] * gc[b][d];
-        Gc[b] -= gq[d] * gc[a][d];
+    for (int a = 0; a < NP; ++a) {
+      S dh = h_new[a] - h_old[a];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        S c_now = S(Real(0));
+#pragma unroll
+        for (int j = 0; j < NM; ++j)
+          c_now += g.chi[a][i * NM + j] * (mc[j] - (g.B0[a][j] + g.B1[a][j] * s));
+        rhs[i] -= c_now * dh;
+        rhs[i] -= h_new[a] * g.dcT[a][i];
       }
     }
+  } else {
+#pragma unroll
+    for (int a = 0; a < NP; ++a)
+#pragma unroll
+      for (int i = 0; i < NM; ++i) rhs[i] -= h_new[a] * g.dcT[a][i];
   }
+  S chi[NM * NM];
+#pragma unroll
+  for (int k = 0; k < NM * NM; ++k) {
+    chi[k] = h_new[0] * g.chi[0][k];
+#pragma unroll
+    for (int a = 1; a < NP; ++a) chi[k] += h_new[a] * g.chi[a][k];
+  }
+  S dmu[NM];
+  solve_small<NM>(chi, rhs, dmu);
+#pragma unroll
+  for (int i = 0; i < NM; ++i) mn[i] = mc[i] + dmu[i];
 }
 
 // The full cell update.  kz = cell index along the last axis (for T).
@@ -509,67 +636,7 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
         gradient_terms<DIM, NP, NM, Real, S, Acc, FEAT, false>(A, g, dp, ph, mask, need_tan, divJ, Gc);
       }
     }
-    // S4: potential derivative
-    S W[NP];
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      W[a] = S(Real(0));
-#pragma unroll
-      for (int b = 0; b < NP; ++b) {
-        if (b == a) continue;
-        if (g.potential == 1)
-          W[a] += g.cw[a][b] * ph[b];
-        else
-          W[a] += g.cw[a][b] * (ph[a] * (ph[b] * ph[b]));
-      }
-      if ((FEAT & kFeatG3) && g.has_g3) {
-#pragma unroll
-        for (int b = 0; b < NP; ++b)
-#pragma unroll
-          for (int e = b + 1; e < NP; ++e)
-            if (b != a && e != a) W[a] += g.g3[a][b][e] * (ph[b] * ph[e]);
-      }
-    }
-    // S4: driving force sum_b psi^b dh_b/dphi_a
-    S psi[NP];
-#pragma unroll
-    for (int b = 0; b < NP; ++b) psi[b] = gg ? S(Real(0)) : grand_potential<NP, NM, Real>(g, b, mc, s);
-    if ((FEAT & kFeatElastic) && g.elw) {   // elasticity: -sigma : eps*^b joins each phase potential
-      const unsigned long long cell = gcell - (unsigned long long)g.zorg * (DIM == 3 ? (unsigned long long)g.nx * g.ny : g.nx);
-      const unsigned long long cells = (unsigned long long)g.nx * g.ny * (DIM == 3 ? g.nz : 1);
-#pragma unroll
-      for (int b = 0; b < NP; ++b) psi[b] = psi[b] + g.elw[b * cells + cell];
-    }
-    S e1 = ph[0];
-#pragma unroll
-    for (int a = 1; a < NP; ++a) e1 += ph[a];
-    S e2 = S(Real(0));
-    {
-      S run = ph[0];
-#pragma unroll
-      for (int a = 1; a < NP; ++a) {
-        e2 += ph[a] * run;
-        run += ph[a];
-      }
-    }
-    S v[NP];
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      S rest = e2 - ph[a] * (e1 - ph[a]);
-      S P = psi[a] * (Real(6) * ph[a] - Real(6) * (ph[a] * ph[a]) + Real(2) * rest);
-#pragma unroll
-      for (int b = 0; b < NP; ++b) {
-        if (b == a) continue;
-        P += psi[b] * (Real(2) * ph[b] * ((e1 - ph[a]) - ph[b]));
-      }
-      // S5: rate of Eq. (phi_eqn) / (tau eps), explicit Euler
-      S r = dp.mob * ((g.eps * (divJ[a] - Gc[a]) - W[a] * g.inv_eps - P) * g.inv_eps);
-      v[a] = ph[a] + g.dt * r;
-      // phi noise on the interface phases of the cell (0 < phi_a < 1)
-      if ((FEAT & kFeatNoise) && g.noise_amp != Real(0) && val(ph[a]) > Real(0) && val(ph[a]) < Real(1))
-        v[a] = v[a] + g.dt * g.noise_amp * noise_variate<Real>(g.noise_seed, g.step, gcell * NP + a);
-    }
-    project<NP>(g.potential, v, pn);
+    phase_update<DIM, NP, NM, Real, S, FEAT>(g, dp, ph, mc, divJ, Gc, s, gcell, pn);
   }
   if (gg) {   // grain growth: mu held
 #pragma unroll
@@ -578,8 +645,6 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
   }
 
   // ---- S6/S7: chemical-potential update
-  S h_new[NP];
-  interp_h<NP>(pn, h_new);
   S Mc[NM * NM];
   if constexpr (!(FEAT & kFeatSolidD) && std::is_same<S, Real>::value) {
     S phc[NP];
@@ -636,42 +701,7 @@ __device__ __forceinline__ void gp_cell(const Acc& A, const StepArgs<Real, NP, N
       }
     }
   }
-  S rhs[NM];
-#pragma unroll
-  for (int i = 0; i < NM; ++i) rhs[i] = g.dt * div[i];
-  if (!bulk) {
-    S h_old[NP];
-    interp_h<NP>(ph, h_old);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      S dh = h_new[a] - h_old[a];
-#pragma unroll
-      for (int i = 0; i < NM; ++i) {
-        S c_now = S(Real(0));
-#pragma unroll
-        for (int j = 0; j < NM; ++j)
-          c_now += g.chi[a][i * NM + j] * (mc[j] - (g.B0[a][j] + g.B1[a][j] * s));
-        rhs[i] -= c_now * dh;
-        rhs[i] -= h_new[a] * g.dcT[a][i];
-      }
-    }
-  } else {
-#pragma unroll
-    for (int a = 0; a < NP; ++a)
-#pragma unroll
-      for (int i = 0; i < NM; ++i) rhs[i] -= h_new[a] * g.dcT[a][i];
-  }
-  S chi[NM * NM];
-#pragma unroll
-  for (int k = 0; k < NM * NM; ++k) {
-    chi[k] = h_new[0] * g.chi[0][k];
-#pragma unroll
-    for (int a = 1; a < NP; ++a) chi[k] += h_new[a] * g.chi[a][k];
-  }
-  S dmu[NM];
-  solve_small<NM>(chi, rhs, dmu);
-#pragma unroll
-  for (int i = 0; i < NM; ++i) mn[i] = mc[i] + dmu[i];
+  mu_update<NP, NM, Real, S>(g, ph, pn, mc, div, s, bulk, mn);
 }
 
 // ------------------------------------------------------------------------

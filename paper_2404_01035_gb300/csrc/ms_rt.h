@@ -30,6 +30,7 @@ struct AdjointStore {
   void* seg = nullptr;         // recompute buffer: `every` states
   size_t seg_bytes = 0;
   void* adj[2] = {nullptr, nullptr};   // adjoint state ping-pong (padded)
+  void* tbar = nullptr;        // per-cell adjoints of the step's tail inputs (reverse pass 1 -> 2)
   double* gpart = nullptr;     // per-block FP64 gradient partials
   int gblocks = 0;
   double* gsum = nullptr;      // accumulated parameter gradients (device)
