@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(128) k_adj_cell(const Real* __restrict__ st, c
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
       }
-      if (threadIdx.x == 0) partials[blockIdx.x * NPRM + k] = red[0];
+      if (threadIdx.x == 0) partials[blockIdx.x * NPRM + k] += red[0];   // summed over the reverse steps
       __syncthreads();
     }
   }
@@ -332,169 +332,204 @@ __device__ __forceinline__ void gather_faces(const Real* __restrict__ st, const 
   }
 }
 
-// Pass 2 (see the file comment).
+// Pass 2 (see the file comment).  A block covers 32 cells with DIM + 1
+// warps: warp w < DIM gathers the face fluxes along axis w, warp DIM the
+// centre terms, the mu flux and the direct part; the parts are summed in
+// warp order through shared memory (deterministic).
+template <int DIM>
+struct GatherShape {
+  static constexpr int PARTS = DIM + 1;
+  static constexpr int THREADS = 32 * PARTS;
+};
+
 template <int DIM, int NP, int NM, class Real>
-__global__ void __launch_bounds__(128) k_adj_gather(const Real* __restrict__ st, const Real* __restrict__ tbar,
-                                                    Real* __restrict__ lam_out,
-                                                    const __grid_constant__ StepArgs<Real, NP, NM> g) {
+__global__ void __launch_bounds__(GatherShape<DIM>::THREADS)
+    k_adj_gather(const Real* __restrict__ st, const Real* __restrict__ tbar, Real* __restrict__ lam_out,
+                 const __grid_constant__ StepArgs<Real, NP, NM> g) {
   constexpr int NF = NP + NM;
   constexpr int P = NP * (NP - 1) / 2;
+  constexpr int PARTS = GatherShape<DIM>::PARTS;
   using TS = TailSlots<NP, NM>;
   using DN = Dual<Real, NP>;
+  __shared__ Real s_acc[PARTS - 1][NF][32];
+  const int part = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long cells = (long long)g.nx * g.ny * g.nz;
   const long long plane = (long long)g.nyp * g.pitch;
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (j >= cells) return;
-  const int x = (int)(j % g.nx), y = (int)((j / g.nx) % g.ny), z = (int)(j / ((long long)g.nx * g.ny));
-  const long long jb = padded_index<DIM>(g, x, y, z);
-  auto dense = [&](int px, int py, int pz) { return ((long long)pz * g.ny + py) * g.nx + px; };
-  const bool need_tan = any_aniso<DIM>(g.aniso, P);
+  const long long j = blockIdx.x * 32ll + lane;
+  const bool live = j < cells;
   Real acc[NF];
 #pragma unroll
-  for (int a = 0; a < NP; ++a) acc[a] = tbar[(TS::PH + a) * cells + j];
+  for (int f = 0; f < NF; ++f) acc[f] = Real(0);
+  if (live) {
+    const int x = (int)(j % g.nx), y = (int)((j / g.nx) % g.ny), z = (int)(j / ((long long)g.nx * g.ny));
+    const long long jb = padded_index<DIM>(g, x, y, z);
+    auto dense = [&](int px, int py, int pz) { return ((long long)pz * g.ny + py) * g.nx + px; };
+    const bool need_tan = any_aniso<DIM>(g.aniso, P);
+    Real phj[NP], muj[NM], Mj[NM * NM], Mbar[NM * NM];
+    if (part == DIM) {
 #pragma unroll
-  for (int k = 0; k < NM; ++k) acc[NP + k] = tbar[(TS::MC + k) * cells + j];
-  Real phj[NP], muj[NM], Mj[NM * NM], Mbar[NM * NM];
+      for (int a = 0; a < NP; ++a) {
+        acc[a] = tbar[(TS::PH + a) * cells + j];
+        phj[a] = st[a * g.fstride + jb];
+      }
 #pragma unroll
-  for (int a = 0; a < NP; ++a) phj[a] = st[a * g.fstride + jb];
+      for (int k = 0; k < NM; ++k) {
+        acc[NP + k] = tbar[(TS::MC + k) * cells + j];
+        muj[k] = st[(NP + k) * g.fstride + jb];
+      }
+      cell_mobility<NP, NM>(phj, g.DX, Mj);
 #pragma unroll
-  for (int k = 0; k < NM; ++k) muj[k] = st[(NP + k) * g.fstride + jb];
-  cell_mobility<NP, NM>(phj, g.DX, Mj);
+      for (int k = 0; k < NM * NM; ++k) Mbar[k] = Real(0);
+    }
+    DiffPrm<DN, P> dpn;
+    dpn.mob = DN(g.mob);
 #pragma unroll
-  for (int k = 0; k < NM * NM; ++k) Mbar[k] = Real(0);
-  DiffPrm<DN, P> dpn;
-  dpn.mob = DN(g.mob);
-#pragma unroll
-  for (int p = 0; p < P; ++p) dpn.delta[p] = DN(g.delta[p]);
+    for (int p = 0; p < P; ++p) dpn.delta[p] = DN(g.delta[p]);
 
-  // positions holding cell j's value: itself and its ghost images
-  int xs[3], ys[3], zs[3], nxs = 1, nys = 1, nzs = 1;
-  xs[0] = x;
-  ys[0] = y;
-  zs[0] = z;
-  if (x == 0) xs[nxs++] = g.bc[0] == 3 ? g.nx : -1;
-  if (x == g.nx - 1) xs[nxs++] = g.bc[0] == 3 ? -1 : g.nx;
-  if (y == 0) ys[nys++] = g.bc[1] == 3 ? g.ny : -1;
-  if (y == g.ny - 1) ys[nys++] = g.bc[1] == 3 ? -1 : g.ny;
-  if (DIM == 3) {
-    if (z == 0) zs[nzs++] = g.bc[2] == 3 ? g.nz : -1;
-    if (z == g.nz - 1) zs[nzs++] = g.bc[2] == 3 ? -1 : g.nz;
-  }
+    // positions holding cell j's value: itself and its ghost images
+    int xs[3], ys[3], zs[3], nxs = 1, nys = 1, nzs = 1;
+    xs[0] = x;
+    ys[0] = y;
+    zs[0] = z;
+    if (x == 0) xs[nxs++] = g.bc[0] == 3 ? g.nx : -1;
+    if (x == g.nx - 1) xs[nxs++] = g.bc[0] == 3 ? -1 : g.nx;
+    if (y == 0) ys[nys++] = g.bc[1] == 3 ? g.ny : -1;
+    if (y == g.ny - 1) ys[nys++] = g.bc[1] == 3 ? -1 : g.ny;
+    if (DIM == 3) {
+      if (z == 0) zs[nzs++] = g.bc[2] == 3 ? g.nz : -1;
+      if (z == g.nz - 1) zs[nzs++] = g.bc[2] == 3 ? -1 : g.nz;
+    }
 #pragma unroll 1
-  for (int iz = 0; iz < nzs; ++iz)
+    for (int iz = 0; iz < nzs; ++iz)
 #pragma unroll 1
-    for (int iy = 0; iy < nys; ++iy)
+      for (int iy = 0; iy < nys; ++iy)
 #pragma unroll 1
-      for (int ix = 0; ix < nxs; ++ix) {
-        const int px = xs[ix], py = ys[iy], pz = zs[iz];
-        const long long seed = padded_index<DIM>(g, px, py, pz);
-        // face fluxes
-        gather_faces<DIM, 0, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
-        gather_faces<DIM, 1, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
-        if constexpr (DIM == 3) gather_faces<DIM, 2, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
-        // centre terms of the cells whose central differences (or own phi) read p
+        for (int ix = 0; ix < nxs; ++ix) {
+          const int px = xs[ix], py = ys[iy], pz = zs[iz];
+          const long long seed = padded_index<DIM>(g, px, py, pz);
+          if (part == 0) gather_faces<DIM, 0, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
+          if (part == 1) gather_faces<DIM, 1, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
+          if constexpr (DIM == 3)
+            if (part == 2) gather_faces<DIM, 2, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
+          if (part != DIM) continue;
+          // centre terms of the cells whose central differences (or own phi) read p
 #pragma unroll 1
-        for (int c = 0; c < 1 + 2 * DIM; ++c) {
-          int cx = px, cy = py, cz = pz;
-          if (c > 0) {
-            const int d = (c - 1) >> 1, sgn = (c & 1) ? 1 : -1;
-            if (d == 0) cx += sgn;
-            if (d == 1) cy += sgn;
-            if (d == 2) cz += sgn;
+          for (int c = 0; c < 1 + 2 * DIM; ++c) {
+            int cx = px, cy = py, cz = pz;
+            if (c > 0) {
+              const int d = (c - 1) >> 1, sgn = (c & 1) ? 1 : -1;
+              if (d == 0) cx += sgn;
+              if (d == 1) cy += sgn;
+              if (d == 2) cz += sgn;
+            }
+            if (!in_grid<DIM>(g, cx, cy, cz)) continue;
+            const long long ci = dense(cx, cy, cz);
+            SeedAcc<NP, NM, Real> A{st, g.fstride, plane, padded_index<DIM>(g, cx, cy, cz), seed, g.pitch};
+            DN ph[NP], gcr[NP][DIM], Gc[NP];
+#pragma unroll
+            for (int a = 0; a < NP; ++a) {
+              ph[a] = A.phi(a, 0, 0, 0);
+              gcr[a][0] = A.phi(a, 1, 0, 0) - A.phi(a, -1, 0, 0);
+              gcr[a][1] = A.phi(a, 0, 1, 0) - A.phi(a, 0, -1, 0);
+              if constexpr (DIM == 3) gcr[a][2] = A.phi(a, 0, 0, 1) - A.phi(a, 0, 0, -1);
+              Gc[a] = DN(Real(0));
+            }
+            centre_term<DIM, NP, NM, Real, DN, kFeatAll, false>(g, dpn, ph, gcr, A.mask(), Gc);
+#pragma unroll
+            for (int a = 0; a < NP; ++a) {
+              const Real gb = tbar[(TS::GC + a) * cells + ci];
+#pragma unroll
+              for (int b = 0; b < NP; ++b) acc[b] += gb * Gc[a].d[b];
+            }
           }
-          if (!in_grid<DIM>(g, cx, cy, cz)) continue;
-          const long long ci = dense(cx, cy, cz);
-          SeedAcc<NP, NM, Real> A{st, g.fstride, plane, padded_index<DIM>(g, cx, cy, cz), seed, g.pitch};
-          DN ph[NP], gcr[NP][DIM], Gc[NP];
-#pragma unroll
-          for (int a = 0; a < NP; ++a) {
-            ph[a] = A.phi(a, 0, 0, 0);
-            gcr[a][0] = A.phi(a, 1, 0, 0) - A.phi(a, -1, 0, 0);
-            gcr[a][1] = A.phi(a, 0, 1, 0) - A.phi(a, 0, -1, 0);
-            if constexpr (DIM == 3) gcr[a][2] = A.phi(a, 0, 0, 1) - A.phi(a, 0, 0, -1);
-            Gc[a] = DN(Real(0));
-          }
-          centre_term<DIM, NP, NM, Real, DN, kFeatAll, false>(g, dpn, ph, gcr, A.mask(), Gc);
-#pragma unroll
-          for (int a = 0; a < NP; ++a) {
-            const Real gb = tbar[(TS::GC + a) * cells + ci];
-#pragma unroll
-            for (int b = 0; b < NP; ++b) acc[b] += gb * Gc[a].d[b];
-          }
-        }
-        // mu flux of the in-grid neighbours i = p - o: p is their neighbour at o
+          // mu flux of the in-grid neighbours i = p - o: p is their neighbour at o
 #pragma unroll 1
-        for (int c = 0; c < 2 * DIM; ++c) {
-          const int d = c >> 1, sgn = (c & 1) ? 1 : -1;
-          const int ix2 = px - (d == 0 ? sgn : 0), iy2 = py - (d == 1 ? sgn : 0), iz2 = pz - (d == 2 ? sgn : 0);
-          if (!in_grid<DIM>(g, ix2, iy2, iz2)) continue;
-          const long long ii = dense(ix2, iy2, iz2), ib = padded_index<DIM>(g, ix2, iy2, iz2);
-          Real phi_i[NP], Mi[NM * NM];
+          for (int c = 0; c < 2 * DIM; ++c) {
+            const int d = c >> 1, sgn = (c & 1) ? 1 : -1;
+            const int ix2 = px - (d == 0 ? sgn : 0), iy2 = py - (d == 1 ? sgn : 0), iz2 = pz - (d == 2 ? sgn : 0);
+            if (!in_grid<DIM>(g, ix2, iy2, iz2)) continue;
+            const long long ii = dense(ix2, iy2, iz2), ib = padded_index<DIM>(g, ix2, iy2, iz2);
+            Real phi_i[NP], Mi[NM * NM];
 #pragma unroll
-          for (int a = 0; a < NP; ++a) phi_i[a] = st[a * g.fstride + ib];
-          cell_mobility<NP, NM>(phi_i, g.DX, Mi);
+            for (int a = 0; a < NP; ++a) phi_i[a] = st[a * g.fstride + ib];
+            cell_mobility<NP, NM>(phi_i, g.DX, Mi);
 #pragma unroll
-          for (int r = 0; r < NM; ++r) {
-            const Real db = tbar[(TS::DIV + r) * cells + ii];
+            for (int r = 0; r < NM; ++r) {
+              const Real db = tbar[(TS::DIV + r) * cells + ii];
 #pragma unroll
-            for (int q = 0; q < NM; ++q) {
-              const Real mci = st[(NP + q) * g.fstride + ib];
-              acc[NP + q] += db * (Real(0.5) * (Mi[r * NM + q] + Mj[r * NM + q])) * g.inv_dx2;
-              Mbar[r * NM + q] += db * (Real(0.5) * (muj[q] - mci)) * g.inv_dx2;
+              for (int q = 0; q < NM; ++q) {
+                const Real mci = st[(NP + q) * g.fstride + ib];
+                acc[NP + q] += db * (Real(0.5) * (Mi[r * NM + q] + Mj[r * NM + q])) * g.inv_dx2;
+                Mbar[r * NM + q] += db * (Real(0.5) * (muj[q] - mci)) * g.inv_dx2;
+              }
             }
           }
         }
-      }
-  // mu flux of cell j itself (its own mu and mobility at the centre)
-  {
-    Real db[NM];
+    if (part == DIM) {
+      // mu flux of cell j itself (its own mu and mobility at the centre)
+      Real db[NM];
 #pragma unroll
-    for (int r = 0; r < NM; ++r) db[r] = tbar[(TS::DIV + r) * cells + j];
+      for (int r = 0; r < NM; ++r) db[r] = tbar[(TS::DIV + r) * cells + j];
 #pragma unroll 1
-    for (int c = 0; c < 2 * DIM; ++c) {
-      const int d = c >> 1, sgn = (c & 1) ? 1 : -1;
-      const long long nb = jb + (d == 0 ? sgn : 0) + (d == 1 ? (long long)sgn * g.pitch : 0) +
-                           (d == 2 ? (long long)sgn * plane : 0);
-      Real phn[NP], Mn[NM * NM];
+      for (int c = 0; c < 2 * DIM; ++c) {
+        const int d = c >> 1, sgn = (c & 1) ? 1 : -1;
+        const long long nb = jb + (d == 0 ? sgn : 0) + (d == 1 ? (long long)sgn * g.pitch : 0) +
+                             (d == 2 ? (long long)sgn * plane : 0);
+        Real phn[NP], Mn[NM * NM];
 #pragma unroll
-      for (int a = 0; a < NP; ++a) phn[a] = st[a * g.fstride + nb];
-      cell_mobility<NP, NM>(phn, g.DX, Mn);
+        for (int a = 0; a < NP; ++a) phn[a] = st[a * g.fstride + nb];
+        cell_mobility<NP, NM>(phn, g.DX, Mn);
 #pragma unroll
-      for (int r = 0; r < NM; ++r)
+        for (int r = 0; r < NM; ++r)
 #pragma unroll
-        for (int q = 0; q < NM; ++q) {
-          const Real mun = st[(NP + q) * g.fstride + nb];
-          acc[NP + q] -= db[r] * (Real(0.5) * (Mj[r * NM + q] + Mn[r * NM + q])) * g.inv_dx2;
-          Mbar[r * NM + q] += db[r] * (Real(0.5) * (mun - muj[q])) * g.inv_dx2;
-        }
+          for (int q = 0; q < NM; ++q) {
+            const Real mun = st[(NP + q) * g.fstride + nb];
+            acc[NP + q] -= db[r] * (Real(0.5) * (Mj[r * NM + q] + Mn[r * NM + q])) * g.inv_dx2;
+            Mbar[r * NM + q] += db[r] * (Real(0.5) * (mun - muj[q])) * g.inv_dx2;
+          }
+      }
+      // M(phi_j): chain the mobility adjoint to the phases
+      DN ph[NP], M[NM * NM];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        ph[a] = DN(phj[a]);
+        ph[a].d[a] = Real(1);
+      }
+      cell_mobility<NP, NM>(ph, g.DX, M);
+#pragma unroll
+      for (int k = 0; k < NM * NM; ++k)
+#pragma unroll
+        for (int b = 0; b < NP; ++b) acc[b] += Mbar[k] * M[k].d[b];
     }
   }
-  // M(phi_j): chain the mobility adjoint to the phases
-  {
-    DN ph[NP], M[NM * NM];
+  if (part > 0) {
 #pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      ph[a] = DN(phj[a]);
-      ph[a].d[a] = Real(1);
-    }
-    cell_mobility<NP, NM>(ph, g.DX, M);
-#pragma unroll
-    for (int k = 0; k < NM * NM; ++k)
-#pragma unroll
-      for (int b = 0; b < NP; ++b) acc[b] += Mbar[k] * M[k].d[b];
+    for (int f = 0; f < NF; ++f) s_acc[part - 1][f][lane] = acc[f];
   }
+  __syncthreads();
+  if (part == 0 && live) {
 #pragma unroll
-  for (int f = 0; f < NF; ++f) lam_out[f * cells + j] = acc[f];
+    for (int f = 0; f < NF; ++f) {
+      Real v = acc[f];
+#pragma unroll
+      for (int q = 0; q < PARTS - 1; ++q) v += s_acc[q][f][lane];
+      lam_out[f * cells + j] = v;
+    }
+  }
 }
 
-// gsum[k] += sum over blocks of partials[b][k], in block order (deterministic).
+// gsum[k] += sum over blocks of partials[b][k]: one warp per parameter, lane
+// l summing blocks l, l + 32, ... in order, then a fixed shuffle tree
+// (deterministic).
 __global__ void k_accumulate_params(const double* __restrict__ partials, int nblocks, int nprm,
                                     double* __restrict__ gsum) {
-  const int k = threadIdx.x;
+  const int k = blockIdx.x, lane = threadIdx.x;
   if (k >= nprm) return;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partials[b * nprm + k];
-  gsum[k] += s;
+  for (int b = lane; b < nblocks; b += 32) s += partials[(long long)b * nprm + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) gsum[k] += s;
 }
 
 struct AdjKernel {
@@ -521,8 +556,8 @@ cudaError_t launch_adjoint(const void* state, const void* lam_in, void* lam_out,
                                                         reinterpret_cast<Real*>(tbar), g, ex, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_adj_gather<DIM, NP, NM, Real><<<blocks, 128, 0, st>>>(s, reinterpret_cast<const Real*>(tbar),
-                                                          reinterpret_cast<Real*>(lam_out), g);
+  k_adj_gather<DIM, NP, NM, Real><<<(unsigned)((cells + 31) / 32), GatherShape<DIM>::THREADS, 0, st>>>(
+      s, reinterpret_cast<const Real*>(tbar), reinterpret_cast<Real*>(lam_out), g);
   return cudaGetLastError();
 }
 
@@ -669,6 +704,7 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
               : cudaMemsetAsync(mu_part, 0, (size_t)m.NM * cells * s, st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(A.gsum, 0, sizeof(double) * 64, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A.gpart, 0, sizeof(double) * (size_t)blocks * nprm, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint seeding");
   int cur = 0;
   const int cur_state = c->cur;
@@ -702,10 +738,12 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
       e = ak->launch(slots + (size_t)k * c->state_bytes, A.adj[cur], A.adj[1 - cur], A.tbar, c->args.data(), m,
                      t, A.gpart, st);
       if (e != cudaSuccess) return cuda_fail(c, e, "adjoint step");
-      k_accumulate_params<<<1, 64, 0, st>>>(A.gpart, blocks, nprm, A.gsum);
       cur = 1 - cur;
     }
   }
+  k_accumulate_params<<<nprm, 32, 0, st>>>(A.gpart, blocks, nprm, A.gsum);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "gradient reduction");
   // the recompute used both code buffers: restore the current state's codes
   {
     ms_status rs = refresh_codes(c);
