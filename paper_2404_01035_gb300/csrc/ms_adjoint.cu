@@ -9,24 +9,26 @@
 // The step of cell i is a stencil part -- the face-flux divergence divJ_i,
 // the centre term Gc_i, the mu flux divergence div_i -- followed by a tail
 // that is local to the cell (potential, driving force, rate, projection, mu
-// update).  The reverse step runs in two passes:
-//   1. k_adj_cell, one thread per cell i: the tail is evaluated once in
-//      forward mode with one derivative slot per tail input (phi_i, mu_i,
-//      divJ_i, Gc_i, div_i, 1/tau) and contracted with lambda_i, which gives
-//      the adjoints of those inputs (tbar_i).  The stencil part is evaluated
-//      with derivative slots on delta (divJ, Gc) and on D (div), so the
-//      parameter gradient of the cell follows from tbar_i at once.
-//   2. k_adj_gather, one thread per input cell j: lambda_j^n is tbar_j's
-//      direct part plus, for every position p holding j's value (j and its
-//      ghost images), the transpose of each stencil part that reads p: every
-//      face whose stencil contains p (its flux adjoint is
-//      (tbar_divJ(L) - tbar_divJ(R)) / dx for the cells L, R it separates),
-//      every centre term reading p, and the mu flux terms (hand-written: div
-//      is linear in mu and in the cell mobilities M(phi)).  The face fluxes and
-//      centre terms are differentiated in forward mode with one slot per phase
-//      at the seeded position; nothing is accumulated with atomics, so the
-//      result is deterministic.
-// Parameter partials are reduced per block in FP64 and summed in block order.
+// update).  The reverse step runs in three passes, none with atomics (the
+// result is deterministic):
+//   1. k_adj_cell, per cell i: the tail once in forward mode with one
+//      derivative slot per tail input (phi_i, mu_i, divJ_i, Gc_i, div_i,
+//      1/tau), contracted with lambda_i: the adjoints of those inputs.  The
+//      centre term's Jacobian in phi_i and in the central differences it
+//      reads turns the Gc_i adjoint into adjoints of those differences.  The
+//      stencil parts carry slots on delta (divJ, Gc) and on D (div), so the
+//      cell's parameter gradient follows at once.
+//   2. k_adj_faces, per face: the flux adjoint (adj divJ(L) - adj divJ(R)) / dx
+//      of the two cells it separates, through the face flux differentiated in
+//      its face values and face gradients, gives one adjoint per place in the
+//      face's stencil (L, R, and the tangential neighbours).
+//   3. k_adj_gather, per input cell j: lambda_j^n is the direct part plus, for
+//      j and each ghost image of it, the face records and the central
+//      differences that read the position, and the transposed mu flux
+//      (written out by hand: div is linear in mu and in the cell mobilities,
+//      chained through M(phi_j) once).
+// Parameter partials are reduced per block in FP64, summed over the reverse
+// steps in place and over the blocks in a fixed order at the end.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,15 +52,43 @@ struct AdjExtra {
   Real D[NP][NM * NM];
 };
 
-// Tail inputs of one cell, in the order of the derivative slots of pass 1
-// (the first TB of them are stored per cell for pass 2).
+// Tail inputs of one cell, in the order of the derivative slots of pass 1.
 template <int NP, int NM>
 struct TailSlots {
   static constexpr int PH = 0, MC = NP, DJ = NP + NM, GC = 2 * NP + NM, DIV = 3 * NP + NM;
-  static constexpr int TB = 3 * NP + 2 * NM;   // stored adjoints per cell
-  static constexpr int MOB = TB;               // the mobility slot (pass 1 only)
-  static constexpr int T = TB + 1;
+  static constexpr int MOB = 3 * NP + 2 * NM;   // the mobility slot
+  static constexpr int T = MOB + 1;
 };
+
+// Per-cell adjoints stored by pass 1 for the later passes: the cell's own phi
+// (tail and centre term) and mu, divJ (for the face fluxes), the unscaled
+// central differences gcr[a][d] of the centre term, and div.
+template <int DIM, int NP, int NM>
+struct CellStore {
+  static constexpr int PH = 0, MC = NP, DJ = NP + NM, GCR = 2 * NP + NM, DIV = GCR + NP * DIM;
+  static constexpr int TB = DIV + NM;
+};
+
+// Per-face adjoints of pass 2: the face's phases at its lower cell L and
+// upper cell R, and the tangential gradient of each phase along each axis t
+// != D (applied with +- 1/(4 dx) to L +- e_t and R +- e_t).
+template <int DIM, int NP>
+struct FaceStore {
+  static constexpr int AL = 0, AR = NP, TG = 2 * NP;   // TG + a (DIM - 1) + tt
+  static constexpr int N = NP * (DIM + 1);
+};
+
+// Faces along axis D, indexed by their lower cell L, whose coordinate along D
+// runs over -1 .. n_D - 1 (shifted by one).
+template <int DIM, int D, class Real, int NP, int NM>
+__device__ __forceinline__ long long face_id(const StepArgs<Real, NP, NM>& g, int lx, int ly, int lz) {
+  const long long ex = g.nx + (D == 0), ey = g.ny + (D == 1);
+  return ((long long)(lz + (D == 2)) * ey + (ly + (D == 1))) * ex + (lx + (D == 0));
+}
+
+inline long long faces_along(const HostModel& m, int D) {
+  return (long long)(m.nx + (D == 0)) * (m.ny + (D == 1)) * (m.nz + (D == 2));
+}
 
 // Stencil accessor yielding plain values as the scalar S (no derivative).
 template <int NP, int NM, class Real, class S>
@@ -245,8 +275,51 @@ __global__ void __launch_bounds__(128) k_adj_cell(const Real* __restrict__ st, c
         for (int k = 0; k < TS::T; ++k) tb[k] += l * mn[m].d[k];
       }
     }
+    // centre term transposed: slots on the cell's phi and the unscaled
+    // central differences gcr[a][d] it reads
+    {
+      using CS = CellStore<DIM, NP, NM>;
+      constexpr int WC = NP * (1 + DIM);
+      using DC = Dual<Real, WC>;
+      ValAcc<NP, NM, Real, Real> V{st, g.fstride, plane, base, g.pitch};
+      DiffPrm<DC, P> dp;
+      dp.mob = DC(g.mob);
 #pragma unroll
-    for (int k = 0; k < TS::TB; ++k) tbar[k * cells + i] = tb[k];
+      for (int p = 0; p < P; ++p) dp.delta[p] = DC(g.delta[p]);
+      DC ph[NP], gcr[NP][DIM], Gcd[NP];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        ph[a] = DC(V.phi(a, 0, 0, 0));
+        ph[a].d[a] = Real(1);
+        gcr[a][0] = DC(V.phi(a, 1, 0, 0) - V.phi(a, -1, 0, 0));
+        gcr[a][1] = DC(V.phi(a, 0, 1, 0) - V.phi(a, 0, -1, 0));
+        if constexpr (DIM == 3) gcr[a][2] = DC(V.phi(a, 0, 0, 1) - V.phi(a, 0, 0, -1));
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) gcr[a][d].d[NP + a * DIM + d] = Real(1);
+        Gcd[a] = DC(Real(0));
+      }
+      centre_term<DIM, NP, NM, Real, DC, kFeatAll, false>(g, dp, ph, gcr, V.mask(), Gcd);
+      Real sb[WC];
+#pragma unroll
+      for (int k = 0; k < WC; ++k) sb[k] = Real(0);
+#pragma unroll
+      for (int a = 0; a < NP; ++a)
+#pragma unroll
+        for (int k = 0; k < WC; ++k) sb[k] += tb[TS::GC + a] * Gcd[a].d[k];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) tbar[(CS::PH + a) * cells + i] = tb[TS::PH + a] + sb[a];
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        tbar[(CS::MC + k) * cells + i] = tb[TS::MC + k];
+        tbar[(CS::DIV + k) * cells + i] = tb[TS::DIV + k];
+      }
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        tbar[(CS::DJ + a) * cells + i] = tb[TS::DJ + a];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) tbar[(CS::GCR + a * DIM + d) * cells + i] = sb[NP + a * DIM + d];
+      }
+    }
     // parameter gradient of cell i's update
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -265,16 +338,20 @@ __global__ void __launch_bounds__(128) k_adj_cell(const Real* __restrict__ st, c
     }
   }
   if (partials) {
-    __shared__ double red[128];
+    // per warp by a fixed shuffle tree, then the 4 warps in order
+    __shared__ double red[4][NPRM];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
     for (int k = 0; k < NPRM; ++k) {
-      red[threadIdx.x] = gpar[k];
-      __syncthreads();
-      for (int w = 64; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) partials[blockIdx.x * NPRM + k] += red[0];   // summed over the reverse steps
-      __syncthreads();
+      double v = gpar[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[w][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NPRM) {
+      const int k = threadIdx.x;
+      partials[blockIdx.x * NPRM + k] += ((red[0][k] + red[1][k]) + red[2][k]) + red[3][k];   // summed over the reverse steps
     }
   }
 }
@@ -332,10 +409,150 @@ __device__ __forceinline__ void gather_faces(const Real* __restrict__ st, const 
   }
 }
 
-// Pass 2 (see the file comment).  A block covers 32 cells with DIM + 1
-// warps: warp w < DIM gathers the face fluxes along axis w, warp DIM the
-// centre terms, the mu flux and the direct part; the parts are summed in
-// warp order through shared memory (deterministic).
+// Pass 2 for the faces along axis D of one cell i: the face with lower cell
+// L = i and, at the lower domain end, the face with L = i - e_D.  The flux
+// adjoint is Jbar = (tbar_divJ(L) - tbar_divJ(R)) / dx over the cells of the
+// grid among L, R; the face flux is differentiated in forward mode with one
+// slot per face value pf_a and face gradient component gr_a,d, and the result
+// is written per stencil position class (FaceStore).
+template <int DIM, int D, int NP, int NM, class Real>
+__device__ __forceinline__ void face_adjoint(const Real* __restrict__ st, const Real* __restrict__ tbar,
+                                             Real* __restrict__ frec, const StepArgs<Real, NP, NM>& g,
+                                             bool need_tan, int lx, int ly, int lz) {
+  constexpr int P = NP * (NP - 1) / 2;
+  constexpr int W = NP * (1 + DIM);
+  using CS = CellStore<DIM, NP, NM>;
+  using FS = FaceStore<DIM, NP>;
+  using DW = Dual<Real, W>;
+  const long long cells = (long long)g.nx * g.ny * g.nz;
+  const long long plane = (long long)g.nyp * g.pitch;
+  const int rx = lx + (D == 0), ry = ly + (D == 1), rz = lz + (D == 2);
+  const bool inL = in_grid<DIM>(g, lx, ly, lz), inR = in_grid<DIM>(g, rx, ry, rz);
+  const long long li = ((long long)lz * g.ny + ly) * g.nx + lx, ri = ((long long)rz * g.ny + ry) * g.nx + rx;
+  Real Jbar[NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    const Real bl = inL ? tbar[(CS::DJ + a) * cells + li] : Real(0);
+    const Real br = inR ? tbar[(CS::DJ + a) * cells + ri] : Real(0);
+    Jbar[a] = (bl - br) * g.inv_dx;
+  }
+  ValAcc<NP, NM, Real, Real> V{st, g.fstride, plane, padded_index<DIM>(g, lx, ly, lz), g.pitch};
+  DW pf[NP], gr[NP][DIM];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    const Real vl = V.phi(a, 0, 0, 0);
+    const Real vr = V.phi(a, D == 0, D == 1, D == 2);
+    pf[a] = DW(Real(0.5) * (vl + vr));
+    pf[a].d[a] = Real(1);
+    gr[a][D] = DW((vr - vl) * g.inv_dx);
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      if (t == D) continue;
+      Real v = Real(0);
+      if (need_tan) {
+        const int ux = t == 0, uy = t == 1, uz = t == 2;
+        const int rdx = D == 0, rdy = D == 1, rdz = D == 2;
+        v = ((V.phi(a, ux, uy, uz) + V.phi(a, rdx + ux, rdy + uy, rdz + uz)) -
+             (V.phi(a, -ux, -uy, -uz) + V.phi(a, rdx - ux, rdy - uy, rdz - uz))) *
+            g.quarter_inv_dx;
+      }
+      gr[a][t] = DW(v);
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) gr[a][d].d[NP + a * DIM + d] = Real(1);
+  }
+  DiffPrm<DW, P> dp;
+  dp.mob = DW(g.mob);
+#pragma unroll
+  for (int p = 0; p < P; ++p) dp.delta[p] = DW(g.delta[p]);
+  DW J[NP];
+  face_flux_from<DIM, D, NP, NM, Real, DW, kFeatAll>(g, dp, (1u << NP) - 1u, pf, gr, J);
+  Real sb[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) sb[k] = Real(0);
+#pragma unroll
+  for (int a = 0; a < NP; ++a)
+#pragma unroll
+    for (int k = 0; k < W; ++k) sb[k] += Jbar[a] * J[a].d[k];
+  const long long fid = face_id<DIM, D>(g, lx, ly, lz);
+  const long long nfaces = (long long)(g.nx + (D == 0)) * (g.ny + (D == 1)) * ((DIM == 3 ? g.nz : 1) + (D == 2));
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    const Real gn = sb[NP + a * DIM + D] * g.inv_dx;
+    frec[(FS::AL + a) * nfaces + fid] = Real(0.5) * sb[a] - gn;
+    frec[(FS::AR + a) * nfaces + fid] = Real(0.5) * sb[a] + gn;
+    int tt = 0;
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      if (t == D) continue;
+      frec[(FS::TG + a * (DIM - 1) + tt) * nfaces + fid] = sb[NP + a * DIM + t] * g.quarter_inv_dx;
+      ++tt;
+    }
+  }
+}
+
+template <int DIM, int NP, int NM, class Real>
+__global__ void __launch_bounds__(128) k_adj_faces(const Real* __restrict__ st, const Real* __restrict__ tbar,
+                                                   Real* __restrict__ frec0, Real* __restrict__ frec1,
+                                                   Real* __restrict__ frec2,
+                                                   const __grid_constant__ StepArgs<Real, NP, NM> g) {
+  constexpr int P = NP * (NP - 1) / 2;
+  const long long cells = (long long)g.nx * g.ny * g.nz;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= cells) return;
+  const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
+  const bool need_tan = any_aniso<DIM>(g.aniso, P);
+  face_adjoint<DIM, 0, NP, NM, Real>(st, tbar, frec0, g, need_tan, x, y, z);
+  if (x == 0) face_adjoint<DIM, 0, NP, NM, Real>(st, tbar, frec0, g, need_tan, -1, y, z);
+  face_adjoint<DIM, 1, NP, NM, Real>(st, tbar, frec1, g, need_tan, x, y, z);
+  if (y == 0) face_adjoint<DIM, 1, NP, NM, Real>(st, tbar, frec1, g, need_tan, x, -1, z);
+  if constexpr (DIM == 3) {
+    face_adjoint<DIM, 2, NP, NM, Real>(st, tbar, frec2, g, need_tan, x, y, z);
+    if (z == 0) face_adjoint<DIM, 2, NP, NM, Real>(st, tbar, frec2, g, need_tan, x, y, -1);
+  }
+}
+
+// Face records along axis D read by position (px, py, pz): acc[a] += the
+// record's entry for the position's place in the face's stencil.
+template <int DIM, int D, int NP, int NM, class Real>
+__device__ __forceinline__ void gather_faces(const Real* __restrict__ frec, const StepArgs<Real, NP, NM>& g,
+                                             bool need_tan, int px, int py, int pz, Real* acc) {
+  using FS = FaceStore<DIM, NP>;
+  const long long nfaces = (long long)(g.nx + (D == 0)) * (g.ny + (D == 1)) * ((DIM == 3 ? g.nz : 1) + (D == 2));
+  // (unrolled: every candidate's loads can be in flight at once)
+#pragma unroll
+  for (int c = 0; c < 2 + 4 * (DIM - 1); ++c) {
+    if (c >= 2 && !need_tan) continue;
+    int o[3] = {0, 0, 0};
+    int slot, sgn = 1;
+    if (c == 0) {
+      o[D] = -1;   // p is R
+      slot = FS::AR;
+    } else if (c == 1) {
+      slot = FS::AL;   // p is L
+    } else {
+      const int k = c - 2;
+      const int t = DIM == 2 ? 1 - D : (D + 1 + (k >> 2)) % 3;   // a tangential axis of D
+      const int tt = t > D ? t - 1 : t;                          // its rank among the axes != D
+      sgn = (k & 1) ? 1 : -1;
+      o[t] = -sgn;                  // p = L + sgn e_t, or
+      if ((k >> 1) & 1) o[D] = -1;  // p = R + sgn e_t
+      slot = FS::TG + tt;           // + a (DIM - 1) below
+    }
+    const int lx = px + o[0], ly = py + o[1], lz = pz + o[2];
+    if (!in_grid<DIM>(g, lx, ly, lz) && !in_grid<DIM>(g, lx + (D == 0), ly + (D == 1), lz + (D == 2))) continue;
+    const long long fid = face_id<DIM, D>(g, lx, ly, lz);
+    const int astride = c < 2 ? 1 : DIM - 1;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) acc[a] += Real(sgn) * frec[(slot + a * astride) * nfaces + fid];
+  }
+}
+
+// Pass 3, per input cell j: the direct part, the face records and
+// centre-term differences that read j's positions, and the mu flux.  A block
+// covers 32 cells with DIM + 1 warps (the loads are latency-bound: more of
+// them in flight): warp w < DIM reads the face records along axis w, warp DIM
+// the rest; the parts are summed in warp order (deterministic).
 template <int DIM>
 struct GatherShape {
   static constexpr int PARTS = DIM + 1;
@@ -344,14 +561,14 @@ struct GatherShape {
 
 template <int DIM, int NP, int NM, class Real>
 __global__ void __launch_bounds__(GatherShape<DIM>::THREADS)
-    k_adj_gather(const Real* __restrict__ st, const Real* __restrict__ tbar, Real* __restrict__ lam_out,
+    k_adj_gather(const Real* __restrict__ st, const Real* __restrict__ tbar, const Real* __restrict__ frec0,
+                 const Real* __restrict__ frec1, const Real* __restrict__ frec2, Real* __restrict__ lam_out,
                  const __grid_constant__ StepArgs<Real, NP, NM> g) {
   constexpr int NF = NP + NM;
   constexpr int P = NP * (NP - 1) / 2;
-  constexpr int PARTS = GatherShape<DIM>::PARTS;
-  using TS = TailSlots<NP, NM>;
+  using CS = CellStore<DIM, NP, NM>;
   using DN = Dual<Real, NP>;
-  __shared__ Real s_acc[PARTS - 1][NF][32];
+  __shared__ Real s_acc[DIM][NF][32];
   const int part = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long cells = (long long)g.nx * g.ny * g.nz;
   const long long plane = (long long)g.nyp * g.pitch;
@@ -369,22 +586,18 @@ __global__ void __launch_bounds__(GatherShape<DIM>::THREADS)
     if (part == DIM) {
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
-        acc[a] = tbar[(TS::PH + a) * cells + j];
+        acc[a] = tbar[(CS::PH + a) * cells + j];
         phj[a] = st[a * g.fstride + jb];
       }
 #pragma unroll
       for (int k = 0; k < NM; ++k) {
-        acc[NP + k] = tbar[(TS::MC + k) * cells + j];
+        acc[NP + k] = tbar[(CS::MC + k) * cells + j];
         muj[k] = st[(NP + k) * g.fstride + jb];
       }
       cell_mobility<NP, NM>(phj, g.DX, Mj);
 #pragma unroll
       for (int k = 0; k < NM * NM; ++k) Mbar[k] = Real(0);
     }
-    DiffPrm<DN, P> dpn;
-    dpn.mob = DN(g.mob);
-#pragma unroll
-    for (int p = 0; p < P; ++p) dpn.delta[p] = DN(g.delta[p]);
 
     // positions holding cell j's value: itself and its ghost images
     int xs[3], ys[3], zs[3], nxs = 1, nys = 1, nzs = 1;
@@ -406,44 +619,23 @@ __global__ void __launch_bounds__(GatherShape<DIM>::THREADS)
 #pragma unroll 1
         for (int ix = 0; ix < nxs; ++ix) {
           const int px = xs[ix], py = ys[iy], pz = zs[iz];
-          const long long seed = padded_index<DIM>(g, px, py, pz);
-          if (part == 0) gather_faces<DIM, 0, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
-          if (part == 1) gather_faces<DIM, 1, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
+          if (part == 0) gather_faces<DIM, 0, NP, NM, Real>(frec0, g, need_tan, px, py, pz, acc);
+          if (part == 1) gather_faces<DIM, 1, NP, NM, Real>(frec1, g, need_tan, px, py, pz, acc);
           if constexpr (DIM == 3)
-            if (part == 2) gather_faces<DIM, 2, NP, NM, Real>(st, tbar, g, need_tan, px, py, pz, seed, acc);
+            if (part == 2) gather_faces<DIM, 2, NP, NM, Real>(frec2, g, need_tan, px, py, pz, acc);
           if (part != DIM) continue;
-          // centre terms of the cells whose central differences (or own phi) read p
-#pragma unroll 1
-          for (int c = 0; c < 1 + 2 * DIM; ++c) {
-            int cx = px, cy = py, cz = pz;
-            if (c > 0) {
-              const int d = (c - 1) >> 1, sgn = (c & 1) ? 1 : -1;
-              if (d == 0) cx += sgn;
-              if (d == 1) cy += sgn;
-              if (d == 2) cz += sgn;
-            }
+          // centre terms: p = i + sgn e_d enters gcr_i[a][d] with sign sgn
+#pragma unroll
+          for (int c = 0; c < 2 * DIM; ++c) {
+            const int d = c >> 1, sgn = (c & 1) ? 1 : -1;
+            const int cx = px - (d == 0 ? sgn : 0), cy = py - (d == 1 ? sgn : 0), cz = pz - (d == 2 ? sgn : 0);
             if (!in_grid<DIM>(g, cx, cy, cz)) continue;
             const long long ci = dense(cx, cy, cz);
-            SeedAcc<NP, NM, Real> A{st, g.fstride, plane, padded_index<DIM>(g, cx, cy, cz), seed, g.pitch};
-            DN ph[NP], gcr[NP][DIM], Gc[NP];
 #pragma unroll
-            for (int a = 0; a < NP; ++a) {
-              ph[a] = A.phi(a, 0, 0, 0);
-              gcr[a][0] = A.phi(a, 1, 0, 0) - A.phi(a, -1, 0, 0);
-              gcr[a][1] = A.phi(a, 0, 1, 0) - A.phi(a, 0, -1, 0);
-              if constexpr (DIM == 3) gcr[a][2] = A.phi(a, 0, 0, 1) - A.phi(a, 0, 0, -1);
-              Gc[a] = DN(Real(0));
-            }
-            centre_term<DIM, NP, NM, Real, DN, kFeatAll, false>(g, dpn, ph, gcr, A.mask(), Gc);
-#pragma unroll
-            for (int a = 0; a < NP; ++a) {
-              const Real gb = tbar[(TS::GC + a) * cells + ci];
-#pragma unroll
-              for (int b = 0; b < NP; ++b) acc[b] += gb * Gc[a].d[b];
-            }
+            for (int a = 0; a < NP; ++a) acc[a] += Real(sgn) * tbar[(CS::GCR + a * DIM + d) * cells + ci];
           }
           // mu flux of the in-grid neighbours i = p - o: p is their neighbour at o
-#pragma unroll 1
+#pragma unroll
           for (int c = 0; c < 2 * DIM; ++c) {
             const int d = c >> 1, sgn = (c & 1) ? 1 : -1;
             const int ix2 = px - (d == 0 ? sgn : 0), iy2 = py - (d == 1 ? sgn : 0), iz2 = pz - (d == 2 ? sgn : 0);
@@ -455,7 +647,7 @@ __global__ void __launch_bounds__(GatherShape<DIM>::THREADS)
             cell_mobility<NP, NM>(phi_i, g.DX, Mi);
 #pragma unroll
             for (int r = 0; r < NM; ++r) {
-              const Real db = tbar[(TS::DIV + r) * cells + ii];
+              const Real db = tbar[(CS::DIV + r) * cells + ii];
 #pragma unroll
               for (int q = 0; q < NM; ++q) {
                 const Real mci = st[(NP + q) * g.fstride + ib];
@@ -469,8 +661,8 @@ __global__ void __launch_bounds__(GatherShape<DIM>::THREADS)
       // mu flux of cell j itself (its own mu and mobility at the centre)
       Real db[NM];
 #pragma unroll
-      for (int r = 0; r < NM; ++r) db[r] = tbar[(TS::DIV + r) * cells + j];
-#pragma unroll 1
+      for (int r = 0; r < NM; ++r) db[r] = tbar[(CS::DIV + r) * cells + j];
+#pragma unroll
       for (int c = 0; c < 2 * DIM; ++c) {
         const int d = c >> 1, sgn = (c & 1) ? 1 : -1;
         const long long nb = jb + (d == 0 ? sgn : 0) + (d == 1 ? (long long)sgn * g.pitch : 0) +
@@ -512,7 +704,7 @@ __global__ void __launch_bounds__(GatherShape<DIM>::THREADS)
     for (int f = 0; f < NF; ++f) {
       Real v = acc[f];
 #pragma unroll
-      for (int q = 0; q < PARTS - 1; ++q) v += s_acc[q][f][lane];
+      for (int q = 0; q < DIM; ++q) v += s_acc[q][f][lane];
       lam_out[f * cells + j] = v;
     }
   }
@@ -538,8 +730,14 @@ struct AdjKernel {
                         const HostModel& m, double t, double* partials, cudaStream_t st);
 };
 
-// Stored tail adjoints per cell of the reverse step (pass 1 -> pass 2).
-inline int tail_slots(const HostModel& m) { return 3 * m.N + 2 * m.NM; }
+// Work buffer of the reverse step, in elements: the per-cell store of pass 1
+// and the face records of pass 2 along every axis.
+inline long long adjoint_work_elems(const HostModel& m) {
+  const long long cells = (long long)m.nx * m.ny * m.nz;
+  long long n = (long long)(2 * m.N + 2 * m.NM + m.N * m.dim) * cells;
+  for (int D = 0; D < m.dim; ++D) n += (long long)m.N * (m.dim + 1) * faces_along(m, D);
+  return n;
+}
 
 template <int DIM, int NP, int NM, class Real>
 cudaError_t launch_adjoint(const void* state, const void* lam_in, void* lam_out, void* tbar, const void* blob,
@@ -556,8 +754,20 @@ cudaError_t launch_adjoint(const void* state, const void* lam_in, void* lam_out,
                                                         reinterpret_cast<Real*>(tbar), g, ex, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  Real* tb = reinterpret_cast<Real*>(tbar);
+  Real* fr[3] = {nullptr, nullptr, nullptr};
+  {
+    Real* q = tb + (long long)CellStore<DIM, NP, NM>::TB * cells;
+    for (int D = 0; D < DIM; ++D) {
+      fr[D] = q;
+      q += (long long)FaceStore<DIM, NP>::N * faces_along(m, D);
+    }
+  }
+  k_adj_faces<DIM, NP, NM, Real><<<blocks, 128, 0, st>>>(s, tb, fr[0], fr[1], fr[2], g);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   k_adj_gather<DIM, NP, NM, Real><<<(unsigned)((cells + 31) / 32), GatherShape<DIM>::THREADS, 0, st>>>(
-      s, reinterpret_cast<const Real*>(tbar), reinterpret_cast<Real*>(lam_out), g);
+      s, tb, fr[0], fr[1], fr[2], reinterpret_cast<Real*>(lam_out), g);
   return cudaGetLastError();
 }
 
@@ -672,7 +882,7 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
   const long long cells = (long long)m.nx * m.ny * m.nz;
   const size_t lam_bytes = (size_t)NF * cells * s;
   const int nprm = ak->nprm;
-  const int blocks = (int)((cells + 127) / 128);
+  const int blocks = (int)((cells + 127) / 128);   // blocks of the cell pass (parameter partials)
   // lazily sized work buffers
   if (!A.adj[0]) {
     for (int b = 0; b < 2; ++b) {
@@ -681,7 +891,7 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
     }
   }
   if (!A.tbar) {
-    A.tbar = dev_alloc(c->hook, (size_t)tail_slots(m) * cells * s);
+    A.tbar = dev_alloc(c->hook, (size_t)adjoint_work_elems(m) * s);
     if (!A.tbar) return fail(c, MS_ERR_OOM, "adjoint tail buffer allocation failed");
   }
   if (!A.gpart) {

@@ -186,6 +186,28 @@ __device__ __forceinline__ Off<DIM> add(Off<DIM> a, Off<DIM> b) {
   return Off<DIM>{a.x + b.x, a.y + b.y, a.z + b.z};
 }
 
+// Normal component (axis D) of J_a on one face from the face values pf and
+// the face gradients gr of the phases (pairs absent from `mask` skipped).
+template <int DIM, int D, int NP, int NM, class Real, class S, int FEAT = kFeatAll>
+__device__ __forceinline__ void face_flux_from(const StepArgs<Real, NP, NM>& g,
+                                               const DiffPrm<S, NP*(NP - 1) / 2>& dp, uint32_t mask, const S* pf,
+                                               const S (*gr)[DIM], S* Jn) {
+#pragma unroll
+  for (int a = 0; a < NP; ++a) Jn[a] = S(Real(0));
+  int p = 0;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int b = a + 1; b < NP; ++b, ++p) {
+      if (!(((mask >> a) & (mask >> b)) & 1u)) continue;
+      const S gD = face_pair_flux<DIM, D>(pf[a], pf[b], gr[a], gr[b], g.gam2[p], dp.delta[p], g.aniso[p] != 0,
+                                          (FEAT & kFeatRot) && g.rotated[p] != 0, g.rot[p]);
+      Jn[a] -= pf[b] * gD;
+      Jn[b] += pf[a] * gD;
+    }
+  }
+}
+
 // Normal component (axis D) of J_a on one face of the cell: side 0 = the
 // face shared with the -D neighbour, side 1 = with the +D neighbour.
 template <int DIM, int D, int NP, int NM, class Real, class S, class Acc, int FEAT = kFeatAll>
@@ -198,7 +220,6 @@ __device__ __forceinline__ void face_flux(const Acc& A, const StepArgs<Real, NP,
   S gr[NP][DIM];
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
-    Jn[a] = S(Real(0));
     if (!((mask >> a) & 1u)) continue;
     S vl = A.phi(a, L.x, L.y, L.z);
     S vr = A.phi(a, R.x, R.y, R.z);
@@ -218,18 +239,7 @@ __device__ __forceinline__ void face_flux(const Acc& A, const StepArgs<Real, NP,
       }
     }
   }
-  int p = 0;
-#pragma unroll
-  for (int a = 0; a < NP; ++a) {
-#pragma unroll
-    for (int b = a + 1; b < NP; ++b, ++p) {
-      if (!(((mask >> a) & (mask >> b)) & 1u)) continue;
-      const S gD = face_pair_flux<DIM, D>(pf[a], pf[b], gr[a], gr[b], g.gam2[p], dp.delta[p], g.aniso[p] != 0,
-                                          (FEAT & kFeatRot) && g.rotated[p] != 0, g.rot[p]);
-      Jn[a] -= pf[b] * gD;
-      Jn[b] += pf[a] * gD;
-    }
-  }
+  face_flux_from<DIM, D, NP, NM, Real, S, FEAT>(g, dp, mask, pf, gr, Jn);
 }
 
 // Both faces along axis D at once in paired FP32 arithmetic (low half: the
