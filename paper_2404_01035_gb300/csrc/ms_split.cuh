@@ -40,7 +40,6 @@ struct StreamShape {
   static constexpr int NWF = TY * WCS;            // combined flags per entry
   static constexpr int CSEG = WCS + 2;
   static constexpr int CODE_ENTRIES = (kMaxZChunk + 2) * SY * CSEG;
-  static constexpr int CODE_ITERS = (CODE_ENTRIES + NTHREADS - 1) / NTHREADS;
   static constexpr int OFF_FLAG = NST * STAGE_STRIDE;
   static constexpr int OFF_CODE = OFF_FLAG + (NST * NWF + 15) / 16 * 16;
   static constexpr int NCOEF = NM * NM + NM;     // Kb_l and eb_l of one phase
@@ -114,23 +113,30 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
     }
   }
   {
-    const int ncode = nplanes * Sh::SY * Sh::CSEG;
-    uint8_t v[Sh::CODE_ITERS];
-#pragma unroll
-    for (int it = 0; it < Sh::CODE_ITERS; ++it) {
-      const int e = tid + it * Sh::NTHREADS;
-      v[it] = 0;
-      if (e < ncode) {
-        const int k = e % Sh::CSEG, r = e / Sh::CSEG;
-        const int ay = r % Sh::SY, j = r / Sh::SY;
-        v[it] = load_code(g, seg0 - 1 + k, y0 - 1 + ay, zb - 1 + j);
-      }
-    }
+    // thread (pair, group): segment k of row ay (boundary-mapped once), for
+    // the entries j = group, group + GROUPS, ... of this CTA's planes
+    constexpr int PAIRS = Sh::SY * Sh::CSEG;
+    constexpr int GROUPS = Sh::NTHREADS / PAIRS;
+    static_assert(GROUPS >= 1, "the code preload needs one thread per (row, segment)");
     uint8_t* scode = smem + Sh::OFF_CODE;
-#pragma unroll
-    for (int it = 0; it < Sh::CODE_ITERS; ++it) {
-      const int e = tid + it * Sh::NTHREADS;
-      if (e < ncode) scode[e] = v[it];
+    if (tid < GROUPS * PAIRS) {
+      const int pr = tid % PAIRS, j0 = tid / PAIRS;
+      const int k = pr % Sh::CSEG, ay = pr / Sh::CSEG;
+      const long long rowoff =
+          (long long)bc_map(y0 - 1 + ay, g.ny, g.bc[1]) * g.segs + bc_map(seg0 - 1 + k, g.segs, g.bc[0]);
+      const long long pstride = (long long)g.ny * g.segs;
+#pragma unroll 4
+      for (int j = j0; j < nplanes; j += GROUPS) {
+        const int z = zb - 1 + j;
+        int zz;   // as load_code: ghost code planes at internal cuts
+        if (z >= 0 && z < g.nz)
+          zz = z + g.zoff;
+        else if (g.bc[2] == kBcHalo)
+          zz = z < 0 ? 0 : g.nz + 1;
+        else
+          zz = bc_map(z, g.nz, g.bc[2]) + g.zoff;
+        scode[(j * Sh::SY + ay) * Sh::CSEG + k] = __ldg(g.codes_in + zz * pstride + rowoff);
+      }
     }
   }
   __syncthreads();   // the last CTA-wide barrier: roles split below
@@ -204,6 +210,10 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
   const long long oy0 = y == 0 ? (long long)(g.bc[1] == 3 ? g.ny : -1) * g.pitch : 0;
   const long long oy1 = y == g.ny - 1 ? (long long)(g.bc[1] == 3 ? -g.ny : 1) * g.pitch : 0;
   const long long cplane = (long long)g.ny * g.segs;
+  // z image offsets of the first / last plane of the grid (internal cuts get
+  // their ghost planes from the exchange)
+  const long long oz_first = g.bc[2] == kBcHalo ? 0 : (g.bc[2] == 3 ? g.nz : -1) * plane;
+  const long long oz_last = g.bc[2] == kBcHalo ? 0 : (g.bc[2] == 3 ? -g.nz : 1) * plane;
   uint8_t* const code0 = g.codes_out + ((long long)(zb + g.zoff) * g.ny + y) * g.segs + seg;
   // input code of this thread's segment at plane k: entry k + 1, row ty + 1,
   // segment wc + 1 of the shared copy
@@ -300,11 +310,7 @@ __global__ void __launch_bounds__(StreamShape<NP, NM, TY>::NTHREADS, StreamShape
         }
       }
       // rows at a y or z boundary (rare): their y / z images, with x images
-      long long oz0 = 0, oz1 = 0;
-      if (g.bc[2] != kBcHalo) {   // internal cuts get their ghost planes from the exchange
-        if (z == 0) oz0 = (g.bc[2] == 3 ? g.nz : -1) * plane;
-        if (z == g.nz - 1) oz1 = (g.bc[2] == 3 ? -g.nz : 1) * plane;
-      }
+      const long long oz0 = z == 0 ? oz_first : 0, oz1 = z == g.nz - 1 ? oz_last : 0;
       if ((oy0 | oy1 | oz0 | oz1) != 0) {
         // (the loops are unrolled so that every array index is a constant
         // and nothing lives in local memory)
