@@ -40,6 +40,66 @@ __device__ __forceinline__ void inv_small(const R* A, R* X) {
   }
 }
 
+// Per-thread running values of the diagnostics other than the solute sums:
+// min / max phi, max |sum phi - 1|, max of the per-cell diffusion sum.  FP64
+// states keep them in FP64.  FP32 states keep them in FP32 and convert once
+// at the end (FP64 is a slow pipe): min and max are exact in either, the
+// diffusion number dt num / dx^2 is monotone in num (its FP64 rounding
+// commutes with the max), and |sum phi - 1| comes from an error-free FP32
+// summation (TwoSum), so the result is the deviation rounded once to FP32.
+template <class Real>
+struct DiagRun {
+  double lo = 1e300, hi = -1e300, dev = 0.0, num = 0.0;
+  __device__ __forceinline__ void phase(Real v) {
+    lo = fmin(lo, (double)v);
+    hi = fmax(hi, (double)v);
+  }
+  template <int NP>
+  __device__ __forceinline__ void sum_dev(const Real* ph) {
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) s += (double)ph[a];
+    dev = fmax(dev, fabs(s - 1.0));
+  }
+  __device__ __forceinline__ void diffusion(Real n, double dt, double inv_dx2) {
+    num = fmax(num, dt * (double)n * inv_dx2);
+  }
+  __device__ __forceinline__ void finish(double dt, double inv_dx2, double* acc, int NM) {
+    acc[NM] = dev;
+    acc[NM + 1] = lo;
+    acc[NM + 2] = hi;
+    acc[NM + 4] = num;
+  }
+};
+
+template <>
+struct DiagRun<float> {
+  float lo = INFINITY, hi = -INFINITY, dev = 0.0f, num = 0.0f;
+  __device__ __forceinline__ void phase(float v) {
+    lo = fminf(lo, v);
+    hi = fmaxf(hi, v);
+  }
+  template <int NP>
+  __device__ __forceinline__ void sum_dev(const float* ph) {
+    float s = ph[0], e = 0.0f;
+#pragma unroll
+    for (int a = 1; a < NP; ++a) {   // TwoSum (Knuth): s + e is the exact sum
+      const float t = __fadd_rn(s, ph[a]);
+      const float bp = __fsub_rn(t, s);
+      e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(ph[a], bp)));
+      s = t;
+    }
+    dev = fmaxf(dev, fabsf(__fadd_rn(__fsub_rn(s, 1.0f), e)));
+  }
+  __device__ __forceinline__ void diffusion(float n, double, double) { num = fmaxf(num, n); }
+  __device__ __forceinline__ void finish(double dt, double inv_dx2, double* acc, int NM) {
+    acc[NM] = (double)dev;
+    acc[NM + 1] = lo == INFINITY ? 1e300 : (double)lo;
+    acc[NM + 2] = hi == -INFINITY ? -1e300 : (double)hi;
+    acc[NM + 4] = dt * (double)num * inv_dx2;
+  }
+};
+
 template <class Real, int NP, int NM>
 struct DiagConsts {
   Real chi[NP][NM * NM];
@@ -63,6 +123,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ 
   acc[NM + 2] = -1e300;   // max phi
   acc[NM + 3] = 0.0;      // non-finite count
   acc[NM + 4] = 0.0;      // max diffusion number
+  DiagRun<Real> run;
   const long long cells = (long long)nx * ny * nz;
   const long long plane = (long long)nyp * pitch;
   auto idx = [&](int x, int y, int z) {
@@ -81,15 +142,12 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ 
     const int z = (int)(cidx / ((long long)nx * ny));
     const long long i0 = idx(x, y, z);
     Real ph[NP], mu[NM];
-    double sum = 0.0;
     bool finite = true;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
       ph[a] = st[a * fstride + i0];
       finite = finite && isfinite(ph[a]);
-      sum += (double)ph[a];
-      acc[NM + 1] = fmin(acc[NM + 1], (double)ph[a]);
-      acc[NM + 2] = fmax(acc[NM + 2], (double)ph[a]);
+      run.phase(ph[a]);
     }
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
@@ -100,7 +158,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ 
       acc[NM + 3] += 1.0;
       continue;
     }
-    acc[NM] = fmax(acc[NM], fabs(sum - 1.0));
+    run.template sum_dev<NP>(ph);
     Real h[NP];
     interp_h<NP>(ph, h);
     const Real s = (Real)(tz0 + tzg * ((DIM == 3 ? z : y) + zorg + 0.5));
@@ -149,8 +207,9 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const Real* __restrict__ 
         }
         num += rmax;
       }
-    acc[NM + 4] = fmax(acc[NM + 4], dt * (double)num * inv_dx2);
+    run.diffusion(num, dt, inv_dx2);
   }
+  run.finish(dt, inv_dx2, acc, NM);
   __shared__ double red[kDiagThreads];
   for (int v = 0; v < NV; ++v) {
     red[threadIdx.x] = acc[v];

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(kNaThreads) k_diag_dense(
   acc[NM + 2] = -1e300;
   acc[NM + 3] = 0.0;
   acc[NM + 4] = 0.0;
+  DiagRun<Real> run;
   const long long cells = (long long)nx * ny * nz;
   auto idx = [&](int x, int y, int z) { return ((long long)z * ny + y) * nx + x; };
   auto mob_at = [&](long long i0, Real* M) {
@@ -72,15 +73,12 @@ __global__ void __launch_bounds__(kNaThreads) k_diag_dense(
     const int y = (int)((cidx / nx) % ny);
     const int z = (int)(cidx / ((long long)nx * ny));
     Real ph[NP], m[NM];
-    double sum = 0.0;
     bool finite = true;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
       ph[a] = phi[a * cells + cidx];
       finite = finite && isfinite(ph[a]);
-      sum += (double)ph[a];
-      acc[NM + 1] = fmin(acc[NM + 1], (double)ph[a]);
-      acc[NM + 2] = fmax(acc[NM + 2], (double)ph[a]);
+      run.phase(ph[a]);
     }
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
@@ -91,7 +89,7 @@ __global__ void __launch_bounds__(kNaThreads) k_diag_dense(
       acc[NM + 3] += 1.0;
       continue;
     }
-    acc[NM] = fmax(acc[NM], fabs(sum - 1.0));
+    run.template sum_dev<NP>(ph);
     Real h[NP];
     interp_h<NP>(ph, h);
     const Real s = (Real)(tz0 + tzg * ((DIM == 3 ? z : y) + zorg + 0.5));
@@ -141,8 +139,9 @@ __global__ void __launch_bounds__(kNaThreads) k_diag_dense(
         }
         num += rmax;
       }
-    acc[NM + 4] = fmax(acc[NM + 4], dt * (double)num * inv_dx2);
+    run.diffusion(num, dt, inv_dx2);
   }
+  run.finish(dt, inv_dx2, acc, NM);
   __shared__ double red[kNaThreads];
   for (int v = 0; v < NV; ++v) {
     red[threadIdx.x] = acc[v];
