@@ -710,14 +710,25 @@ def committed_profile(launch, n):
 
 
 def kernel_digest():
-    """Digest of the CUDA sources: ties a committed ncu traffic figure to a kernel version."""
+    """Digest of the sources of the benchmark's step kernels: the translation
+    unit that instantiates the 3-phase, 2-solute kernels and every header it
+    includes (recursively).  Ties a committed ncu traffic figure to the
+    kernel version it was measured on."""
     import hashlib
+    import re
     d = os.path.join(ROOT, "paper_2404_01035_gb300", "csrc")
+    seen, todo = [], ["ms_inst_3d_n3.cu"]
+    while todo:
+        f = todo.pop(0)
+        if f in seen or not os.path.exists(os.path.join(d, f)):
+            continue
+        seen.append(f)
+        with open(os.path.join(d, f)) as fh:
+            todo += re.findall(r'#include "([A-Za-z0-9_.]+)"', fh.read())
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in sorted(seen):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 

@@ -310,7 +310,10 @@ ms_status ms_tune(ms_ctx* ctx, const char* cache_path, int steps_per_trial,
  * a device snapshot of the state every `every` steps (0 turns recording off).
  * Memory: one state per snapshot plus `every` states during ms_grad.
  * Returns MS_ERR_UNSUPPORTED if no adjoint kernel is compiled for the
- * context's (dim, N, K, dtype).  Resets on ms_set_fields / ms_restore. */
+ * context's (dim, N, K, dtype), with phi noise, the anti-trapping current,
+ * grain growth or elasticity on, and for a slab context with halo z faces
+ * (the adjoint needs the whole domain).  Resets on ms_set_fields /
+ * ms_restore. */
 ms_status ms_enable_checkpoints(ms_ctx* ctx, int every);
 
 /* Number of parameters in theta: N(N-1)/2 + 1 + N (K-1)^2. */
@@ -323,8 +326,9 @@ int ms_grad_param_count(const ms_ctx* ctx);
  * ms_grad_param_count doubles (dL/dtheta, accumulated in FP64); dphi0 /
  * dmu0, dense device arrays dL/dphi and dL/dmu of the state at the first
  * recorded step.  Synchronous.  Segments between snapshots are recomputed with
- * the forward kernel; per reverse step one adjoint kernel runs (deterministic
- * gather, no atomics).  The current state is left unchanged. */
+ * the forward kernel; per reverse step three adjoint kernels run (per cell,
+ * per face, per cell: a gather, no atomics, deterministic).  The current
+ * state is left unchanged. */
 ms_status ms_grad(ms_ctx* ctx, const void* dphi_T, const void* dmu_T, double* dparams,
                   void* dphi0, void* dmu0);
 

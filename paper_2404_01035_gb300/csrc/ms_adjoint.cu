@@ -851,6 +851,10 @@ ms_status ms_enable_checkpoints(ms_ctx* c, int every) {
   if (every > 0 && (c->m.at || c->m.gg || c->m.el))
     return fail(c, MS_ERR_UNSUPPORTED,
                 "the adjoint does not support the anti-trapping current, grain growth or elasticity");
+  // the reverse step maps ghost positions back to their source cells by the
+  // boundary rule; a halo face's ghosts belong to another slab
+  if (every > 0 && c->m.dim == 3 && c->m.bc[2] == kBcHalo)
+    return fail(c, MS_ERR_UNSUPPORTED, "the adjoint needs the whole domain (no halo faces)");
   ms_reset_extra(c);
   c->adj.every = every;
   return MS_OK;
@@ -871,6 +875,8 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
   if (c->m.at || c->m.gg || c->m.el)
     return fail(c, MS_ERR_UNSUPPORTED,
                 "the adjoint does not support the anti-trapping current, grain growth or elasticity");
+  if (c->m.dim == 3 && c->m.bc[2] == kBcHalo)
+    return fail(c, MS_ERR_UNSUPPORTED, "the adjoint needs the whole domain (no halo faces)");
   const AdjKernel* ak = find_adjoint(c->m);
   if (!ak) return fail(c, MS_ERR_UNSUPPORTED, "no compiled adjoint kernel for this (dim, N, K, dtype)");
   const int64_t nsteps = c->step - A.first_step;

@@ -102,6 +102,20 @@ def test_update_params_while_recording_refuses_extensions_and_restarts_the_recor
     np.testing.assert_allclose(phiA.cpu().numpy(), phiB.cpu().numpy(), rtol=0, atol=1e-13)
 
 
+def test_adjoint_is_refused_on_a_slab_with_halo_faces():
+    # the reverse step maps ghost positions back to their cells by the
+    # boundary rule, which a halo face does not have: refused, not wrong
+    from paper_2404_01035_gb300 import Simulation
+    from paper_2404_01035_gb300._binding import MS_BC_HALO, MSError
+    p = W.binary_problem("slab", 8, dim=3, delta=0.03, R=3.0, potential="well", ny=7, nz=6,
+                         bc=[W.BC_PERIODIC, W.BC_PERIODIC, MS_BC_HALO])
+    sim = Simulation(p, dtype="f64")
+    with pytest.raises(MSError) as ex:
+        sim.enable_checkpoints(4)
+    assert ex.value.status == 9 and "halo" in str(ex.value)
+    sim.close()
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_non_finite_state_is_reported(dtype):
     from paper_2404_01035_gb300 import Simulation
