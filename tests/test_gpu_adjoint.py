@@ -157,13 +157,24 @@ def test_cfg4_gradients_match_central_differences_and_fp32():
         assert g32[k] == pytest.approx(g64[k], rel=1e-2)
 
 
-@pytest.mark.parametrize("case", ["well2d", "ternary2d"])
+@pytest.mark.parametrize("case", ["well2d", "ternary2d", "binary3d", "thin2d"])
 def test_gradients_equal_the_oracle_reverse_sweep(case):
     # ms_grad (FP64) against the oracle's own reverse adjoint, element by element
     if case == "well2d":
         p = W.binary_problem("adjr", 40, delta=0.02, Delta=0.2, R=8.0, potential="well", ny=36,
                              tau=1.25, dt=0.2 * 0.25 / 1.45)
         steps, every = 60, 25
+    elif case == "binary3d":
+        # 3-D faces and tangential neighbours, periodic and no-flux axes
+        p = W.binary_problem("adjr3", 10, dim=3, delta=0.03, R=3.5, potential="well", ny=9, nz=8,
+                             bc=[W.BC_PERIODIC, W.BC_NOFLUX, W.BC_PERIODIC])
+        steps, every = 8, 3
+    elif case == "thin2d":
+        # rows of two cells along y: every cell is at both ends of that axis,
+        # so its value sits at both ghost images (periodic x, no-flux y)
+        p = W.binary_problem("adjt", 24, delta=0.02, Delta=0.2, R=6.0, potential="well", ny=2,
+                             bc=[W.BC_PERIODIC, W.BC_NOFLUX, W.BC_PERIODIC])
+        steps, every = 12, 5
     else:
         p = W.small_multiphase(n=16, dim=2, N=3, NM=2, nx=18, ny=16, rotate=True)
         steps, every = 16, 6
