@@ -35,3 +35,26 @@ def test_pure_stencil_mask_matches_brute_force(bc):
                 want = len(vals) == 1 and max(next(iter(vals))) == 1.0
                 assert got[z, y, x] == want, (z, y, x)
     assert got.any() and not got.all()
+
+
+def test_kernel_digest_follows_the_step_kernels_sources(tmp_path, monkeypatch):
+    # the digest that ties a committed ncu traffic figure to a kernel version
+    # covers the step kernels' translation unit and the headers it includes:
+    # editing one of those changes it, editing another unit does not
+    import os
+    import shutil
+    src = os.path.join(bench.ROOT, "paper_2404_01035_gb300", "csrc")
+    dst = tmp_path / "paper_2404_01035_gb300" / "csrc"
+    shutil.copytree(src, dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d0 = bench.kernel_digest()
+    with open(dst / "ms_adjoint.cu", "a") as fh:
+        fh.write("\n// unrelated edit\n")
+    assert bench.kernel_digest() == d0
+    with open(dst / "ms_split.cuh", "a") as fh:
+        fh.write("\n// step kernel edit\n")
+    d1 = bench.kernel_digest()
+    assert d1 != d0
+    with open(dst / "ms_device.cuh", "a") as fh:   # reached through the includes
+        fh.write("\n// header edit\n")
+    assert bench.kernel_digest() != d1
