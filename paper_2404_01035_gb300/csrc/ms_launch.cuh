@@ -184,6 +184,9 @@ cudaError_t launch_split(const CUtensorMap* tm, const CUtensorMap* tmi, void* bl
   if (!lg.iface || !lg.iface2 || !tmi || lg.iface_blocks < 1) return cudaErrorInvalidValue;
   auto& g = *reinterpret_cast<StepArgs<float, NP, NM>*>(blob);
   set_launch_args(g, m, t, out, codes_in, codes_out, lg);
+  // the interface kernel fills the anti-trapping list only when the
+  // correction runs after this step (launch_at with LISTED)
+  if (!m.at) g.at_list = nullptr;
   // the interface kernels in two builds: every optional path of the cell
   // update, and none of them (when the model uses none: the common case)
   const bool plain = plain_model(m);
@@ -222,7 +225,10 @@ cudaError_t launch_split(const CUtensorMap* tm, const CUtensorMap* tmi, void* bl
   return cudaGetLastError();
 }
 
-template <int DIM, int NP, int NM, class Real>
+// The anti-trapping correction after a step.  LISTED: the step's interface
+// kernel has already listed the segments (split step), so the listing pass
+// is skipped.
+template <int DIM, int NP, int NM, class Real, bool LISTED = false>
 cudaError_t launch_at(const void* in, void* blob, const HostModel& m, double t, void* out, const uint8_t* codes_in,
                       uint8_t* codes_out, const LaunchGeom& lg, cudaStream_t st) {
   using Sh = AtShape<DIM, NP, NM, Real>;
@@ -241,8 +247,10 @@ cudaError_t launch_at(const void* in, void* blob, const HostModel& m, double t, 
     per_sm = per_sm < 1 ? 1 : per_sm;
     configured = true;
   }
-  const long long nseg = (long long)segments(m) * m.ny * (DIM == 3 ? m.nz : 1);
-  k_at_list<DIM, NP, NM, Real><<<(int)((nseg + 255) / 256), 256, 0, st>>>(g);
+  if constexpr (!LISTED) {
+    const long long nseg = (long long)segments(m) * m.ny * (DIM == 3 ? m.nz : 1);
+    k_at_list<DIM, NP, NM, Real><<<(int)((nseg + 255) / 256), 256, 0, st>>>(g);
+  }
   kw<<<lg.sms * per_sm, Sh::THREADS, Sh::SMEM_BYTES, st>>>(g, reinterpret_cast<const Real*>(in));
   return cudaGetLastError();
 }
@@ -292,7 +300,7 @@ StepKernel make_split_kernel() {
   k.fill = &fill_args<3, NP, NM, float>;
   k.launch = &launch_split<NP, NM, TY>;
   k.codes = &launch_codes<3, NP, float>;
-  k.at = &launch_at<3, NP, NM, float>;
+  k.at = &launch_at<3, NP, NM, float, true>;
   return k;
 }
 

@@ -547,6 +547,8 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + Sh::OFF_BAR) + 2 * wid;
   Real* buf0 = reinterpret_cast<Real*>(smem + (2 * wid) * Sh::BOX_STRIDE);
   if (threadIdx.x == 0) s_count = min(*(volatile unsigned int*)&list[0], g.iface_cap);
+  if (MODE == 0 && g.at_list && blockIdx.x == 0 && threadIdx.x == 0)   // see the copy below
+    g.at_list[0] = min(*(volatile unsigned int*)&list[0], g.at_cap);
   if (lane == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -599,6 +601,12 @@ __global__ void __launch_bounds__(IfaceShape<NP, NM, Real>::THREADS, IfaceShape<
     const unsigned int r = list[2 + i];
     const int sg = (int)(r & seg_mask);
     const int y = (int)((r >> g.seg_bits) & y_mask), z = (int)(r >> zshift);
+    // with the anti-trapping current on, its correction works on the same
+    // segments (a block of segments that is not one pure phase in phi^n, plus
+    // cut segments, where the current vanishes): the list is copied, by
+    // linear segment index, at the same positions
+    if (MODE == 0 && g.at_list && lane == 0 && i < g.at_cap)
+      g.at_list[2 + i] = (unsigned int)(((long long)z * g.ny + y) * g.segs + sg);
     const int x = 32 * sg + lane;
     const bool active = x < g.nx;
     const Real* box = reinterpret_cast<const Real*>(reinterpret_cast<unsigned char*>(buf0) + b * Sh::BOX_STRIDE);
