@@ -161,7 +161,7 @@ typedef struct {
  * MS_ERR_DT_UNSTABLE when above it), allocates the ping-pong device state and
  * enqueues nothing.  stream is a cudaStream_t (NULL = legacy default stream).
  * n_phases in [2, 8], n_components in [2, 4].  Returns MS_ERR_UNSUPPORTED when
- * the (dim, N, K, dtype) step kernel is not compiled into this build. */
+ * the (dim, N, K, dtype) step kernel is not compiled into the library. */
 ms_status ms_create(const ms_grid* grid, int n_phases, int n_components,
                     const ms_params* params, void* stream, const ms_allocator* alloc,
                     ms_ctx** out);

@@ -71,7 +71,7 @@ def test_create_rejects_bad_boundary_and_potential():
 
 
 def test_create_reports_uncompiled_combination():
-    # 3-D with 5 phases is not compiled into this build
+    # 3-D with 5 phases is not compiled into the library
     p = W.small_multiphase(n=8, dim=3, N=5, NM=1)
     rc, h, msg = _create(p)
     assert rc == 9 and "no compiled step kernel" in msg
