@@ -26,8 +26,12 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
     equal to the forward-mode tangent in a dot-product test: pinned.
   * count_flops (the op-counting scalar, ``tests/test_oracle_flops.py``):
     exact counts of hand-countable updates: pinned.
+  * Grid refinement (``tests/test_oracle_refinement.py``): second-order
+    convergence of a smooth three-phase anisotropic trajectory under dx ->
+    dx/2 -> dx/4 with dt ~ dx^2, which pins the dx scaling of every term.
   * The full multiphase (N >= 3) anisotropic dendrite / eutectic / multigrain
-    trajectories: parity unpinned beyond the identities above.
+    trajectories: parity unpinned beyond the identities above and the
+    convergence order.
 """
 from __future__ import annotations
 

@@ -151,6 +151,21 @@ def test_one_row_strip_2d_fp64():
     assert max_err(g, o) <= FP64_TOL
 
 
+@pytest.mark.parametrize("dim,dtype,steps,tol", [(2, "f64", 40, FP64_TOL), (3, "f64", 30, FP64_TOL),
+                                                   (3, "f32", 200, FP32_TOL)])
+def test_grid_spacing_other_than_one(dim, dtype, steps, tol):
+    # dx = 1/2 with the interface width in cells held (eps = 2) and dt ~ dx^2:
+    # every dx-scaled term of the step (gradients, divergences, Laplacians,
+    # the temperature position) against the oracle, which a refinement test
+    # pins on its own
+    p = W.small_multiphase(n=20, dim=dim, N=3, NM=2, rotate=True)
+    p = p.copy(dx=0.5, dt=0.25 * p.dt, eps=0.5 * p.eps)
+    g = gpu_run(p, steps, dtype)
+    o = oracle.run(p, p.phi0, p.mu0, steps)
+    assert max_err(g, o) <= tol
+    assert np.abs(o[0] - p.phi0).max() > 1e-3   # the state moved
+
+
 def test_zero_steps_is_identity():
     p = W.cfg1()
     g = gpu_run(p, 0, "f64")
