@@ -45,6 +45,20 @@ def test_3d_multiphase_fp64(bc):
     assert _err(off, o) > 1e-5
 
 
+@pytest.mark.parametrize("split", [False, True])
+def test_grid_spacing_other_than_one(split):
+    # dx = 1/2 (interface width in cells held, dt ~ dx^2): the current's face
+    # gradients, rates and divergence against the oracle, FP64 fused and the
+    # FP32 split step (whose work list the interface kernel fills)
+    p = _at(W.small_multiphase(n=14, dim=3, N=3, NM=2, nx=30, ny=17, nz=15, bc=[3, 1, 1]))
+    p = p.copy(dx=0.5, dt=0.25 * p.dt, eps=0.5 * p.eps)
+    g = _run(p, 40 if split else 20, "f32" if split else "f64", split=split)
+    o = oracle.run(p, p.phi0, p.mu0, 40 if split else 20)
+    assert _err(g, o) <= (FP32_TOL if split else FP64_TOL)
+    off = oracle.run(p, p.phi0, p.mu0, 40 if split else 20, anti_trapping=0)
+    assert _err(off, o) > 1e-5
+
+
 @pytest.mark.parametrize("potential", ["obstacle", "well"])
 def test_2d_binary_seed_fp64(potential):
     p = _at(W.binary_problem("at2d", 48, dim=2, R=8.0, potential=potential, bc=[1, 1, 1]))

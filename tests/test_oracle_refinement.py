@@ -59,3 +59,39 @@ def test_second_order_convergence_under_refinement():
         e2 = np.abs(change[1][q] - change[2][q]).max()
         assert e1 < 0.05 * np.abs(change[2][q]).max()   # resolved: differences well below the change
         assert 3.5 < e1 / e2 < 4.6, (q, e1, e2)
+
+
+def _front_state(p, nx, ny, Lx, Ly):
+    """A solid-liquid front across x, modulated along y (so the normals have
+    both components and are defined wherever the rate is not negligible)."""
+    dx = Lx / nx
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dx
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    xf = 0.5 * Lx + 1.5 * np.cos(2 * math.pi * Y / Ly)
+    s = 0.5 * (1 + np.tanh(1.5 * (xf - X) / p.eps))
+    phi = np.stack([s, 1 - s])[:, None]
+    mu = (p.mu0.mean(axis=(1, 2, 3))[:, None, None] + 0.02 * np.cos(2 * math.pi * Y / Ly))[:, None]
+    return phi, mu
+
+
+def test_anti_trapping_current_converges_at_second_order():
+    # the current's face normals, face rates and divergence scale with dx as
+    # well: a moving front with the current on, no-flux across it (the liquid
+    # fraction is monotone along x, so its normal never flips)
+    Lx, Ly, n0 = 24.0, 12.0, 12
+    base = W.binary_problem("atref", 24, delta=0.02, Delta=0.2, R=5.0, potential="well", ny=12,
+                            bc=[W.BC_NOFLUX, W.BC_PERIODIC, W.BC_PERIODIC])
+    dt0 = 0.25 * base.dt
+    change = []
+    for f in (1, 2, 4):
+        nx, ny = 2 * n0 * f, n0 * f
+        p = base.copy(nx=nx, ny=ny, dx=Lx / nx, dt=dt0 / f ** 2, eps=3.0, anti_trapping=1)
+        phi0, mu0 = _front_state(p, nx, ny, Lx, Ly)
+        phi, mu = oracle.run(p, phi0, mu0, 40 * f ** 2)
+        change.append((_restrict(phi - phi0, f), _restrict(mu - mu0, f)))
+    for q in (0, 1):
+        e1 = np.abs(change[0][q] - change[1][q]).max()
+        e2 = np.abs(change[1][q] - change[2][q]).max()
+        assert e1 < 0.1 * np.abs(change[2][q]).max()
+        assert 3.5 < e1 / e2 < 5.0, (q, e1, e2)
