@@ -79,6 +79,14 @@ def test_adjoint_2d_three_phase_ternary_matches_oracle_tangent():
     _dot_product_check(p, steps=24, every=10, seed=3)
 
 
+def test_adjoint_at_a_grid_spacing_of_one_half():
+    # the reverse passes' face gradients, divergences and mu flux at dx = 1/2
+    p = W.binary_problem("adjdx", 24, delta=0.02, Delta=0.2, R=6.0, potential="well", ny=20,
+                         tau=1.25, dt=0.2 * 0.25 / 1.45)
+    p = p.copy(dx=0.5, dt=0.25 * p.dt, eps=0.5 * p.eps)
+    _dot_product_check(p, 12, 5, seed=17)
+
+
 def test_adjoint_3d_binary_matches_oracle_tangent():
     p = W.binary_problem("adj3", 14, dim=3, delta=0.03, R=4.0, potential="well", ny=12, nz=11,
                          bc=[W.BC_PERIODIC, W.BC_NOFLUX, W.BC_PERIODIC])

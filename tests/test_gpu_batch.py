@@ -52,6 +52,27 @@ def test_batch_matches_standalone_runs_and_oracle():
     b.close()
 
 
+def test_simulations_at_different_grid_spacings_in_one_batch():
+    # each simulation's own dx (interface width in cells held, dt ~ dx^2)
+    from paper_2404_01035_gb300.batch import Batch
+    probs = []
+    for i, dx in enumerate((1.0, 0.5, 0.25)):
+        p = W.binary_problem(f"dx{i}", 48, ny=40, delta=0.03, Delta=0.2, R=6.0, potential="obstacle",
+                             dtype_note="f32")
+        probs.append(p.copy(dx=dx, dt=p.dt * dx * dx, eps=p.eps * dx))
+    b = Batch(probs)
+    for i, p in enumerate(probs):
+        b.set_fields(i, p.phi0, p.mu0)
+    b.step(200)
+    b.sync()
+    for i, p in enumerate(probs):
+        phi, mu = b.get_fields(i)
+        ophi, omu = oracle.run(p, p.phi0, p.mu0, 200)
+        assert max(np.abs(phi - ophi).max(), np.abs(mu - omu).max()) <= 1e-3, i
+        assert np.abs(ophi - p.phi0).max() > 1e-3
+    b.close()
+
+
 def test_cfg3_batch_of_512_runs_500_steps():
     from paper_2404_01035_gb300.batch import Batch
     probs = W.cfg3()

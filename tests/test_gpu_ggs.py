@@ -36,6 +36,16 @@ def test_fp64_matches_the_oracle(dim, grains, n, steps):
     assert (o > 0).sum(axis=0).max() <= 8
 
 
+def test_grid_spacing_other_than_one_fp64():
+    # the sparse kernels' own gradients and divergences at dx = 1/2
+    p = W.sparse_grain_growth(n=64, dim=2, grains=16)
+    p = p.copy(dx=0.5, dt=0.25 * p.dt, eps=0.5 * p.eps)
+    g, _ = _run(p, 40, "f64")
+    o, _ = oracle.run(p, p.phi0, p.mu0, 40)
+    assert np.abs(g - o).max() <= 1e-10
+    assert np.abs(o - p.phi0).max() > 1e-3
+
+
 def test_fp32_matches_the_oracle():
     p = W.sparse_grain_growth(n=128, dim=2, grains=32)
     g, _ = _run(p, 200, "f32")
