@@ -54,6 +54,17 @@ def test_fp64_matches_oracle(dim):
     assert _err(off, o) > 1e-6          # the elastic force acted
 
 
+def test_fp64_at_a_grid_spacing_of_one_half():
+    # the FFT equilibrium and the step's own dx terms together at dx = 1/2
+    p = _elastic(W.small_multiphase(n=20, dim=3, N=3, NM=2, nx=24, ny=20, nz=18, bc=[3, 3, 3]))
+    p = p.copy(dx=0.5, dt=0.25 * p.dt, eps=0.5 * p.eps)
+    g = _run(p, 30, "f64")
+    o = oracle.run(p, p.phi0, p.mu0, 30)
+    assert _err(g, o) <= 1e-10
+    off = oracle.run(p, p.phi0, p.mu0, 30, elastic_C=None)
+    assert _err(off, o) > 1e-6
+
+
 @pytest.mark.parametrize("zchunk", [6, 16])
 def test_fp32_split_matches_oracle(zchunk):
     p = _elastic(W.small_multiphase(n=24, dim=3, N=3, NM=2, nx=48, ny=40, nz=36, bc=[3, 3, 3]))

@@ -146,3 +146,27 @@ def test_isotropic_dilatational_energy_is_shape_independent():
         phi[1] = 1.0 - phi[0]
         _, w = oracle.elastic_fields(p, phi)
         assert _energy(w, phi) == pytest.approx(expect, rel=1e-10)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fields_do_not_depend_on_the_grid_spacing(dim):
+    # strain is dimensionless: the same eigenstrain pattern in cells gives the
+    # same stress at any dx (the wavenumbers' 1/dx cancels between the
+    # displacement and its gradient); a missing dx in one of them would not
+    rng = np.random.default_rng(4)
+    n = 12
+    nz = 10 if dim == 3 else 1
+    p = W.binary_problem("el_dx", n, dim=dim, ny=11, nz=nz if dim == 3 else None,
+                         bc=[W.BC_PERIODIC] * 3)
+    phi = np.zeros((2, nz, 11, n))
+    phi[0] = rng.uniform(0.0, 1.0, size=(nz, 11, n))
+    phi[1] = 1.0 - phi[0]
+    p.elastic_C = _cubic()
+    eig = np.zeros((2, 3, 3))
+    eig[0] = np.array([[0.01, 0.002, 0.0], [0.002, -0.004, 0.001], [0.0, 0.001, 0.006]])
+    p.eigenstrain = eig
+    s1, w1 = oracle.elastic_fields(p, phi)
+    s2, w2 = oracle.elastic_fields(p.copy(dx=0.37), phi)
+    assert np.abs(s1).max() > 0.1
+    np.testing.assert_allclose(s2, s1, rtol=0, atol=1e-12 * np.abs(s1).max())
+    np.testing.assert_allclose(w2, w1, rtol=0, atol=1e-12 * np.abs(w1).max())
