@@ -156,6 +156,8 @@ def run_reference(args, rank, world):
     import oracle
     import workloads
     prob = workloads.cfg2(n=args.n)
+    if world > 1:   # the launcher caps every rank at one thread; rank 0 alone computes here
+        oracle.set_threads(os.cpu_count() or 1)
     cores = oracle.num_threads()
     # size one bench step so that warmup + steps stay within ~3 minutes
     budget = 150.0 / max(1, args.steps + args.warmup)
