@@ -1,0 +1,172 @@
+"""Pins of the oracle's phase-field step against the free-energy functional it descends.
+
+For the well potential with curvature-driven motion only (grain growth, no
+chemical driving force), the phase-field equation of Sec. 2 is the
+Allen-Cahn gradient flow of the functional
+
+    F[phi] = sum over cells dx^dim [ eps * sum_{a<b} gamma_ab |q_ab|^2 + w(phi) / eps ],
+    q_ab   = phi_a grad(phi_b) - phi_b grad(phi_a),
+
+relaxed with mobility 1/(tau eps) and projected onto the hyperplane
+sum_a phi_a = 1 (for the well potential the projection subtracts the mean
+over the phases).  One explicit Euler step therefore moves every cell by
+
+    (phi^{n+1} - phi^n) / dt = -1/(tau eps) * Proj[ dF/dphi_a / dx^dim ].
+
+Here dF/dphi is taken by central differences of F itself.  The gradient
+energy is evaluated with spectral derivatives of the periodic field.  The
+well energy w comes from the oracle's pointwise potential, and only its value
+is used, never its derivative.  The oracle's step assembles the same
+derivative from face fluxes and centre terms.  The two therefore agree only
+up to the flux scheme's second-order truncation error.  A dropped or
+sign-flipped term breaks the agreement by O(1): the centre term, the sign of
+q, a pair index, or eps placed on the wrong term.  The check needs three or
+more phases: with two phases the centre terms of the two phases are equal and
+cancel in the projection.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+L = 32.0
+
+
+def _state(dim, n, N):
+    """A smooth periodic N-phase field on [0, L)^dim with every pair in contact,
+    sampled at x = i dx (so that cell i of a grid is cell 2i of the grid twice as fine)."""
+    x = np.arange(n) * (L / n)
+    g = np.meshgrid(*([x] * dim), indexing="ij")      # g[0] is the slowest axis
+    k = 2 * math.pi / L
+    f = []
+    for a in range(N):
+        s = 0.0
+        for d in range(dim):
+            s = s + (1.2 - 0.2 * a) * math.cos(0.7 * a + 1.3 * d) * \
+                np.cos(k * (1 + (a + d) % 2) * g[d] + 0.4 * a + d)
+        f.append(s)
+    f = np.stack(f)
+    e = np.exp(f - f.max(axis=0))
+    phi = e / e.sum(axis=0)
+    return phi if dim == 3 else phi[:, None]
+
+
+def _problem(dim, n, N, g3=0.0):
+    p = W.small_multiphase(n=n, dim=dim, N=N, NM=1, aniso=False, potential="well",
+                           bc=[W.BC_PERIODIC] * 3, gamma3=g3)
+    p.dx = L / n
+    p.grain_growth = 1
+    p.tau = 1.3
+    p.eps = 4.0
+    p.dt = 1e-3
+    return p
+
+
+class _Functional:
+    """F[phi] on the periodic grid, spectral gradients, pointwise well energy."""
+
+    def __init__(self, p, dim, n):
+        self.p, self.dim, self.n = p, dim, n
+        self.axes = tuple(range(3 - dim, 3))          # the grid axes of one [nz][ny][nx] field
+        self.k = 2 * math.pi * np.fft.fftfreq(n, d=L / n)
+        self.vol = (L / n) ** dim
+
+    def _grad(self, f):
+        F = np.fft.fftn(f, axes=self.axes)
+        out = []
+        for ax in self.axes:
+            sh = [1, 1, 1]
+            sh[ax] = self.n
+            out.append(np.real(np.fft.ifftn(1j * self.k.reshape(sh) * F, axes=self.axes)))
+        return out
+
+    def gradient_energy(self, phi):
+        p, N = self.p, phi.shape[0]
+        g = [self._grad(phi[a]) for a in range(N)]
+        E = 0.0
+        for a in range(N):
+            for b in range(a + 1, N):
+                for d in range(self.dim):
+                    q = phi[a] * g[b][d] - phi[b] * g[a][d]
+                    E += p.gamma[a, b] * float((q * q).sum())
+        return E * self.vol
+
+    def derivative(self, phi, a, cell, h=1e-5):
+        """dF/dphi_a at one cell, divided by the cell volume (central differences)."""
+        p = self.p
+        pp, pm = phi.copy(), phi.copy()
+        pp[(a,) + cell] += h
+        pm[(a,) + cell] -= h
+        dEg = (self.gradient_energy(pp) - self.gradient_energy(pm)) / (2 * h * self.vol)
+        wp, _ = oracle.potential(p, pp[(slice(None),) + cell])
+        wm, _ = oracle.potential(p, pm[(slice(None),) + cell])
+        dw = (wp - wm) / (2 * h)
+        return p.eps * dEg + dw / p.eps
+
+
+def _cells(dim, n, count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        z, y, x = (int(v) for v in rng.integers(0, n, 3))
+        out.append((z if dim == 3 else 0, y, x))
+    return out
+
+
+def _step_error(dim, n, N, cells=6, refine=1, g3=0.0):
+    """max over sampled cells and phases of |oracle step rate - projected gradient flow|,
+    and the largest |rate| there (the scale).  The cells are drawn on the grid of n
+    cells; `refine` runs the same points on a grid `refine` times as fine."""
+    m = n * refine
+    p = _problem(dim, m, N, g3)
+    phi = _state(dim, m, N)
+    mu = np.zeros((1,) + phi.shape[1:])
+    phi1, _ = oracle.run(p, phi, mu, 1)
+    rate = (phi1 - phi) / p.dt
+    F = _Functional(p, dim, m)
+    err = scale = 0.0
+    for c0 in _cells(dim, n, cells, seed=n + 10 * N):
+        c = (c0[0] * refine if dim == 3 else 0, c0[1] * refine, c0[2] * refine)
+        dF = np.array([F.derivative(phi, a, c) for a in range(N)])
+        expect = -(dF - dF.mean()) / (p.tau * p.eps)
+        got = rate[(slice(None),) + c]
+        err = max(err, float(np.abs(got - expect).max()))
+        scale = max(scale, float(np.abs(expect).max()))
+    return err, scale
+
+
+@pytest.mark.parametrize("N,g3", [(3, 0.0), (4, 0.0), (3, 6.0)])
+def test_step_is_the_projected_gradient_flow_of_the_functional_2d(N, g3):
+    """2-D, three and four phases, with and without the triple-junction term
+    Gamma_abc phi_a phi_b phi_c of the well energy: the step rate converges to
+    -Proj dF/dphi / (tau eps) at second order as dx halves on a fixed domain
+    (error ratio about 4)."""
+    e1, s1 = _step_error(2, 32, N, g3=g3)
+    e2, s2 = _step_error(2, 32, N, refine=2, g3=g3)
+    assert e1 < 0.05 * s1, (e1, s1)
+    assert 3.5 < e1 / e2 < 4.6, (e1, e2)
+
+
+def test_step_is_the_projected_gradient_flow_of_the_functional_3d():
+    """3-D, three phases, one resolution: the step rate and the functional's derivative
+    agree to the flux scheme's truncation error."""
+    e, s = _step_error(3, 24, 3, cells=4)
+    assert e < 0.06 * s, (e, s)
+
+
+def test_the_centre_term_carries_the_multiphase_signal():
+    """The state is one on which the pins above can see the centre term.  After the
+    projection, the oracle's centre term is more than 20% of the whole gradient part
+    there.  A dropped or sign-flipped centre term would therefore miss the 5%
+    tolerance by a wide margin."""
+    n, N = 32, 3
+    p = _problem(2, n, N)
+    phi = _state(2, n, N)
+    mu = np.zeros((1,) + phi.shape[1:])
+    divJ, Gc, _, _ = oracle.rate_parts(p, phi, mu)
+    Gp = Gc - Gc.mean(axis=0, keepdims=True)          # what survives the projection
+    gp = (divJ - Gc) - (divJ - Gc).mean(axis=0, keepdims=True)
+    assert np.abs(Gp).max() > 0.2 * np.abs(gp).max()
