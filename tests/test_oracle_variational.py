@@ -1,10 +1,11 @@
 """Pins of the oracle's phase-field step against the free-energy functional it descends.
 
-For the well potential with curvature-driven motion only (grain growth, no
-chemical driving force), the phase-field equation of Sec. 2 is the
-Allen-Cahn gradient flow of the functional
+For the well potential at a uniform chemical potential mu and temperature T,
+the phase-field equation of Sec. 2 is the Allen-Cahn gradient flow of the
+grand-potential functional
 
-    F[phi] = sum over cells dx^dim [ eps * sum_{a<b} gamma_ab |q_ab|^2 + w(phi) / eps ],
+    F[phi] = sum over cells dx^dim [ eps * sum_{a<b} gamma_ab |q_ab|^2 + w(phi) / eps
+                                     + sum_b psi_b(mu, T) h_b(phi) ],
     q_ab   = phi_a grad(phi_b) - phi_b grad(phi_a),
 
 relaxed with mobility 1/(tau eps) and projected onto the hyperplane
@@ -16,7 +17,9 @@ over the phases).  One explicit Euler step therefore moves every cell by
 Here dF/dphi is taken by central differences of F itself.  The gradient
 energy is evaluated with spectral derivatives of the periodic field.  The
 well energy w comes from the oracle's pointwise potential, and only its value
-is used, never its derivative.  The oracle's step assembles the same
+is used, never its derivative.  The same holds for the driving term: h comes
+from the oracle's interpolation and psi from its thermodynamics, values only.
+Curvature-driven motion (grain growth) drops that term.  The oracle's step assembles the same
 derivative from face fluxes and centre terms.  The two therefore agree only
 up to the flux scheme's second-order truncation error.  A dropped or
 sign-flipped term breaks the agreement by O(1): the centre term, the sign of
@@ -54,22 +57,36 @@ def _state(dim, n, N):
     return phi if dim == 3 else phi[:, None]
 
 
-def _problem(dim, n, N, g3=0.0):
+MU = 0.37          # the uniform chemical potential of the driven cases
+T_UNIFORM = 0.15   # and their uniform temperature
+
+
+def _problem(dim, n, N, g3=0.0, drive=False):
     p = W.small_multiphase(n=n, dim=dim, N=N, NM=1, aniso=False, potential="well",
                            bc=[W.BC_PERIODIC] * 3, gamma3=g3)
     p.dx = L / n
-    p.grain_growth = 1
     p.tau = 1.3
     p.eps = 4.0
     p.dt = 1e-3
+    if drive:
+        # no temperature gradient, distinct phase free energies: psi_b(mu, T) differ
+        p.G, p.V, p.T0 = 0.0, 0.0, T_UNIFORM
+        p.f0 = np.array([0.05 * (b % 3) - 0.04 * b for b in range(N)])
+    else:
+        p.grain_growth = 1
     return p
 
 
 class _Functional:
-    """F[phi] on the periodic grid, spectral gradients, pointwise well energy."""
+    """F[phi] on the periodic grid: spectral gradients, pointwise well energy and,
+    when driven, the pointwise term sum_b psi_b h_b(phi)."""
 
-    def __init__(self, p, dim, n):
+    def __init__(self, p, dim, n, drive=False):
         self.p, self.dim, self.n = p, dim, n
+        self.psi = None
+        if drive:
+            self.psi = np.array([oracle.thermo(p, b, np.array([MU]), T_UNIFORM)[1]
+                                 for b in range(p.n_phases)])
         self.axes = tuple(range(3 - dim, 3))          # the grid axes of one [nz][ny][nx] field
         self.k = 2 * math.pi * np.fft.fftfreq(n, d=L / n)
         self.vol = (L / n) ** dim
@@ -104,7 +121,12 @@ class _Functional:
         wp, _ = oracle.potential(p, pp[(slice(None),) + cell])
         wm, _ = oracle.potential(p, pm[(slice(None),) + cell])
         dw = (wp - wm) / (2 * h)
-        return p.eps * dEg + dw / p.eps
+        dpsi = 0.0
+        if self.psi is not None:
+            hp, _ = oracle.interp(pp[(slice(None),) + cell])
+            hm, _ = oracle.interp(pm[(slice(None),) + cell])
+            dpsi = float(self.psi @ (hp - hm)) / (2 * h)
+        return p.eps * dEg + dw / p.eps + dpsi
 
 
 def _cells(dim, n, count, seed):
@@ -116,17 +138,17 @@ def _cells(dim, n, count, seed):
     return out
 
 
-def _step_error(dim, n, N, cells=6, refine=1, g3=0.0):
+def _step_error(dim, n, N, cells=6, refine=1, g3=0.0, drive=False):
     """max over sampled cells and phases of |oracle step rate - projected gradient flow|,
     and the largest |rate| there (the scale).  The cells are drawn on the grid of n
     cells; `refine` runs the same points on a grid `refine` times as fine."""
     m = n * refine
-    p = _problem(dim, m, N, g3)
+    p = _problem(dim, m, N, g3, drive)
     phi = _state(dim, m, N)
-    mu = np.zeros((1,) + phi.shape[1:])
+    mu = np.full((1,) + phi.shape[1:], MU)
     phi1, _ = oracle.run(p, phi, mu, 1)
     rate = (phi1 - phi) / p.dt
-    F = _Functional(p, dim, m)
+    F = _Functional(p, dim, m, drive)
     err = scale = 0.0
     for c0 in _cells(dim, n, cells, seed=n + 10 * N):
         c = (c0[0] * refine if dim == 3 else 0, c0[1] * refine, c0[2] * refine)
@@ -138,14 +160,15 @@ def _step_error(dim, n, N, cells=6, refine=1, g3=0.0):
     return err, scale
 
 
-@pytest.mark.parametrize("N,g3", [(3, 0.0), (4, 0.0), (3, 6.0)])
-def test_step_is_the_projected_gradient_flow_of_the_functional_2d(N, g3):
+@pytest.mark.parametrize("N,g3,drive", [(3, 0.0, False), (4, 0.0, False), (3, 6.0, False),
+                                        (3, 0.0, True), (4, 6.0, True)])
+def test_step_is_the_projected_gradient_flow_of_the_functional_2d(N, g3, drive):
     """2-D, three and four phases, with and without the triple-junction term
-    Gamma_abc phi_a phi_b phi_c of the well energy: the step rate converges to
-    -Proj dF/dphi / (tau eps) at second order as dx halves on a fixed domain
-    (error ratio about 4)."""
-    e1, s1 = _step_error(2, 32, N, g3=g3)
-    e2, s2 = _step_error(2, 32, N, refine=2, g3=g3)
+    Gamma_abc phi_a phi_b phi_c of the well energy, curvature-driven or with the
+    chemical driving force: the step rate converges to -Proj dF/dphi / (tau eps)
+    at second order as dx halves on a fixed domain (error ratio about 4)."""
+    e1, s1 = _step_error(2, 32, N, g3=g3, drive=drive)
+    e2, s2 = _step_error(2, 32, N, refine=2, g3=g3, drive=drive)
     assert e1 < 0.05 * s1, (e1, s1)
     assert 3.5 < e1 / e2 < 4.6, (e1, e2)
 
