@@ -1,22 +1,26 @@
 """Pins of the oracle's phase-field step against the free-energy functional it descends.
 
-For the well potential at a uniform chemical potential mu and temperature T,
-the phase-field equation of Sec. 2 is the Allen-Cahn gradient flow of the
-grand-potential functional
+At a uniform chemical potential mu and temperature T, the phase-field
+equation of Sec. 2 is the Allen-Cahn gradient flow of the grand-potential
+functional
 
     F[phi] = sum over cells dx^dim [ eps * sum_{a<b} gamma_ab |q_ab|^2 + w(phi) / eps
                                      + sum_b psi_b(mu, T) h_b(phi) ],
     q_ab   = phi_a grad(phi_b) - phi_b grad(phi_a),
 
-relaxed with mobility 1/(tau eps) and projected onto the hyperplane
-sum_a phi_a = 1 (for the well potential the projection subtracts the mean
-over the phases).  One explicit Euler step therefore moves every cell by
+relaxed with mobility 1/(tau eps) and projected onto sum_a phi_a = 1.  For
+the well potential the projection is onto the hyperplane: it subtracts the
+mean over the phases.  For the obstacle potential it is onto the simplex.
+That projection is the same as the hyperplane one wherever every phase stays
+positive, which holds at every cell of the smooth states used here (each
+phase exceeds 1e-3 and one step of dt = 1e-3 moves it by far less).  One
+explicit Euler step therefore moves every cell by
 
     (phi^{n+1} - phi^n) / dt = -1/(tau eps) * Proj[ dF/dphi_a / dx^dim ].
 
 Here dF/dphi is taken by central differences of F itself.  The gradient
 energy is evaluated with spectral derivatives of the periodic field.  The
-well energy w comes from the oracle's pointwise potential, and only its value
+multi-well or obstacle energy w comes from the oracle's pointwise potential, and only its value
 is used, never its derivative.  The same holds for the driving term: h comes
 from the oracle's interpolation and psi from its thermodynamics, values only.
 Curvature-driven motion (grain growth) drops that term.  The oracle's step assembles the same
@@ -61,8 +65,8 @@ MU = 0.37          # the uniform chemical potential of the driven cases
 T_UNIFORM = 0.15   # and their uniform temperature
 
 
-def _problem(dim, n, N, g3=0.0, drive=False):
-    p = W.small_multiphase(n=n, dim=dim, N=N, NM=1, aniso=False, potential="well",
+def _problem(dim, n, N, g3=0.0, drive=False, pot="well"):
+    p = W.small_multiphase(n=n, dim=dim, N=N, NM=1, aniso=False, potential=pot,
                            bc=[W.BC_PERIODIC] * 3, gamma3=g3)
     p.dx = L / n
     p.tau = 1.3
@@ -138,13 +142,14 @@ def _cells(dim, n, count, seed):
     return out
 
 
-def _step_error(dim, n, N, cells=6, refine=1, g3=0.0, drive=False):
+def _step_error(dim, n, N, cells=6, refine=1, g3=0.0, drive=False, pot="well"):
     """max over sampled cells and phases of |oracle step rate - projected gradient flow|,
     and the largest |rate| there (the scale).  The cells are drawn on the grid of n
     cells; `refine` runs the same points on a grid `refine` times as fine."""
     m = n * refine
-    p = _problem(dim, m, N, g3, drive)
+    p = _problem(dim, m, N, g3, drive, pot)
     phi = _state(dim, m, N)
+    assert phi.min() > 1e-3      # interior of the simplex: both projections agree
     mu = np.full((1,) + phi.shape[1:], MU)
     phi1, _ = oracle.run(p, phi, mu, 1)
     rate = (phi1 - phi) / p.dt
@@ -160,16 +165,19 @@ def _step_error(dim, n, N, cells=6, refine=1, g3=0.0, drive=False):
     return err, scale
 
 
-@pytest.mark.parametrize("N,g3,drive", [(3, 0.0, False), (4, 0.0, False), (3, 6.0, False),
-                                        (3, 0.0, True), (4, 6.0, True)])
-def test_step_is_the_projected_gradient_flow_of_the_functional_2d(N, g3, drive):
-    """2-D, three and four phases, with and without the triple-junction term
-    Gamma_abc phi_a phi_b phi_c of the well energy, curvature-driven or with the
-    chemical driving force: the step rate converges to -Proj dF/dphi / (tau eps)
-    at second order as dx halves on a fixed domain (error ratio about 4)."""
-    e1, s1 = _step_error(2, 32, N, g3=g3, drive=drive)
-    e2, s2 = _step_error(2, 32, N, refine=2, g3=g3, drive=drive)
-    assert e1 < 0.05 * s1, (e1, s1)
+@pytest.mark.parametrize("N,g3,drive,pot", [(3, 0.0, False, "well"), (4, 0.0, False, "well"),
+                                            (3, 6.0, False, "well"), (3, 0.0, True, "well"),
+                                            (4, 6.0, True, "well"), (3, 0.0, False, "obstacle"),
+                                            (4, 6.0, True, "obstacle")])
+def test_step_is_the_projected_gradient_flow_of_the_functional_2d(N, g3, drive, pot):
+    """2-D, three and four phases, the multi-well or the obstacle potential, with
+    and without the triple-junction term Gamma_abc phi_a phi_b phi_c,
+    curvature-driven or with the chemical driving force: the step rate converges
+    to -Proj dF/dphi / (tau eps) at second order as dx halves on a fixed domain
+    (error ratio about 4)."""
+    e1, s1 = _step_error(2, 32, N, g3=g3, drive=drive, pot=pot)
+    e2, s2 = _step_error(2, 32, N, refine=2, g3=g3, drive=drive, pot=pot)
+    assert e1 < 0.08 * s1, (e1, s1)
     assert 3.5 < e1 / e2 < 4.6, (e1, e2)
 
 
@@ -183,7 +191,7 @@ def test_step_is_the_projected_gradient_flow_of_the_functional_3d():
 def test_the_centre_term_carries_the_multiphase_signal():
     """The state is one on which the pins above can see the centre term.  After the
     projection, the oracle's centre term is more than 20% of the whole gradient part
-    there.  A dropped or sign-flipped centre term would therefore miss the 5%
+    there.  A dropped or sign-flipped centre term would therefore miss the 8%
     tolerance by a wide margin."""
     n, N = 32, 3
     p = _problem(2, n, N)
