@@ -724,6 +724,10 @@ __global__ void k_accumulate_params(const double* __restrict__ partials, int nbl
   if (lane == 0) gsum[k] += s;
 }
 
+// Size of the gradient sum buffer: an upper bound on the parameter count of
+// every compiled adjoint (checked at compile time for each one).
+constexpr int kMaxGradParams = 64;
+
 struct AdjKernel {
   int dim, np, nm, dtype, nprm;
   cudaError_t (*launch)(const void* state, const void* lam_in, void* lam_out, void* tbar, const void* blob,
@@ -773,6 +777,7 @@ cudaError_t launch_adjoint(const void* state, const void* lam_in, void* lam_out,
 
 template <int DIM, int NP, int NM, class Real>
 AdjKernel make_adjoint() {
+  static_assert(ParamCount<NP, NM>::value <= kMaxGradParams, "gradient scratch too small");
   return AdjKernel{DIM, NP, NM, sizeof(Real) == 8 ? 1 : 0, ParamCount<NP, NM>::value,
                    &launch_adjoint<DIM, NP, NM, Real>};
 }
@@ -889,25 +894,30 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
   const size_t lam_bytes = (size_t)NF * cells * s;
   const int nprm = ak->nprm;
   const int blocks = (int)((cells + 127) / 128);   // blocks of the cell pass (parameter partials)
-  // lazily sized work buffers
-  if (!A.adj[0]) {
-    for (int b = 0; b < 2; ++b) {
+  if (nprm > kMaxGradParams) return fail(c, MS_ERR_UNSUPPORTED, "too many parameters for the gradient scratch");
+  // lazily sized work buffers, each allocated while it is missing: a failed
+  // allocation leaves its pointer null and the next call retries it
+  for (int b = 0; b < 2; ++b)
+    if (!A.adj[b]) {
       A.adj[b] = dev_alloc(c->hook, lam_bytes);
       if (!A.adj[b]) return fail(c, MS_ERR_OOM, "adjoint state allocation failed");
     }
-  }
   if (!A.tbar) {
     A.tbar = dev_alloc(c->hook, (size_t)adjoint_work_elems(m) * s);
     if (!A.tbar) return fail(c, MS_ERR_OOM, "adjoint tail buffer allocation failed");
   }
   if (!A.gpart) {
     A.gpart = static_cast<double*>(dev_alloc(c->hook, sizeof(double) * (size_t)blocks * nprm));
-    A.gsum = static_cast<double*>(dev_alloc(c->hook, sizeof(double) * 64));
-    if (!A.gpart || !A.gsum) return fail(c, MS_ERR_OOM, "gradient scratch allocation failed");
+    if (!A.gpart) return fail(c, MS_ERR_OOM, "gradient scratch allocation failed");
+  }
+  if (!A.gsum) {
+    A.gsum = static_cast<double*>(dev_alloc(c->hook, sizeof(double) * kMaxGradParams));
+    if (!A.gsum) return fail(c, MS_ERR_OOM, "gradient scratch allocation failed");
   }
   const size_t seg_need = (size_t)A.every * c->state_bytes;
-  if (A.seg_bytes < seg_need) {
+  if (!A.seg || A.seg_bytes < seg_need) {
     dev_free(c->hook, A.seg);
+    A.seg_bytes = 0;
     A.seg = dev_alloc(c->hook, seg_need);
     if (!A.seg) return fail(c, MS_ERR_OOM, "adjoint segment allocation failed");
     A.seg_bytes = seg_need;
@@ -919,7 +929,7 @@ ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dpar
     e = dmu_T ? cudaMemcpyAsync(mu_part, dmu_T, (size_t)m.NM * cells * s, cudaMemcpyDeviceToDevice, st)
               : cudaMemsetAsync(mu_part, 0, (size_t)m.NM * cells * s, st);
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(A.gsum, 0, sizeof(double) * 64, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A.gsum, 0, sizeof(double) * kMaxGradParams, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(A.gpart, 0, sizeof(double) * (size_t)blocks * nprm, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint seeding");
   int cur = 0;
