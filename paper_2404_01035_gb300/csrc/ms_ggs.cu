@@ -648,7 +648,7 @@ ms_status ms_ggs_create(const ms_grid* grid, int n_grains, const ms_params* p, v
 
 void ms_ggs_destroy(ms_ggs* s) {
   if (!s) return;
-  if (s->stream || true) cudaStreamSynchronize(s->stream);
+  cudaStreamSynchronize(s->stream);
   for (int b = 0; b < 2; ++b) dev_free(s->hook, s->buf[b]);
   dev_free(s->hook, s->tables);
   dev_free(s->hook, s->list);

@@ -656,7 +656,7 @@ ms_status ms_create(const ms_grid* grid, int n_phases, int n_components, const m
 
 void ms_destroy(ms_ctx* c) {
   if (!c) return;
-  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->stream);
   ms_release_extra(c);
   elastic_free(c);
   for (int b = 0; b < 2; ++b) {
