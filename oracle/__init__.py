@@ -29,6 +29,11 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   * Grid refinement (``tests/test_oracle_refinement.py``): second-order
     convergence of a smooth three-phase anisotropic trajectory under dx ->
     dx/2 -> dx/4 with dt ~ dx^2, which pins the dx scaling of every term.
+  * Gradient flow (``tests/test_oracle_variational.py``): at uniform mu and T,
+    with isotropic pairs and three or four phases, one step's rate equals the
+    projected variational derivative of the grand-potential functional.  That
+    derivative is taken by finite differences of the functional, with spectral
+    gradients, and the two agree at second order: pinned.
   * The full multiphase (N >= 3) anisotropic dendrite / eutectic / multigrain
     trajectories: parity unpinned beyond the identities above and the
     convergence order.
