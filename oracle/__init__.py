@@ -34,6 +34,9 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
     projected variational derivative of the grand-potential functional.  That
     derivative is taken by finite differences of the functional, with spectral
     gradients, and the two agree at second order: pinned.
+  * Covariance (``tests/test_oracle_covariance.py``): the 3-D step with
+    rotated anisotropic pairs commutes with the grid's axis permutations and
+    mirrors when each rotation is composed with the inverse move: pinned.
   * The full multiphase (N >= 3) anisotropic dendrite / eutectic / multigrain
     trajectories: parity unpinned beyond the identities above and the
     convergence order.
