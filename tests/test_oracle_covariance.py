@@ -99,3 +99,14 @@ def test_axis_matrix_moves_a_gradient_like_the_array():
         grad = np.array([(g[c, c, c + 1] - g[c, c, c - 1]) / 2, (g[c, c + 1, c] - g[c, c - 1, c]) / 2,
                          (g[c + 1, c, c] - g[c - 1, c, c]) / 2])
         np.testing.assert_allclose(grad, _axis_matrix(perm, flip) @ np.array([0.3, 0.5, 0.7]), atol=1e-12)
+
+
+@pytest.mark.parametrize("shift", [(3, 0, 0), (0, 5, 0), (0, 0, 7), (4, 9, 2)])
+def test_step_commutes_with_periodic_translation(shift):
+    """On a periodic grid a translation by whole cells is a symmetry: rolling the state
+    rolls the trajectory (same arithmetic in the same order, so to round-off)."""
+    p = _problem()
+    ref_phi, ref_mu = oracle.run(p, p.phi0, p.mu0, STEPS, anti_trapping=1)
+    roll = lambda f: np.ascontiguousarray(np.roll(f, shift, axis=(1, 2, 3)))
+    phi, mu = oracle.run(p, roll(p.phi0), roll(p.mu0), STEPS, anti_trapping=1)
+    assert max(np.abs(phi - roll(ref_phi)).max(), np.abs(mu - roll(ref_mu)).max()) < 1e-13
