@@ -1,4 +1,8 @@
-"""Covariance of the oracle's 3-D step under the symmetries of the cubic grid.
+"""Covariance of the oracle's step under the symmetries of the grid.
+
+Covered: axis permutations and mirrors with rotated anisotropic pairs (3-D);
+periodic translations; and the no-flux boundary as the mirror-extended
+periodic domain.
 
 The model of Sec. 2 is written in lab coordinates except for the anisotropy.
 The anisotropy a_c depends on each pair's interface normal in its crystal
@@ -110,3 +114,37 @@ def test_step_commutes_with_periodic_translation(shift):
     roll = lambda f: np.ascontiguousarray(np.roll(f, shift, axis=(1, 2, 3)))
     phi, mu = oracle.run(p, roll(p.phi0), roll(p.mu0), STEPS, anti_trapping=1)
     assert max(np.abs(phi - roll(ref_phi)).max(), np.abs(mu - roll(ref_mu)).max()) < 1e-13
+
+
+def _mirror_extend(f, axes):
+    """Double the grid along each array axis in `axes` by appending the mirror image
+    (cell 2n-1-i holds cell i)."""
+    for ax in axes:
+        f = np.concatenate([f, np.flip(f, axis=ax)], axis=ax)
+    return np.ascontiguousarray(f)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_no_flux_boundary_is_the_mirror_extended_periodic_domain(dim):
+    """The no-flux boundary takes the ghost cell equal to the adjacent interior cell,
+    i.e. zero gradient across the boundary face.  A domain of n cells with no-flux
+    faces therefore steps exactly like the first half of a periodic domain of 2n cells
+    that holds the state and its mirror image.  The mirror is a symmetry of the model
+    there: unrotated cubic anisotropy, and no temperature gradient along the mirrored
+    axes (in 3-D the pulled gradient runs along the periodic z axis and stays on).
+    The anti-trapping current is on."""
+    n = 10
+    bc = [W.BC_NOFLUX, W.BC_NOFLUX, W.BC_PERIODIC]
+    p = W.small_multiphase(n=n, dim=dim, N=3, NM=2, rotate=False, nz=8 if dim == 3 else None, bc=bc)
+    if dim == 2:
+        p.G = 0.0
+        p.V = 0.0
+    ref_phi, ref_mu = oracle.run(p, p.phi0, p.mu0, STEPS, anti_trapping=1)
+    axes = (2, 3)                       # y and x of [field][z][y][x]
+    big = p.copy(nx=2 * n, ny=2 * n, bc=[W.BC_PERIODIC] * 3)
+    phi, mu = oracle.run(big, _mirror_extend(p.phi0, axes), _mirror_extend(p.mu0, axes), STEPS, anti_trapping=1)
+    err = max(np.abs(phi[..., :n, :n] - ref_phi).max(), np.abs(mu[..., :n, :n] - ref_mu).max())
+    assert err < 1e-13, err
+    # the extended run keeps its mirror symmetry, and the boundary cells did change
+    assert np.abs(phi - _mirror_extend(phi[..., :n, :n], axes)).max() < 1e-13
+    assert np.abs(ref_phi - p.phi0)[..., [0, n - 1], :].max() > 1e-6
