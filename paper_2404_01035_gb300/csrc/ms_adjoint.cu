@@ -38,6 +38,7 @@
 #include "../../include/microsim_gb.h"
 #include "ms_launch.cuh"
 #include "ms_rt.h"
+#include "ms_trace.h"
 
 namespace msgb {
 
@@ -873,6 +874,7 @@ int ms_grad_param_count(const ms_ctx* c) {
 
 ms_status ms_grad(ms_ctx* c, const void* dphi_T, const void* dmu_T, double* dparams, void* dphi0,
                   void* dmu0) {
+  TraceRange trace("ms_grad");
   if (!c || !dphi_T) return fail(c, MS_ERR_ARG, "ctx and dphi_T are required");
   AdjointStore& A = c->adj;
   if (A.every <= 0) return fail(c, MS_ERR_STATE, "checkpoints are not enabled (ms_enable_checkpoints)");

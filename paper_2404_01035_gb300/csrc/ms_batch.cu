@@ -25,6 +25,7 @@
 #include "../../include/microsim_gb.h"
 #include "ms_launch.cuh"
 #include "ms_rt.h"
+#include "ms_trace.h"
 
 namespace msgb {
 
@@ -486,6 +487,7 @@ ms_status ms_batch_get_fields(ms_batch* b, int sim, void* phi, void* mu, int on_
 }
 
 ms_status ms_batch_step(ms_batch* b, int64_t n) {
+  TraceRange trace("ms_batch_step");
   if (!b || n < 0) return bfail(b, MS_ERR_ARG, "bad argument");
   if (n == 0) return MS_OK;
   // the grid barrier counts (steps x CTAs) in 32 bits: at most 2^20 steps per launch
@@ -551,6 +553,7 @@ ms_status ms_batch_set_tile(ms_batch* b, int ty) {
 int ms_batch_tile(const ms_batch* b) { return b ? b->ty : 0; }
 
 ms_status ms_batch_tune(ms_batch* b, int steps_per_trial, double* best_ms_per_step) {
+  TraceRange trace("ms_batch_tune");
   if (!b || steps_per_trial < 1) return bfail(b, MS_ERR_ARG, "bad argument");
   size_t tot = 0;
   for (int i = 0; i < b->nsims; ++i) tot = std::max(tot, b->off[i] + 2 * ((b->sbytes[i] + 255) / 256 * 256));

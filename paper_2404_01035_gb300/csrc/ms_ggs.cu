@@ -39,6 +39,7 @@
 #include "../../include/microsim_gb.h"
 #include "ms_device.cuh"
 #include "ms_rt.h"
+#include "ms_trace.h"
 
 namespace msgb {
 ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params* p, HostModel& m);
@@ -719,6 +720,7 @@ ms_status ms_ggs_get_fields(ms_ggs* s, void* phi, int on_device) {
 }
 
 ms_status ms_ggs_step(ms_ggs* s, int64_t n) {
+  TraceRange trace("ms_ggs_step");
   if (!s || n < 0) return gfail(s, MS_ERR_ARG, "bad argument");
   for (int64_t k = 0; k < n; ++k) {
     cudaError_t e = s->s == 8 ? step_once<double>(s) : step_once<float>(s);

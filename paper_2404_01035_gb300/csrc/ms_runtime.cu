@@ -17,6 +17,7 @@
 #include "../../include/microsim_gb.h"
 #include "ms_internal.h"
 #include "ms_rt.h"
+#include "ms_trace.h"
 
 namespace msgb {
 
@@ -749,6 +750,7 @@ ms_status ms_fields(ms_ctx* c, void** phi_dev, void** mu_dev, int64_t strides[4]
 }
 
 ms_status ms_step(ms_ctx* c, int64_t n) {
+  TraceRange trace("ms_step");
   if (!c) return fail(nullptr, MS_ERR_ARG, "ctx is NULL");
   if (n < 0) return fail(c, MS_ERR_ARG, "n must be >= 0");
   for (int64_t i = 0; i < n; ++i) {
@@ -789,6 +791,7 @@ ms_status ms_sync(ms_ctx* c) {
 }
 
 ms_status ms_diag(ms_ctx* c, double* out) {
+  TraceRange trace("ms_diag");
   if (!c || !out) return fail(c, MS_ERR_ARG, "ctx and out are required");
   ms_status s = launch_diag_now(c);
   if (s != MS_OK) return s;

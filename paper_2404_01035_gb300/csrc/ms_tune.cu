@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ms_rt.h"
+#include "ms_trace.h"
 
 using namespace msgb;
 
@@ -66,6 +67,7 @@ bool parse_int(const std::string& s, const char* field, int* v) {
 }  // namespace
 
 extern "C" ms_status ms_tune(ms_ctx* c, const char* cache_path, int steps, double* best_ms) {
+  TraceRange trace("ms_tune");
   if (!c) return fail(nullptr, MS_ERR_ARG, "ctx is NULL");
   if (steps < 1) steps = 10;
   const std::string key = cache_key(c);
