@@ -5,3 +5,4 @@ ABI in include/microsim_gb.h; this package is its thin Python binding.
 """
 from ._binding import MSError, lib  # noqa: F401
 from .simulation import Simulation  # noqa: F401
+from .infile import ModelSpec, read_filling, read_infile, write_infile  # noqa: F401

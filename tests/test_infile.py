@@ -1,0 +1,258 @@
+"""The paper-format input reader (`paper_2404_01035_gb300.infile`), on the CPU.
+
+Expected values are typed from the format the paper prints (Sec. "Input
+files"), not computed by the reader: pair lists in the order 12, 13, ..., 23;
+per-phase lists headed by the phase index; BOUNDARY codes per face; the
+Tempgrady tuple.  A spec written out and read back must drive the oracle
+exactly like the workload it came from.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from paper_2404_01035_gb300 import infile as I
+from paper_2404_01035_gb300.simulation import make_grid, make_params
+
+TERNARY_3D = """
+## a hand-written three-phase ternary deck in the paper's format
+DIMENSION = 3;
+MESH_X = 12;  MESH_Y = 10;  MESH_Z = 8;
+DELTA_X = 0.5; DELTA_Y = 0.5; DELTA_Z = 0.5;
+DELTA_t = 0.004;
+NUMPHASES = 3;
+NUMCOMPONENTS = 3;
+NTIMESTEPS = 250;
+COMPONENTS = {Al, Cu, Ag};
+PHASES = {alpha, beta, liquid};
+GAMMA = {1.1, 0.9, 1.3};                     # 12, 13, 23
+DIFFUSIVITY = {1, 0, 0.01, 0.02};            # diagonal: phase 0, D11, D22
+DIFFUSIVITY = {0, 2, 1.0, 0.8, 0.1};         # full: phase 2, D11, D22, D12
+BOUNDARY = {phi, 3, 3, 1, 1, 3, 3};
+BOUNDARY = {mu, 3, 3, 1, 1, 3, 3};
+BOUNDARY = {c, 3, 3, 1, 1, 3, 3};
+BOUNDARY = {T, 1, 1, 1, 1, 1, 1};            # the frozen temperature: not used
+BOUNDARY_VALUE = {phi, 0, 0, 0, 0, 0, 0};
+epsilon = 2.5;
+tau = 0.8;
+Tau = {0.28};                                # pairwise relaxation: not used
+Function_anisotropy = 1;
+Anisotropy_type = 4;
+dab = {0.01, 0.02, 0.03};
+Rotation_matrix = {0, 2, 0, 0, 30};
+Rotation_matrix = {1, 2, 90, 0, 0};
+Function_W = 2;
+Gamma_abc = {4.5};
+ISOTHERMAL = 0;
+Equilibrium_temperature = 1.0;
+Tempgrady = {0.97, 0.2, 40, 3, 0.05};
+Function_F = 1;
+A = {0, 1.0, 1.1, 0.05};                     # phase 0: A11, A22, A12
+A = {1, 0.9, 1.2, -0.02};
+A = {2, 1.0, 1.0, 0.0};
+ceq = {0, 0, 0.8, 0.1};
+ceq = {0, 2, 0.4, 0.3};                      # the liquid's value again: not used for phase 0
+ceq = {1, 1, 0.1, 0.7};
+ceq = {2, 2, 0.4, 0.3};
+slopes = {0, 0, -0.1, 0.02};
+slopes = {1, 1, 0.05, -0.03};
+slopes = {2, 2, 0.0, 0.0};
+Noise_phasefield = 1;
+Amp_Noise_Phase = 0.02;
+SAVET = 50;
+"""
+
+
+def test_parse_values_lists_comments_and_repeats():
+    kv = I.parse("A = 1;  # one\nB = {1, x, 'y', 2e-3};\nB = {};\nC = word;\n## D = 5;\n")
+    assert kv["A"] == [1.0]
+    assert kv["B"] == [[1.0, "x", "y", 0.002], []]
+    assert kv["C"] == ["word"]
+    assert "D" not in kv
+    for bad in ("A 1;", "A = {1, 2;", "1A = 3;"):
+        with pytest.raises(ValueError):
+            I.parse(bad)
+
+
+def test_ternary_deck_maps_onto_the_spec():
+    s = I.read_infile(TERNARY_3D)
+    assert (s.dim, s.nx, s.ny, s.nz, s.n_phases, s.n_components) == (3, 12, 10, 8, 3, 3)
+    assert (s.dx, s.dt, s.eps, s.tau, s.steps) == (0.5, 0.004, 2.5, 0.8, 250)
+    assert s.bc == [3, 1, 3] and s.potential == "well"
+    np.testing.assert_array_equal(s.gamma, [[0, 1.1, 0.9], [1.1, 0, 1.3], [0.9, 1.3, 0]])
+    np.testing.assert_array_equal(s.delta, [[0, 0.01, 0.02], [0.01, 0, 0.03], [0.02, 0.03, 0]])
+    np.testing.assert_array_equal(s.D[0], [[0.01, 0], [0, 0.02]])
+    np.testing.assert_array_equal(s.D[1], np.zeros((2, 2)))
+    np.testing.assert_array_equal(s.D[2], [[1.0, 0.1], [0.1, 0.8]])
+    np.testing.assert_array_equal(s.A[0], [[1.0, 0.05], [0.0, 1.1]])      # i <= j entries
+    np.testing.assert_array_equal(s.A[1], [[0.9, -0.02], [0.0, 1.2]])
+    np.testing.assert_array_equal(s.ceq, [[0.8, 0.1], [0.1, 0.7], [0.4, 0.3]])
+    np.testing.assert_array_equal(s.slopes, [[-0.1, 0.02], [0.05, -0.03], [0.0, 0.0]])
+    assert s.gamma3[0, 1, 2] == s.gamma3[2, 1, 0] == 4.5 and s.gamma3[0, 0, 1] == 0.0
+    # T = 0.97 + (0.2 / 40) (s - 3 - 0.05 t) along the last axis
+    assert (s.T0, s.G, s.z0, s.V, s.T_ref) == (0.97, 0.2 / 40, 3.0, 0.05, 1.0)
+    assert s.noise_amp == 0.02
+    assert s.meta["phases"] == ["alpha", "beta", "liquid"]
+    assert s.meta["components"] == ["Al", "Cu", "Ag"]
+    assert s.meta["ignored"] == ["SAVET", "Tau"]
+    # rotations: 30 degrees about z for (0, 2), 90 degrees about x for (1, 2)
+    c, h = math.cos(math.radians(30)), math.sin(math.radians(30))
+    np.testing.assert_allclose(s.rot[0, 2], [[c, -h, 0], [h, c, 0], [0, 0, 1]], atol=1e-15)
+    np.testing.assert_allclose(s.rot[2, 0], s.rot[0, 2], atol=0)
+    np.testing.assert_allclose(s.rot[1, 2] @ [0, 1, 0], [0, 0, 1], atol=1e-15)   # y turns into z
+    np.testing.assert_array_equal(s.rot[0, 1], np.eye(3))
+
+
+def test_euler_rotation_order_and_inverse():
+    # Rz Ry Rx: x first.  (90, 90, 0) takes y -> z (x-turn) -> +x (y-turn), while
+    # the other order (y-turn first) would leave y alone and then take it to z
+    R = I.euler_rotation(90, 90, 0)
+    np.testing.assert_allclose(R @ [0, 1, 0], [1, 0, 0], atol=1e-15)
+    np.testing.assert_allclose(I.euler_rotation(0, 0, 90) @ [1, 0, 0], [0, 1, 0], atol=1e-15)
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        ang = rng.uniform(-170, 170, 3)
+        ang[1] = rng.uniform(-85, 85)
+        R = I.euler_rotation(*ang)
+        np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-14)
+        assert np.linalg.det(R) == pytest.approx(1.0, abs=1e-14)
+        np.testing.assert_allclose(I._euler_angles(R), ang, atol=1e-9)
+
+
+@pytest.mark.parametrize("edit,match", [
+    (("Function_F = 1;", "Function_F = 3;"), "CALPHAD"),
+    (("BOUNDARY = {mu, 3, 3, 1, 1, 3, 3};", "BOUNDARY = {mu, 3, 3, 2, 2, 3, 3};"), "not supported"),
+    (("BOUNDARY = {phi, 3, 3, 1, 1, 3, 3};", "BOUNDARY = {phi, 3, 1, 1, 1, 3, 3};"), "differ"),
+    (("BOUNDARY = {c, 3, 3, 1, 1, 3, 3};", "BOUNDARY = {c, 1, 1, 1, 1, 3, 3};"), "other fields"),
+    (("DELTA_Z = 0.5;", "DELTA_Z = 0.25;"), "uniform"),
+    (("Anisotropy_type = 4;", "Anisotropy_type = 6;"), "four-fold"),
+    (("GAMMA = {1.1, 0.9, 1.3};", "GAMMA = {1.1, 0.9};"), "pair values"),
+    (("A = {1, 0.9, 1.2, -0.02};", "A = {1, 0.9, 1.2, -0.02, 7};"), "off-diagonal"),
+    (("DIMENSION = 3;", "DIMENSION = 4;"), "DIMENSION"),
+])
+def test_unsupported_input_is_refused(edit, match):
+    old, new = edit
+    assert TERNARY_3D.count(old) == 1
+    with pytest.raises(ValueError, match=match):
+        I.read_infile(TERNARY_3D.replace(old, new))
+
+
+def test_calphad_deck_reads_with_the_parabolic_coefficients_on_request():
+    s = I.read_infile(TERNARY_3D.replace("Function_F = 1;", "Function_F = 3;"), free_energy="parabolic")
+    np.testing.assert_array_equal(s.ceq[0], [0.8, 0.1])
+
+
+def test_elasticity_needs_one_homogeneous_stiffness():
+    base = TERNARY_3D + "EIGEN_STRAIN = {0, 0.01, 0.02, 0.03, 0.004, 0.005, 0.006};\n"
+    iso = base + "VOIGT_ISOTROPIC = {0, 3.0, 1.0, 1.0};\nVOIGT_ISOTROPIC = {2, 3.0, 1.0, 1.0};\n"
+    s = I.read_infile(iso, elasticity=True)
+    C = np.array([[3, 1, 1, 0, 0, 0], [1, 3, 1, 0, 0, 0], [1, 1, 3, 0, 0, 0],
+                  [0, 0, 0, 1, 0, 0], [0, 0, 0, 0, 1, 0], [0, 0, 0, 0, 0, 1]], dtype=float)
+    np.testing.assert_array_equal(s.elastic_C, C)
+    np.testing.assert_array_equal(s.eigenstrain[0], [[0.01, 0.006, 0.005], [0.006, 0.02, 0.004],
+                                                     [0.005, 0.004, 0.03]])
+    np.testing.assert_array_equal(s.eigenstrain[1], np.zeros((3, 3)))
+    assert I.read_infile(iso).elastic_C is None          # elasticity is opt-in
+    tet = base + "VOIGT_TETRAGONAL = {0, 3.0, 1.0, 0.8, 2.5, 0.9, 0.7};\n"
+    C = I.read_infile(tet, elasticity=True).elastic_C
+    assert (C[0, 0], C[1, 1], C[2, 2], C[0, 1], C[0, 2], C[1, 2], C[3, 3], C[4, 4], C[5, 5]) == \
+        (3.0, 3.0, 2.5, 1.0, 0.8, 0.8, 0.9, 0.9, 0.7)
+    with pytest.raises(ValueError, match="homogeneous"):
+        I.read_infile(base + "VOIGT_CUBIC = {0, 3.0, 1.0, 1.0};\nVOIGT_CUBIC = {2, 6.0, 2.0, 2.0};\n",
+                      elasticity=True)
+
+
+def _same_spec(a, b):
+    for k in ("dim", "nx", "ny", "n_phases", "n_components", "dx", "dt", "eps", "tau", "potential",
+              "T_ref", "T0", "G", "z0", "V"):
+        assert getattr(a, k) == pytest.approx(getattr(b, k), rel=1e-15, abs=1e-15), k
+    assert list(a.bc)[: a.dim] == list(b.bc)[: b.dim]
+    for k in ("gamma", "delta", "D", "A", "ceq", "slopes"):
+        np.testing.assert_allclose(np.asarray(getattr(a, k)), np.asarray(getattr(b, k)), atol=1e-15, err_msg=k)
+    np.testing.assert_allclose(a.rot, b.rot, atol=1e-14)
+    ga, gb = getattr(a, "gamma3", None), getattr(b, "gamma3", None)
+    assert (ga is None or not np.any(ga)) == (gb is None or not np.any(gb))
+    if ga is not None and np.any(ga):
+        np.testing.assert_allclose(ga, gb, atol=1e-15)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.cfg1(),
+    lambda: W.small_multiphase(n=10, dim=3, N=3, NM=2, rotate=True),
+    lambda: W.small_multiphase(n=12, dim=2, N=4, NM=1, potential="well", gamma3=2.0),
+])
+def test_written_deck_reads_back_and_drives_the_oracle_identically(make):
+    p = make()
+    p.f0 = np.zeros(p.n_phases)        # the infile has no isothermal offsets
+    s = I.read_infile(I.write_infile(p))
+    _same_spec(s, p)
+    a = oracle.run(p, p.phi0, p.mu0, 3)
+    b = oracle.run(s, p.phi0, p.mu0, 3)
+    assert max(np.abs(a[0] - b[0]).max(), np.abs(a[1] - b[1]).max()) < 1e-13
+
+
+def test_spec_marshals_like_the_workload_problem():
+    p = W.small_multiphase(n=10, dim=3, N=3, NM=2, rotate=True)
+    p.f0 = np.zeros(3)
+    s = I.read_infile(I.write_infile(p))
+    ka, kb = [], []
+    pa, pb = make_params(p, "f64", ka), make_params(s, "f64", kb)
+    for name, ctype in pa._fields_:
+        if ctype is ctypes.c_void_p:
+            continue                   # addresses: the arrays behind them are compared below
+        assert getattr(pa, name) == pytest.approx(getattr(pb, name), abs=1e-14), name
+    assert len(ka) == len(kb)
+    for x, y in zip(ka, kb):
+        np.testing.assert_allclose(x, y, atol=1e-14)
+    ga, gb = make_grid(p), make_grid(s)
+    assert (ga.dim, ga.nx, ga.ny, ga.nz, ga.dx, list(ga.bc)) == (gb.dim, gb.nx, gb.ny, gb.nz, gb.dx, list(gb.bc))
+
+
+def test_filling_shapes_sharp():
+    s = I.read_infile(TERNARY_3D)
+    fill = """
+    FILLCUBE = {0, 2, 3, 1, 5, 6, 4};          # cells x 2..5, y 3..6, z 1..4
+    #FILLSPHERE = {1, 6, 5, 4, 3};             # commented out
+    FILLSPHERE = {1, 9, 2, 6, 1.5};
+    """
+    phi = I.read_filling(fill, s, diffuse=False)
+    assert phi.shape == (3, 8, 10, 12)
+    np.testing.assert_array_equal(phi.sum(axis=0), 1.0)
+    assert phi[0].sum() == 4 * 4 * 4
+    assert phi[0, 1:5, 3:7, 2:6].min() == 1.0
+    # sphere of radius 1.5 about cell (9, 2, 6): cells at distance < 1.5 (1 + 6 + 12 = 19)
+    assert phi[1].sum() == 19
+    assert phi[2].sum() == 8 * 10 * 12 - 64 - 19
+
+
+def test_filling_later_lines_paint_over_and_profiles_are_diffuse():
+    s = I.read_infile(TERNARY_3D.replace("DIMENSION = 3;", "DIMENSION = 2;").replace("MESH_X = 12;", "MESH_X = 64;")
+                      .replace("MESH_Y = 10;", "MESH_Y = 64;").replace("Function_W = 2;", "Function_W = 1;"))
+    assert s.dim == 2 and s.nz == 1 and s.potential == "obstacle"
+    fill = "FILLCYLINDER = {0, 32, 32, 0, 0, 20};\nFILLELLIPSE = {1, 32, 32, 6, 0.6, 30};\n"
+    sharp = I.read_filling(fill, s, diffuse=False)
+    # ellipse: semi-axes 6 and 4.8 (eccentricity 0.6) painted over the disc
+    assert abs(sharp[1].sum() - math.pi * 6 * 4.8) < 0.1 * math.pi * 6 * 4.8
+    assert abs(sharp[0].sum() - (math.pi * 400 - math.pi * 6 * 4.8)) < 0.03 * math.pi * 400
+    phi = I.read_filling(fill, s)
+    np.testing.assert_allclose(phi.sum(axis=0), 1.0, atol=1e-14)
+    assert phi.min() >= 0.0
+    # the disc's boundary along +x, beyond the ellipse's compact profile: phi_0 is
+    # exactly 1/2 at radius 20, and the sine profile spans pi^2 eps / 4 cells
+    row = phi[0, 0, 32]
+    assert row[52] == 0.5
+    half = math.pi ** 2 * (s.eps / s.dx) / 8
+    assert row[52 - int(half) + 1] < 1.0 and row[52 - int(half) - 1] == 1.0
+    assert row[52 + int(half) - 1] > 0.0 and row[52 + int(half) + 1] == 0.0
+
+
+def test_liquid_mu_gives_the_liquid_its_composition():
+    s = I.read_infile(TERNARY_3D)
+    for c in ([0.4, 0.3], [0.2, 0.5]):
+        mu = I.liquid_mu(s, c)
+        for T in (0.9, 1.0, 1.1):
+            cl, _, _ = oracle.thermo(s, s.n_phases - 1, mu, T)
+            np.testing.assert_allclose(cl, c, atol=1e-14)
