@@ -132,7 +132,7 @@ _USED = {
     "Rotation_matrix", "Function_W", "Gamma_abc", "ISOTHERMAL", "T", "Tempgrady",
     "Equilibrium_temperature", "Function_F", "A", "ceq", "slopes", "Noise_phasefield",
     "Amp_Noise_Phase", "EIGEN_STRAIN", "VOIGT_ISOTROPIC", "VOIGT_CUBIC", "VOIGT_TETRAGONAL",
-    "COMPONENTS", "PHASES",
+    "COMPONENTS", "PHASES", "cfill", "SAVET",
 }
 
 
@@ -379,7 +379,13 @@ def read_infile(src: str, *, free_energy: Optional[str] = None, elasticity: bool
     if elasticity:
         spec.elastic_C = _stiffness(kv, N)
         spec.eigenstrain = _eigenstrain(kv, N)
+    cfill = {}
+    for e in kv.get("cfill", []):
+        if int(e[0]) == int(e[1]):    # phase a's own fill composition, like ceq
+            cfill[int(e[0])] = [float(v) for v in e[2:2 + NM]]
     spec.meta = {
+        "cfill": cfill,
+        "savet": int(_num(kv, "SAVET", 0.0)),
         "phases": [str(v) for v in _one(kv, "PHASES", [], required=False) or []],
         "components": [str(v) for v in _one(kv, "COMPONENTS", [], required=False) or []],
         "ignored": sorted(k for k in kv if k not in _USED),

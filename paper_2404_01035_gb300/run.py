@@ -1,0 +1,113 @@
+"""Run a simulation from the paper's input files.
+
+    python -m paper_2404_01035_gb300.run INFILE FILLING [--steps N] [--save-every K]
+                                         [--out DIR] [--dtype f32|f64] [--dry-run] ...
+
+The infile gives the grid and the parameters (`read_infile`), the filling
+file the initial phases (`read_filling`).  The initial chemical potential is
+uniform, the value at which the liquid has its fill composition (cfill of the
+liquid, else its ceq).  Every `--save-every` steps (default SAVET, else
+NTIMESTEPS) the driver prints the FP64 diagnostics as one JSON line and
+writes the state to DIR/step_<n>.npz (phi, mu, step, t).  It stops with
+exit code 3 if the library reports a non-finite state.  `--dry-run` reads and
+checks the inputs and prints their summary without touching the GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+from typing import List, Optional
+
+import numpy as np
+
+from .infile import liquid_mu, read_filling, read_infile
+
+
+def build_inputs(args):
+    spec = read_infile(args.infile, free_energy=args.free_energy, elasticity=args.elasticity,
+                       anti_trapping=args.anti_trapping, grain_growth=args.grain_growth,
+                       noise_seed=args.noise_seed)
+    phi0 = read_filling(args.filling, spec, diffuse=not args.sharp)
+    liq = spec.n_phases - 1
+    c = spec.meta["cfill"].get(liq, list(spec.ceq[liq]))
+    mu_val = liquid_mu(spec, c)
+    mu0 = np.broadcast_to(mu_val[:, None, None, None], (spec.n_mu,) + phi0.shape[1:]).copy()
+    return spec, phi0, mu0
+
+
+def _summary(spec, phi0, mu0, steps, every):
+    return {
+        "grid": [spec.dim, spec.nx, spec.ny, spec.nz], "dx": spec.dx, "dt": spec.dt,
+        "phases": spec.n_phases, "components": spec.n_components, "bc": list(spec.bc)[: spec.dim],
+        "potential": spec.potential, "anisotropic": bool(np.any(spec.delta)),
+        "temperature": {"T0": spec.T0, "G": spec.G, "z0": spec.z0, "V": spec.V},
+        "options": {"anti_trapping": spec.anti_trapping, "grain_growth": spec.grain_growth,
+                    "elasticity": spec.elastic_C is not None, "noise_amp": spec.noise_amp},
+        "phase_fractions": [float(v) for v in phi0.reshape(spec.n_phases, -1).mean(axis=1)],
+        "mu0": [float(v) for v in mu0.reshape(spec.n_mu, -1)[:, 0]],
+        "steps": steps, "save_every": every, "ignored_keys": spec.meta["ignored"],
+    }
+
+
+def main(argv: Optional[List[str]] = None) -> int:
+    ap = argparse.ArgumentParser(prog="python -m paper_2404_01035_gb300.run", description=__doc__.split("\n\n")[0])
+    ap.add_argument("infile")
+    ap.add_argument("filling")
+    ap.add_argument("--steps", type=int, default=None, help="default: NTIMESTEPS")
+    ap.add_argument("--save-every", type=int, default=None, help="default: SAVET, else the whole run")
+    ap.add_argument("--out", default="microsim_out")
+    ap.add_argument("--dtype", choices=("f32", "f64"), default="f32")
+    ap.add_argument("--sharp", action="store_true", help="fill shapes without the equilibrium profile")
+    ap.add_argument("--free-energy", choices=("parabolic",), default=None)
+    ap.add_argument("--elasticity", action="store_true")
+    ap.add_argument("--anti-trapping", action="store_true")
+    ap.add_argument("--grain-growth", action="store_true")
+    ap.add_argument("--noise-seed", type=int, default=0)
+    ap.add_argument("--dry-run", action="store_true")
+    args = ap.parse_args(argv)
+
+    spec, phi0, mu0 = build_inputs(args)
+    steps = args.steps if args.steps is not None else spec.steps
+    if steps < 0:
+        ap.error("--steps must be >= 0")
+    every = args.save_every or spec.meta.get("savet") or steps or 1
+    info = _summary(spec, phi0, mu0, steps, every)
+    print(json.dumps({"inputs": info}), flush=True)
+    if args.dry_run:
+        return 0
+
+    from ._binding import MSError
+    from .simulation import Simulation      # needs the CUDA library and a GPU
+    os.makedirs(args.out, exist_ok=True)
+
+    def save(sim, d):
+        phi, mu = sim.get_fields()
+        np.savez(os.path.join(args.out, f"step_{d['step']:010d}.npz"), phi=phi, mu=mu, step=d["step"], t=d["t"])
+
+    with Simulation(spec, dtype=args.dtype) as sim:
+        sim.set_fields(phi0, mu0)
+        d = sim.diag()
+        save(sim, d)
+        done = 0
+        while done < steps:
+            k = min(every, steps - done)
+            try:
+                sim.step(k)
+                d = sim.diag()
+            except MSError as e:
+                if e.status != 5:               # anything but MS_ERR_NONFINITE
+                    raise
+                print(json.dumps({"error": "the state became non-finite", "after_step": done + k}), flush=True)
+                return 3
+            done += k
+            print(json.dumps({"step": d["step"], "t": d["t"], "mass": [float(v) for v in d["mass"]],
+                              "sum_err": d["sum_err"], "phi_min": d["phi_min"], "phi_max": d["phi_max"]}),
+                  flush=True)
+            save(sim, d)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

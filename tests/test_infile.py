@@ -97,7 +97,8 @@ def test_ternary_deck_maps_onto_the_spec():
     assert s.noise_amp == 0.02
     assert s.meta["phases"] == ["alpha", "beta", "liquid"]
     assert s.meta["components"] == ["Al", "Cu", "Ag"]
-    assert s.meta["ignored"] == ["SAVET", "Tau"]
+    assert s.meta["ignored"] == ["Tau"]
+    assert s.meta["savet"] == 50
     # rotations: 30 degrees about z for (0, 2), 90 degrees about x for (1, 2)
     c, h = math.cos(math.radians(30)), math.sin(math.radians(30))
     np.testing.assert_allclose(s.rot[0, 2], [[c, -h, 0], [h, c, 0], [0, 0, 1]], atol=1e-15)
@@ -256,3 +257,32 @@ def test_liquid_mu_gives_the_liquid_its_composition():
         for T in (0.9, 1.0, 1.1):
             cl, _, _ = oracle.thermo(s, s.n_phases - 1, mu, T)
             np.testing.assert_allclose(cl, c, atol=1e-14)
+
+
+FILLING_2D = """
+FILLCYLINDER = {0, 16, 16, 0, 0, 6};
+FILLCUBE = {1, 30, 4, 0, 40, 12, 0};
+"""
+
+
+def test_run_driver_dry_run(tmp_path, capsys):
+    """The command-line driver reads and checks a deck and a filling file and
+    reports them without a GPU (--dry-run)."""
+    import json
+    from paper_2404_01035_gb300 import run
+    deck = (TERNARY_3D.replace("DIMENSION = 3;", "DIMENSION = 2;").replace("MESH_X = 12;", "MESH_X = 48;")
+            .replace("MESH_Y = 10;", "MESH_Y = 32;") + "cfill = {2, 2, 0.35, 0.25};\n")
+    (tmp_path / "deck.in").write_text(deck)
+    (tmp_path / "fill.in").write_text(FILLING_2D)
+    rc = run.main([str(tmp_path / "deck.in"), str(tmp_path / "fill.in"), "--dry-run"])
+    assert rc == 0
+    info = json.loads(capsys.readouterr().out.strip().splitlines()[-1])["inputs"]
+    assert info["grid"] == [2, 48, 32, 1] and info["steps"] == 250 and info["save_every"] == 50
+    assert info["bc"] == [3, 1] and info["potential"] == "well" and info["ignored_keys"] == ["Tau"]
+    s = I.read_infile(deck)
+    np.testing.assert_allclose(info["mu0"], I.liquid_mu(s, [0.35, 0.25]), atol=1e-15)
+    assert sum(info["phase_fractions"]) == pytest.approx(1.0, abs=1e-14)
+    assert 0.0 < info["phase_fractions"][0] < info["phase_fractions"][2]
+    with pytest.raises(ValueError, match="CALPHAD"):
+        (tmp_path / "bad.in").write_text(deck.replace("Function_F = 1;", "Function_F = 2;"))
+        run.main([str(tmp_path / "bad.in"), str(tmp_path / "fill.in"), "--dry-run"])
