@@ -328,7 +328,13 @@ int ms_grad_param_count(const ms_ctx* ctx);
  * recorded step.  Synchronous.  Segments between snapshots are recomputed with
  * the forward kernel; per reverse step three adjoint kernels run (per cell,
  * per face, per cell: a gather, no atomics, deterministic).  The current
- * state is left unchanged. */
+ * state is left unchanged.  Work buffers (two adjoint states, the per-face
+ * records, one segment of `every` states, FP64 partials) are allocated on
+ * first use through the context's allocator and kept until ms_destroy.
+ * Errors: MS_ERR_STATE without checkpoints or with snapshots missing;
+ * MS_ERR_UNSUPPORTED as for ms_enable_checkpoints; MS_ERR_OOM when a work
+ * buffer cannot be allocated (nothing is left half-made: the next call
+ * allocates what is missing); MS_ERR_CUDA on a failed launch or copy. */
 ms_status ms_grad(ms_ctx* ctx, const void* dphi_T, const void* dmu_T, double* dparams,
                   void* dphi0, void* dmu0);
 
