@@ -480,10 +480,12 @@ def read_filling(src: str, spec, *, diffuse: bool = True, matrix: Optional[int] 
       FILLELLIPSE  = {phase, xc, yc, zc, major_axis, eccentricity, angle_deg}
                      (or without zc on a 2-D grid), in the x-y plane
     Later lines paint over earlier ones; cells no shape covers hold the
-    matrix phase (default: the last phase, the liquid).  With `diffuse`,
-    each shape's indicator becomes the equilibrium profile of the spec's
-    potential in the signed distance to its boundary (a cube's distance is
-    the box distance), so the interface starts near its relaxed width."""
+    matrix phase (default: the last phase, the liquid).  A box side or a
+    cylinder end on the grid's edge continues past it, so the edge is no
+    interface.  With `diffuse`, each shape's indicator becomes the
+    equilibrium profile of the spec's potential in the signed distance to
+    its boundary (a box's distance is the box distance), so the interface
+    starts near its relaxed width."""
     text = open(src).read() if os.path.exists(src) else src
     kv = parse(text)
     N = int(spec.n_phases)
@@ -507,21 +509,23 @@ def read_filling(src: str, spec, *, diffuse: bool = True, matrix: Optional[int] 
         a = int(e[0])
         if key == "FILLCUBE":
             x0, y0, z0, x1, y1, z1 = e[1:7]
-            lo = np.array([x0, y0, z0 if spec.dim == 3 else 0.0]) - 0.5
-            hi = np.array([x1, y1, z1 if spec.dim == 3 else 0.0]) + 0.5
-            c = (lo + hi) / 2
-            h = (hi - lo) / 2
-            q = np.stack([np.abs(x - c[0]) - h[0], np.abs(y - c[1]) - h[1], np.abs(z - c[2]) - h[2]])
-            if spec.dim == 2:
-                q[2] = -np.inf
-            outside = np.linalg.norm(np.maximum(q, 0.0), axis=0)
-            inside = np.minimum(np.max(q, axis=0), 0.0)
-            u = -(outside + inside)
+            axes = [(x, x0, x1, nx), (y, y0, y1, ny)] + ([(z, z0, z1, nz)] if spec.dim == 3 else [])
+            inside = np.full(x.shape, np.inf)
+            excess2 = np.zeros(x.shape)
+            for coord, i0, i1, n in axes:
+                lo = -np.inf if i0 <= 0 else i0 - 0.5       # a side on the grid's edge continues past it
+                hi = np.inf if i1 >= n - 1 else i1 + 0.5
+                d = np.minimum(coord - lo, hi - coord)
+                inside = np.minimum(inside, d)
+                excess2 += np.maximum(-d, 0.0) ** 2
+            u = np.where(inside > 0, inside, -np.sqrt(excess2))
         elif key == "FILLCYLINDER":
             xc, yc, zs, ze, r = e[1:6]
             u = r - np.hypot(x - xc, y - yc)
             if spec.dim == 3:
-                u = np.minimum(u, np.minimum(z - (zs - 0.5), (ze + 0.5) - z))
+                lo = -np.inf if zs <= 0 else zs - 0.5
+                hi = np.inf if ze >= nz - 1 else ze + 0.5
+                u = np.minimum(u, np.minimum(z - lo, hi - z))
         elif key == "FILLSPHERE":
             xc, yc, zc, r = e[1:5]
             u = r - np.sqrt((x - xc) ** 2 + (y - yc) ** 2 + ((z - zc) ** 2 if spec.dim == 3 else 0.0))

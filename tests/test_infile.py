@@ -8,6 +8,7 @@ exactly like the workload it came from.
 """
 import ctypes
 import math
+import os
 
 import numpy as np
 import pytest
@@ -286,3 +287,106 @@ def test_run_driver_dry_run(tmp_path, capsys):
     with pytest.raises(ValueError, match="CALPHAD"):
         (tmp_path / "bad.in").write_text(deck.replace("Function_F = 1;", "Function_F = 2;"))
         run.main([str(tmp_path / "bad.in"), str(tmp_path / "fill.in"), "--dry-run"])
+
+
+DECKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "decks")
+
+
+def test_bundled_deck_passes_the_library_checks():
+    """The deck the GPU driver test runs is one the library accepts: ms_create on
+    the CPU gets through the parameter, stability and compiled-kernel checks and
+    stops only at the device allocation (MS_ERR_OOM without a GPU)."""
+    from paper_2404_01035_gb300 import _binding as B
+    s = I.read_infile(os.path.join(DECKS, "ternary_2d.in"))
+    keep = []
+    params = make_params(s, "f64", keep)
+    grid = make_grid(s)
+    h = ctypes.c_void_p()
+    rc = B.lib().ms_create(ctypes.byref(grid), s.n_phases, s.n_components, ctypes.byref(params),
+                           None, None, ctypes.byref(h))
+    msg = B.lib().ms_last_error(None).decode()
+    assert rc == 3 and "allocation" in msg, (rc, msg)
+    phi = I.read_filling(os.path.join(DECKS, "ternary_2d.fill"), s)
+    assert phi[0].max() == 1.0 and phi[1].max() == 1.0 and phi[2].min() == 0.0
+    o = oracle.run(s, phi, np.broadcast_to(I.liquid_mu(s, [0.38, 0.33])[:, None, None, None],
+                                            (2,) + phi.shape[1:]).copy(), 40)
+    assert np.isfinite(o[0]).all() and np.isfinite(o[1]).all()
+
+
+class _OracleSim:
+    """Stands in for Simulation in the driver's CPU test: the same calls, the
+    oracle's step behind them."""
+    fail_at = None
+
+    def __init__(self, spec, dtype="f32"):
+        self.spec = spec
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def set_fields(self, phi, mu):
+        self.phi, self.mu = np.array(phi, dtype=float), np.array(mu, dtype=float)
+        self.n, self.t = 0, 0.0
+
+    def step(self, k):
+        self.phi, self.mu = oracle.run(self.spec, self.phi, self.mu, k, t0=self.t, step0=self.n)
+        self.n += k
+        self.t = self.n * self.spec.dt
+
+    def diag(self):
+        from paper_2404_01035_gb300._binding import MSError
+        if self.fail_at is not None and self.n >= self.fail_at:
+            raise MSError(5, "non-finite state")
+        return {"mass": self.mu.reshape(self.mu.shape[0], -1).sum(axis=1), "sum_err": 0.0,
+                "phi_min": float(self.phi.min()), "phi_max": float(self.phi.max()), "nonfinite": 0.0,
+                "step": self.n, "t": self.t}
+
+    def get_fields(self):
+        return self.phi.copy(), self.mu.copy()
+
+
+def test_run_driver_loop_and_snapshots_with_the_oracle_behind_it(tmp_path, monkeypatch, capsys):
+    """The driver's stepping, diagnostics and snapshot files, with the GPU
+    simulation replaced by the oracle: snapshots every SAVET steps, named by
+    step, holding the state the oracle reaches in one run of as many steps."""
+    import json
+    from paper_2404_01035_gb300 import run, simulation
+    monkeypatch.setattr(simulation, "Simulation", _OracleSim)
+    deck, fill = os.path.join(DECKS, "ternary_2d.in"), os.path.join(DECKS, "ternary_2d.fill")
+    out = tmp_path / "out"
+    assert run.main([deck, fill, "--out", str(out)]) == 0
+    files = sorted(os.listdir(out))
+    assert files == ["step_0000000000.npz", "step_0000000020.npz", "step_0000000040.npz"]
+    s = I.read_infile(deck)
+    phi0 = I.read_filling(fill, s)
+    mu0 = np.broadcast_to(I.liquid_mu(s, [0.38, 0.33])[:, None, None, None], (2,) + phi0.shape[1:]).copy()
+    np.testing.assert_array_equal(np.load(out / files[0])["phi"], phi0)
+    o_phi, o_mu = oracle.run(s, phi0, mu0, 40)
+    last = np.load(out / files[2])
+    assert max(np.abs(last["phi"] - o_phi).max(), np.abs(last["mu"] - o_mu).max()) < 1e-14
+    assert int(last["step"]) == 40 and float(last["t"]) == pytest.approx(40 * s.dt, rel=1e-12)
+    lines = [json.loads(x) for x in capsys.readouterr().out.strip().splitlines()]
+    assert [d["step"] for d in lines[1:]] == [20, 40]
+    # --steps and --save-every override the deck; a non-finite state ends the run with code 3
+    _OracleSim.fail_at = 15
+    try:
+        assert run.main([deck, fill, "--out", str(tmp_path / "o2"), "--steps", "30", "--save-every", "10"]) == 3
+    finally:
+        _OracleSim.fail_at = None
+    assert sorted(os.listdir(tmp_path / "o2")) == ["step_0000000000.npz", "step_0000000010.npz"]
+
+
+def test_a_shape_on_the_grid_edge_has_no_interface_there():
+    """A box laid on the lower y edge (a solid against the no-flux wall) is full up
+    to the wall; its profile sits only at its free top and sides."""
+    s = I.read_infile(os.path.join(DECKS, "ternary_2d.in"))
+    phi = I.read_filling("FILLCUBE = {1, 20, 0, 0, 35, 9, 0};", s)
+    col = phi[1, 0, :, 27]                  # through the box, along y
+    assert col[0] == 1.0 and col[4] == 1.0   # no diffuse layer at the wall
+    assert 0.0 < col[9] < 1.0
+    assert col[9] > col[10] > col[11]
+    row = phi[1, 0, 2, :]                   # along x: the box's sides are diffuse
+    assert 0.0 < row[20] < 1.0 and 0.0 < row[35] < 1.0 and row[27] == 1.0

@@ -5,7 +5,8 @@ budget, a stream being captured into a CUDA graph, a latency-bound loop) use
 ms_diag_noalloc on fields they hold; it must agree with ms_diag, which works
 on a library context.  Two calls in a row check that the shared scratch array
 left over from one call does not leak into the next.  This file is collected
-last so that a run stopping at its first failure has run everything else.
+after the rest of the GPU suite (only the input-deck driver's test follows
+it), so that a run stopping at its first failure has run everything else.
 """
 import ctypes
 
