@@ -8,7 +8,9 @@ file the initial phases (`read_filling`).  The initial chemical potential is
 uniform, the value at which the liquid has its fill composition (cfill of the
 liquid, else its ceq).  Every `--save-every` steps (default SAVET, else
 NTIMESTEPS) the driver prints the FP64 diagnostics as one JSON line and
-writes the state to DIR/step_<n>.npz (phi, mu, step, t).  It stops with
+writes the state to DIR/step_<n>.npz (phi, mu, step, t), or with
+`--format vtk` to DIR/step_<n>.vtk (legacy VTK, one scalar per phase and
+solute).  It stops with
 exit code 3 if the library reports a non-finite state.  `--dry-run` reads and
 checks the inputs and prints their summary without touching the GPU.
 """
@@ -37,6 +39,23 @@ def build_inputs(args):
     return spec, phi0, mu0
 
 
+def write_vtk(path: str, phi: np.ndarray, mu: np.ndarray, dx: float, names=None, title: str = "microsim"):
+    """Legacy VTK structured points (binary, big-endian FP64), one point per
+    cell at its centre: phi_<phase> then mu_<solute> scalars, readable by
+    ParaView and VisIt."""
+    nz, ny, nx = phi.shape[1:]
+    names = names or [f"phi_{a}" for a in range(phi.shape[0])] + [f"mu_{i}" for i in range(mu.shape[0])]
+    with open(path, "wb") as f:
+        head = (f"# vtk DataFile Version 3.0\n{title}\nBINARY\nDATASET STRUCTURED_POINTS\n"
+                f"DIMENSIONS {nx} {ny} {nz}\nORIGIN {dx / 2!r} {dx / 2!r} {dx / 2!r}\n"
+                f"SPACING {dx!r} {dx!r} {dx!r}\nPOINT_DATA {nx * ny * nz}\n")
+        f.write(head.encode())
+        for name, field_ in zip(names, list(phi) + list(mu)):
+            f.write(f"SCALARS {name} double 1\nLOOKUP_TABLE default\n".encode())
+            f.write(np.ascontiguousarray(field_, dtype=">f8").tobytes())
+            f.write(b"\n")
+
+
 def _summary(spec, phi0, mu0, steps, every):
     return {
         "grid": [spec.dim, spec.nx, spec.ny, spec.nz], "dx": spec.dx, "dt": spec.dt,
@@ -58,6 +77,7 @@ def main(argv: Optional[List[str]] = None) -> int:
     ap.add_argument("--steps", type=int, default=None, help="default: NTIMESTEPS")
     ap.add_argument("--save-every", type=int, default=None, help="default: SAVET, else the whole run")
     ap.add_argument("--out", default="microsim_out")
+    ap.add_argument("--format", choices=("npz", "vtk"), default="npz", help="snapshot format")
     ap.add_argument("--dtype", choices=("f32", "f64"), default="f32")
     ap.add_argument("--sharp", action="store_true", help="fill shapes without the equilibrium profile")
     ap.add_argument("--free-energy", choices=("parabolic",), default=None)
@@ -82,9 +102,16 @@ def main(argv: Optional[List[str]] = None) -> int:
     from .simulation import Simulation      # needs the CUDA library and a GPU
     os.makedirs(args.out, exist_ok=True)
 
+    names = ([f"phi_{n}" for n in spec.meta["phases"]] if len(spec.meta["phases"]) == spec.n_phases
+             else [f"phi_{a}" for a in range(spec.n_phases)]) + [f"mu_{i}" for i in range(spec.n_mu)]
+
     def save(sim, d):
         phi, mu = sim.get_fields()
-        np.savez(os.path.join(args.out, f"step_{d['step']:010d}.npz"), phi=phi, mu=mu, step=d["step"], t=d["t"])
+        stem = os.path.join(args.out, f"step_{d['step']:010d}")
+        if args.format == "vtk":
+            write_vtk(stem + ".vtk", phi, mu, spec.dx, names, f"step {d['step']} t {d['t']!r}")
+        else:
+            np.savez(stem + ".npz", phi=phi, mu=mu, step=d["step"], t=d["t"])
 
     with Simulation(spec, dtype=args.dtype) as sim:
         sim.set_fields(phi0, mu0)

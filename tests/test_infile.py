@@ -390,3 +390,49 @@ def test_a_shape_on_the_grid_edge_has_no_interface_there():
     assert col[9] > col[10] > col[11]
     row = phi[1, 0, 2, :]                   # along x: the box's sides are diffuse
     assert 0.0 < row[20] < 1.0 and 0.0 < row[35] < 1.0 and row[27] == 1.0
+
+
+def _read_vtk(path):
+    """A reader for the legacy VTK files the driver writes (header lines, then
+    one big-endian FP64 block per scalar)."""
+    data = open(path, "rb").read()
+    pos, header, fields = 0, {}, {}
+
+    def line():
+        nonlocal pos
+        end = data.index(b"\n", pos)
+        s = data[pos:end].decode()
+        pos = end + 1
+        return s
+
+    assert line().startswith("# vtk DataFile")
+    header["title"] = line()
+    assert line() == "BINARY" and line() == "DATASET STRUCTURED_POINTS"
+    header["dims"] = [int(v) for v in line().split()[1:]]
+    header["origin"] = [float(v) for v in line().split()[1:]]
+    header["spacing"] = [float(v) for v in line().split()[1:]]
+    n = int(line().split()[1])
+    while pos < len(data):
+        name = line().split()[1]
+        assert line() == "LOOKUP_TABLE default"
+        fields[name] = np.frombuffer(data[pos:pos + 8 * n], dtype=">f8")
+        pos += 8 * n + 1
+    return header, fields
+
+
+def test_run_driver_writes_vtk_snapshots(tmp_path, monkeypatch):
+    from paper_2404_01035_gb300 import run, simulation
+    monkeypatch.setattr(simulation, "Simulation", _OracleSim)
+    deck, fill = os.path.join(DECKS, "ternary_2d.in"), os.path.join(DECKS, "ternary_2d.fill")
+    out = tmp_path / "vtk"
+    assert run.main([deck, fill, "--out", str(out), "--format", "vtk", "--steps", "20"]) == 0
+    assert sorted(os.listdir(out)) == ["step_0000000000.vtk", "step_0000000020.vtk"]
+    head, fields = _read_vtk(out / "step_0000000020.vtk")
+    s = I.read_infile(deck)
+    assert head["dims"] == [56, 40, 1] and head["spacing"] == [1.0, 1.0, 1.0] and head["origin"] == [0.5] * 3
+    assert list(fields) == ["phi_alpha", "phi_beta", "phi_liquid", "mu_0", "mu_1"]
+    phi0 = I.read_filling(fill, s)
+    mu0 = np.broadcast_to(I.liquid_mu(s, [0.38, 0.33])[:, None, None, None], (2,) + phi0.shape[1:]).copy()
+    o_phi, o_mu = oracle.run(s, phi0, mu0, 20)
+    np.testing.assert_array_equal(fields["phi_beta"], o_phi[1].ravel())   # x fastest, as the array
+    np.testing.assert_array_equal(fields["mu_1"], o_mu[1].ravel())
