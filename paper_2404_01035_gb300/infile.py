@@ -184,6 +184,17 @@ def euler_rotation(ax: float, ay: float, az: float) -> np.ndarray:
     return Rz @ Ry @ Rx
 
 
+def _phase(v, N, key) -> int:
+    a = int(v)
+    if a != v or not 0 <= a < N:
+        raise ValueError(f"{key}: phase index {v!r} is not one of 0..{N - 1}")
+    return a
+
+
+def _names(v):
+    return [] if v is None else [str(x) for x in (v if isinstance(v, list) else [v])]
+
+
 def _sym_from_list(vals, n, key):
     """[diag_1..diag_n, off_12, off_13, ..., off_23, ...] -> symmetric n x n."""
     off = [(i, j) for i in range(n) for j in range(i + 1, n)]
@@ -234,8 +245,10 @@ def _stiffness(kv, N):
     Cs = {}
     for key in ("VOIGT_ISOTROPIC", "VOIGT_CUBIC", "VOIGT_TETRAGONAL"):
         for e in kv.get(key, []):
-            a = int(e[0])
+            a = _phase(e[0], N, key)
             v = [float(x) for x in e[1:]]
+            if len(v) != (6 if key == "VOIGT_TETRAGONAL" else 3):
+                raise ValueError(f"{key} entry {e!r} has the wrong number of constants")
             C = np.zeros((6, 6))
             if key == "VOIGT_TETRAGONAL":
                 c11, c12, c13, c33, c44, c66 = v
@@ -267,7 +280,9 @@ def _eigenstrain(kv, N):
     components) -> [N][3][3]; phases without an entry have none."""
     E = np.zeros((N, 3, 3))
     for e in kv.get("EIGEN_STRAIN", []):
-        a = int(e[0])
+        if len(e) != 7:
+            raise ValueError(f"EIGEN_STRAIN entry {e!r}: expected {{phase, xx, yy, zz, yz, xz, xy}}")
+        a = _phase(e[0], N, "EIGEN_STRAIN")
         xx, yy, zz, yz, xz, xy = (float(v) for v in e[1:7])
         E[a] = [[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]
     return E
@@ -313,7 +328,11 @@ def read_infile(src: str, *, free_energy: Optional[str] = None, elasticity: bool
         delta = _pair_matrix(_one(kv, "dab"), N, "dab")
     rot = np.broadcast_to(np.eye(3), (N, N, 3, 3)).copy()
     for e in kv.get("Rotation_matrix", []):
-        a, b = int(e[0]), int(e[1])
+        if len(e) != 5:
+            raise ValueError(f"Rotation_matrix entry {e!r}: expected {{a, b, ax, ay, az}}")
+        a, b = _phase(e[0], N, "Rotation_matrix"), _phase(e[1], N, "Rotation_matrix")
+        if a == b:
+            raise ValueError("Rotation_matrix: a pair needs two different phases")
         R = euler_rotation(*(float(v) for v in e[2:5]))
         rot[a, b] = rot[b, a] = R
     gamma3 = None
@@ -332,7 +351,7 @@ def read_infile(src: str, *, free_energy: Optional[str] = None, elasticity: bool
 
     D = np.zeros((N, NM, NM))
     for e in kv.get("DIFFUSIVITY", []):
-        diag, a = int(e[0]), int(e[1])
+        diag, a = int(e[0]), _phase(e[1], N, "DIFFUSIVITY")
         vals = e[2:]
         if diag:
             if len(vals) != NM:
@@ -342,14 +361,16 @@ def read_infile(src: str, *, free_energy: Optional[str] = None, elasticity: bool
             D[a] = _sym_from_list(vals, NM, f"DIFFUSIVITY of phase {a}")
     A = np.zeros((N, NM, NM))
     for e in kv.get("A", []):
-        a = int(e[0])
+        a = _phase(e[0], N, "A")
         M = _sym_from_list(e[1:], NM, f"A of phase {a}") if len(e) - 1 > NM else np.diag([float(v) for v in e[1:]])
         A[a] = np.triu(M)             # the parabolic form uses A_ij with i <= j
     ceq = np.zeros((N, NM))
     slopes = np.zeros((N, NM))
     for key, out in (("ceq", ceq), ("slopes", slopes)):
         for e in kv.get(key, []):
-            a, b = int(e[0]), int(e[1])
+            a, b = _phase(e[0], N, key), _phase(e[1], N, key)
+            if len(e) != 2 + NM:
+                raise ValueError(f"{key} entry {e!r}: expected {{a, b}} and {NM} values")
             if a == b:                # phase a's own value; the {a, b != a} entries repeat the liquid's
                 out[a] = [float(v) for v in e[2:2 + NM]]
 
@@ -357,7 +378,12 @@ def read_infile(src: str, *, free_energy: Optional[str] = None, elasticity: bool
     T0 = G = z0 = V = 0.0
     isothermal = int(_num(kv, "ISOTHERMAL", 0.0))
     if "Tempgrady" in kv and not isothermal:
-        base, dT, dist, off, vel = (float(v) for v in _one(kv, "Tempgrady"))
+        tg = _one(kv, "Tempgrady")
+        if not isinstance(tg, list) or len(tg) != 5:
+            raise ValueError("Tempgrady needs {BASETEMP, DELTAT, DISTANCE, OFFSET, VELOCITY}")
+        base, dT, dist, off, vel = (float(v) for v in tg)
+        if dist == 0.0:
+            raise ValueError("Tempgrady: DISTANCE must not be 0")
         # T = BASETEMP + (DELTAT / DISTANCE) (s - OFFSET - VELOCITY t), s along the grid's last axis
         T0, G, z0, V = base, dT / dist, off, vel
     else:
@@ -386,8 +412,8 @@ def read_infile(src: str, *, free_energy: Optional[str] = None, elasticity: bool
     spec.meta = {
         "cfill": cfill,
         "savet": int(_num(kv, "SAVET", 0.0)),
-        "phases": [str(v) for v in _one(kv, "PHASES", [], required=False) or []],
-        "components": [str(v) for v in _one(kv, "COMPONENTS", [], required=False) or []],
+        "phases": _names(_one(kv, "PHASES", [], required=False)),
+        "components": _names(_one(kv, "COMPONENTS", [], required=False)),
         "ignored": sorted(k for k in kv if k not in _USED),
     }
     return spec
@@ -447,8 +473,10 @@ def write_infile(spec) -> str:
 
 
 def _euler_angles(R: np.ndarray):
-    """Angles (degrees) with euler_rotation(ax, ay, az) == R, for a proper rotation."""
+    """Angles (degrees) with euler_rotation(ax, ay, az) == R (R a proper rotation)."""
     R = np.asarray(R, dtype=float)
+    if not (np.allclose(R @ R.T, np.eye(3), atol=1e-10) and np.linalg.det(R) > 0):
+        raise ValueError("a pair's matrix is not a proper rotation: it has no Euler angles")
     ay = math.asin(max(-1.0, min(1.0, -R[2, 0])))
     if abs(math.cos(ay)) > 1e-12:
         ax = math.atan2(R[2, 1], R[2, 2])

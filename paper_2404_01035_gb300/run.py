@@ -92,6 +92,8 @@ def main(argv: Optional[List[str]] = None) -> int:
     steps = args.steps if args.steps is not None else spec.steps
     if steps < 0:
         ap.error("--steps must be >= 0")
+    if args.save_every is not None and args.save_every <= 0:
+        ap.error("--save-every must be > 0")
     every = args.save_every or spec.meta.get("savet") or steps or 1
     info = _summary(spec, phi0, mu0, steps, every)
     print(json.dumps({"inputs": info}), flush=True)

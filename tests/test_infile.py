@@ -134,6 +134,11 @@ def test_euler_rotation_order_and_inverse():
     (("GAMMA = {1.1, 0.9, 1.3};", "GAMMA = {1.1, 0.9};"), "pair values"),
     (("A = {1, 0.9, 1.2, -0.02};", "A = {1, 0.9, 1.2, -0.02, 7};"), "off-diagonal"),
     (("DIMENSION = 3;", "DIMENSION = 4;"), "DIMENSION"),
+    (("Rotation_matrix = {0, 2, 0, 0, 30};", "Rotation_matrix = {0, 3, 0, 0, 30};"), "phase index"),
+    (("Rotation_matrix = {0, 2, 0, 0, 30};", "Rotation_matrix = {2, 2, 0, 0, 30};"), "two different"),
+    (("ceq = {1, 1, 0.1, 0.7};", "ceq = {1, 1, 0.1};"), "values"),
+    (("Tempgrady = {0.97, 0.2, 40, 3, 0.05};", "Tempgrady = {0.97, 0.2, 0, 3, 0.05};"), "DISTANCE"),
+    (("DIFFUSIVITY = {1, 0, 0.01, 0.02};", "DIFFUSIVITY = {1, 1.5, 0.01, 0.02};"), "phase index"),
 ])
 def test_unsupported_input_is_refused(edit, match):
     old, new = edit
@@ -436,3 +441,11 @@ def test_run_driver_writes_vtk_snapshots(tmp_path, monkeypatch):
     o_phi, o_mu = oracle.run(s, phi0, mu0, 20)
     np.testing.assert_array_equal(fields["phi_beta"], o_phi[1].ravel())   # x fastest, as the array
     np.testing.assert_array_equal(fields["mu_1"], o_mu[1].ravel())
+
+
+def test_single_names_and_improper_rotations():
+    s = I.read_infile(TERNARY_3D.replace("PHASES = {alpha, beta, liquid};", "PHASES = solid;"))
+    assert s.meta["phases"] == ["solid"]
+    s.rot[0, 1] = s.rot[1, 0] = np.diag([1.0, 1.0, -1.0])          # a mirror, not a rotation
+    with pytest.raises(ValueError, match="proper rotation"):
+        I.write_infile(s)
