@@ -2,6 +2,7 @@
 
     python -m paper_2404_01035_gb300.run INFILE FILLING [--steps N] [--save-every K]
                                          [--out DIR] [--dtype f32|f64] [--dry-run] ...
+    python -m paper_2404_01035_gb300.run INFILE --restart DIR/checkpoint.bin [--steps N] ...
 
 The infile gives the grid and the parameters (`read_infile`), the filling
 file the initial phases (`read_filling`).  The initial chemical potential is
@@ -10,8 +11,11 @@ liquid, else its ceq).  Every `--save-every` steps (default SAVET, else
 NTIMESTEPS) the driver prints the FP64 diagnostics as one JSON line and
 writes the state to DIR/step_<n>.npz (phi, mu, step, t), or with
 `--format vtk` to DIR/step_<n>.vtk (legacy VTK, one scalar per phase and
-solute).  It stops with
-exit code 3 if the library reports a non-finite state.  `--dry-run` reads and
+solute).  With `--checkpoint` it also keeps DIR/checkpoint.bin, the
+library's checkpoint of the latest saved state (its step and time included);
+`--restart` resumes from such a file, bitwise where the run left off, and
+steps on to the same total.  It stops with exit code 3 if the library reports
+a non-finite state.  `--dry-run` reads and
 checks the inputs and prints their summary without touching the GPU.
 """
 from __future__ import annotations
@@ -31,6 +35,8 @@ def build_inputs(args):
     spec = read_infile(args.infile, free_energy=args.free_energy, elasticity=args.elasticity,
                        anti_trapping=args.anti_trapping, grain_growth=args.grain_growth,
                        noise_seed=args.noise_seed)
+    if args.filling is None:                # a restart: the state comes from the checkpoint
+        return spec, None, None
     phi0 = read_filling(args.filling, spec, diffuse=not args.sharp)
     liq = spec.n_phases - 1
     c = spec.meta["cfill"].get(liq, list(spec.ceq[liq]))
@@ -64,8 +70,8 @@ def _summary(spec, phi0, mu0, steps, every):
         "temperature": {"T0": spec.T0, "G": spec.G, "z0": spec.z0, "V": spec.V},
         "options": {"anti_trapping": spec.anti_trapping, "grain_growth": spec.grain_growth,
                     "elasticity": spec.elastic_C is not None, "noise_amp": spec.noise_amp},
-        "phase_fractions": [float(v) for v in phi0.reshape(spec.n_phases, -1).mean(axis=1)],
-        "mu0": [float(v) for v in mu0.reshape(spec.n_mu, -1)[:, 0]],
+        "phase_fractions": None if phi0 is None else [float(v) for v in phi0.reshape(spec.n_phases, -1).mean(axis=1)],
+        "mu0": None if mu0 is None else [float(v) for v in mu0.reshape(spec.n_mu, -1)[:, 0]],
         "steps": steps, "save_every": every, "ignored_keys": spec.meta["ignored"],
     }
 
@@ -73,7 +79,7 @@ def _summary(spec, phi0, mu0, steps, every):
 def main(argv: Optional[List[str]] = None) -> int:
     ap = argparse.ArgumentParser(prog="python -m paper_2404_01035_gb300.run", description=__doc__.split("\n\n")[0])
     ap.add_argument("infile")
-    ap.add_argument("filling")
+    ap.add_argument("filling", nargs="?", default=None)
     ap.add_argument("--steps", type=int, default=None, help="default: NTIMESTEPS")
     ap.add_argument("--save-every", type=int, default=None, help="default: SAVET, else the whole run")
     ap.add_argument("--out", default="microsim_out")
@@ -85,8 +91,12 @@ def main(argv: Optional[List[str]] = None) -> int:
     ap.add_argument("--anti-trapping", action="store_true")
     ap.add_argument("--grain-growth", action="store_true")
     ap.add_argument("--noise-seed", type=int, default=0)
+    ap.add_argument("--checkpoint", action="store_true", help="keep DIR/checkpoint.bin of the latest save")
+    ap.add_argument("--restart", default=None, help="resume from a checkpoint file")
     ap.add_argument("--dry-run", action="store_true")
     args = ap.parse_args(argv)
+    if (args.filling is None) == (args.restart is None):
+        ap.error("give a FILLING file for a new run or --restart CHECKPOINT to resume one")
 
     spec, phi0, mu0 = build_inputs(args)
     steps = args.steps if args.steps is not None else spec.steps
@@ -108,6 +118,11 @@ def main(argv: Optional[List[str]] = None) -> int:
              else [f"phi_{a}" for a in range(spec.n_phases)]) + [f"mu_{i}" for i in range(spec.n_mu)]
 
     def save(sim, d):
+        if args.checkpoint:
+            tmp = os.path.join(args.out, "checkpoint.bin.tmp")
+            with open(tmp, "wb") as f:
+                f.write(sim.checkpoint())
+            os.replace(tmp, os.path.join(args.out, "checkpoint.bin"))
         phi, mu = sim.get_fields()
         stem = os.path.join(args.out, f"step_{d['step']:010d}")
         if args.format == "vtk":
@@ -116,10 +131,15 @@ def main(argv: Optional[List[str]] = None) -> int:
             np.savez(stem + ".npz", phi=phi, mu=mu, step=d["step"], t=d["t"])
 
     with Simulation(spec, dtype=args.dtype) as sim:
-        sim.set_fields(phi0, mu0)
-        d = sim.diag()
-        save(sim, d)
-        done = 0
+        if args.restart:
+            with open(args.restart, "rb") as f:
+                sim.restore(f.read())
+            d = sim.diag()
+        else:
+            sim.set_fields(phi0, mu0)
+            d = sim.diag()
+            save(sim, d)
+        done = int(d["step"])
         while done < steps:
             k = min(every, steps - done)
             try:

@@ -352,6 +352,14 @@ class _OracleSim:
     def get_fields(self):
         return self.phi.copy(), self.mu.copy()
 
+    def checkpoint(self):
+        import pickle
+        return pickle.dumps((self.phi, self.mu, self.n, self.t))
+
+    def restore(self, blob):
+        import pickle
+        self.phi, self.mu, self.n, self.t = pickle.loads(blob)
+
 
 def test_run_driver_loop_and_snapshots_with_the_oracle_behind_it(tmp_path, monkeypatch, capsys):
     """The driver's stepping, diagnostics and snapshot files, with the GPU
@@ -449,3 +457,27 @@ def test_single_names_and_improper_rotations():
     s.rot[0, 1] = s.rot[1, 0] = np.diag([1.0, 1.0, -1.0])          # a mirror, not a rotation
     with pytest.raises(ValueError, match="proper rotation"):
         I.write_infile(s)
+
+
+def test_run_driver_checkpoint_and_restart(tmp_path, monkeypatch):
+    """A run stopped at step 20 with --checkpoint and resumed with --restart ends
+    where an uninterrupted run ends (the oracle standing in for the GPU)."""
+    from paper_2404_01035_gb300 import run, simulation
+    monkeypatch.setattr(simulation, "Simulation", _OracleSim)
+    deck, fill = os.path.join(DECKS, "ternary_2d.in"), os.path.join(DECKS, "ternary_2d.fill")
+    a, b = tmp_path / "a", tmp_path / "b"
+    assert run.main([deck, fill, "--out", str(a), "--steps", "20", "--checkpoint"]) == 0
+    assert (a / "checkpoint.bin").exists()
+    assert run.main([deck, "--restart", str(a / "checkpoint.bin"), "--out", str(b), "--steps", "40"]) == 0
+    assert sorted(os.listdir(b)) == ["step_0000000040.npz"]
+    s = I.read_infile(deck)
+    phi0 = I.read_filling(fill, s)
+    mu0 = np.broadcast_to(I.liquid_mu(s, [0.38, 0.33])[:, None, None, None], (2,) + phi0.shape[1:]).copy()
+    o_phi, o_mu = oracle.run(s, phi0, mu0, 40)
+    last = np.load(b / "step_0000000040.npz")
+    np.testing.assert_array_equal(last["phi"], o_phi)
+    np.testing.assert_array_equal(last["mu"], o_mu)
+    with pytest.raises(SystemExit):
+        run.main([deck, "--out", str(b)])                       # neither a filling nor a restart
+    with pytest.raises(SystemExit):
+        run.main([deck, fill, "--restart", str(a / "checkpoint.bin")])   # both
