@@ -132,7 +132,7 @@ _USED = {
     "Rotation_matrix", "Function_W", "Gamma_abc", "ISOTHERMAL", "T", "Tempgrady",
     "Equilibrium_temperature", "Function_F", "A", "ceq", "slopes", "Noise_phasefield",
     "Amp_Noise_Phase", "EIGEN_STRAIN", "VOIGT_ISOTROPIC", "VOIGT_CUBIC", "VOIGT_TETRAGONAL",
-    "COMPONENTS", "PHASES", "cfill", "SAVET",
+    "COMPONENTS", "PHASES", "cfill", "SAVET", "Shift", "Shiftj",
 }
 
 
@@ -412,6 +412,9 @@ def read_infile(src: str, *, free_energy: Optional[str] = None, elasticity: bool
     spec.meta = {
         "cfill": cfill,
         "savet": int(_num(kv, "SAVET", 0.0)),
+        # moving frame (SHIFT): on, and the index along the last axis the front is kept at
+        "shift": int(_num(kv, "Shift", 0.0)),
+        "shiftj": int(_num(kv, "Shiftj", 0.0)),
         "phases": _names(_one(kv, "PHASES", [], required=False)),
         "components": _names(_one(kv, "COMPONENTS", [], required=False)),
         "ignored": sorted(k for k in kv if k not in _USED),

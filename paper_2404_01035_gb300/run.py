@@ -14,7 +14,9 @@ writes the state to DIR/step_<n>.npz (phi, mu, step, t), or with
 solute).  With `--checkpoint` it also keeps DIR/checkpoint.bin, the
 library's checkpoint of the latest saved state (its step and time included);
 `--restart` resumes from such a file, bitwise where the run left off, and
-steps on to the same total.  It stops with exit code 3 if the library reports
+steps on to the same total.  A deck with `Shift = 1` runs in the moving frame:
+the growth front is kept at index Shiftj of the last axis, and liquid of the
+alloy's chemical potential refills the far end.  It stops with exit code 3 if the library reports
 a non-finite state.  `--dry-run` reads and
 checks the inputs and prints their summary without touching the GPU.
 """
@@ -31,6 +33,13 @@ import numpy as np
 from .infile import liquid_mu, read_filling, read_infile
 
 
+def alloy_mu(spec) -> np.ndarray:
+    """The uniform chemical potential of the alloy: the liquid at its fill
+    composition (cfill), else at its equilibrium composition (ceq)."""
+    liq = spec.n_phases - 1
+    return liquid_mu(spec, spec.meta["cfill"].get(liq, list(spec.ceq[liq])))
+
+
 def build_inputs(args):
     spec = read_infile(args.infile, free_energy=args.free_energy, elasticity=args.elasticity,
                        anti_trapping=args.anti_trapping, grain_growth=args.grain_growth,
@@ -38,10 +47,7 @@ def build_inputs(args):
     if args.filling is None:                # a restart: the state comes from the checkpoint
         return spec, None, None
     phi0 = read_filling(args.filling, spec, diffuse=not args.sharp)
-    liq = spec.n_phases - 1
-    c = spec.meta["cfill"].get(liq, list(spec.ceq[liq]))
-    mu_val = liquid_mu(spec, c)
-    mu0 = np.broadcast_to(mu_val[:, None, None, None], (spec.n_mu,) + phi0.shape[1:]).copy()
+    mu0 = np.broadcast_to(alloy_mu(spec)[:, None, None, None], (spec.n_mu,) + phi0.shape[1:]).copy()
     return spec, phi0, mu0
 
 
@@ -72,6 +78,7 @@ def _summary(spec, phi0, mu0, steps, every):
                     "elasticity": spec.elastic_C is not None, "noise_amp": spec.noise_amp},
         "phase_fractions": None if phi0 is None else [float(v) for v in phi0.reshape(spec.n_phases, -1).mean(axis=1)],
         "mu0": None if mu0 is None else [float(v) for v in mu0.reshape(spec.n_mu, -1)[:, 0]],
+        "moving_frame": {"on": bool(spec.meta["shift"]), "keep": spec.meta["shiftj"]},
         "steps": steps, "save_every": every, "ignored_keys": spec.meta["ignored"],
     }
 
@@ -143,7 +150,13 @@ def main(argv: Optional[List[str]] = None) -> int:
         while done < steps:
             k = min(every, steps - done)
             try:
-                sim.step(k)
+                if spec.meta["shift"]:
+                    # SHIFT: keep the growth front at index Shiftj of the last axis,
+                    # refilling the far end with liquid of the alloy's mu
+                    sim.step_moving_frame(k, keep=spec.meta["shiftj"], mu_fill=alloy_mu(spec),
+                                          check_every=min(100, k))
+                else:
+                    sim.step(k)
                 d = sim.diag()
             except MSError as e:
                 if e.status != 5:               # anything but MS_ERR_NONFINITE

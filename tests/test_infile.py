@@ -352,6 +352,10 @@ class _OracleSim:
     def get_fields(self):
         return self.phi.copy(), self.mu.copy()
 
+    def step_moving_frame(self, n, keep, mu_fill, check_every=100):
+        self.frame_calls = getattr(self, "frame_calls", []) + [(n, keep, list(mu_fill), check_every)]
+        self.step(n)
+
     def checkpoint(self):
         import pickle
         return pickle.dumps((self.phi, self.mu, self.n, self.t))
@@ -481,3 +485,27 @@ def test_run_driver_checkpoint_and_restart(tmp_path, monkeypatch):
         run.main([deck, "--out", str(b)])                       # neither a filling nor a restart
     with pytest.raises(SystemExit):
         run.main([deck, fill, "--restart", str(a / "checkpoint.bin")])   # both
+
+
+def test_run_driver_moving_frame_from_the_shift_keys(tmp_path, monkeypatch, capsys):
+    """Shift = 1, Shiftj = j in the deck: the driver steps in the moving frame that
+    keeps the front at j, refilling with liquid of the alloy's chemical potential."""
+    import json
+    from paper_2404_01035_gb300 import run, simulation
+    made = []
+
+    class Sim(_OracleSim):
+        def __init__(self, spec, dtype="f32"):
+            super().__init__(spec, dtype)
+            made.append(self)
+
+    monkeypatch.setattr(simulation, "Simulation", Sim)
+    deck = open(os.path.join(DECKS, "ternary_2d.in")).read() + "Shift = 1;\nShiftj = 24;\n"
+    (tmp_path / "shift.in").write_text(deck)
+    fill = os.path.join(DECKS, "ternary_2d.fill")
+    assert run.main([str(tmp_path / "shift.in"), fill, "--out", str(tmp_path / "o"), "--steps", "40"]) == 0
+    s = I.read_infile(deck)
+    mu = list(I.liquid_mu(s, [0.38, 0.33]))
+    assert made[0].frame_calls == [(20, 24, mu, 20), (20, 24, mu, 20)]
+    info = json.loads(capsys.readouterr().out.strip().splitlines()[0])["inputs"]
+    assert info["moving_frame"] == {"on": True, "keep": 24}
