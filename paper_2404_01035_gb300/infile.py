@@ -27,7 +27,7 @@ from __future__ import annotations
 import math
 import os
 import re
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 from typing import Dict, List, Optional, Union
 
 import numpy as np
@@ -113,11 +113,18 @@ class ModelSpec:
     grain_growth: int = 0
     elastic_C: Optional[np.ndarray] = None
     eigenstrain: Optional[np.ndarray] = None
+    phi0: Optional[np.ndarray] = None   # an initial state may ride along (read_filling fills none in)
+    mu0: Optional[np.ndarray] = None
     meta: dict = field(default_factory=dict)
 
     @property
     def n_mu(self) -> int:
         return self.n_components - 1
+
+    def copy(self, **kw) -> "ModelSpec":
+        """A copy with the given fields replaced (the slab decomposition makes
+        its sub-domains this way)."""
+        return replace(self, **kw)
 
     @property
     def cells(self) -> int:

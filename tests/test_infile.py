@@ -509,3 +509,12 @@ def test_run_driver_moving_frame_from_the_shift_keys(tmp_path, monkeypatch, caps
     assert made[0].frame_calls == [(20, 24, mu, 20), (20, 24, mu, 20)]
     info = json.loads(capsys.readouterr().out.strip().splitlines()[0])["inputs"]
     assert info["moving_frame"] == {"on": True, "keep": 24}
+
+
+def test_spec_copies_like_the_workload_problem():
+    """The slab decomposition derives each slab's problem with copy(); a spec
+    read from a deck supports the same call."""
+    s = I.read_infile(TERNARY_3D)
+    sub = s.copy(nz=3, bc=[s.bc[0], s.bc[1], 16], phi0=None, mu0=None, meta={**s.meta, "z_origin": 5})
+    assert (sub.nz, sub.bc, sub.meta["z_origin"], s.nz) == (3, [3, 1, 16], 5, 8)
+    assert make_grid(sub).z_origin == 5 and make_grid(sub).nz == 3
