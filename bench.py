@@ -155,7 +155,7 @@ def run_reference(args, rank, world):
         return
     import oracle
     import workloads
-    prob = workloads.cfg2(n=args.n)
+    prob = workloads.eutectic_3d(n=args.n)
     if world > 1:   # the launcher caps every rank at one thread; rank 0 alone computes here
         oracle.set_threads(os.cpu_count() or 1)
     cores = oracle.num_threads()
@@ -200,7 +200,7 @@ def run_ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    prob = workloads.cfg2(n=args.n)
+    prob = workloads.eutectic_3d(n=args.n)
     prob.anti_trapping = int(args.anti_trapping)
     cells = prob.cells
     stream = torch.cuda.Stream(device=dev)
@@ -444,7 +444,7 @@ def bench_batched(stream):
     import workloads
     from paper_2404_01035_gb300 import Simulation
     from paper_2404_01035_gb300.batch import Batch
-    probs = workloads.cfg3()
+    probs = workloads.batched_dendrites_2d()
     b = Batch(probs, stream=stream)
     for i, p in enumerate(probs):
         b.set_fields(i, p.phi0, p.mu0)
@@ -511,7 +511,7 @@ def bench_multigrain(stream, pre_steps=1000, steps=1000):
     timed after `pre_steps` untimed ones from the seeded state."""
     import workloads
     from paper_2404_01035_gb300 import Simulation
-    p = workloads.cfg5()
+    p = workloads.multigrain_3d()
     sim = Simulation(p, dtype="f32", stream=stream)
     sim.set_fields(p.phi0, p.mu0)
     sim.step(pre_steps)
@@ -540,7 +540,7 @@ def bench_frame_noise(stream):
     the cost of one moving-frame check (ms_front) and one 8-plane shift."""
     import workloads
     from paper_2404_01035_gb300 import Simulation
-    p = workloads.cfg2()
+    p = workloads.eutectic_3d()
     p.noise_amp, p.noise_seed = 0.01, 20240401
     sim = Simulation(p, dtype="f32", stream=stream)
     sim.set_fields(p.phi0, p.mu0)
@@ -570,7 +570,7 @@ def bench_anti_trapping(stream):
     out = {"workload": "3-D 256^3 eutectic with the anti-trapping current (obstacle form), 200 steps"}
     steps = 200
     for at in (1, 0):
-        p = workloads.cfg2()
+        p = workloads.eutectic_3d()
         p.anti_trapping = at
         sim = Simulation(p, dtype="f32", stream=stream)
         sim.set_fields(p.phi0, p.mu0)
@@ -643,7 +643,7 @@ def bench_elasticity(stream):
                        "in the grains, 100 steps"}
     steps = 100
     for el in (1, 0):
-        p = workloads.cfg5(n=256)
+        p = workloads.multigrain_3d(n=256)
         if el:
             C = np.zeros((6, 6))
             C[:3, :3] = 60.0
@@ -673,7 +673,7 @@ def bench_adjoint(stream):
     from paper_2404_01035_gb300 import Simulation
     out = {"workload": "2-D 256^2, N=2 K=2, well potential, 2000 steps, checkpoint every 100"}
     for dtype in ("f32", "f64"):
-        p = workloads.cfg4(n=256, steps=2000, delta=0.02, mob=0.8)
+        p = workloads.adjoint_well_2d(n=256, steps=2000, delta=0.02, mob=0.8)
         sim = Simulation(p, dtype=dtype, stream=stream)
         sim.set_fields(p.phi0, p.mu0)
         sim.step(50)
@@ -698,8 +698,8 @@ def bench_adjoint(stream):
 
 def committed_profile(launch, n):
     """The ncu figures committed for this source version, launch variant and grid
-    (profiles/traffic_cfg2_step.json), or None."""
-    path = os.path.join(ROOT, "profiles", "traffic_cfg2_step.json")
+    (profiles/traffic_eutectic_3d_step.json), or None."""
+    path = os.path.join(ROOT, "profiles", "traffic_eutectic_3d_step.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:

@@ -38,5 +38,5 @@ def make_case(W, case):
     if case.startswith("periodic"):
         return W.small_multiphase(n=20, dim=3, N=3, NM=2, nx=24, ny=18, nz=22, bc=[3, 3, 3], rotate=True), "f64"
     if case.startswith("eutectic"):
-        return W.cfg2(n=48, steps=40), "f32"
+        return W.eutectic_3d(n=48, steps=40), "f32"
     return W.small_multiphase(n=20, dim=3, N=3, NM=2, nx=24, ny=18, nz=21, bc=[3, 1, 1]), "f64"

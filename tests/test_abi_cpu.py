@@ -50,13 +50,13 @@ def _create(prob, dtype="f32", **override):
 
 
 def test_create_rejects_unstable_dt():
-    p = W.cfg1()
+    p = W.dendrite_2d()
     rc, h, msg = _create(p, dt=10.0)
     assert rc == 4 and "stability" in msg and not h.value
 
 
 def test_create_rejects_bad_dimension_and_sizes():
-    p = W.cfg1()
+    p = W.dendrite_2d()
     bad = p.copy(dim=4)
     assert _create(bad)[0] == 1
     assert _create(p.copy(nx=0))[0] == 1
@@ -65,7 +65,7 @@ def test_create_rejects_bad_dimension_and_sizes():
 
 
 def test_create_rejects_bad_boundary_and_potential():
-    p = W.cfg1()
+    p = W.dendrite_2d()
     assert _create(p.copy(bc=[2, 3, 3]))[0] == 1
     assert _create(p, eps=-1.0)[0] == 1
 
@@ -120,7 +120,7 @@ def test_params_struct_layout_matches_the_header(tmp_path):
 
 
 def test_create_rejects_inconsistent_options():
-    p = W.cfg1()
+    p = W.dendrite_2d()
     C = np.eye(6) * 100.0
     eig = np.zeros((2, 3, 3))
     # a stiffness without eigenstrains
@@ -149,5 +149,5 @@ def test_create_refuses_grids_beyond_the_fft_plans():
 def test_create_rejects_a_malformed_fault_spec(monkeypatch, spec):
     # MS_FAULT is parsed before any device work, so a bad spec fails on CPU
     monkeypatch.setenv("MS_FAULT", spec)
-    rc, h, msg = _create(W.cfg1())
+    rc, h, msg = _create(W.dendrite_2d())
     assert rc == 1 and "MS_FAULT" in msg and not h.value

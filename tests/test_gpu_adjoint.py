@@ -94,16 +94,16 @@ def test_adjoint_3d_binary_matches_oracle_tangent():
 
 
 # ---------------------------------------------------- the 256^2 adjoint workload
-def _cfg4_setup(dtype, n=256, steps=2000):
+def _adjoint_well_2d_setup(dtype, n=256, steps=2000):
     import torch
     from paper_2404_01035_gb300 import Simulation
-    target = W.cfg4(n=n, steps=steps, delta=0.03, mob=1.0)
+    target = W.adjoint_well_2d(n=n, steps=steps, delta=0.03, mob=1.0)
     sim = Simulation(target, dtype="f64")
     sim.set_fields(target.phi0, target.mu0)
     sim.step(steps)
     phi_hat, _ = sim.get_fields()
     sim.close()
-    evalp = W.cfg4(n=n, steps=steps, delta=0.02, mob=0.8)
+    evalp = W.adjoint_well_2d(n=n, steps=steps, delta=0.02, mob=0.8)
     return evalp, phi_hat
 
 
@@ -117,7 +117,7 @@ def _loss(prob, phi_hat, steps, dtype="f64", phi0=None, **override):
     return 0.5 * ((phi.astype(np.float64) - phi_hat) ** 2).sum()
 
 
-def _cfg4_grad(prob, phi_hat, steps, dtype):
+def _adjoint_well_2d_grad(prob, phi_hat, steps, dtype):
     import torch
     from paper_2404_01035_gb300 import Simulation
     sim = Simulation(prob, dtype=dtype)
@@ -131,10 +131,10 @@ def _cfg4_grad(prob, phi_hat, steps, dtype):
     return dparams, dphi0.cpu().numpy()
 
 
-def test_cfg4_gradients_match_central_differences_and_fp32():
+def test_adjoint_well_2d_gradients_match_central_differences_and_fp32():
     steps = 2000
-    prob, phi_hat = _cfg4_setup("f64", steps=steps)
-    g64, dphi0 = _cfg4_grad(prob, phi_hat, steps, "f64")
+    prob, phi_hat = _adjoint_well_2d_setup("f64", steps=steps)
+    g64, dphi0 = _adjoint_well_2d_grad(prob, phi_hat, steps, "f64")
     h = 1e-4
     d = prob.delta[0, 1]
     dl = lambda s: np.array([[0, d + s], [d + s, 0]])
@@ -160,7 +160,7 @@ def test_cfg4_gradients_match_central_differences_and_fp32():
               _loss(prob, phi_hat, steps, phi0=prob.phi0 - h * v)) / (2 * h)
     assert (dphi0 * v).sum() == pytest.approx(fd_phi, rel=1e-5)
     # FP32 build of the same gradient
-    g32, _ = _cfg4_grad(prob, phi_hat, steps, "f32")
+    g32, _ = _adjoint_well_2d_grad(prob, phi_hat, steps, "f32")
     for k in (0, 1, 3):
         assert g32[k] == pytest.approx(g64[k], rel=1e-2)
 

@@ -77,7 +77,7 @@ def test_2d_multiphase_fp32():
 @pytest.mark.parametrize("zchunk", [5, 16])
 def test_3d_split_fp32(zchunk):
     # the split step (bulk stream + interface kernel), then the correction
-    p = _at(W.cfg2(n=48, steps=10))
+    p = _at(W.eutectic_3d(n=48, steps=10))
     p.nz = 40
     p.phi0, p.mu0 = p.phi0[:, :40], p.mu0[:, :40]
     g = _run(p, 200, "f32", split=True, zchunk=zchunk)
@@ -86,7 +86,7 @@ def test_3d_split_fp32(zchunk):
 
 
 def test_3d_eight_phases_fp32():
-    p = _at(W.cfg5(n=40, grains=7, R=5.0, min_sep=14.0, seed=3))
+    p = _at(W.multigrain_3d(n=40, grains=7, R=5.0, min_sep=14.0, seed=3))
     g = _run(p, 100, "f32", split=True)
     o = oracle.run(p, p.phi0, p.mu0, 100)
     assert _err(g, o) <= FP32_TOL
@@ -107,12 +107,12 @@ def test_refused_by_the_adjoint_the_batch_and_halo_faces():
         Simulation(q, dtype="f64")
 
 
-def test_cfg2_full_size_sampled_one_step_fp32():
+def test_eutectic_3d_full_size_sampled_one_step_fp32():
     # 256^3 eutectic in the tuned launch, 300 steps with the current, then one
     # step checked at sampled cells (random, interface, corners) against the
     # oracle on a window (radius 3: mu needs phi^{n+1} of the neighbours)
     from paper_2404_01035_gb300 import Simulation
-    p = _at(W.cfg2())
+    p = _at(W.eutectic_3d())
     rng = np.random.default_rng(5)
     sim = Simulation(p, dtype="f32")
     sim.set_fields(p.phi0, p.mu0)

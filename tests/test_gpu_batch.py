@@ -73,9 +73,9 @@ def test_simulations_at_different_grid_spacings_in_one_batch():
     b.close()
 
 
-def test_cfg3_batch_of_512_runs_500_steps():
+def test_batch_of_512_dendrites_runs_500_steps():
     from paper_2404_01035_gb300.batch import Batch
-    probs = W.cfg3()
+    probs = W.batched_dendrites_2d()
     b = Batch(probs)
     for i, p in enumerate(probs):
         b.set_fields(i, p.phi0, p.mu0)

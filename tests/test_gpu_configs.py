@@ -29,7 +29,7 @@ def _split_launch(sim, tx=128, ty=6, zchunk=12):
 
 def test_eutectic_recipe_64_cubed_full_2000_steps_fp32():
     from paper_2404_01035_gb300 import Simulation
-    p = W.cfg2(n=64, steps=2000)
+    p = W.eutectic_3d(n=64, steps=2000)
     steps = 2000
     sim = Simulation(p, dtype="f32")
     _split_launch(sim)
@@ -51,7 +51,7 @@ def test_eutectic_recipe_64_cubed_full_2000_steps_fp32():
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-10), ("f32", 1e-3)])
 def test_adjoint_workload_forward_2000_steps(dtype, tol):
     from paper_2404_01035_gb300 import Simulation
-    p = W.cfg4(n=256, steps=2000, delta=0.02, mob=0.8)
+    p = W.adjoint_well_2d(n=256, steps=2000, delta=0.02, mob=0.8)
     steps = 2000
     sim = Simulation(p, dtype=dtype)
     sim.set_fields(p.phi0, p.mu0)
@@ -69,13 +69,13 @@ def test_autograd_function_backward_matches_ms_grad_and_finite_differences():
     from paper_2404_01035_gb300 import Simulation
     from paper_2404_01035_gb300.autograd import GPSteps, overrides_of, theta_of
     n, steps, every = 48, 120, 40
-    target = W.cfg4(n=n, steps=steps, delta=0.03, mob=1.0)
+    target = W.adjoint_well_2d(n=n, steps=steps, delta=0.03, mob=1.0)
     t = Simulation(target, dtype="f64")
     t.set_fields(target.phi0, target.mu0)
     t.step(steps)
     phi_hat = torch.tensor(t.get_fields()[0], device="cuda")
     t.close()
-    p = W.cfg4(n=n, steps=steps, delta=0.02, mob=0.8)
+    p = W.adjoint_well_2d(n=n, steps=steps, delta=0.02, mob=0.8)
     sim = Simulation(p, dtype="f64")
     theta0 = theta_of(p)
 

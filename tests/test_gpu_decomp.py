@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 def test_slabs_equal_whole_domain_bitwise(outer, nslabs):
     from paper_2404_01035_gb300 import Simulation
     from paper_2404_01035_gb300.decomp import SlabDomain
-    p = W.cfg2(n=48, steps=40)
+    p = W.eutectic_3d(n=48, steps=40)
     p.bc = [W.BC_PERIODIC, W.BC_PERIODIC, outer]
     whole = Simulation(p, dtype="f32")
     whole.set_fields(p.phi0, p.mu0)

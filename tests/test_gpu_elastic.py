@@ -74,7 +74,7 @@ def test_fp32_split_matches_oracle(zchunk):
 
 
 def test_fp32_eight_phases():
-    p = _elastic(W.cfg5(n=40, grains=7, R=5.0, min_sep=14.0, seed=3))
+    p = _elastic(W.multigrain_3d(n=40, grains=7, R=5.0, min_sep=14.0, seed=3))
     g = _run(p, 60, "f32", split=True)
     o = oracle.run(p, p.phi0, p.mu0, 60)
     assert _err(g, o) <= 1e-3

@@ -62,7 +62,7 @@ def test_noise_and_lab_origin_2d_fp64():
 @pytest.mark.parametrize("dim", [3, 2])
 def test_shift_then_steps_match_oracle_fp64(dim):
     if dim == 3:
-        p = W.cfg2(n=24, steps=10)
+        p = W.eutectic_3d(n=24, steps=10)
         p.nz = 24
         p.phi0, p.mu0 = p.phi0[:, :24], p.mu0[:, :24]
     else:
@@ -82,7 +82,7 @@ def test_shift_then_steps_match_oracle_fp64(dim):
 
 
 def test_front_and_moving_frame():
-    p = W.cfg2(n=32, steps=10)
+    p = W.eutectic_3d(n=32, steps=10)
     sim = _sim(p, "f32")
     phi, _ = sim.get_fields()
     solid = (phi[-1] != 1.0).any(axis=(1, 2))
@@ -100,7 +100,7 @@ def test_front_and_moving_frame():
 def test_noise_is_refused_by_the_adjoint_and_the_batch():
     from paper_2404_01035_gb300 import Simulation
     from paper_2404_01035_gb300.batch import Batch
-    p = _noisy(W.cfg4(n=32, steps=10, delta=0.02, mob=1.0))
+    p = _noisy(W.adjoint_well_2d(n=32, steps=10, delta=0.02, mob=1.0))
     sim = Simulation(p, dtype="f64")
     with pytest.raises(Exception):
         sim.enable_checkpoints(5)

@@ -36,15 +36,15 @@ def max_err(a, b):
 
 
 # ------------------------------------------------------------ whole-grid runs
-def test_cfg1_fp64_1000_steps():
-    p = W.cfg1()
+def test_dendrite_2d_fp64_1000_steps():
+    p = W.dendrite_2d()
     g = gpu_run(p, p.steps, "f64")
     o = oracle.run(p, p.phi0, p.mu0, p.steps)
     assert max_err(g, o) <= FP64_TOL
 
 
-def test_cfg1_fp32_1000_steps():
-    p = W.cfg1()
+def test_dendrite_2d_fp32_1000_steps():
+    p = W.dendrite_2d()
     g = gpu_run(p, p.steps, "f32")
     o = oracle.run(p, p.phi0, p.mu0, p.steps)
     assert max_err(g, o) <= FP32_TOL
@@ -76,7 +76,7 @@ def test_3d_three_phase_ternary_fp32_1000_steps():
 
 @pytest.mark.parametrize("dtype,steps,tol", [("f64", 30, FP64_TOL), ("f32", 300, FP32_TOL)])
 def test_3d_eight_phase_multigrain(dtype, steps, tol):
-    p = W.cfg5(n=40, grains=7, R=5.0, min_sep=14.0, seed=3)
+    p = W.multigrain_3d(n=40, grains=7, R=5.0, min_sep=14.0, seed=3)
     g = gpu_run(p, steps, dtype)
     o = oracle.run(p, p.phi0, p.mu0, steps)
     assert max_err(g, o) <= tol
@@ -93,7 +93,7 @@ def _split_tile(prob):
 def test_3d_eight_phase_multigrain_split_variant():
     # the split step with 8 phases: rows around a grain hold few phases and
     # take the compact update (MODE 0 of the interface kernel)
-    p = W.cfg5(n=40, grains=7, R=5.0, min_sep=14.0, seed=3)
+    p = W.multigrain_3d(n=40, grains=7, R=5.0, min_sep=14.0, seed=3)
     t, _ = _split_tile(p)
     g = gpu_run(p, 300, "f32", set_launch=(t, 16))
     o = oracle.run(p, p.phi0, p.mu0, 300)
@@ -167,7 +167,7 @@ def test_grid_spacing_other_than_one(dim, dtype, steps, tol):
 
 
 def test_zero_steps_is_identity():
-    p = W.cfg1()
+    p = W.dendrite_2d()
     g = gpu_run(p, 0, "f64")
     assert np.array_equal(g[0], p.phi0) and np.array_equal(g[1], p.mu0)
 
@@ -255,7 +255,7 @@ def test_bulk_phi_reuse_survives_state_loads_and_adjoint_recompute():
     # later step bitwise equal to a fresh context started from the same state.
     from paper_2404_01035_gb300 import Simulation
     import torch
-    p = W.cfg2(n=48, steps=10)
+    p = W.eutectic_3d(n=48, steps=10)
     p.nz = 40
     p.phi0, p.mu0 = p.phi0[:, :40], p.mu0[:, :40]
     sim = Simulation(p, dtype="f32")
@@ -303,7 +303,7 @@ def test_switching_between_split_and_fused_steps_mid_run():
     # partner's codes instead.  Alternating the two on one context, without
     # reloading the state, must still track the oracle.
     from paper_2404_01035_gb300 import Simulation
-    p = W.cfg2(n=48, steps=10)
+    p = W.eutectic_3d(n=48, steps=10)
     p.nz = 40
     p.phi0, p.mu0 = p.phi0[:, :40], p.mu0[:, :40]
     sim = Simulation(p, dtype="f32")
@@ -339,7 +339,7 @@ def test_device_and_host_field_io_agree():
 
 def test_autotuner_picks_a_variant_and_caches(tmp_path):
     from paper_2404_01035_gb300 import Simulation
-    p = W.cfg2(n=64, steps=10)
+    p = W.eutectic_3d(n=64, steps=10)
     sim = Simulation(p, dtype="f32")
     sim.set_fields(p.phi0, p.mu0)
     cache = str(tmp_path / "tune.json")
@@ -374,14 +374,14 @@ def _full_size_sampled(prob, dtype, warm_steps, seed, tol):
     return d
 
 
-def test_cfg2_full_size_sampled_parity_fp32():
-    p = W.cfg2()
+def test_eutectic_3d_full_size_sampled_parity_fp32():
+    p = W.eutectic_3d()
     _full_size_sampled(p, "f32", warm_steps=300, seed=1, tol=2e-5)
 
 
-def test_cfg2_full_size_invariants_2000_steps():
+def test_eutectic_3d_full_size_invariants_2000_steps():
     from paper_2404_01035_gb300 import Simulation
-    p = W.cfg2()
+    p = W.eutectic_3d()
     sim = Simulation(p, dtype="f32")
     sim.set_fields(p.phi0, p.mu0)
     d0 = sim.diag()
@@ -392,6 +392,6 @@ def test_cfg2_full_size_invariants_2000_steps():
     assert d1["sum_err"] < 1e-5 and d1["phi_min"] >= 0 and d1["nonfinite"] == 0
 
 
-def test_cfg5_full_size_sampled_parity_fp32():
-    p = W.cfg5()
+def test_multigrain_3d_full_size_sampled_parity_fp32():
+    p = W.multigrain_3d()
     _full_size_sampled(p, "f32", warm_steps=20, seed=2, tol=2e-5)

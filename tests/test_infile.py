@@ -187,7 +187,7 @@ def _same_spec(a, b):
 
 
 @pytest.mark.parametrize("make", [
-    lambda: W.cfg1(),
+    lambda: W.dendrite_2d(),
     lambda: W.small_multiphase(n=10, dim=3, N=3, NM=2, rotate=True),
     lambda: W.small_multiphase(n=12, dim=2, N=4, NM=1, potential="well", gamma3=2.0),
 ])

@@ -88,7 +88,7 @@ def test_shift_definition():
 
 
 def test_lab_origin_equals_moved_temperature_field():
-    p = W.cfg2(n=24, steps=5)
+    p = W.eutectic_3d(n=24, steps=5)
     p.nz = 20
     p.phi0, p.mu0 = p.phi0[:, :20], p.mu0[:, :20]
     s = 4
@@ -100,7 +100,7 @@ def test_lab_origin_equals_moved_temperature_field():
 def test_shift_commutes_with_a_step_on_a_z_uniform_base():
     # isothermal directional state: lamellae uniform along z up to the front,
     # uniform liquid at mu_fill above it; no-flux z
-    p = W.cfg2(n=24, steps=5)
+    p = W.eutectic_3d(n=24, steps=5)
     p.nz = 24
     p.G = 0.0
     lam = p.phi0[:, :1].copy()            # the bottom plane's lamellae, repeated up to z = 11

@@ -403,8 +403,8 @@ def test_gibbs_thomson_direction(R_over_Rstar, grows):
     assert abs(s1 - s0) > 5.0
 
 
-def test_cfg1_mirror_and_transpose_symmetry():
-    p = W.cfg1()
+def test_dendrite_2d_mirror_and_transpose_symmetry():
+    p = W.dendrite_2d()
     phi, mu = oracle.run(p, p.phi0, p.mu0, 100)
     f = phi[0, 0]
     np.testing.assert_allclose(f, f.T, atol=1e-13)

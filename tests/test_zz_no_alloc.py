@@ -62,7 +62,7 @@ def test_noalloc_rejects_grids_beyond_its_limit():
     from paper_2404_01035_gb300 import lib
     from paper_2404_01035_gb300.simulation import make_grid, make_params
 
-    p = W.cfg2(n=8)
+    p = W.eutectic_3d(n=8)
     big = p.copy(nx=1024, ny=1024, nz=512)   # 536,870,912 cells > 268,435,456
     keep = []
     params = make_params(big, "f32", keep)

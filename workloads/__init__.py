@@ -208,9 +208,9 @@ def binary_problem(name: str, n: int, *, dim: int = 2, delta: float = 0.0,
                    meta={"Delta": Delta, "R": R, "dtype": dtype_note})
 
 
-def cfg1() -> Problem:
+def dendrite_2d() -> Problem:
     """2-D 128^2, 2 phases, binary, isotropic, obstacle, R=10 seed, FP64, 1000 steps."""
-    return binary_problem("cfg1_2d128_n2_fp64", 128, delta=0.0, Delta=0.2, R=10.0,
+    return binary_problem("dendrite_2d128_n2_fp64", 128, delta=0.0, Delta=0.2, R=10.0,
                           potential="obstacle", dtype_note="f64", steps=1000)
 
 
@@ -226,7 +226,7 @@ def lamellae_x(nx: int, rng: PCG32, wmin: int = 8, wmax: int = 24) -> np.ndarray
     return lab
 
 
-def cfg2(n: int = 256, steps: int = 2000, seed: int = BASE_SEED) -> Problem:
+def eutectic_3d(n: int = 256, steps: int = 2000, seed: int = BASE_SEED) -> Problem:
     """3-D n^3 directional eutectic: alpha/beta lamellae under liquid, ternary.
 
     Symmetric synthetic eutectic: c_eq^alpha = (0.75, 0.125),
@@ -254,14 +254,14 @@ def cfg2(n: int = 256, steps: int = 2000, seed: int = BASE_SEED) -> Problem:
         phi0[ph] = solid[:, None, None] * col[None, None, :]
     phi0[2] = 1.0 - phi0[0] - phi0[1]
     mu0 = np.full((NM, n, n, n), 0.8)
-    return Problem(name=f"cfg2_3d{n}_n3k3_fp32", dim=3, nx=n, ny=n, nz=n, n_phases=N,
+    return Problem(name=f"eutectic_3d{n}_n3k3_fp32", dim=3, nx=n, ny=n, nz=n, n_phases=N,
                    n_components=3, bc=[BC_PERIODIC, BC_PERIODIC, BC_NOFLUX], dt=dt,
                    gamma=gamma, delta=dl, rot=rot, D=D, A=A, ceq=ceq, slopes=slopes,
                    f0=np.zeros(N), T_ref=0.0, T0=0.0, G=1e-3, z0=24.0, V=0.05,
                    steps=steps, phi0=phi0, mu0=mu0, meta={"dtype": "f32"})
 
 
-def cfg3(nsims: int = 512, steps: int = 500, seed: int = BASE_SEED) -> List[Problem]:
+def batched_dendrites_2d(nsims: int = 512, steps: int = 500, seed: int = BASE_SEED) -> List[Problem]:
     """Batched 2-D dendrites: edge in {64,...,512}, Delta~U[0.1,0.4], delta~U[0.01,0.05]."""
     rng = PCG32(seed, seq=3)
     edges = list(range(64, 513, 32))
@@ -270,16 +270,16 @@ def cfg3(nsims: int = 512, steps: int = 500, seed: int = BASE_SEED) -> List[Prob
         e = edges[rng.randint(0, len(edges) - 1)]
         Delta = 0.1 + 0.3 * rng.uniform()
         delta = 0.01 + 0.04 * rng.uniform()
-        p = binary_problem(f"cfg3_sim{s}", e, delta=delta, Delta=Delta, R=6.0,
+        p = binary_problem(f"batched_dendrite{s}", e, delta=delta, Delta=Delta, R=6.0,
                            potential="obstacle", dtype_note="f32", steps=steps)
         sims.append(p)
     return sims
 
 
-def cfg4(n: int = 256, steps: int = 2000, delta: float = 0.03, mob: float = 1.0) -> Problem:
+def adjoint_well_2d(n: int = 256, steps: int = 2000, delta: float = 0.03, mob: float = 1.0) -> Problem:
     """Adjoint case: 2-D n^2 binary, well potential; dt fixed from delta = 0.03."""
     dt = 0.2 * dt_stab(2, 1.0, 1.0, 1.0, 0.03, 1.0)
-    p = binary_problem(f"cfg4_2d{n}_well", n, delta=delta, Delta=0.2, R=10.0,
+    p = binary_problem(f"adjoint_well_2d{n}_well", n, delta=delta, Delta=0.2, R=10.0,
                        potential="well", dtype_note="f32", steps=steps, dt=dt,
                        tau=1.0 / mob)
     p.meta.update({"ckpt_every": 100, "delta_eval": 0.02, "mob_eval": 0.8})
@@ -306,7 +306,7 @@ def periodic_dist(a, b, n):
     return float(np.sqrt((d ** 2).sum()))
 
 
-def cfg5(n: int = 512, steps: int = 1000, grains: int = 7, R: float = 8.0,
+def multigrain_3d(n: int = 512, steps: int = 1000, grains: int = 7, R: float = 8.0,
          min_sep: float = 24.0, seed: int = BASE_SEED, make_fields: bool = True) -> Problem:
     """3-D n^3 multigrain: 7 rotated grains + liquid, binary, obstacle, periodic."""
     N, NM = grains + 1, 1
@@ -326,7 +326,7 @@ def cfg5(n: int = 512, steps: int = 1000, grains: int = 7, R: float = 8.0,
     ceq = np.array([[0.926]] * grains + [[0.817]])
     f0 = np.array([-0.2] * grains + [0.0])
     dt = 0.2 * dt_stab(3, 1.0, 1.0, 1.0, 0.02, 1.0)
-    p = Problem(name=f"cfg5_3d{n}_n8_fp32", dim=3, nx=n, ny=n, nz=n, n_phases=N,
+    p = Problem(name=f"multigrain_3d{n}_n8_fp32", dim=3, nx=n, ny=n, nz=n, n_phases=N,
                 n_components=2, bc=[BC_PERIODIC] * 3, dt=dt, gamma=gamma, delta=dl,
                 rot=rot, D=D, A=A, ceq=ceq, slopes=np.zeros((N, NM)), f0=f0,
                 steps=steps, meta={"dtype": "f32", "centres": centres, "R": R})
