@@ -18,9 +18,12 @@ def _problems():
     yield W.small_multiphase(n=12, dim=2, N=3, NM=2, nx=14, ny=12, rotate=True), 6
     yield W.binary_problem("adj3", 8, dim=3, delta=0.03, R=3.0, potential="well", ny=7, nz=6,
                            bc=[W.BC_PERIODIC, W.BC_NOFLUX, W.BC_PERIODIC]), 5
+    # a grid spacing of one half (dt scaled with dx^2)
+    q = W.small_multiphase(n=12, dim=2, N=3, NM=2, nx=14, ny=12, rotate=True)
+    yield q.copy(dx=0.5, dt=q.dt * 0.25), 6
 
 
-@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("case", range(5))
 def test_reverse_sweep_equals_the_tangent(case):
     p, steps = list(_problems())[case]
     N, NM = p.n_phases, p.n_components - 1
