@@ -431,7 +431,11 @@ def read_infile(src: str, *, free_energy: Optional[str] = None, elasticity: bool
 
 # ------------------------------------------------------------------ writing
 def _fmt(v) -> str:
-    return repr(float(v)) if not isinstance(v, str) else v
+    if isinstance(v, str):
+        return v
+    if isinstance(v, (int, np.integer)):
+        return str(int(v))          # phase indices and flags
+    return repr(float(v))
 
 
 def _list(vals) -> str:
@@ -479,7 +483,30 @@ def write_infile(spec) -> str:
             L.append(f"{key} = {_list([a, a] + list(np.asarray(arr)[a]))};")
     if getattr(spec, "noise_amp", 0.0):
         L += ["Noise_phasefield = 1;", f"Amp_Noise_Phase = {_fmt(spec.noise_amp)};"]
+    C = getattr(spec, "elastic_C", None)
+    if C is not None:
+        key, vals = _voigt_form(np.asarray(C, dtype=float))
+        E = np.asarray(spec.eigenstrain, dtype=float)
+        for a in range(N):
+            L.append(f"{key} = {_list([a] + vals)};")
+            L.append(f"EIGEN_STRAIN = {_list([a, E[a, 0, 0], E[a, 1, 1], E[a, 2, 2], E[a, 1, 2], E[a, 0, 2], E[a, 0, 1]])};")
     return "\n".join(L) + "\n"
+
+
+def _voigt_form(C: np.ndarray):
+    """The stiffness as the infile's VOIGT_CUBIC or VOIGT_TETRAGONAL constants
+    (the forms the reader takes); any other 6x6 matrix is refused."""
+    z = C.copy()
+    c11, c12, c13, c33, c44, c66 = C[0, 0], C[0, 1], C[0, 2], C[2, 2], C[3, 3], C[5, 5]
+    for i, j in ((0, 0), (1, 1), (2, 2), (0, 1), (1, 0), (0, 2), (2, 0), (1, 2), (2, 1), (3, 3), (4, 4), (5, 5)):
+        z[i, j] = 0.0
+    tetragonal = (C[1, 1] == c11 and C[1, 0] == c12 and C[2, 0] == C[1, 2] == C[2, 1] == c13
+                  and C[4, 4] == c44 and not np.any(z))
+    if tetragonal and c13 == c12 and c33 == c11 and c66 == c44:
+        return "VOIGT_CUBIC", [c11, c12, c44]
+    if tetragonal:
+        return "VOIGT_TETRAGONAL", [c11, c12, c13, c33, c44, c66]
+    raise ValueError("the stiffness has neither the cubic nor the tetragonal Voigt form the infile can hold")
 
 
 def _euler_angles(R: np.ndarray):

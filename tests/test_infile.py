@@ -518,3 +518,31 @@ def test_spec_copies_like_the_workload_problem():
     sub = s.copy(nz=3, bc=[s.bc[0], s.bc[1], 16], phi0=None, mu0=None, meta={**s.meta, "z_origin": 5})
     assert (sub.nz, sub.bc, sub.meta["z_origin"], s.nz) == (3, [3, 1, 16], 5, 8)
     assert make_grid(sub).z_origin == 5 and make_grid(sub).nz == 3
+
+
+def test_elasticity_survives_writing_and_reading():
+    p = W.small_multiphase(n=8, dim=3, N=3, NM=2)
+    p.f0 = np.zeros(3)
+    C = np.zeros((6, 6))
+    C[:3, :3] = 1.2
+    C[np.arange(3), np.arange(3)] = 3.0
+    C[3, 3] = C[4, 4] = C[5, 5] = 0.9
+    E = np.zeros((3, 3, 3))
+    E[0] = [[0.01, 0.002, 0.0], [0.002, 0.01, 0.001], [0.0, 0.001, 0.012]]
+    p.elastic_C, p.eigenstrain = C, E
+    text = I.write_infile(p)
+    assert "VOIGT_CUBIC = {0, 3.0, 1.2, 0.9};" in text
+    s = I.read_infile(text, elasticity=True)
+    np.testing.assert_array_equal(s.elastic_C, C)
+    np.testing.assert_array_equal(s.eigenstrain, E)
+    a = oracle.run(p, p.phi0, p.mu0, 2)
+    b = oracle.run(s, p.phi0, p.mu0, 2)
+    assert max(np.abs(a[0] - b[0]).max(), np.abs(a[1] - b[1]).max()) < 1e-13
+    T = C.copy()
+    T[2, 2], T[5, 5] = 2.5, 0.7                                  # tetragonal
+    p.elastic_C = T
+    np.testing.assert_array_equal(I.read_infile(I.write_infile(p), elasticity=True).elastic_C, T)
+    T[0, 3] = 0.1                                                # neither form
+    p.elastic_C = T
+    with pytest.raises(ValueError, match="Voigt form"):
+        I.write_infile(p)
