@@ -139,7 +139,7 @@ _USED = {
     "Rotation_matrix", "Function_W", "Gamma_abc", "ISOTHERMAL", "T", "Tempgrady",
     "Equilibrium_temperature", "Function_F", "A", "ceq", "slopes", "Noise_phasefield",
     "Amp_Noise_Phase", "EIGEN_STRAIN", "VOIGT_ISOTROPIC", "VOIGT_CUBIC", "VOIGT_TETRAGONAL",
-    "COMPONENTS", "PHASES", "cfill", "SAVET", "Shift", "Shiftj",
+    "COMPONENTS", "PHASES", "cfill", "SAVET", "Shift", "Shiftj", "GRAINGROWTH",
 }
 
 
@@ -302,7 +302,8 @@ def read_infile(src: str, *, free_energy: Optional[str] = None, elasticity: bool
 
     The options switch on what the paper selects elsewhere than in the infile
     keys read here: `elasticity` (then VOIGT_* and EIGEN_STRAIN are used),
-    `anti_trapping`, `grain_growth`.  `free_energy="parabolic"` reads the
+    `anti_trapping`, and `grain_growth` (which the key GRAINGROWTH = 1 also
+    turns on).  `free_energy="parabolic"` reads the
     parabolic coefficients A, ceq, slopes of a file whose Function_F names a
     CALPHAD database (which the library does not evaluate)."""
     text = open(src).read() if os.path.exists(src) else src
@@ -403,7 +404,8 @@ def read_infile(src: str, *, free_energy: Optional[str] = None, elasticity: bool
         gamma=gamma, delta=delta, rot=rot, gamma3=gamma3, D=D, A=A, ceq=ceq, slopes=slopes,
         f0=np.zeros(N), T_ref=T_ref, T0=T0, G=G, z0=z0, V=V,
         steps=int(_num(kv, "NTIMESTEPS", 0.0)),
-        anti_trapping=int(bool(anti_trapping)), grain_growth=int(bool(grain_growth)),
+        anti_trapping=int(bool(anti_trapping)),
+        grain_growth=int(bool(grain_growth) or bool(int(_num(kv, "GRAINGROWTH", 0.0)))),
         noise_seed=int(noise_seed))
     if int(_num(kv, "Function_W", 1.0)) not in (1, 2):
         raise ValueError("Function_W must be 1 (obstacle) or 2 (well)")
@@ -483,6 +485,8 @@ def write_infile(spec) -> str:
             L.append(f"{key} = {_list([a, a] + list(np.asarray(arr)[a]))};")
     if getattr(spec, "noise_amp", 0.0):
         L += ["Noise_phasefield = 1;", f"Amp_Noise_Phase = {_fmt(spec.noise_amp)};"]
+    if getattr(spec, "grain_growth", 0):
+        L.append("GRAINGROWTH = 1;")
     C = getattr(spec, "elastic_C", None)
     if C is not None:
         key, vals = _voigt_form(np.asarray(C, dtype=float))

@@ -546,3 +546,10 @@ def test_elasticity_survives_writing_and_reading():
     p.elastic_C = T
     with pytest.raises(ValueError, match="Voigt form"):
         I.write_infile(p)
+
+
+def test_graingrowth_key():
+    assert I.read_infile(TERNARY_3D).grain_growth == 0
+    s = I.read_infile(TERNARY_3D + "GRAINGROWTH = 1;\n")
+    assert s.grain_growth == 1
+    assert I.read_infile(I.write_infile(s)).grain_growth == 1
