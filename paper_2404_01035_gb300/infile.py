@@ -241,6 +241,15 @@ def _axis_codes(kv, dim):
         codes = axes
     if codes is None:
         codes = [BC_PERIODIC] * dim
+    # BOUNDARY_VALUE = {field, X+, X-, ...}: a no-flux face takes zero flux only
+    for entry in kv.get("BOUNDARY_VALUE", []):
+        if not isinstance(entry, list) or len(entry) < 2 or str(entry[0]) == "T":
+            continue
+        vals = [float(v) for v in entry[1:]]
+        for d in range(dim):
+            if codes[d] == BC_NOFLUX and any(vals[i] != 0.0 for i in (2 * d, 2 * d + 1) if i < len(vals)):
+                raise ValueError(f"BOUNDARY_VALUE {entry[0]}: a non-zero flux on axis {'xyz'[d]} is not "
+                                 "supported (no-flux faces take zero flux)")
     return codes + [BC_PERIODIC] * (3 - dim)
 
 

@@ -134,6 +134,7 @@ def test_euler_rotation_order_and_inverse():
     (("GAMMA = {1.1, 0.9, 1.3};", "GAMMA = {1.1, 0.9};"), "pair values"),
     (("A = {1, 0.9, 1.2, -0.02};", "A = {1, 0.9, 1.2, -0.02, 7};"), "off-diagonal"),
     (("DIMENSION = 3;", "DIMENSION = 4;"), "DIMENSION"),
+    (("BOUNDARY_VALUE = {phi, 0, 0, 0, 0, 0, 0};", "BOUNDARY_VALUE = {phi, 0, 0, 0.1, 0, 0, 0};"), "non-zero flux"),
     (("Rotation_matrix = {0, 2, 0, 0, 30};", "Rotation_matrix = {0, 3, 0, 0, 30};"), "phase index"),
     (("Rotation_matrix = {0, 2, 0, 0, 30};", "Rotation_matrix = {2, 2, 0, 0, 30};"), "two different"),
     (("ceq = {1, 1, 0.1, 0.7};", "ceq = {1, 1, 0.1};"), "values"),
@@ -553,3 +554,9 @@ def test_graingrowth_key():
     s = I.read_infile(TERNARY_3D + "GRAINGROWTH = 1;\n")
     assert s.grain_growth == 1
     assert I.read_infile(I.write_infile(s)).grain_growth == 1
+
+
+def test_boundary_values_on_periodic_axes_are_not_used():
+    s = I.read_infile(TERNARY_3D.replace("BOUNDARY_VALUE = {phi, 0, 0, 0, 0, 0, 0};",
+                                         "BOUNDARY_VALUE = {phi, 0.3, 0.3, 0, 0, 0.2, 0.2};"))
+    assert s.bc == [3, 1, 3]
