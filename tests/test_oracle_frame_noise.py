@@ -87,8 +87,12 @@ def test_shift_definition():
     assert np.array_equal(q2[:, :, :4], phi[:, :1, 1:]) and (q2[2, :, 4:] == 1).all()
 
 
-def test_lab_origin_equals_moved_temperature_field():
+@pytest.mark.parametrize("dx", [1.0, 0.5])
+def test_lab_origin_equals_moved_temperature_field(dx):
+    """A grid whose first cell is lab cell s sees the temperature field moved
+    by s dx (at a spacing other than 1 too)."""
     p = W.eutectic_3d(n=24, steps=5)
+    p = p.copy(dx=dx, dt=p.dt * dx * dx)
     p.nz = 20
     p.phi0, p.mu0 = p.phi0[:, :20], p.mu0[:, :20]
     s = 4
