@@ -12,22 +12,29 @@ driving force of the ordinary model would move them, and mu never changes.
 import math
 
 import numpy as np
+import pytest
 
 import oracle
 import workloads as W
 
 
-def test_circular_grain_loses_area_at_the_curvature_rate():
-    p = W.binary_problem("gg_circle", 64, dim=2, R=20.0, Delta=0.3)
+@pytest.mark.parametrize("dx", [1.0, 0.5])
+def test_circular_grain_loses_area_at_the_curvature_rate(dx):
+    """The same physical grain (radius 20, eps 4 on a 64-long box) on grids of
+    spacing 1 and 1/2 (dt scaled with dx^2): the same area loss rate."""
+    m = int(round(64 / dx))
+    p = W.binary_problem("gg_circle", m, dim=2, R=20.0, Delta=0.3)
+    ps = W.circular_seed(m, m, 20.0 / dx, p.eps, p.potential, dx=dx)
+    p = p.copy(dx=dx, dt=p.dt * dx * dx, phi0=np.stack([ps, 1.0 - ps])[:, None])
     p.grain_growth = 1
     phi, mu = p.phi0, p.mu0
-    areas = [phi[0].sum()]
-    n = 300
+    areas = [phi[0].sum() * dx * dx]
+    n = int(round(300 / (dx * dx)))
     for k in range(3):
         phi, mu_k = oracle.run(p, phi, mu, n, t0=k * n * p.dt)
         assert np.array_equal(mu_k, mu)          # mu held
-        areas.append(phi[0].sum())
-    rates = np.diff(areas) / (n * p.dt * p.dx ** 2)
+        areas.append(phi[0].sum() * dx * dx)
+    rates = np.diff(areas) / (n * p.dt)
     expect = -2.0 * math.pi * p.gamma[0, 1] / p.tau
     np.testing.assert_allclose(rates, expect, rtol=0.03)
     # a constant rate while the radius falls from 20 to ~17.5
