@@ -33,7 +33,9 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
     with isotropic pairs and three or four phases, one step's rate equals the
     projected variational derivative of the grand-potential functional.  That
     derivative is taken by finite differences of the functional, with spectral
-    gradients, and the two agree at second order: pinned.
+    gradients, and the two agree at second order.  With rotated anisotropic
+    pairs, the functional falls along the step's rate r at -tau eps |r|^2,
+    also at second order: pinned.
   * Covariance (``tests/test_oracle_covariance.py``): the 3-D step with
     rotated anisotropic pairs commutes with the grid's axis permutations and
     mirrors when each rotation is composed with the inverse move: pinned.
