@@ -18,7 +18,10 @@ Parity status per function (pins live in ``tests/test_oracle_pins.py``):
   * Grain growth (``tests/test_oracle_gg.py``): frozen mu, stationary planar
     boundary, the curvature-driven area loss rate of a circular grain: pinned.
   * Elasticity (``tests/test_oracle_elastic.py``): closed-form laminate,
-    Voigt shear factor, divergence-free stress: pinned.
+    Voigt shear factor, divergence-free stress: pinned.  With one stiffness
+    per phase (elastic_fields_inhomogeneous): the homogeneous limit, the
+    closed-form laminate of two stiffnesses, divergence-free stress, and the
+    potentials as the phi-derivative of the equilibrium energy: pinned.
   * The chemical mobility inside interfaces, M = sum_a h_a D^a chi^a with
     phi^n (``tests/test_oracle_mobility.py``): exact one-step and frozen-phi
     mode decay, two-solute matrix order: pinned.
@@ -276,20 +279,87 @@ def elastic_fields(prob, phi):
     return sigma, w
 
 
+def elastic_fields_inhomogeneous(prob, phi, C_phases, tol: float = 1e-13, max_iter: int = 5000):
+    """Mechanical equilibrium with a stiffness that varies with the phases,
+    C(x) = sum_a C^a h_a(phi) (Eqs. 43-44), in the Fourier-space form of
+    Sec. 2 "Elastic equilibrium in a multiphase setting": the homogeneous part
+    is the mean stiffness Cbar = (1/N) sum_a C^a (Eq. 47) and
+    Delta C(x) = sum_a (C^a - Cbar) h_a (Eq. 48); Eqs. 51-55 are solved by
+    their fixed point.  Each iteration applies the homogeneous operator of
+    `elastic_fields` (same wavenumbers, clamped periodic box) for Cbar to the
+    polarisation P = Cbar eps* - Delta C (eps - eps*) of the current strain,
+    starting from eps = 0, until the strain changes by less than
+    tol * max|eps*|.  C_phases: [N][6][6] Voigt matrices.
+
+    Returns (sigma [dim][dim][grid], w [N][grid], iterations).
+    w_b = 1/2 e : C^b : e - sigma : eps*^b with e = eps - eps*.  Contracted
+    with dh_b/dphi_a it gives d f_el / d phi_a of
+    f_el = 1/2 e : C(phi) : e at equilibrium.  With equal stiffnesses the
+    first term cancels in that contraction (sum_b dh_b/dphi_a = 0), which
+    leaves the homogeneous w_b."""
+    dim = prob.dim
+    N = prob.n_phases
+    nz = prob.nz if dim == 3 else 1
+    shape = (nz, prob.ny, prob.nx)
+    phi = np.asarray(phi, dtype=np.float64).reshape((N,) + shape)
+    Cs = [stiffness_tensor(np.asarray(C_phases[b], dtype=np.float64), dim) for b in range(N)]
+    Cbar = sum(Cs) / N
+    eig = np.asarray(prob.eigenstrain, dtype=np.float64).reshape(N, 3, 3)[:, :dim, :dim]
+    h = interp_field(phi)
+    E = np.einsum("amn,a...->mn...", eig, h)                      # eps*(x)
+    dC = sum(np.einsum("ijkl,...->ijkl...", Cs[b] - Cbar, h[b]) for b in range(N))
+    axes = tuple(a + 2 for a in ((0, 1, 2) if dim == 3 else (1, 2)))
+    ks = [_wavenumbers(n, prob.dx) for n in (prob.nx, prob.ny, nz)[:dim]]
+    K = np.zeros((dim,) + shape)
+    grids = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")   # z, y, x
+    for d in range(dim):
+        K[d] = ks[d][grids[2 - d]]
+    Ginv = np.moveaxis(np.einsum("ijkl,j...,l...->ik...", Cbar, K, K), (0, 1), (-2, -1))
+    zero = (K ** 2).sum(axis=0) == 0.0
+    Ginv[zero] = np.eye(dim)
+    G = np.linalg.inv(Ginv)
+    G[zero] = 0.0
+    eps = np.zeros_like(E)
+    scale = max(np.abs(E).max(), 1e-300)
+    it = 0
+    for it in range(1, max_iter + 1):
+        P = np.einsum("ijkl,kl...->ij...", Cbar, E) - np.einsum("ijkl...,kl...->ij...", dC, eps - E)
+        t = np.einsum("j...,ij...->i...", K, np.fft.fftn(P, axes=axes))
+        Gt = np.einsum("...ki,i...->k...", G, t)
+        epsh = 0.5 * (np.einsum("k...,l...->kl...", K, Gt) + np.einsum("l...,k...->kl...", K, Gt))
+        new = np.real(np.fft.ifftn(epsh, axes=axes))
+        change = np.abs(new - eps).max()
+        eps = new
+        if change <= tol * scale:
+            break
+    else:
+        raise RuntimeError(f"inhomogeneous elasticity did not converge in {max_iter} iterations")
+    e = eps - E
+    sigma = np.einsum("ijkl,kl...->ij...", Cbar, e) + np.einsum("ijkl...,kl...->ij...", dC, e)
+    w = np.stack([0.5 * np.einsum("ij...,ijkl,kl...->...", e, Cs[b], e)
+                  - np.einsum("ij...,ij->...", sigma, eig[b]) for b in range(N)])
+    return sigma, w, it
+
+
 def _elastic(prob, override):
     C = override.get("elastic_C", getattr(prob, "elastic_C", None))
-    return C is not None
+    return C is not None or override.get("elastic_C_phases") is not None
 
 
 def run(prob, phi0, mu0, nsteps: int, t0: float = 0.0, step0: int = 0, **override):
     """nsteps explicit steps in FP64; returns (phi, mu) shaped [F][nz][ny][nx].
     step0 = step index of the input state (the counter of the phi noise).
     With a stiffness (`elastic_C`) the elastic potentials are solved from the
-    state before every step."""
+    state before every step; `elastic_C_phases` ([N][6][6]) takes one
+    stiffness per phase instead (the inhomogeneous solve)."""
     if _elastic(prob, override) and "elw" not in override:
         phi, mu = phi0, mu0
+        Cph = override.pop("elastic_C_phases", None)
         for n in range(int(nsteps)):
-            _, w = elastic_fields(prob, phi)
+            if Cph is not None:
+                _, w, _ = elastic_fields_inhomogeneous(prob, phi, Cph)
+            else:
+                _, w = elastic_fields(prob, phi)
             phi, mu = run(prob, phi, mu, 1, t0=t0 + n * prob.dt, step0=step0 + n, elw=w, **override)
         return phi, mu
     op = OracleProblem(prob, t0, step0, **override)
