@@ -166,6 +166,16 @@ ms_status ms_create(const ms_grid* grid, int n_phases, int n_components,
                     const ms_params* params, void* stream, const ms_allocator* alloc,
                     ms_ctx** out);
 
+/* The checks of ms_create without a device: the inputs, the derived
+ * coefficients and the compiled (dim, N, K, dtype) kernels, with the same
+ * status codes.  *dt_bound (may be NULL) receives the explicit stability
+ * bound on dt, (dx^2 / 2 dim) min(tau / (gamma_max (1 + 15 delta_max)),
+ * 1 / max_a ||chi^a^-1 D^a chi^a||_inf), whenever the checks before it pass,
+ * also when dt exceeds it (MS_ERR_DT_UNSTABLE).  Allocates nothing and
+ * touches no GPU. */
+ms_status ms_check_params(const ms_grid* grid, int n_phases, int n_components,
+                          const ms_params* params, double* dt_bound);
+
 /* Release all device and host resources (synchronises the stream first). */
 void ms_destroy(ms_ctx* ctx);
 

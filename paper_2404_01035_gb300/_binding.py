@@ -24,7 +24,7 @@ MS_BC_HALO = 16
 
 # Every function the header declares (checked by the CPU test-suite).
 EXPORTS = [
-    "ms_create", "ms_destroy", "ms_last_error", "ms_update_params", "ms_set_fields",
+    "ms_create", "ms_check_params", "ms_destroy", "ms_last_error", "ms_update_params", "ms_set_fields",
     "ms_get_fields", "ms_fields", "ms_step", "ms_diag", "ms_set_diag_every", "ms_sync",
     "ms_time", "ms_checkpoint_bytes", "ms_checkpoint", "ms_restore", "ms_set_launch",
     "ms_tile_count", "ms_tile_shape", "ms_tile_split", "ms_get_launch", "ms_tune",
@@ -95,6 +95,8 @@ def lib(build_if_missing: bool = True):
         L.ms_create.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(Params), vp, ctypes.POINTER(Allocator),
                                 ctypes.POINTER(vp)]
+        L.ms_check_params.argtypes = [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(Params), dp]
         L.ms_destroy.argtypes = [vp]
         L.ms_destroy.restype = None
         L.ms_last_error.argtypes = [vp]

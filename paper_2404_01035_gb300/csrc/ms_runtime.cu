@@ -111,7 +111,17 @@ static bool invert(int n, const double* M, double* out) {
 }
 
 // Derive the FP64 model constants from the paper's inputs.
+// build_model, also reporting the explicit stability bound on dt (when
+// bound_out is not NULL and the checks before it passed).
+ms_status build_model_bound(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params* p, HostModel& m,
+                            double* bound_out);
+
 ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params* p, HostModel& m) {
+  return build_model_bound(c, g, N, K, p, m, nullptr);
+}
+
+ms_status build_model_bound(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params* p, HostModel& m,
+                            double* bound_out) {
   if (!g || !p) return fail(c, MS_ERR_ARG, "grid and params are required");
   if (g->dim != 2 && g->dim != 3) return fail(c, MS_ERR_ARG, "dim must be 2 or 3");
   if (N < 2 || N > kNMax) return fail(c, MS_ERR_ARG, "n_phases must be in [2, 8]");
@@ -270,6 +280,7 @@ ms_status build_model(ms_ctx* c, const ms_grid* g, int N, int K, const ms_params
   const double lim_phi = gmax > 0 ? m.tau / (gmax * (1.0 + 15.0 * dmax)) : 1e300;
   const double lim_mu = Dmax > 0 ? 1.0 / Dmax : 1e300;
   const double bound = m.dx * m.dx / (2.0 * m.dim) * std::min(lim_phi, lim_mu);
+  if (bound_out) *bound_out = bound;
   if (m.dt > bound * (1.0 + 1e-12)) {
     char buf[160];
     std::snprintf(buf, sizeof buf, "dt = %.6g exceeds the explicit stability bound %.6g", m.dt, bound);
@@ -575,6 +586,23 @@ extern "C" {
 const char* ms_last_error(const ms_ctx* ctx) {
   if (ctx) return ctx->err.c_str();
   return g_thread_error.c_str();
+}
+
+ms_status ms_check_params(const ms_grid* grid, int n_phases, int n_components, const ms_params* params,
+                          double* dt_bound) {
+  ensure_registered();
+  HostModel m;
+  double bound = 0.0;
+  ms_status s = build_model_bound(nullptr, grid, n_phases, n_components, params, m, &bound);
+  if (dt_bound) *dt_bound = bound;
+  if (s != MS_OK) return s;
+  if (!find_step(m.dim, m.N, m.NM, m.dtype, 0, 0) || !find_diag(m.dim, m.N, m.NM, m.dtype)) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf, "no compiled step kernel for dim=%d N=%d K=%d dtype=%s", m.dim, m.N,
+                  n_components, m.dtype ? "f64" : "f32");
+    return fail(nullptr, MS_ERR_UNSUPPORTED, buf);
+  }
+  return MS_OK;
 }
 
 ms_status ms_create(const ms_grid* grid, int n_phases, int n_components, const ms_params* params,

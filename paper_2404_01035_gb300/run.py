@@ -18,7 +18,10 @@ steps on to the same total.  A deck with `Shift = 1` runs in the moving frame:
 the growth front is kept at index Shiftj of the last axis, and liquid of the
 alloy's chemical potential refills the far end.  It stops with exit code 3 if the library reports
 a non-finite state.  `--dry-run` reads and
-checks the inputs and prints their summary without touching the GPU.
+checks the inputs and prints their summary without touching the GPU; the
+summary carries the library's own verdict on them (`library_check`) and
+the stability bound on dt (`dt_bound`), and a refused deck ends with exit
+code 2 before any GPU work.
 """
 from __future__ import annotations
 
@@ -113,11 +116,22 @@ def main(argv: Optional[List[str]] = None) -> int:
         ap.error("--save-every must be > 0")
     every = args.save_every or spec.meta.get("savet") or steps or 1
     info = _summary(spec, phi0, mu0, steps, every)
+    # the library's own checks (inputs, derived coefficients, compiled kernels,
+    # dt against the stability bound), on the host: no GPU is touched
+    from ._binding import MSError
+    from .simulation import check_params
+    try:
+        info["dt_bound"] = check_params(spec, args.dtype)
+        info["library_check"] = "ok"
+    except MSError as e:
+        info["dt_bound"] = getattr(e, "dt_bound", None)
+        info["library_check"] = str(e)
     print(json.dumps({"inputs": info}), flush=True)
+    if info["library_check"] != "ok":
+        return 2
     if args.dry_run:
         return 0
 
-    from ._binding import MSError
     from .simulation import Simulation      # needs the CUDA library and a GPU
     os.makedirs(args.out, exist_ok=True)
 

@@ -65,6 +65,23 @@ def make_grid(prob) -> Grid:
     return gr
 
 
+def check_params(prob, dtype: str = "f32", **override) -> float:
+    """The library's checks of ms_create, without a device (ms_check_params).
+    Returns the explicit stability bound on dt.  A failed check raises MSError,
+    with the bound (when it was reached) as its `dt_bound` attribute."""
+    keep = []
+    params = make_params(prob, dtype, keep, **override)
+    grid = make_grid(prob)
+    bound = ctypes.c_double(0.0)
+    rc = lib().ms_check_params(ctypes.byref(grid), int(prob.n_phases), int(prob.n_components),
+                               ctypes.byref(params), ctypes.byref(bound))
+    if rc != 0:
+        err = MSError(rc, lib().ms_last_error(None).decode(errors="replace"))
+        err.dt_bound = bound.value or None
+        raise err
+    return bound.value
+
+
 class Simulation:
     """One grand-potential simulation living on the GPU."""
 

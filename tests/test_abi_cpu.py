@@ -151,3 +151,19 @@ def test_create_rejects_a_malformed_fault_spec(monkeypatch, spec):
     monkeypatch.setenv("MS_FAULT", spec)
     rc, h, msg = _create(W.dendrite_2d())
     assert rc == 1 and "MS_FAULT" in msg and not h.value
+
+
+def test_check_params_reports_the_stability_bound():
+    """ms_check_params runs ms_create's checks without a device and returns the
+    explicit bound: for the 2-D dendrite (gamma = 1, delta = 0, tau = 1, D = 1,
+    dx = 1) it is (1 / 4) min(1, 1)."""
+    from paper_2404_01035_gb300.simulation import check_params
+    p = W.dendrite_2d()
+    assert check_params(p, "f64") == pytest.approx(0.25, rel=1e-12)
+    with pytest.raises(B.MSError) as ex:
+        check_params(p, "f64", dt=10.0)
+    assert ex.value.status == 4 and ex.value.dt_bound == pytest.approx(0.25, rel=1e-12)
+    q = W.small_multiphase(n=8, dim=2, N=4, NM=1)          # (2-D, N=4, K=2) is not compiled
+    with pytest.raises(B.MSError) as ex:
+        check_params(q, "f32")
+    assert ex.value.status == 9

@@ -285,6 +285,7 @@ def test_run_driver_dry_run(tmp_path, capsys):
     assert rc == 0
     info = json.loads(capsys.readouterr().out.strip().splitlines()[-1])["inputs"]
     assert info["grid"] == [2, 48, 32, 1] and info["steps"] == 250 and info["save_every"] == 50
+    assert info["library_check"] == "ok" and 0.004 < info["dt_bound"]
     assert info["bc"] == [3, 1] and info["potential"] == "well" and info["ignored_keys"] == ["Tau"]
     s = I.read_infile(deck)
     np.testing.assert_allclose(info["mu0"], I.liquid_mu(s, [0.35, 0.25]), atol=1e-15)
@@ -293,6 +294,12 @@ def test_run_driver_dry_run(tmp_path, capsys):
     with pytest.raises(ValueError, match="CALPHAD"):
         (tmp_path / "bad.in").write_text(deck.replace("Function_F = 1;", "Function_F = 2;"))
         run.main([str(tmp_path / "bad.in"), str(tmp_path / "fill.in"), "--dry-run"])
+    # a time step above the library's stability bound is refused before any GPU work
+    capsys.readouterr()
+    (tmp_path / "fast.in").write_text(deck.replace("DELTA_t = 0.004;", "DELTA_t = 0.5;"))
+    assert run.main([str(tmp_path / "fast.in"), str(tmp_path / "fill.in"), "--dry-run"]) == 2
+    info = json.loads(capsys.readouterr().out.strip().splitlines()[-1])["inputs"]
+    assert "stability" in info["library_check"] and 0.0 < info["dt_bound"] < 0.5
 
 
 DECKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "decks")
